@@ -1,0 +1,169 @@
+/*
+ * sc.h - C ABI of the GB300 smooth-and-clip (S+C) source finder.
+ *
+ * S+C is the default source finder of SoFiA 2 (Westmeier et al. 2021,
+ * arXiv:2106.15789, Sect. 4.2): the data cube is smoothed on several spatial
+ * (Gaussian, FWHM in pixels) and spectral (boxcar, channels) scales; on each
+ * scale the noise sigma of the smoothed cube is measured and every voxel with
+ * |S| > t*sigma, positive or negative, is added to one 8-bit source mask.
+ * Voxels already in the mask are set to +-n*sigma_0 (sign kept) before each
+ * smoothing (Sect. 6.2, "Integrated flux"). NaN voxels are blanked.
+ *
+ * Conventions of every entry point
+ *   - Cubes are float32, C-contiguous, axis order [z][y][x] with x fastest
+ *     (FITS order, Sect. 4.1). dims[3] = {nx, ny, nz}, all > 0.
+ *   - "_dev" pointers are CUDA device pointers on the context's device, owned
+ *     by the caller; "_host" pointers are host memory owned by the caller.
+ *     The library never frees caller memory.
+ *   - All GPU work is enqueued on the caller's stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream). Calls that return sigma values to
+ *     the host synchronise that stream once, at the end.
+ *   - Every call returns SC_OK (0) or a negative SC_ERR_* code; nothing
+ *     aborts, traps or prints. sc_strerror() names a code.
+ *   - A context is not thread-safe: one host thread per context at a time.
+ *     Calls on one context share its workspace, so calls on different streams
+ *     of one context must not overlap.
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define SC_OK 0
+#define SC_ERR_ARG (-1)         /* invalid argument (dims, kernel, threshold, NULL pointer, size) */
+#define SC_ERR_NOMEM (-2)       /* device or pinned-host allocation failed */
+#define SC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define SC_ERR_ALLNAN (-4)      /* the cube has no finite voxel: no noise level exists */
+#define SC_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define SC_ERR_UNSUPPORTED (-6) /* option not implemented (noise mode SC_NOISE_GAUSS) */
+#define SC_ERR_BUDGET (-7)      /* request exceeds the context's sizes / memory budget */
+#define SC_ERR_INTERNAL (-8)    /* a device-side consistency check failed */
+
+/* ---- noise estimators (Sect. 4.1: robust RMS from the MAD) ------------ */
+#define SC_NOISE_MAD 0   /* 1.4826 * median(|S - median(S)|), exact medians */
+#define SC_NOISE_STD 1   /* sqrt(sum((S - mean)^2) / (n - 1)) */
+#define SC_NOISE_GAUSS 2 /* Gaussian fit: not defined by the paper -> SC_ERR_UNSUPPORTED */
+
+/* ---- flags for sc_run ------------------------------------------------- */
+#define SC_FLAG_ACCUMULATE 0x1u /* start from the caller's mask (nonzero = detected) instead of an empty one */
+#define SC_FLAG_GENERIC 0x2u    /* use the generic (any-width) smoothing kernels even where a specialised one exists */
+#define SC_FLAG_NO_FAST_SELECT 0x4u /* skip the one-pass candidate selection; select by full passes (slow, for tests) */
+
+/* ---- warning bits (sc_stats.warnings, set per run) -------------------- */
+#define SC_WARN_ZERO_SIGMA 0x1u     /* some pair had sigma == 0 and added nothing to the mask */
+#define SC_WARN_FULL_SELECT 0x2u    /* a selection needed full passes (candidate set above capacity) */
+#define SC_WARN_FULL_CLIP 0x4u      /* a clip needed a separate pass (ambiguous set above capacity) */
+#define SC_WARN_RANGE 0x8u          /* max|X| / sigma_0 exceeds 2^20: smoothed values may lose exactness */
+
+typedef struct sc_ctx sc_ctx;
+
+/* One smoothing kernel pair. fwhm_spatial_px <= 0: no spatial smoothing.
+ * boxcar_chan: odd width in channels; 0 or 1: no spectral smoothing. */
+typedef struct {
+  float fwhm_spatial_px;
+  int32_t boxcar_chan;
+} sc_kernel;
+
+/* Counters and timings of the context (cumulative unless reset). */
+typedef struct {
+  uint64_t launches;      /* CUDA kernels this library launched */
+  uint64_t runs;          /* completed sc_run / sc_run_host calls */
+  uint32_t warnings;      /* SC_WARN_* bits of the last run */
+  uint32_t reserved;
+  double ms_smooth;       /* device time of smoothing kernels (only while profiling is on) */
+  double ms_select;       /* device time of histogram/plan/candidate/select kernels */
+  double ms_clip;         /* device time of mask kernels */
+  uint64_t smooth_launches; /* smoothing-kernel launches timed in ms_smooth */
+  uint64_t smooth_voxels;   /* output voxels those launches produced */
+} sc_stats;
+
+/* Create a context on CUDA device `device` with workspace for cubes of up to
+ * max_voxels voxels: one float32 smoothed cube (the second cube copy of the
+ * paper's memory model, Sect. 5), a 1-bit working mask and small selection
+ * buffers. *out receives the context. Errors: SC_ERR_ARG (out NULL,
+ * max_voxels 0), SC_ERR_CUDA (bad device), SC_ERR_NOMEM. */
+int sc_create(sc_ctx **out, int device, size_t max_voxels);
+
+/* Free the context and all its device memory. NULL is accepted. */
+void sc_destroy(sc_ctx *ctx);
+
+/* Static description of a status code (never NULL). */
+const char *sc_strerror(int code);
+
+/* Host helper: the 3 boxcar widths whose cascade approximates a Gaussian of
+ * this FWHM (Kovesi 2010 construction; FWHM <= 0 gives widths {1,1,1}, the
+ * identity). widths must hold 3 ints. Errors: SC_ERR_ARG (NULL, FWHM not
+ * finite or so large that a width exceeds 4095). */
+int sc_cascade_widths(float fwhm_px, int32_t *widths);
+
+/* Full S+C (Sect. 4.2) on a device cube.
+ *   cube_dev     float32 [nz][ny][nx], read only.
+ *   kernels      n_kernels pairs, run in the order given (Sect. 5 uses
+ *                spatial {0,5,10} x spectral {0,3,7,15}).
+ *   threshold    t > 0: a voxel is detected when |S| > t*sigma_k.
+ *   noise_mode   SC_NOISE_MAD or SC_NOISE_STD.
+ *   replacement  n: masked voxels become sign(C)*n*sigma_0 before smoothing
+ *                (Sect. 6.2); n <= 0 switches replacement off.
+ *   mask_dev     uint8 [nz][ny][nx] output, 1 = detected, 0 = not. Zeroed
+ *                first unless flags has SC_FLAG_ACCUMULATE.
+ *   sigma_host   NULL or double[n_kernels]: sigma of every pair (0 when a
+ *                pair's sigma is 0; that pair then adds nothing).
+ *   sigma0_host  NULL or double[1]: noise of the raw cube.
+ * Returns after the stream has finished when sigma_host or sigma0_host is
+ * given (needed to copy them); otherwise returns once all work is enqueued
+ * and device-side errors surface at the next synchronising call.
+ * Errors: SC_ERR_ARG (dims <= 0, more voxels than max_voxels -> SC_ERR_BUDGET,
+ * even boxcar, negative or non-finite FWHM, t <= 0 or not finite, n_kernels
+ * outside 1..SC_MAX_KERNELS, NULL pointers), SC_ERR_UNSUPPORTED
+ * (SC_NOISE_GAUSS), SC_ERR_ALLNAN (no finite voxel; mask left zero),
+ * SC_ERR_CUDA. */
+#define SC_MAX_KERNELS 64
+int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_kernel *kernels, int n_kernels,
+           float threshold, int noise_mode, float replacement, uint8_t *mask_dev, double *sigma_host,
+           double *sigma0_host, uint32_t flags, void *cuda_stream);
+
+/* sc_run on host buffers: copies cube_host to a device staging cube owned by
+ * the context (allocated on first use, max_voxels floats), runs S+C and copies
+ * the mask back to mask_host. Pinned (cudaHostAlloc'd / registered) host
+ * buffers give full copy bandwidth; pageable memory works but is slower.
+ * Same arguments and errors as sc_run; always synchronises the stream. */
+int sc_run_host(sc_ctx *ctx, const float *cube_host, const int64_t *dims, const sc_kernel *kernels,
+                int n_kernels, float threshold, int noise_mode, float replacement, uint8_t *mask_host,
+                double *sigma_host, double *sigma0_host, uint32_t flags, void *cuda_stream);
+
+/* One pair's smoothed cube S (Sect. 4.2 smoothing, Sect. 6.2 replacement):
+ *   X = C with NaN -> 0 and, where mask_dev != 0 and C is finite,
+ *       sign(C)*replacement_value (sign(0) = +1; replacement_value <= 0: off);
+ *   S = spectral boxcar * spatial cascade (x, y) of the zero-padded X;
+ *   S = NaN where C is NaN.
+ * mask_dev may be NULL (empty mask). out_dev: float32 [nz][ny][nx], may not
+ * alias cube_dev. The smoothing is exact fixed-point integer arithmetic
+ * rounded once to float32. Errors as sc_run. Asynchronous. */
+int sc_smooth(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, sc_kernel kernel, const uint8_t *mask_dev,
+              float replacement_value, float *out_dev, uint32_t flags, void *cuda_stream);
+
+/* Noise level (Sect. 4.1 estimator) of the finite values of a device float32
+ * array of n elements (NaN skipped). *sigma_host receives it (synchronises).
+ * Errors: SC_ERR_ARG, SC_ERR_BUDGET (n > max_voxels), SC_ERR_ALLNAN,
+ * SC_ERR_UNSUPPORTED. */
+int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, double *sigma_host, uint32_t flags,
+             void *cuda_stream);
+
+/* Device-timed profiling of the library's kernels with CUDA events on the
+ * launching stream (adds a few microseconds per launch). on = 0 / 1. */
+int sc_set_profiling(sc_ctx *ctx, int on);
+
+/* Copy the context's counters to *out; reset = 1 zeroes them afterwards.
+ * Synchronises the last stream used so that timings are complete. */
+int sc_get_stats(sc_ctx *ctx, sc_stats *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_H */

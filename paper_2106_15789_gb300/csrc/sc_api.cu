@@ -1,0 +1,503 @@
+// C ABI of the smooth-and-clip library: context, workspace and the order of
+// the device steps of one S+C run (SoFiA 2, Sect. 4.2).
+//
+// One run, all on the caller's stream, no host synchronisation until the end:
+//   sigma_0      histogram + plan + candidate pass + exact selections over
+//                the raw cube (also max|C| for the fixed-point scales); when
+//                the first pair is (0, 0) on an empty mask it is the same
+//                measurement, and its clip is done in the same passes.
+//   every pair   smoothing kernel (writes S and its histogram), plan,
+//                candidate pass over S (also sets the certain mask bits),
+//                selections of median and MAD, clip of the undecided voxels.
+//   end          1-bit working mask -> caller's uint8 mask; sigmas to host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sc_internal.h"
+
+using namespace sc;
+
+namespace sc {
+void init_kernel_attrs();
+}  // namespace sc
+
+struct sc_ctx {
+  int device = 0;
+  int sms = 0;
+  size_t max_voxels = 0;
+  float* S = nullptr;
+  uint32_t* mbits = nullptr;
+  unsigned long long* hist = nullptr;
+  Lists L{};
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;   // pinned mirror for read-back
+  float* stage_cube = nullptr;   // sc_run_host staging (lazy)
+  uint8_t* stage_mask = nullptr;
+  int profiling = 0;
+  sc_stats stats{};
+  struct Ev {
+    cudaEvent_t a, b;
+    int kind;
+    unsigned long long voxels;
+  };
+  std::vector<Ev> events;     // recorded, not yet accumulated
+  std::vector<cudaEvent_t> pool;
+  cudaStream_t last = nullptr;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaEvent_t take_event(sc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2 };
+
+struct Phase {
+  sc_ctx* c;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  int kind;
+  unsigned long long vox;
+  Phase(sc_ctx* c_, cudaStream_t s_, int kind_, unsigned long long vox_ = 0) : c(c_), s(s_), kind(kind_), vox(vox_) {
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Phase() {
+    if (c->profiling && a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c->events.push_back({a, b, kind, vox});
+    }
+  }
+};
+
+void flush_events(sc_ctx* c) {
+  for (auto& e : c->events) {
+    cudaEventSynchronize(e.b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    if (e.kind == EV_SMOOTH) {
+      c->stats.ms_smooth += ms;
+      c->stats.smooth_launches += 1;
+      c->stats.smooth_voxels += e.voxels;
+    } else if (e.kind == EV_SELECT) {
+      c->stats.ms_select += ms;
+    } else {
+      c->stats.ms_clip += ms;
+    }
+    c->pool.push_back(e.a);
+    c->pool.push_back(e.b);
+  }
+  c->events.clear();
+}
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return SC_ERR_CUDA; \
+  } while (0)
+
+int check_dims(const sc_ctx* c, const int64_t* dims, long long* n) {
+  if (!dims) return SC_ERR_ARG;
+  if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0) return SC_ERR_ARG;
+  if (dims[0] > (1 << 30) || dims[1] > (1 << 30) || dims[2] > (1 << 30)) return SC_ERR_ARG;
+  const long double nn = (long double)dims[0] * dims[1] * dims[2];
+  if (nn > (long double)c->max_voxels) return SC_ERR_BUDGET;
+  *n = (long long)dims[0] * dims[1] * dims[2];
+  return SC_OK;
+}
+
+int status_to_code(const DevState& h) {
+  if (h.status & SC_ST_ALLNAN) return SC_ERR_ALLNAN;
+  if (h.status & (SC_ST_INTERNAL | SC_ST_OVERFLOW)) return SC_ERR_INTERNAL;
+  return SC_OK;
+}
+
+// One noise measurement (and optional clip) over src, whose histogram is in
+// c->hist. pair: index for sigma[] (-1: none).
+int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip, int std_mode, int pair,
+            unsigned int force, cudaStream_t s) {
+  {
+    Phase ph(c, s, EV_SELECT);
+    CK(launch_plan(c->st, c->hist, win, src, n, c->L, t, clip, std_mode, force, s));
+    c->stats.launches += 1;
+    if (std_mode) {
+      CK(launch_std(src, n, c->st, c->sms, s));
+      CK(launch_std_final(c->st, pair, s));
+      c->stats.launches += 3;
+    } else {
+      CK(launch_pass2(src, n, c->mbits, c->st, c->L, win, c->sms, s));
+      CK(launch_select(c->st, 0, -1, c->sms, s));
+      CK(launch_select(c->st, 1, pair, c->sms, s));
+      c->stats.launches += 11;
+    }
+  }
+  if (clip) {
+    Phase ph(c, s, EV_CLIP);
+    if (!std_mode) {
+      CK(launch_resolve(src, c->mbits, c->st, c->L, c->sms, s));
+      c->stats.launches += 1;
+    }
+    CK(launch_clip_full(src, n, c->mbits, c->st, c->sms, s));
+    c->stats.launches += 1;
+  }
+  return SC_OK;
+}
+
+int validate_common(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kernel* kernels, int nk, float t,
+                    int noise_mode, long long* n, std::vector<PairDesc>* pds) {
+  if (!c || !cube || !kernels) return SC_ERR_ARG;
+  int rc = check_dims(c, dims, n);
+  if (rc) return rc;
+  if (nk < 1 || nk > SC_MAX_KERNELS) return SC_ERR_ARG;
+  if (!(t > 0.0f) || !std::isfinite(t)) return SC_ERR_ARG;
+  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  pds->resize(nk);
+  for (int k = 0; k < nk; ++k) {
+    rc = make_pair(kernels[k], &(*pds)[k]);
+    if (rc) return rc;
+  }
+  return SC_OK;
+}
+
+SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims) {
+  SmoothArgs a;
+  memset(&a, 0, sizeof(a));
+  a.C = cube;
+  a.mbits = c->mbits;
+  a.S = c->S;
+  a.nx = (int)dims[0];
+  a.ny = (int)dims[1];
+  a.nz = (int)dims[2];
+  a.st = c->st;
+  return a;
+}
+
+int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kernel* kernels, int nk, float t,
+               int noise_mode, float replacement, uint8_t* mask_dev, uint32_t flags, cudaStream_t s) {
+  long long n = 0;
+  std::vector<PairDesc> pds;
+  int rc = validate_common(c, cube, dims, kernels, nk, t, noise_mode, &n, &pds);
+  if (rc) return rc;
+  if (!mask_dev) return SC_ERR_ARG;
+  if (!std::isfinite(replacement)) return SC_ERR_ARG;
+  const int std_mode = (noise_mode == SC_NOISE_STD);
+  const unsigned int force = (flags & SC_FLAG_NO_FAST_SELECT) ? (PLAN_MED_FULL | PLAN_MAD_FULL | PLAN_CLIP_FULL) : 0u;
+  PairWeights W{};
+  for (int k = 0; k < nk; ++k) W.w[k] = pds[k].W;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  const long long nwords = (n + 31) / 32;
+  if (flags & SC_FLAG_ACCUMULATE) {
+    CK(launch_pack(mask_dev, n, c->mbits, s));
+    c->stats.launches += 1;
+  } else {
+    CK(cudaMemsetAsync(c->mbits, 0, sizeof(uint32_t) * nwords, s));
+  }
+  const bool first_identity = (pds[0].h == 0 && pds[0].wz == 1) && !(flags & SC_FLAG_ACCUMULATE);
+
+  // sigma_0 of the raw cube (and the first pair when it is (0, 0))
+  CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  {
+    Phase ph(c, s, EV_SELECT);
+    CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));
+    c->stats.launches += 1;
+  }
+  rc = measure(c, cube, n, 0, t, first_identity ? 1 : 0, std_mode, first_identity ? 0 : -1, force, s);
+  if (rc) return rc;
+  CK(launch_sigma0_done(c->st, replacement, W, nk, s));
+  c->stats.launches += 1;
+
+  for (int k = first_identity ? 1 : 0; k < nk; ++k) {
+    CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
+    SmoothArgs a = base_args(c, cube, dims);
+    a.pd = pds[k];
+    a.pair = k;
+    a.hist = c->hist;
+    a.win = 1;
+    a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
+    {
+      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
+      if (a.pd.h == 0 && a.pd.wz == 1) {
+        CK(launch_identity(a, c->sms, s));
+        c->stats.launches += 1;
+      } else {
+        int l = 0;
+        CK(launch_smooth(a, c->sms, s, &l));
+        c->stats.launches += l;
+      }
+    }
+    rc = measure(c, c->S, n, 1, t, 1, std_mode, k, force, s);
+    if (rc) return rc;
+  }
+  {
+    Phase ph(c, s, EV_CLIP);
+    CK(launch_expand(c->mbits, n, mask_dev, s));
+    c->stats.launches += 1;
+  }
+  return SC_OK;
+}
+
+int finish(sc_ctx* c, int nk, double* sigma_host, double* sigma0_host, cudaStream_t s, bool force_sync) {
+  if (!sigma_host && !sigma0_host && !force_sync) return SC_OK;
+  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const DevState& h = *c->st_host;
+  c->stats.warnings = h.warn;
+  const int rc = status_to_code(h);
+  if (sigma0_host) *sigma0_host = (rc == SC_OK) ? (double)h.sigma0 : 0.0;
+  if (sigma_host)
+    for (int k = 0; k < nk; ++k) sigma_host[k] = (rc == SC_OK) ? (double)h.sigma[k] : 0.0;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sc_strerror(int code) {
+  switch (code) {
+    case SC_OK: return "ok";
+    case SC_ERR_ARG: return "invalid argument";
+    case SC_ERR_NOMEM: return "out of memory";
+    case SC_ERR_CUDA: return "CUDA error";
+    case SC_ERR_ALLNAN: return "cube has no finite voxel";
+    case SC_ERR_TIMEOUT: return "device-side wait timed out";
+    case SC_ERR_UNSUPPORTED: return "unsupported option";
+    case SC_ERR_BUDGET: return "request exceeds the context's budget";
+    case SC_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status code";
+  }
+}
+
+int sc_cascade_widths(float fwhm_px, int32_t* widths) {
+  if (!widths || !std::isfinite(fwhm_px)) return SC_ERR_ARG;
+  int w[3];
+  if (cascade_widths(fwhm_px, w) != 0) return SC_ERR_ARG;
+  for (int i = 0; i < 3; ++i) widths[i] = w[i];
+  return SC_OK;
+}
+
+int sc_create(sc_ctx** out, int device, size_t max_voxels) {
+  if (!out || max_voxels == 0) return SC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SC_ERR_CUDA;
+  DeviceGuard g(device);
+  sc_ctx* c = new (std::nothrow) sc_ctx();
+  if (!c) return SC_ERR_NOMEM;
+  c->device = device;
+  c->max_voxels = max_voxels;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  init_kernel_attrs();
+  const unsigned long long nv = max_voxels;
+  c->L.cap.med = std::max<unsigned long long>(1ull << 20, nv / 64);
+  c->L.cap.mad = std::max<unsigned long long>(1ull << 22, nv / 16);
+  c->L.cap.amb = std::max<unsigned long long>(1ull << 20, nv / 64);
+  const size_t nwords = (max_voxels + 31) / 32 + 8;
+  bool ok = cudaMalloc(&c->S, sizeof(float) * max_voxels) == cudaSuccess &&
+            cudaMalloc(&c->mbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
+            cudaMalloc(&c->hist, sizeof(unsigned long long) * kNumBins) == cudaSuccess &&
+            cudaMalloc(&c->L.med, sizeof(float) * c->L.cap.med) == cudaSuccess &&
+            cudaMalloc(&c->L.mad, sizeof(float) * c->L.cap.mad) == cudaSuccess &&
+            cudaMalloc(&c->L.amb, sizeof(unsigned long long) * c->L.cap.amb) == cudaSuccess &&
+            cudaMalloc(&c->st, sizeof(DevState)) == cudaSuccess &&
+            cudaHostAlloc(&c->st_host, sizeof(DevState), cudaHostAllocDefault) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    sc_destroy(c);
+    return SC_ERR_NOMEM;
+  }
+  cudaMemset(c->mbits, 0, sizeof(uint32_t) * nwords);
+  cudaMemset(c->st, 0, sizeof(DevState));
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    sc_destroy(c);
+    return SC_ERR_CUDA;
+  }
+  *out = c;
+  return SC_OK;
+}
+
+void sc_destroy(sc_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  for (auto& e : c->events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  cudaFree(c->S);
+  cudaFree(c->mbits);
+  cudaFree(c->hist);
+  cudaFree(c->L.med);
+  cudaFree(c->L.mad);
+  cudaFree(c->L.amb);
+  cudaFree(c->st);
+  cudaFree(c->stage_cube);
+  cudaFree(c->stage_mask);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  cudaGetLastError();
+  delete c;
+}
+
+int sc_run(sc_ctx* c, const float* cube_dev, const int64_t* dims, const sc_kernel* kernels, int n_kernels,
+           float threshold, int noise_mode, float replacement, uint8_t* mask_dev, double* sigma_host,
+           double* sigma0_host, uint32_t flags, void* cuda_stream) {
+  if (!c) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  int rc = run_device(c, cube_dev, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, s);
+  if (rc) return rc;
+  rc = finish(c, n_kernels, sigma_host, sigma0_host, s, false);
+  if (rc == SC_OK) c->stats.runs += 1;
+  return rc;
+}
+
+int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc_kernel* kernels, int n_kernels,
+                float threshold, int noise_mode, float replacement, uint8_t* mask_host, double* sigma_host,
+                double* sigma0_host, uint32_t flags, void* cuda_stream) {
+  if (!c || !cube_host || !mask_host) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  long long n = 0;
+  int rc = check_dims(c, dims, &n);
+  if (rc) return rc;
+  if (!c->stage_cube) {
+    if (cudaMalloc(&c->stage_cube, sizeof(float) * c->max_voxels) != cudaSuccess ||
+        cudaMalloc(&c->stage_mask, c->max_voxels) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->stage_cube);
+      c->stage_cube = nullptr;
+      return SC_ERR_NOMEM;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  CK(cudaMemcpyAsync(c->stage_cube, cube_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  if (flags & SC_FLAG_ACCUMULATE) CK(cudaMemcpyAsync(c->stage_mask, mask_host, n, cudaMemcpyHostToDevice, s));
+  rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, c->stage_mask, flags,
+                  s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(mask_host, c->stage_mask, n, cudaMemcpyDeviceToHost, s));
+  rc = finish(c, n_kernels, sigma_host, sigma0_host, s, true);
+  if (rc == SC_OK) c->stats.runs += 1;
+  return rc;
+}
+
+int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel kernel, const uint8_t* mask_dev,
+              float replacement_value, float* out_dev, uint32_t flags, void* cuda_stream) {
+  if (!c || !cube_dev || !out_dev || (const void*)cube_dev == (const void*)out_dev) return SC_ERR_ARG;
+  if (!std::isfinite(replacement_value)) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  long long n = 0;
+  int rc = check_dims(c, dims, &n);
+  if (rc) return rc;
+  PairDesc pd;
+  rc = make_pair(kernel, &pd);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  if (mask_dev) {
+    CK(launch_pack(mask_dev, n, c->mbits, s));
+    c->stats.launches += 1;
+  }
+  const float repl = replacement_value > 0.0f ? replacement_value : 0.0f;  // quantised exactly per pair
+  PairWeights W{};
+  W.w[0] = pd.W;
+  CK(launch_maxabs(cube_dev, n, c->st, c->sms, s));
+  CK(launch_fx_setup(c->st, repl, W, 1, s));
+  c->stats.launches += 2;
+  SmoothArgs a = base_args(c, cube_dev, dims);
+  a.mbits = mask_dev ? c->mbits : nullptr;
+  a.S = out_dev;
+  a.pd = pd;
+  a.pair = 0;
+  a.use_fixed_repl = 1;
+  a.repl_value = repl;
+  a.hist = nullptr;
+  a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
+  {
+    Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
+    if (pd.h == 0 && pd.wz == 1) {
+      CK(launch_identity(a, c->sms, s));
+      c->stats.launches += 1;
+    } else {
+      int l = 0;
+      CK(launch_smooth(a, c->sms, s, &l));
+      c->stats.launches += l;
+    }
+  }
+  return SC_OK;
+}
+
+int sc_noise(sc_ctx* c, const float* data_dev, int64_t n, int noise_mode, double* sigma_host, uint32_t flags,
+             void* cuda_stream) {
+  if (!c || !data_dev || !sigma_host || n <= 0) return SC_ERR_ARG;
+  if ((unsigned long long)n > c->max_voxels) return SC_ERR_BUDGET;
+  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  const unsigned int force = (flags & SC_FLAG_NO_FAST_SELECT) ? (PLAN_MED_FULL | PLAN_MAD_FULL) : 0u;
+  CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
+  CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  CK(launch_hist(data_dev, n, c->st, c->hist, 0, 0, c->sms, s));
+  c->stats.launches += 1;
+  int rc = measure(c, data_dev, n, 0, 1.0f, 0, noise_mode == SC_NOISE_STD, SC_MAX_KERNELS, force, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  rc = status_to_code(*c->st_host);
+  *sigma_host = rc == SC_OK ? (double)c->st_host->sigma_cur : 0.0;
+  return rc;
+}
+
+int sc_set_profiling(sc_ctx* c, int on) {
+  if (!c) return SC_ERR_ARG;
+  c->profiling = on ? 1 : 0;
+  return SC_OK;
+}
+
+int sc_get_stats(sc_ctx* c, sc_stats* out, int reset) {
+  if (!c || !out) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  flush_events(c);
+  *out = c->stats;
+  if (reset) {
+    const uint32_t w = c->stats.warnings;
+    memset(&c->stats, 0, sizeof(c->stats));
+    c->stats.warnings = w;
+  }
+  return SC_OK;
+}
+
+}  // extern "C"

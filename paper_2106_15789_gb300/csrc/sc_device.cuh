@@ -1,0 +1,149 @@
+// Device helpers: order-preserving float keys, histogram bins, exact
+// fixed-point conversions.
+#pragma once
+
+#include <cstdint>
+
+#include "sc_internal.h"
+
+namespace sc {
+
+// Order-preserving uint32 key of a float: key(a) < key(b) iff a < b for
+// non-NaN a, b (with -0 just below +0).
+__device__ __forceinline__ unsigned int fkey(float s) {
+  unsigned int u = __float_as_uint(s);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned int k) {
+  unsigned int u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+__host__ __device__ __forceinline__ BinCfg window_cfg(float sigma0) {
+  // 32 octaves [2^-20, 2^12) x sigma0, clamped to the exponent range.
+  unsigned int u;
+#ifdef __CUDA_ARCH__
+  u = __float_as_uint(sigma0);
+#else
+  __builtin_memcpy(&u, &sigma0, 4);
+#endif
+  int e = (int)((u >> 23) & 0xff) - kWindowBelow;
+  if (e < 1) e = 1;
+  if (e > 255 - kWindowE) e = 255 - kWindowE;
+  return BinCfg{e, kWindowE, kWindowMB};
+}
+
+// Histogram bin of a non-NaN float (monotone in the value).
+__host__ __device__ __forceinline__ int bin_of_bits(unsigned int u, BinCfg c) {
+  unsigned int mag = u & 0x7fffffffu;
+  int e = (int)(mag >> 23);
+  int b;
+  if (e < c.e_base) {
+    b = 0;
+  } else if (e >= c.e_base + c.E) {
+    b = (c.E << c.MB) + 1;
+  } else {
+    b = 1 + ((e - c.e_base) << c.MB) + (int)((mag >> (23 - c.MB)) & ((1u << c.MB) - 1u));
+  }
+  return (u >> 31) ? (kBinsPerSign - 1 - b) : (kBinsPerSign + b);
+}
+__device__ __forceinline__ int bin_of(float s, BinCfg c) { return bin_of_bits(__float_as_uint(s), c); }
+
+// Smallest and largest magnitude (inclusive, conservative) of magnitude bin mb.
+__device__ __forceinline__ double mag_lo(int mb, BinCfg c) {
+  if (mb == 0) return 0.0;
+  if (mb == (c.E << c.MB) + 1) return (double)__uint_as_float((unsigned)(c.e_base + c.E) << 23);
+  int e = c.e_base + ((mb - 1) >> c.MB);
+  unsigned int mt = (unsigned)(mb - 1) & ((1u << c.MB) - 1u);
+  unsigned int bits = ((unsigned)e << 23) | (mt << (23 - c.MB));
+  if (e >= 255) return __longlong_as_double(0x7ff0000000000000LL);
+  return (double)__uint_as_float(bits);
+}
+__device__ __forceinline__ double mag_hi(int mb, BinCfg c) {
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  if (mb == (c.E << c.MB) + 1) return inf;
+  unsigned int bits;
+  if (mb == 0) {
+    bits = (unsigned)c.e_base << 23;
+  } else {
+    int e = c.e_base + ((mb - 1) >> c.MB);
+    unsigned int mt = (unsigned)(mb - 1) & ((1u << c.MB) - 1u);
+    bits = (((unsigned)e << 23) | (mt << (23 - c.MB))) + (1u << (23 - c.MB));
+  }
+  if ((bits >> 23) >= 255u) return inf;
+  return (double)__uint_as_float(bits);
+}
+__device__ __forceinline__ double bin_lo_value(int i, BinCfg c) {
+  return i >= kBinsPerSign ? mag_lo(i - kBinsPerSign, c) : -mag_hi(kBinsPerSign - 1 - i, c);
+}
+__device__ __forceinline__ double bin_hi_value(int i, BinCfg c) {
+  return i >= kBinsPerSign ? mag_hi(i - kBinsPerSign, c) : -mag_lo(kBinsPerSign - 1 - i, c);
+}
+
+// x * 2^f rounded to the nearest integer (halves away from zero), exactly,
+// built from the float's bits (the 64-bit cvt instructions run on the FP64
+// pipe). Requires |x| * 2^f < 2^62; zero and subnormal x give 0.
+__device__ __forceinline__ long long quantize(float x, int f) {
+  unsigned int u = __float_as_uint(x);
+  int e = (int)((u >> 23) & 0xffu);
+  unsigned int m = (u & 0x7fffffu) | 0x800000u;
+  int sh = e - 150 + f;
+  unsigned long long q;
+  if (e == 0) {
+    q = 0ull;
+  } else if (sh >= 0) {
+    q = (unsigned long long)m << sh;
+  } else if (sh >= -25) {
+    q = (unsigned long long)((m + (1u << (-sh - 1))) >> (-sh));
+  } else {
+    q = 0ull;
+  }
+  long long r = (long long)q;
+  return (u >> 31) ? -r : r;
+}
+
+// Correctly rounded (to nearest, ties to even) float of an unsigned 64-bit
+// integer, from integer operations (the 64-bit cvt runs on the FP64 pipe).
+__device__ __forceinline__ float u64_to_float_rn(unsigned long long a) {
+  if (a == 0ull) return 0.0f;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << lz;             // leading one at bit 63
+  unsigned int mant = (unsigned int)(n >> 40);      // 24 significant bits
+  const unsigned long long rest = n & 0xffffffffffull;
+  const unsigned long long half = 0x8000000000ull;
+  if (rest > half || (rest == half && (mant & 1u))) mant += 1u;  // may carry to 2^24
+  const unsigned int e = (unsigned int)(63 - lz + 127);
+  return __uint_as_float((e << 23) + (mant - 0x800000u));  // a carry moves into the exponent
+}
+
+// float of q * inv: q rounded once to float, then one multiply (<= 1.5 ulp
+// of the exact product plus the rounding of inv).
+__device__ __forceinline__ float dequantize(long long q, float inv) {
+  const unsigned long long a = q < 0 ? (unsigned long long)0 - (unsigned long long)q : (unsigned long long)q;
+  const float v = __fmul_rn(u64_to_float_rn(a), inv);
+  return q < 0 ? -v : v;
+}
+
+__device__ __forceinline__ bool mask_bit(const uint32_t* mbits, long long v) {
+  return mbits != nullptr && ((__ldg(mbits + (v >> 5)) >> (v & 31)) & 1u);
+}
+
+// Spread the 8 bits of b to bit positions 0, 4, 8, ..., 28.
+__device__ __forceinline__ unsigned int spread4(unsigned int b) {
+  b &= 0xffu;
+  b = (b | (b << 12)) & 0x000f000fu;
+  b = (b | (b << 6)) & 0x03030303u;
+  b = (b | (b << 3)) & 0x11111111u;
+  return b;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace sc

@@ -1,0 +1,194 @@
+// Internal declarations shared by the host library and its CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "sc.h"
+
+namespace sc {
+
+// ---------------------------------------------------------------------------
+// Value histogram used by the exact median / MAD selection.
+//
+// Bins follow the float's own bits: per sign, an underflow bin, E exponents
+// of 2^MB mantissa sub-bins each (E << MB == 4096), and an overflow bin.
+// Negative values map below positive ones, so the bin index is monotone in
+// the value. The full-range layout (e_base 0, E 256, MB 4) needs no prior
+// knowledge of the data; the windowed one (E 32, MB 7) centres 32 octaves on
+// the raw cube's noise level for 8x finer bins where the order statistics lie.
+constexpr int kBinsPerSign = 4096 + 2;
+constexpr int kNumBins = 2 * kBinsPerSign;
+
+struct BinCfg {
+  int e_base;  // first exponent field value with its own bins
+  int E;       // number of exponents with their own bins
+  int MB;      // mantissa bits per exponent (E << MB == 4096)
+};
+
+constexpr BinCfg kFullRange = {0, 256, 4};
+constexpr int kWindowE = 32, kWindowMB = 7, kWindowBelow = 20;  // window [2^-20, 2^12) x sigma_0
+
+// ---------------------------------------------------------------------------
+// Radix selection of one order statistic among candidate values.
+// digits of 11, 11 and 10 bits, from the top of the 32-bit key
+__host__ __device__ constexpr int sel_bits(int r) { return r < 2 ? 11 : 10; }
+__host__ __device__ constexpr int sel_shift(int r) { return r == 0 ? 21 : (r == 1 ? 10 : 0); }  // key >> shift after round r
+constexpr int kSelBins = 2048;
+
+enum SelMode : int { SEL_VALUE = 0, SEL_ABSDEV = 1 };
+
+struct SelJob {
+  const float* list;              // candidate values (or the whole array in full mode)
+  unsigned long long count_fixed; // element count when count_ptr is null
+  unsigned long long* count_ptr;  // element count filled in by the candidate pass
+  int mode;                       // SEL_VALUE: key(s); SEL_ABSDEV: key(|s - m|)
+  int pad;
+  unsigned long long rank_lo;     // order statistics wanted, relative to the list
+  unsigned long long rank_hi;
+  unsigned int prefix[4];         // key prefix after each round (prefix[0] unused)
+  unsigned long long rank_in[4];  // remaining rank of rank_lo inside the prefix
+  unsigned long long hist[3][kSelBins];
+  unsigned long long c_le;        // elements with key <= key_lo
+  unsigned int min_gt;            // smallest key > key_lo
+  unsigned int key_lo;
+};
+
+// ---------------------------------------------------------------------------
+// Plan of one noise measurement, written by k_plan from the value histogram.
+enum PlanFlags : int {
+  PLAN_EMPTY = 1,      // no finite value
+  PLAN_MED_FULL = 2,   // median candidates above capacity: select over the whole array
+  PLAN_MAD_FULL = 4,   // MAD candidates above capacity (or no bracket): whole array
+  PLAN_CLIP = 8,       // this measurement also clips into the mask
+  PLAN_CLIP_FULL = 16, // clip needs its own pass after sigma is known
+  PLAN_STD = 32,       // STD noise mode
+};
+
+struct NoisePlan {
+  unsigned long long n;           // finite values
+  unsigned long long k_lo, k_hi;  // median / MAD order statistics (0-based)
+  unsigned long long below_med;   // values in bins below the median bins
+  int b_med_lo, b_med_hi;         // bins holding the two middle values
+  int flags;
+  int has_B;
+  float B_lo, B_hi;  // s in [B_lo, B_hi]  =>  |s - m| <= T1 < MAD for sure
+  float A_lo, A_hi;  // s < A_lo or > A_hi =>  |s - m| >  T2 > MAD for sure
+  float thr_lo, thr_hi;  // |S| > thr_hi: detected for sure; |S| <= thr_lo: not detected
+  float threshold;       // t
+  float T1, T2;
+  unsigned long long bound_med, bound_mad, bound_amb;  // candidate counts bounds from the histogram
+};
+
+// Device-resident state of one sc_run (one context owns one).
+struct DevState {
+  unsigned int status;   // SC_ST_* error bits
+  unsigned int warn;     // SC_WARN_* bits
+  float sigma0;          // noise of the raw cube
+  float repl;            // n * sigma0 (0: replacement off)
+  unsigned int maxabs_bits;  // max |C| over finite voxels (float bits; monotone for >= 0)
+  double m;              // median of the current measurement (exact: mean of two floats)
+  double mad;            // MAD of the current measurement
+  float sigma_cur;       // sigma of the current measurement
+  double sigma_cur_d;    // the same before rounding to float
+  double repl_d;         // n * sigma0 in float64 (replacement value)
+  BinCfg win;            // windowed bin layout for smoothed cubes
+  double sum, sum2;      // STD mode accumulators
+  unsigned long long count;
+  // counters filled by the candidate pass
+  unsigned long long n_cand_med, n_cand_mad, n_amb, n_below;
+  NoisePlan plan;
+  SelJob sel_med, sel_mad;
+  // fixed-point smoothing scale of every pair
+  int fx_shift[SC_MAX_KERNELS];      // f: X_q = rint(X * 2^f)
+  float fx_scale[SC_MAX_KERNELS];    // 2^f
+  float fx_inv[SC_MAX_KERNELS];      // 2^-f / W (W = integer weight total of the pair)
+  long long fx_qrepl[SC_MAX_KERNELS];  // rint(repl_d * 2^f): replaced voxels in fixed point
+  float sigma[SC_MAX_KERNELS + 1];   // per pair; [SC_MAX_KERNELS] = scratch for sc_noise
+};
+
+enum StatusBits : unsigned int {
+  SC_ST_ALLNAN = 1u,
+  SC_ST_INTERNAL = 2u,
+  SC_ST_OVERFLOW = 4u,
+};
+
+struct Caps {
+  unsigned long long med, mad, amb;
+};
+
+// Candidate lists owned by the context.
+struct Lists {
+  float* med;
+  float* mad;
+  unsigned long long* amb;
+  Caps cap;
+};
+
+// ---------------------------------------------------------------------------
+// Smoothing of one kernel pair.
+constexpr int kMaxHalf = 40;    // largest spatial half-width (sum of (w-1)/2)
+constexpr int kMaxBoxcar = 127; // largest spectral boxcar
+
+struct PairDesc {
+  int w[3];       // spatial cascade widths (1 = identity)
+  int h;          // spatial half-width
+  int wz;         // spectral width (1 = identity)
+  long long W;    // integer weight total (w0 w1 w2)^2 * wz
+  int taps[2 * kMaxHalf + 1];  // composed integer kernel, 2h+1 taps, sum = w0 w1 w2
+};
+
+struct PairWeights {
+  long long w[SC_MAX_KERNELS];  // integer weight total of every pair (passed by value to kernels)
+};
+
+struct SmoothArgs {
+  const float* C;
+  const uint32_t* mbits;  // working mask, 1 bit per voxel, flat order (may be null: empty)
+  float* S;
+  int nx, ny, nz;
+  int pair;               // index into DevState fixed-point arrays
+  int use_fixed_repl;     // 1: replacement value below instead of DevState::repl
+  float repl_value;
+  DevState* st;
+  unsigned long long* hist;  // null: no histogram
+  int win;                   // 1: windowed bins (DevState::win), 0: full range
+  PairDesc pd;
+  int tx, ty, lz;            // tile and z-chunk sizes
+  int tiles_x, tiles_y, zchunks;
+  int generic;               // force the generic FIR path
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (all enqueue on `s`, return cudaError_t of the launch).
+cudaError_t launch_hist(const float* x, long long n, DevState* st, unsigned long long* hist, int win,
+                        int want_maxabs, int sms, cudaStream_t s);
+cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, const float* src, long long n_total,
+                        Lists L, float threshold, int clip, int std_mode, unsigned int force_flags, cudaStream_t s);
+cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int win, int sms,
+                         cudaStream_t s);
+// which: 0 median (result in DevState::m), 1 MAD (DevState::mad, sigma_cur, sigma[pair] if pair >= 0)
+cudaError_t launch_select(DevState* st, int which, int pair, int sms, cudaStream_t s);
+cudaError_t launch_resolve(const float* src, uint32_t* mbits, DevState* st, Lists L, int sms, cudaStream_t s);
+cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, DevState* st, int sms,
+                             cudaStream_t s);
+cudaError_t launch_std(const float* src, long long n, DevState* st, int sms, cudaStream_t s);
+cudaError_t launch_std_final(DevState* st, int pair, cudaStream_t s);
+cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,
+                               cudaStream_t s);
+cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s);
+cudaError_t launch_pack(const uint8_t* m8, long long n, uint32_t* mbits, cudaStream_t s);
+cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, cudaStream_t s);
+cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s);
+cudaError_t launch_identity(const SmoothArgs& a, int sms, cudaStream_t s);
+cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);
+
+// Host helpers.
+int cascade_widths(double fwhm, int w[3]);
+int make_pair(const sc_kernel& k, PairDesc* pd);
+void choose_tiles(SmoothArgs* a);
+size_t smooth_smem_bytes(const SmoothArgs& a);
+
+}  // namespace sc

@@ -1,0 +1,895 @@
+// Robust noise measurement and clipping (SoFiA 2, Sect. 4.1 and 4.2).
+//
+// sigma = 1.4826 * median(|S - median(S)|) over the finite voxels, with both
+// medians exact order statistics of the float32 values (mean of the two
+// middle ones for an even count), then mask |= |S| > t * sigma.
+//
+// Data flow for one measurement over an array S of n values:
+//   k_hist      (or the smoothing kernel's epilogue): histogram of S over
+//               bins of the float bits (monotone in the value).
+//   k_plan      one block: ranks of the middle order statistics -> the bins
+//               holding the median; from the bin counts alone, thresholds
+//               T1 < MAD < T2 and the value windows that can hold the MAD's
+//               elements; bounds on t*sigma for the clip; capacity checks.
+//   k_pass2     one read of S: collects median candidates (values in the
+//               median bins), MAD candidates (values not surely inside or
+//               outside the MAD band), counts values surely inside the band,
+//               sets the mask bits that are certain whatever sigma is inside
+//               its bounds, and lists the few voxels whose clip is not yet
+//               decided.
+//   k_sel_*     exact radix selection (11+11+10 bits) of the wanted order
+//               statistics inside the candidate lists, then of |s - m|.
+//   k_resolve   decides the listed voxels with the exact sigma.
+// When a candidate set would exceed its buffer, the plan switches that part
+// to full passes over S (k_sel_* on the whole array, k_clip_full); results are
+// identical, only slower.
+#include <cfloat>
+#include <cstdio>
+
+#include "sc_device.cuh"
+#include "sc_internal.h"
+
+namespace sc {
+
+constexpr double kMadToSigma = 1.4826;
+
+// sigma from the MAD, rounded once to float. Monotone in mad, so the plan's
+// bounds on the MAD give bounds on sigma through the same function.
+__device__ __forceinline__ float sigma_of_mad(double mad) { return __double2float_rn(kMadToSigma * mad); }
+
+// ---------------------------------------------------------------------------
+// Histogram (and max |x|) of the finite values of an array.
+__global__ void __launch_bounds__(512) k_hist(const float* __restrict__ x, long long n, DevState* st,
+                                              unsigned long long* __restrict__ hist, int win, int want_maxabs) {
+  extern __shared__ unsigned int sh[];
+  for (int i = threadIdx.x; i < kNumBins; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const BinCfg cfg = win ? st->win : kFullRange;
+  unsigned int mx = 0u;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x) & 15u) == 0);
+  if (vec) {
+    const long long n4 = n >> 2;
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      float4 v = __ldg(x4 + i);
+      float a[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (isfinite(a[c])) {
+          atomicAdd(&sh[bin_of(a[c], cfg)], 1u);
+          mx = max(mx, __float_as_uint(fabsf(a[c])));
+        }
+      }
+    }
+    for (long long i = (n4 << 2) + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      float a = __ldg(x + i);
+      if (isfinite(a)) {
+        atomicAdd(&sh[bin_of(a, cfg)], 1u);
+        mx = max(mx, __float_as_uint(fabsf(a)));
+      }
+    }
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      float a = __ldg(x + i);
+      if (isfinite(a)) {
+        atomicAdd(&sh[bin_of(a, cfg)], 1u);
+        mx = max(mx, __float_as_uint(fabsf(a)));
+      }
+    }
+  }
+  if (want_maxabs) {
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxabs_bits, mx);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNumBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+}
+
+cudaError_t launch_hist(const float* x, long long n, DevState* st, unsigned long long* hist, int win,
+                        int want_maxabs, int sms, cudaStream_t s) {
+  const size_t smem = kNumBins * sizeof(unsigned int);
+  long long want = (n / 4 + 511) / 512;
+  int grid = (int)(want < 1 ? 1 : (want > 4LL * sms ? 4LL * sms : want));
+  k_hist<<<grid, 512, smem, s>>>(x, n, st, hist, win, want_maxabs);
+  return cudaGetLastError();
+}
+
+// Max |x| over finite values only (for sc_smooth's fixed-point scale).
+__global__ void k_maxabs(const float* __restrict__ x, long long n, DevState* st) {
+  unsigned int mx = 0u;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float a = __ldg(x + i);
+    if (isfinite(a)) mx = max(mx, __float_as_uint(fabsf(a)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxabs_bits, mx);
+}
+
+cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s) {
+  long long want = (n + 255) / 256;
+  int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
+  k_maxabs<<<grid, 256, 0, s>>>(x, n, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plan: one block of 1024 threads.
+struct PlanCtx {
+  const unsigned long long* cum;  // exclusive prefix counts, kNumBins + 1 entries
+  BinCfg cfg;
+  double m_min, m_max;
+};
+
+__device__ __forceinline__ unsigned long long cum_range(const PlanCtx& P, int b1, int b2) {
+  // count of values in bins b1..b2 inclusive (0 if empty range)
+  if (b2 < b1) return 0ull;
+  return P.cum[b2 + 1] - P.cum[b1];
+}
+__device__ __forceinline__ float f_down(double v) { return nextafterf(__double2float_rd(v), -INFINITY); }
+__device__ __forceinline__ float f_up(double v) { return nextafterf(__double2float_ru(v), INFINITY); }
+
+// Values that can possibly lie within T of some m in [m_min, m_max].
+__device__ unsigned long long f_possible(const PlanCtx& P, float T) {
+  float lo = f_down(P.m_min - (double)T), hi = f_up(P.m_max + (double)T);
+  return cum_range(P, bin_of(lo, P.cfg), bin_of(hi, P.cfg));
+}
+// Values that surely lie within T of every m in [m_min, m_max] (whole bins
+// strictly inside [m_max - T, m_min + T]).
+__device__ unsigned long long f_sure(const PlanCtx& P, float T) {
+  float lo = f_up(P.m_max - (double)T), hi = f_down(P.m_min + (double)T);
+  if (!(lo <= hi)) return 0ull;
+  return cum_range(P, bin_of(lo, P.cfg) + 1, bin_of(hi, P.cfg) - 1);
+}
+
+__global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long long* __restrict__ hist, int win,
+                                               const float* src, long long n_total, Lists L, float threshold,
+                                               int clip, int std_mode, unsigned int force_flags) {
+  extern __shared__ unsigned long long cum[];  // kNumBins + 1
+  __shared__ unsigned long long wsum[32];
+  const int tid = threadIdx.x;
+  constexpr int kPer = (kNumBins + 1023) / 1024;
+  unsigned long long loc[kPer];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    int b = tid * kPer + j;
+    loc[j] = b < kNumBins ? hist[b] : 0ull;
+    s += loc[j];
+  }
+  // block exclusive scan of s
+  unsigned long long incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((tid & 31) >= o) incl += t;
+  }
+  if ((tid & 31) == 31) wsum[tid >> 5] = incl;
+  __syncthreads();
+  if (tid < 32) {
+    unsigned long long w = wsum[tid], wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (tid >= o) wi += t;
+    }
+    wsum[tid] = wi - w;
+  }
+  __syncthreads();
+  unsigned long long run = wsum[tid >> 5] + incl - s;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    int b = tid * kPer + j;
+    if (b < kNumBins) cum[b] = run;
+    run += loc[j];
+  }
+  if (tid == 1023) cum[kNumBins] = run;
+  // reset counters and selection state
+  for (int i = tid; i < 3 * kSelBins; i += blockDim.x) {
+    (&st->sel_med.hist[0][0])[i] = 0ull;
+    (&st->sel_mad.hist[0][0])[i] = 0ull;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+
+  NoisePlan p;
+  p.flags = (int)force_flags;
+  p.threshold = threshold;
+  p.has_B = 0;
+  p.B_lo = 1.0f;
+  p.B_hi = 0.0f;
+  p.A_lo = -INFINITY;
+  p.A_hi = INFINITY;
+  p.thr_lo = 0.0f;
+  p.thr_hi = INFINITY;
+  p.T1 = 0.0f;
+  p.T2 = INFINITY;
+  p.bound_med = p.bound_mad = p.bound_amb = 0ull;
+  const unsigned long long n = cum[kNumBins];
+  p.n = n;
+  st->n_cand_med = st->n_cand_mad = st->n_amb = st->n_below = 0ull;
+  st->sum = st->sum2 = 0.0;
+  st->count = 0ull;
+  if (clip) p.flags |= PLAN_CLIP;
+  if (std_mode) p.flags |= PLAN_STD | PLAN_CLIP_FULL;
+  SelJob* J[2] = {&st->sel_med, &st->sel_mad};
+  for (int w = 0; w < 2; ++w) {
+    J[w]->c_le = 0ull;
+    J[w]->min_gt = 0xffffffffu;
+    J[w]->key_lo = 0u;
+    J[w]->count_fixed = 0ull;
+    J[w]->count_ptr = nullptr;
+    J[w]->list = src;
+    J[w]->rank_lo = J[w]->rank_hi = 0ull;
+  }
+  if (n == 0ull) {
+    p.flags |= PLAN_EMPTY;
+    st->status |= SC_ST_ALLNAN;
+    st->plan = p;
+    return;
+  }
+  p.k_lo = (n - 1ull) / 2ull;
+  p.k_hi = n / 2ull;
+  // bins of the two middle order statistics
+  int lo = 0, hi = kNumBins - 1;
+  while (lo < hi) {  // first bin b with cum[b + 1] > k_lo
+    int mid = (lo + hi) >> 1;
+    if (cum[mid + 1] > p.k_lo) hi = mid; else lo = mid + 1;
+  }
+  p.b_med_lo = lo;
+  hi = kNumBins - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cum[mid + 1] > p.k_hi) hi = mid; else lo = mid + 1;
+  }
+  p.b_med_hi = lo;
+  p.below_med = cum[p.b_med_lo];
+  p.bound_med = cum[p.b_med_hi + 1] - cum[p.b_med_lo];
+  if (p.bound_med > L.cap.med) p.flags |= PLAN_MED_FULL;
+
+  if (!std_mode) {
+    const BinCfg cfg = win ? st->win : kFullRange;
+    PlanCtx P{cum, cfg, bin_lo_value(p.b_med_lo, cfg), bin_hi_value(p.b_med_hi, cfg)};
+    if (!(isfinite(P.m_min) && isfinite(P.m_max))) {
+      p.flags |= PLAN_MAD_FULL | PLAN_CLIP_FULL;
+    } else {
+      // T1: largest T with possibly-within count <= k_lo (then MAD > T1)
+      if (f_possible(P, 0.0f) <= p.k_lo) {
+        unsigned int a = 0u, b = 0x7f800000u;
+        while (b - a > 1u) {
+          unsigned int mid = a + ((b - a) >> 1);
+          if (f_possible(P, __uint_as_float(mid)) <= p.k_lo) a = mid; else b = mid;
+        }
+        p.T1 = __uint_as_float(a);
+        p.has_B = 1;
+        p.B_lo = f_up(P.m_max - (double)p.T1);
+        p.B_hi = f_down(P.m_min + (double)p.T1);
+      }
+      // T2: smallest T with surely-within count >= k_hi + 1 (then MAD < T2)
+      const unsigned int fmax_bits = 0x7f7fffffu;
+      if (f_sure(P, __uint_as_float(fmax_bits)) >= p.k_hi + 1ull) {
+        unsigned int a = 0u, b = fmax_bits;
+        while (b - a > 1u) {
+          unsigned int mid = a + ((b - a) >> 1);
+          if (f_sure(P, __uint_as_float(mid)) >= p.k_hi + 1ull) b = mid; else a = mid;
+        }
+        p.T2 = __uint_as_float(b);
+        p.A_lo = f_down(P.m_min - (double)p.T2);
+        p.A_hi = f_up(P.m_max + (double)p.T2);
+      }
+      // bound on the MAD candidates: values neither surely inside nor outside
+      const int bA0 = bin_of(p.A_lo, cfg), bA1 = bin_of(p.A_hi, cfg);
+      if (p.has_B && p.B_lo <= p.B_hi) {
+        p.bound_mad = cum_range(P, bA0, bin_of(p.B_lo, cfg)) + cum_range(P, bin_of(p.B_hi, cfg), bA1);
+      } else {
+        p.bound_mad = cum_range(P, bA0, bA1);
+      }
+      if (p.bound_mad > L.cap.mad) p.flags |= PLAN_MAD_FULL;
+      if (clip) {
+        if (!p.has_B || !(p.T1 > 0.0f) || !isfinite(p.T2)) {
+          p.flags |= PLAN_CLIP_FULL;
+        } else {
+          const float s_lo = sigma_of_mad((double)p.T1), s_hi = sigma_of_mad((double)p.T2);
+          p.thr_lo = __fmul_rn(threshold, s_lo);
+          p.thr_hi = __fmul_rn(threshold, s_hi);
+          p.bound_amb = cum_range(P, bin_of(-p.thr_hi, cfg), bin_of(-p.thr_lo, cfg)) +
+                        cum_range(P, bin_of(p.thr_lo, cfg), bin_of(p.thr_hi, cfg));
+          if (p.bound_amb > L.cap.amb) p.flags |= PLAN_CLIP_FULL;
+        }
+      }
+    }
+  }
+  // selection jobs
+  const bool med_full = (p.flags & PLAN_MED_FULL) != 0, mad_full = (p.flags & PLAN_MAD_FULL) != 0;
+  st->sel_med.list = med_full ? src : L.med;
+  st->sel_med.count_fixed = med_full ? (unsigned long long)n_total : L.cap.med;
+  st->sel_med.count_ptr = med_full ? nullptr : &st->n_cand_med;
+  st->sel_med.mode = SEL_VALUE;
+  st->sel_med.rank_lo = med_full ? p.k_lo : p.k_lo - p.below_med;
+  st->sel_med.rank_hi = st->sel_med.rank_lo + (p.k_hi - p.k_lo);
+  st->sel_mad.list = mad_full ? src : L.mad;
+  st->sel_mad.count_fixed = mad_full ? (unsigned long long)n_total : L.cap.mad;
+  st->sel_mad.count_ptr = mad_full ? nullptr : &st->n_cand_mad;
+  st->sel_mad.mode = SEL_ABSDEV;
+  st->sel_mad.rank_lo = p.k_lo;  // minus n_below (known after k_pass2) unless full
+  st->sel_mad.rank_hi = p.k_hi;
+  st->plan = p;
+}
+
+cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, const float* src, long long n_total,
+                        Lists L, float threshold, int clip, int std_mode, unsigned int force_flags,
+                        cudaStream_t s) {
+  const size_t smem = (kNumBins + 1) * sizeof(unsigned long long);
+  k_plan<<<1, 1024, smem, s>>>(st, hist, win, src, n_total, L, threshold, clip, std_mode, force_flags);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Candidate pass. Each warp handles chunks of 128 consecutive values (4 per
+// lane) and stages list entries in its own shared-memory region, flushing to
+// the global lists with one atomic per >= 64 entries.
+constexpr int kStage = 192;   // entries per warp and list
+constexpr int kFlushAt = 64;  // flush when more than this many are staged
+
+struct WarpStage {
+  float* med;
+  float* mad;
+  unsigned long long* amb;
+  int nmed, nmad, namb;
+};
+
+template <typename T>
+__device__ __forceinline__ void stage_flush(T* stage, int& cnt, T* glob, unsigned long long* gcount,
+                                            unsigned long long cap, unsigned int* status) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0 && cnt > 0) base = atomicAdd(gcount, (unsigned long long)cnt);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (base + (unsigned long long)cnt > cap) {
+    if (lane == 0) atomicOr(status, (unsigned int)SC_ST_OVERFLOW);
+  } else {
+    for (int i = lane; i < cnt; i += 32) glob[base + i] = stage[i];
+  }
+  __syncwarp();
+  cnt = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_push(bool pred, T val, T* stage, int& cnt) {
+  const unsigned int b = __ballot_sync(0xffffffffu, pred);
+  if (pred) {
+    const int off = __popc(b & ((1u << (threadIdx.x & 31)) - 1u));
+    stage[cnt + off] = val;
+  }
+  cnt += __popc(b);
+}
+
+__global__ void __launch_bounds__(256) k_pass2(const float* __restrict__ src, long long n, uint32_t* mbits,
+                                               DevState* st, Lists L, int win) {
+  __shared__ float sh_med[8][kStage];
+  __shared__ float sh_mad[8][kStage];
+  __shared__ unsigned long long sh_amb[8][kStage];
+  const NoisePlan p = st->plan;
+  if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
+  const BinCfg cfg = win ? st->win : kFullRange;
+  const bool do_med = !(p.flags & PLAN_MED_FULL);
+  const bool do_mad = !(p.flags & PLAN_MAD_FULL);
+  const bool do_clip = (p.flags & PLAN_CLIP) && !(p.flags & PLAN_CLIP_FULL);
+  if (!do_med && !do_mad && !do_clip) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* smed = sh_med[warp];
+  float* smad = sh_mad[warp];
+  unsigned long long* samb = sh_amb[warp];
+  int nmed = 0, nmad = 0, namb = 0;
+  unsigned long long below = 0;
+  const long long nchunks = (n + 127) / 128;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+  const long long wstride = (long long)gridDim.x * 8;
+  for (long long ch = (long long)blockIdx.x * 8 + warp; ch < nchunks; ch += wstride) {
+    const long long v0 = ch * 128 + lane * 4;
+    float a[4];
+    if (vec && v0 + 3 < n) {
+      float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
+      a[0] = t4.x; a[1] = t4.y; a[2] = t4.z; a[3] = t4.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = (v0 + c < n) ? __ldg(src + v0 + c) : __int_as_float(0x7fc00000);
+    }
+    unsigned int sure_bits[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float s = a[c];
+      const bool fin = isfinite(s);
+      bool pm = false, pa = false, pamb = false, sure = false;
+      if (fin) {
+        if (do_med) {
+          const int b = bin_of(s, cfg);
+          pm = (b >= p.b_med_lo && b <= p.b_med_hi);
+        }
+        if (do_mad) {
+          if (p.has_B && s >= p.B_lo && s <= p.B_hi) {
+            ++below;
+          } else if (s >= p.A_lo && s <= p.A_hi) {
+            pa = true;
+          }
+        }
+        if (do_clip) {
+          const float as = fabsf(s);
+          if (as > p.thr_hi) sure = true;
+          else if (as > p.thr_lo) pamb = true;
+        }
+      }
+      stage_push(pm, s, smed, nmed);
+      stage_push(pa, s, smad, nmad);
+      stage_push(pamb, (unsigned long long)(v0 + c), samb, namb);
+      sure_bits[c] = __ballot_sync(0xffffffffu, sure);
+    }
+    if (do_clip) {
+      if (lane < 4) {
+        unsigned int w = 0u;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w |= spread4(sure_bits[c] >> (8 * lane)) << c;
+        const long long wi = ch * 4 + lane;
+        if (w && wi * 32 < n) mbits[wi] |= w;
+      }
+    }
+    if (nmed > kFlushAt) stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
+    if (nmad > kFlushAt) stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
+    if (namb > kFlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
+  }
+  stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
+  stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
+  stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
+  below = warp_sum_u64(below);
+  if (lane == 0 && below) atomicAdd(&st->n_below, below);
+}
+
+cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int win, int sms,
+                         cudaStream_t s) {
+  long long want = (n + 1023) / 1024;
+  int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
+  k_pass2<<<grid, 256, 0, s>>>(src, n, mbits, st, L, win);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Radix selection. MAD keys are the correctly rounded float of the exact
+// |s - m| (m is the exact median, a double): rounding is monotone, so the
+// order statistics of the keys are the rounded order statistics of |s - m|.
+__device__ __forceinline__ bool sel_key(const SelJob& J, double m, float s, unsigned int* key) {
+  if (!isfinite(s)) return false;
+  if (J.mode == SEL_VALUE) {
+    *key = fkey(s);
+  } else {
+    *key = fkey(__double2float_rn(fabs((double)s - m)));
+  }
+  return true;
+}
+
+// Elements in the list: the candidate count, clamped to the buffer capacity
+// (count_fixed), or the whole array.
+__device__ __forceinline__ unsigned long long sel_count(const SelJob& J) {
+  return J.count_ptr ? min(*J.count_ptr, J.count_fixed) : J.count_fixed;
+}
+
+// Every block redoes the pick of round r-1 from its histogram (same result
+// everywhere); block 0 records it.
+__device__ void sel_pick(SelJob* J, int r, unsigned int* prefix, unsigned long long* rank, unsigned int* status) {
+  __shared__ unsigned long long s_part[32];
+  __shared__ unsigned int s_digit;
+  __shared__ unsigned long long s_rank;
+  const unsigned long long* h = J->hist[r - 1];
+  const int tid = threadIdx.x, nt = blockDim.x;  // nt == 256 or 1024
+  const int per = kSelBins / nt;
+  unsigned long long loc = 0;
+  for (int j = 0; j < per; ++j) loc += h[tid * per + j];
+  // exclusive scan over threads
+  unsigned long long incl = loc;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long t = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((tid & 31) >= o) incl += t;
+  }
+  if ((tid & 31) == 31) s_part[tid >> 5] = incl;
+  __syncthreads();
+  if (tid < 32) {
+    unsigned long long w = (tid < nt / 32) ? s_part[tid] : 0ull, wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (tid >= o) wi += t;
+    }
+    s_part[tid] = wi - w;
+  }
+  if (tid == 0) { s_digit = 0xffffffffu; s_rank = 0ull; }
+  __syncthreads();
+  const unsigned long long want = *rank;
+  unsigned long long run = s_part[tid >> 5] + incl - loc;
+  for (int j = 0; j < per; ++j) {
+    const unsigned long long c = h[tid * per + j];
+    if (want >= run && want < run + c) {
+      s_digit = (unsigned)(tid * per + j);
+      s_rank = want - run;
+    }
+    run += c;
+  }
+  __syncthreads();
+  if (s_digit == 0xffffffffu) {
+    if (tid == 0) atomicOr(status, (unsigned int)SC_ST_INTERNAL);
+    *prefix = 0u;
+    *rank = 0ull;
+  } else {
+    *prefix = ((*prefix) << sel_bits(r - 1)) | s_digit;
+    *rank = s_rank;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned long long sel_rank0(const DevState* st, const SelJob* J, int which) {
+  unsigned long long r = J->rank_lo;
+  if (which == 1 && J->count_ptr != nullptr) r -= st->n_below;
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_sel_round(DevState* st, int which, int r) {
+  __shared__ unsigned int sh[kSelBins];
+  SelJob* J = which ? &st->sel_mad : &st->sel_med;
+  const NoisePlan& p = st->plan;
+  if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
+  unsigned int prefix = 0u;
+  unsigned long long rank = sel_rank0(st, J, which);
+  const unsigned long long count = sel_count(*J);
+  if (r == 0 && rank >= count) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&st->status, (unsigned int)SC_ST_INTERNAL);
+    return;
+  }
+  if (r > 0) {
+    prefix = J->prefix[r - 1 + 0];
+    rank = J->rank_in[r - 1 + 0];
+    if (r == 1) { prefix = 0u; rank = sel_rank0(st, J, which); }
+    sel_pick(J, r, &prefix, &rank, &st->status);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      J->prefix[r] = prefix;
+      J->rank_in[r] = rank;
+    }
+  }
+  for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const double m = st->m;
+  const int shift_prev = (r == 0) ? 32 : sel_shift(r - 1);
+  const int shift = sel_shift(r);
+  const unsigned int dmask = (1u << sel_bits(r)) - 1u;
+  const float* list = J->list;
+  const SelJob Jl = *J;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned int key;
+    if (!sel_key(Jl, m, __ldg(list + i), &key)) continue;
+    if (shift_prev < 32 && (key >> shift_prev) != prefix) continue;
+    atomicAdd(&sh[(key >> shift) & dmask], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(&J->hist[r][i], (unsigned long long)sh[i]);
+}
+
+__global__ void __launch_bounds__(256) k_sel_succ(DevState* st, int which) {
+  __shared__ unsigned long long s_c[8];
+  __shared__ unsigned int s_m[8];
+  SelJob* J = which ? &st->sel_mad : &st->sel_med;
+  const NoisePlan& p = st->plan;
+  if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
+  const unsigned long long count = sel_count(*J);
+  if (sel_rank0(st, J, which) >= count) return;
+  unsigned int prefix = J->prefix[2];
+  unsigned long long rank = J->rank_in[2];
+  sel_pick(J, 3, &prefix, &rank, &st->status);
+  const unsigned int key_lo = prefix;
+  if (blockIdx.x == 0 && threadIdx.x == 0) J->key_lo = key_lo;
+  const double m = st->m;
+  const SelJob Jl = *J;
+  unsigned long long c = 0;
+  unsigned int mn = 0xffffffffu;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned int key;
+    if (!sel_key(Jl, m, __ldg(Jl.list + i), &key)) continue;
+    if (key <= key_lo) ++c; else mn = min(mn, key);
+  }
+  c = warp_sum_u64(c);
+  for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_c[warp] = c; s_m[warp] = mn; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long ct = 0;
+    unsigned int mt = 0xffffffffu;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ct += s_c[w]; mt = min(mt, s_m[w]); }
+    if (ct) atomicAdd(&J->c_le, ct);
+    if (mt != 0xffffffffu) atomicMin(&J->min_gt, mt);
+  }
+}
+
+__global__ void k_sel_final(DevState* st, int which, int pair) {
+  SelJob* J = which ? &st->sel_mad : &st->sel_med;
+  const NoisePlan& p = st->plan;
+  if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
+  const unsigned long long count = sel_count(*J);
+  const unsigned long long r_lo = sel_rank0(st, J, which);
+  if (r_lo >= count) {
+    atomicOr(&st->status, (unsigned int)SC_ST_INTERNAL);
+    return;
+  }
+  const unsigned long long r_hi = r_lo + (p.k_hi - p.k_lo);
+  const unsigned int k_lo = J->key_lo;
+  unsigned int k_hi = k_lo;
+  if (r_hi >= J->c_le) {
+    k_hi = J->min_gt;
+    if (k_hi == 0xffffffffu) {
+      atomicOr(&st->status, (unsigned int)SC_ST_INTERNAL);
+      k_hi = k_lo;
+    }
+  }
+  const double v_lo = (double)fkey_inv(k_lo), v_hi = (double)fkey_inv(k_hi);
+  const double v = (k_hi == k_lo) ? v_lo : 0.5 * (v_lo + v_hi);
+  if (which == 0) {
+    st->m = v;
+  } else {
+    st->mad = v;
+    st->sigma_cur_d = kMadToSigma * v;
+    const float sg = sigma_of_mad(v);
+    st->sigma_cur = sg;
+    if (pair >= 0) st->sigma[pair] = sg;
+    if (!(sg > 0.0f)) st->warn |= SC_WARN_ZERO_SIGMA;
+  }
+}
+
+cudaError_t launch_select(DevState* st, int which, int pair, int sms, cudaStream_t s) {
+  const int grid = 2 * sms;
+  for (int r = 0; r < 3; ++r) {
+    k_sel_round<<<grid, 256, 0, s>>>(st, which, r);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_sel_succ<<<grid, 256, 0, s>>>(st, which);
+  k_sel_final<<<1, 1, 0, s>>>(st, which, pair);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// STD mode: float64 sums (the float32 data's squares can overflow or
+// underflow float32), two passes: mean, then sum of squared deviations.
+__global__ void __launch_bounds__(256) k_std_pass(const float* __restrict__ x, long long n, DevState* st, int second) {
+  __shared__ double s_a[8];
+  __shared__ unsigned long long s_n[8];
+  if (st->plan.flags & PLAN_EMPTY) return;
+  const double mean = second ? st->sum / (double)st->count : 0.0;
+  double acc = 0.0;
+  unsigned long long cnt = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float s = __ldg(x + i);
+    if (!isfinite(s)) continue;
+    if (second) {
+      const double d = (double)s - mean;
+      acc = fma(d, d, acc);
+    } else {
+      acc += (double)s;
+    }
+    ++cnt;
+  }
+  double a = acc;
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  cnt = warp_sum_u64(cnt);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { s_a[warp] = a; s_n[warp] = cnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double at = 0.0;
+    unsigned long long ct = 0;
+    for (int w = 0; w < 8; ++w) { at += s_a[w]; ct += s_n[w]; }
+    if (second) {
+      atomicAdd(&st->sum2, at);
+    } else {
+      atomicAdd(&st->sum, at);
+      atomicAdd(&st->count, ct);
+    }
+  }
+}
+
+__global__ void k_std_final(DevState* st, int pair) {
+  if (st->plan.flags & PLAN_EMPTY) return;
+  const unsigned long long c = st->count;
+  const double sd = c > 1ull ? sqrt(st->sum2 / (double)(c - 1ull)) : 0.0;
+  const float sg = (float)sd;
+  st->sigma_cur = sg;
+  st->sigma_cur_d = sd;
+  if (pair >= 0) st->sigma[pair] = sg;
+  if (!(sg > 0.0f)) st->warn |= SC_WARN_ZERO_SIGMA;
+}
+
+cudaError_t launch_std(const float* src, long long n, DevState* st, int sms, cudaStream_t s) {
+  long long want = (n + 255) / 256;
+  int grid = (int)(want < 1 ? 1 : (want > 4LL * sms ? 4LL * sms : want));
+  k_std_pass<<<grid, 256, 0, s>>>(src, n, st, 0);
+  k_std_pass<<<grid, 256, 0, s>>>(src, n, st, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_std_final(DevState* st, int pair, cudaStream_t s) {
+  k_std_final<<<1, 1, 0, s>>>(st, pair);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Clip: the undecided voxels, or a full pass when the plan asked for one.
+__global__ void k_resolve(const float* __restrict__ src, uint32_t* mbits, DevState* st, Lists L) {
+  const NoisePlan& p = st->plan;
+  if (!(p.flags & PLAN_CLIP) || (p.flags & (PLAN_CLIP_FULL | PLAN_EMPTY))) return;
+  const float sg = st->sigma_cur;
+  if (!(sg > 0.0f)) return;
+  const float thr = __fmul_rn(p.threshold, sg);
+  const unsigned long long na = min(st->n_amb, L.cap.amb);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < na;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long v = L.amb[i];
+    if (fabsf(__ldg(src + v)) > thr) atomicOr(mbits + (v >> 5), 1u << (v & 31ull));
+  }
+}
+
+cudaError_t launch_resolve(const float* src, uint32_t* mbits, DevState* st, Lists L, int sms, cudaStream_t s) {
+  k_resolve<<<sms, 256, 0, s>>>(src, mbits, st, L);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_clip_full(const float* __restrict__ src, long long n, uint32_t* mbits,
+                                                   DevState* st) {
+  const NoisePlan& p = st->plan;
+  if (!(p.flags & PLAN_CLIP) || !(p.flags & PLAN_CLIP_FULL) || (p.flags & PLAN_EMPTY)) return;
+  const float sg = st->sigma_cur;
+  if (!(sg > 0.0f)) return;
+  const float thr = __fmul_rn(p.threshold, sg);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nchunks = (n + 127) / 128;
+  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
+  for (long long ch = (long long)blockIdx.x * 8 + warp; ch < nchunks; ch += (long long)gridDim.x * 8) {
+    const long long v0 = ch * 128 + lane * 4;
+    float a[4];
+    if (vec && v0 + 3 < n) {
+      float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
+      a[0] = t4.x; a[1] = t4.y; a[2] = t4.z; a[3] = t4.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = (v0 + c < n) ? __ldg(src + v0 + c) : 0.0f;
+    }
+    unsigned int bits[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) bits[c] = __ballot_sync(0xffffffffu, isfinite(a[c]) && fabsf(a[c]) > thr);
+    if (lane < 4) {
+      unsigned int w = 0u;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) w |= spread4(bits[c] >> (8 * lane)) << c;
+      const long long wi = ch * 4 + lane;
+      if (w && wi * 32 < n) mbits[wi] |= w;
+    }
+  }
+}
+
+cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, DevState* st, int sms,
+                             cudaStream_t s) {
+  long long want = (n + 1023) / 1024;
+  int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
+  k_clip_full<<<grid, 256, 0, s>>>(src, n, mbits, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// After sigma_0: replacement value, bin window, fixed-point scales.
+// Fixed-point shift of every pair: X_q = rint(X * 2^f) with
+// max|X| * 2^f * W < 2^62, so that no exact sum can overflow int64. The
+// replacement value repl_d (float64) is quantised once per pair.
+__device__ void fx_setup(DevState* st, double repl_d, const PairWeights& W, int n_pairs) {
+  const float maxabs = __uint_as_float(st->maxabs_bits);
+  const float mx = fmaxf(maxabs, __double2float_ru(repl_d));
+  int ex = 0;
+  frexpf(mx, &ex);  // mx < 2^ex
+  if (mx == 0.0f) ex = 0;
+  for (int k = 0; k < n_pairs; ++k) {
+    const long long w = W.w[k];
+    const int bits = 64 - __clzll((unsigned long long)(w - 1));  // bit length of w - 1
+    int f = 62 - ex - bits;
+    if (f > 120) f = 120;
+    if (f < -120) f = -120;
+    st->fx_shift[k] = f;
+    st->fx_scale[k] = ldexpf(1.0f, f);
+    st->fx_inv[k] = (float)(ldexp(1.0, -f) / (double)w);
+    st->fx_qrepl[k] = __double2ll_rn(ldexp(repl_d, f));
+  }
+}
+
+__global__ void k_fx_setup(DevState* st, float repl_value, PairWeights W, int n_pairs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->repl_d = (double)repl_value;
+    st->repl = repl_value;
+    fx_setup(st, (double)repl_value, W, n_pairs);
+  }
+}
+
+cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s) {
+  k_fx_setup<<<1, 1, 0, s>>>(st, repl_value, W, n_pairs);
+  return cudaGetLastError();
+}
+
+__global__ void k_sigma0_done(DevState* st, float replacement, PairWeights W, int n_pairs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float s0 = st->sigma_cur;
+  st->sigma0 = s0;
+  st->repl_d = (replacement > 0.0f) ? (double)replacement * st->sigma_cur_d : 0.0;
+  st->repl = __double2float_rn(st->repl_d);
+  st->win = window_cfg(s0);
+  const float mx = fmaxf(__uint_as_float(st->maxabs_bits), st->repl);
+  if (s0 > 0.0f && mx > s0 * 1048576.0f) st->warn |= SC_WARN_RANGE;
+  fx_setup(st, st->repl_d, W, n_pairs);
+}
+
+cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs, cudaStream_t s) {
+  k_sigma0_done<<<1, 1, 0, s>>>(st, replacement, W, n_pairs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// uint8 mask <-> 1-bit working mask.
+__global__ void k_pack(const uint8_t* __restrict__ m8, long long n, uint32_t* __restrict__ mbits) {
+  const long long nw = (n + 31) / 32;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (long long)gridDim.x * blockDim.x) {
+    unsigned int bits = 0u;
+    const long long v0 = w * 32;
+    for (int i = 0; i < 32; ++i)
+      if (v0 + i < n && m8[v0 + i]) bits |= 1u << i;
+    mbits[w] = bits;
+  }
+}
+
+cudaError_t launch_pack(const uint8_t* m8, long long n, uint32_t* mbits, cudaStream_t s) {
+  long long nw = (n + 31) / 32;
+  long long want = (nw + 255) / 256;
+  int grid = (int)(want < 1 ? 1 : (want > 4096 ? 4096 : want));
+  k_pack<<<grid, 256, 0, s>>>(m8, n, mbits);
+  return cudaGetLastError();
+}
+
+__global__ void k_expand(const uint32_t* __restrict__ mbits, long long n, uint8_t* __restrict__ m8) {
+  // each thread writes 16 bytes
+  const bool vec = ((reinterpret_cast<uintptr_t>(m8) & 15u) == 0);
+  const long long ng = (n + 15) / 16;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    const long long v0 = g * 16;
+    const unsigned int w = __ldg(mbits + (v0 >> 5)) >> (v0 & 31);
+    if (vec && v0 + 16 <= n) {
+      uint4 o;
+      unsigned int* po = &o.x;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        unsigned int b = 0u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b |= ((w >> (4 * q + i)) & 1u) << (8 * i);
+        po[q] = b;
+      }
+      *reinterpret_cast<uint4*>(m8 + v0) = o;
+    } else {
+      for (int i = 0; i < 16 && v0 + i < n; ++i) m8[v0 + i] = (uint8_t)((w >> i) & 1u);
+    }
+  }
+}
+
+cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, cudaStream_t s) {
+  long long ng = (n + 15) / 16;
+  long long want = (ng + 255) / 256;
+  int grid = (int)(want < 1 ? 1 : (want > 8192 ? 8192 : want));
+  k_expand<<<grid, 256, 0, s>>>(mbits, n, m8);
+  return cudaGetLastError();
+}
+
+void init_noise_attrs() {
+  cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((kNumBins + 1) * sizeof(unsigned long long)));
+}
+
+}  // namespace sc

@@ -1,0 +1,268 @@
+"""ctypes binding of libsc.so (include/sc.h), with the C names.
+
+Argument marshalling only: every step of smooth-and-clip runs in the CUDA
+library. Device arrays are torch CUDA tensors (contiguous); the stream is the
+tensor device's current torch stream unless one is passed. Loading fails
+loudly when the library has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsc.so")
+
+SC_OK = 0
+SC_ERR_ARG = -1
+SC_ERR_NOMEM = -2
+SC_ERR_CUDA = -3
+SC_ERR_ALLNAN = -4
+SC_ERR_TIMEOUT = -5
+SC_ERR_UNSUPPORTED = -6
+SC_ERR_BUDGET = -7
+SC_ERR_INTERNAL = -8
+
+SC_NOISE_MAD = 0
+SC_NOISE_STD = 1
+SC_NOISE_GAUSS = 2
+NOISE_MODES = {"mad": SC_NOISE_MAD, "std": SC_NOISE_STD, "gauss": SC_NOISE_GAUSS}
+
+SC_FLAG_ACCUMULATE = 0x1
+SC_FLAG_GENERIC = 0x2
+SC_FLAG_NO_FAST_SELECT = 0x4
+
+SC_WARN_ZERO_SIGMA = 0x1
+SC_WARN_FULL_SELECT = 0x2
+SC_WARN_FULL_CLIP = 0x4
+SC_WARN_RANGE = 0x8
+
+SC_MAX_KERNELS = 64
+
+
+class sc_kernel(C.Structure):
+    _fields_ = [("fwhm_spatial_px", C.c_float), ("boxcar_chan", C.c_int32)]
+
+
+class sc_stats(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("runs", C.c_uint64), ("warnings", C.c_uint32), ("reserved", C.c_uint32),
+                ("ms_smooth", C.c_double), ("ms_select", C.c_double), ("ms_clip", C.c_double),
+                ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64)]
+
+
+class ScError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {sc_strerror(code)} ({code})" if what else f"{sc_strerror(code)} ({code})")
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "sc_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t]),
+    "sc_destroy": (None, [_P]),
+    "sc_strerror": (C.c_char_p, [C.c_int]),
+    "sc_cascade_widths": (C.c_int, [C.c_float, C.POINTER(C.c_int32)]),
+    "sc_run": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int, C.c_float,
+                         _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_run_host": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int,
+                              C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
+    "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_set_profiling": (C.c_int, [_P, C.c_int]),
+    "sc_get_stats": (C.c_int, [_P, C.POINTER(sc_stats), C.c_int]),
+}
+
+
+def lib() -> C.CDLL:
+    """Load libsc.so (built in-tree by paper_2106_15789_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first (python -c 'import __graft_entry__ as g; g.build()')")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def sc_strerror(code: int) -> str:
+    return lib().sc_strerror(int(code)).decode()
+
+
+def _check(code: int, what: str) -> int:
+    if code != SC_OK:
+        raise ScError(code, what)
+    return code
+
+
+def _kernels(kernels) -> tuple:
+    arr = (sc_kernel * len(kernels))()
+    for i, (fs, wz) in enumerate(kernels):
+        arr[i].fwhm_spatial_px = float(fs)
+        arr[i].boxcar_chan = int(wz)
+    return arr, len(kernels)
+
+
+def _dims(shape) -> C.Array:
+    nz, ny, nx = shape
+    return (C.c_int64 * 3)(nx, ny, nz)
+
+
+def _stream(t: torch.Tensor, stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> None:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def sc_cascade_widths(fwhm_px: float) -> tuple:
+    w = (C.c_int32 * 3)()
+    _check(lib().sc_cascade_widths(float(fwhm_px), w), "sc_cascade_widths")
+    return tuple(int(x) for x in w)
+
+
+def sc_create(device: int, max_voxels: int) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().sc_create(C.byref(h), int(device), int(max_voxels)), "sc_create")
+    return h
+
+
+def sc_destroy(ctx) -> None:
+    if ctx:
+        lib().sc_destroy(ctx)
+
+
+def sc_run(ctx, cube: torch.Tensor, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0,
+           mask: torch.Tensor | None = None, flags: int = 0, stream=None, want_sigma: bool = True):
+    """S+C on a CUDA cube of shape (nz, ny, nx). Returns (mask uint8, sigmas, sigma0)."""
+    _dev(cube, torch.float32, "cube")
+    if mask is None:
+        mask = torch.empty(cube.shape, dtype=torch.uint8, device=cube.device)
+    _dev(mask, torch.uint8, "mask")
+    kk, nk = _kernels(kernels)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    sig = (C.c_double * nk)() if want_sigma else None
+    sig0 = (C.c_double * 1)() if want_sigma else None
+    code = lib().sc_run(ctx, C.c_void_p(cube.data_ptr()), _dims(cube.shape), kk, nk, float(threshold), int(mode),
+                        float(replacement), C.c_void_p(mask.data_ptr()), sig, sig0, int(flags),
+                        _stream(cube, stream))
+    _check(code, "sc_run")
+    if not want_sigma:
+        return mask, None, None
+    return mask, [float(x) for x in sig], float(sig0[0])
+
+
+def sc_run_host(ctx, cube_host: torch.Tensor, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0,
+                mask_host: torch.Tensor | None = None, flags: int = 0, stream=None, device: int = 0):
+    """S+C on a host (CPU) cube; copies in and out are part of the call."""
+    if cube_host.device.type != "cpu" or cube_host.dtype != torch.float32 or not cube_host.is_contiguous():
+        raise ValueError("cube_host must be a contiguous CPU float32 tensor")
+    if mask_host is None:
+        mask_host = torch.empty(cube_host.shape, dtype=torch.uint8)
+    kk, nk = _kernels(kernels)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    sig = (C.c_double * nk)()
+    sig0 = (C.c_double * 1)()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    code = lib().sc_run_host(ctx, C.c_void_p(cube_host.data_ptr()), _dims(cube_host.shape), kk, nk, float(threshold),
+                             int(mode), float(replacement), C.c_void_p(mask_host.data_ptr()), sig, sig0, int(flags),
+                             C.c_void_p(stream.cuda_stream))
+    _check(code, "sc_run_host")
+    return mask_host, [float(x) for x in sig], float(sig0[0])
+
+
+def sc_smooth(ctx, cube: torch.Tensor, kernel, mask: torch.Tensor | None = None, replacement_value: float = 0.0,
+              out: torch.Tensor | None = None, flags: int = 0, stream=None) -> torch.Tensor:
+    """Smoothed cube S of one (spatial FWHM, spectral width) pair."""
+    _dev(cube, torch.float32, "cube")
+    if out is None:
+        out = torch.empty_like(cube)
+    _dev(out, torch.float32, "out")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+    k = sc_kernel(float(kernel[0]), int(kernel[1]))
+    code = lib().sc_smooth(ctx, C.c_void_p(cube.data_ptr()), _dims(cube.shape), k,
+                           C.c_void_p(mask.data_ptr()) if mask is not None else None, float(replacement_value),
+                           C.c_void_p(out.data_ptr()), int(flags), _stream(cube, stream))
+    _check(code, "sc_smooth")
+    return out
+
+
+def sc_noise(ctx, data: torch.Tensor, noise_mode="mad", flags: int = 0, stream=None) -> float:
+    """Noise level of the finite values of a CUDA float32 tensor."""
+    _dev(data, torch.float32, "data")
+    out = C.c_double()
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    code = lib().sc_noise(ctx, C.c_void_p(data.data_ptr()), int(data.numel()), int(mode), C.byref(out), int(flags),
+                          _stream(data, stream))
+    _check(code, "sc_noise")
+    return out.value
+
+
+def sc_set_profiling(ctx, on: bool) -> None:
+    _check(lib().sc_set_profiling(ctx, 1 if on else 0), "sc_set_profiling")
+
+
+def sc_get_stats(ctx, reset: bool = False) -> dict:
+    st = sc_stats()
+    _check(lib().sc_get_stats(ctx, C.byref(st), 1 if reset else 0), "sc_get_stats")
+    return {name: getattr(st, name) for name, _ in sc_stats._fields_ if name != "reserved"}
+
+
+class Context:
+    """Owns one sc_ctx (device workspace for cubes of up to max_voxels voxels)."""
+
+    def __init__(self, device: int = 0, max_voxels: int = 1 << 20):
+        self.device = device
+        self.max_voxels = int(max_voxels)
+        self.handle = sc_create(device, self.max_voxels)
+
+    def close(self) -> None:
+        if self.handle:
+            sc_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, flags=0, stream=None,
+            want_sigma=True):
+        return sc_run(self.handle, cube, kernels, threshold, noise_mode, replacement, mask, flags, stream, want_sigma)
+
+    def run_host(self, cube_host, kernels, threshold, noise_mode="mad", replacement=2.0, mask_host=None, flags=0,
+                 stream=None):
+        return sc_run_host(self.handle, cube_host, kernels, threshold, noise_mode, replacement, mask_host, flags,
+                           stream, self.device)
+
+    def smooth(self, cube, kernel, mask=None, replacement_value=0.0, out=None, flags=0, stream=None):
+        return sc_smooth(self.handle, cube, kernel, mask, replacement_value, out, flags, stream)
+
+    def noise(self, data, noise_mode="mad", flags=0, stream=None):
+        return sc_noise(self.handle, data, noise_mode, flags, stream)
+
+    def set_profiling(self, on=True):
+        sc_set_profiling(self.handle, on)
+
+    def stats(self, reset=False):
+        return sc_get_stats(self.handle, reset)

@@ -1,0 +1,87 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every
+symbol include/sc.h declares, and its host-only entry points behave (no GPU
+compute here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.sc_oracle import cascade_widths
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_15789_gb300 import build, sc
+
+    if not os.path.exists(sc.LIB_PATH):
+        build.build()
+    return sc.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(sc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("sc_create", "sc_destroy", "sc_strerror", "sc_run", "sc_run_host", "sc_smooth", "sc_noise",
+                 "sc_cascade_widths", "sc_get_stats", "sc_set_profiling"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror(lib):
+    from paper_2106_15789_gb300 import sc
+
+    for code in range(0, -9, -1):
+        s = sc.sc_strerror(code)
+        assert s and s != "unknown status code"
+    assert sc.sc_strerror(-99) == "unknown status code"
+
+
+def test_cascade_widths_match_oracle(lib):
+    from paper_2106_15789_gb300 import sc
+
+    for f in np.linspace(0.05, 60.0, 1200):
+        f32 = float(np.float32(f))
+        assert sc.sc_cascade_widths(f32) == (cascade_widths(f32) or (1, 1, 1)), f32
+    assert sc.sc_cascade_widths(0.0) == (1, 1, 1)
+    with pytest.raises(sc.ScError):
+        sc.sc_cascade_widths(float("nan"))
+    w = (ctypes.c_int32 * 3)()
+    assert lib.sc_cascade_widths(ctypes.c_float(1e9), w) == sc.SC_ERR_ARG
+
+
+def test_null_and_bad_args(lib):
+    from paper_2106_15789_gb300 import sc
+
+    assert lib.sc_create(None, 0, 10) == sc.SC_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.sc_create(ctypes.byref(h), 0, 0) == sc.SC_ERR_ARG
+    dims = (ctypes.c_int64 * 3)(4, 4, 4)
+    assert lib.sc_run(None, None, dims, None, 1, 3.5, 0, 2.0, None, None, None, 0, None) == sc.SC_ERR_ARG
+    assert lib.sc_noise(None, None, 10, 0, None, 0, None) == sc.SC_ERR_ARG
+    lib.sc_destroy(None)  # accepted
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+
+    from paper_2106_15789_gb300 import sc
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.sc_create(ctypes.byref(h), 0, 1000) == sc.SC_ERR_CUDA
+    assert not h.value

@@ -1,0 +1,233 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (from the method's target): smoothed voxels within 1e-5 * sigma,
+sigma within 1e-6 relative, mask bit-exact except voxels whose smoothed value
+lies within 1e-4 of the threshold (|S/sigma - t| < 1e-4) at some pair; those
+are counted. The smoothing is exact fixed-point arithmetic, so a tighter bound
+(a few float ulps of |S|) is checked as well.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.sc_oracle as O
+from synth.cubes import KERNELS_12, KERNELS_20, SMALL, CubeSpec, make_cube
+
+pytestmark = pytest.mark.gpu
+
+T = 3.5
+N_REPL = 2.0
+SIG_RTOL = 1e-6
+S_TOL = 1e-5
+BAND = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2106_15789_gb300 import Context
+
+    c = Context(0, 1 << 22)
+    yield c
+    c.close()
+
+
+def small_cube():
+    return make_cube(SMALL)
+
+
+def band_disagreements(mask_gpu, m_ref, ss, sigmas, t):
+    diff = np.argwhere(mask_gpu != m_ref)
+    bad = []
+    for p in diff:
+        p = tuple(p)
+        if not any(sk > 0 and abs(abs(s[p]) / sk - t) < BAND for s, sk in zip(ss, sigmas)):
+            bad.append(p)
+    return len(diff), bad
+
+
+def check_run(ctx, cube, kernels, t=T, mode="mad", n=N_REPL, flags=0, mask0=None):
+    c_np = cube.numpy()
+    dev = cube.cuda()
+    mask = None
+    if mask0 is not None:
+        mask = torch.from_numpy(mask0.astype(np.uint8)).cuda()
+    m, sig, s0 = ctx.run(dev, kernels, t, mode, n, mask=mask, flags=flags)
+    m_ref, s_ref, s0_ref, ss = O.sc_filter(c_np, kernels, t, mode, n, mask=mask0, return_smoothed=True)
+    assert abs(s0 - s0_ref) <= SIG_RTOL * s0_ref, (s0, s0_ref)
+    for k, (a, b) in enumerate(zip(sig, s_ref)):
+        assert abs(a - b) <= SIG_RTOL * b, (k, kernels[k], a, b)
+    ndiff, bad = band_disagreements(m.cpu().numpy(), m_ref, ss, s_ref, t)
+    assert not bad, f"{len(bad)} mask disagreements outside the threshold band, e.g. {bad[:5]}"
+    return m, sig, s0, ndiff
+
+
+# ---------------------------------------------------------------------------
+def noise_cases():
+    rng = np.random.default_rng(123)
+    cases = {f"normal{n}": rng.standard_normal(n) for n in (1, 2, 3, 10, 101, 1000, 100_001, 2_000_000)}
+    x = rng.standard_normal(300_000)
+    x[rng.random(x.size) < 0.1] = np.nan
+    x[:7] = np.inf
+    x[7:9] = -np.inf
+    cases["nan_inf"] = x
+    cases["rounded"] = np.round(rng.standard_normal(200_000), 1)
+    cases["integers"] = rng.integers(-3, 4, 100_000).astype(float)
+    cases["offset"] = 1000.0 + rng.standard_normal(100_000)
+    cases["tiny"] = 1e-20 * rng.standard_normal(50_000)
+    cases["huge"] = 1e20 * rng.standard_normal(50_000)
+    cases["cauchy"] = rng.standard_cauchy(300_000)
+    cases["skewed"] = rng.exponential(1.0, 100_000)
+    cases["constant"] = np.full(1000, 2.5)
+    return cases
+
+
+@pytest.mark.parametrize("name", list(noise_cases().keys()))
+def test_noise_matches_oracle(ctx, name):
+    from paper_2106_15789_gb300 import sc
+
+    v = noise_cases()[name].astype(np.float32)
+    d = torch.from_numpy(v).cuda()
+    fin = v[np.isfinite(v)].astype(np.float64)
+    for mode in ("mad", "std"):
+        ref = O.noise(fin, mode)
+        got = ctx.noise(d, mode)
+        if ref == 0.0:
+            assert got == 0.0
+        else:
+            assert abs(got - ref) <= SIG_RTOL * ref, (mode, got, ref)
+    # full passes instead of candidate lists: identical float result
+    assert ctx.noise(d, "mad", flags=sc.SC_FLAG_NO_FAST_SELECT) == ctx.noise(d, "mad")
+
+
+def test_noise_all_nan(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    d = torch.full((1000,), float("nan"), device="cuda")
+    with pytest.raises(sc.ScError) as e:
+        ctx.noise(d)
+    assert e.value.code == sc.SC_ERR_ALLNAN
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel", KERNELS_20 + [(5.0, 3), (2.2, 1), (14.0, 9)])
+def test_smooth_matches_oracle(ctx, kernel):
+    cube = small_cube()
+    c_np = cube.numpy().astype(np.float64)
+    rng = np.random.default_rng(5)
+    mask = (rng.random(c_np.shape) < 0.03) | (np.abs(np.nan_to_num(c_np)) > 3.0)
+    mask_t = torch.from_numpy(mask.astype(np.uint8)).cuda()
+    value = float(np.float32(2.0 * 1.05))  # the library takes the value as float32
+    for m_np, m_t in ((None, None), (mask, mask_t)):
+        got = ctx.smooth(cube.cuda(), kernel, mask=m_t, replacement_value=value if m_t is not None else 0.0)
+        got = got.cpu().numpy().astype(np.float64)
+        ref = O.smoothed(c_np, m_np if m_np is not None else np.zeros(c_np.shape, bool), kernel[0], kernel[1],
+                         value if m_np is not None else 0.0)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        fin = np.isfinite(ref)
+        sig = O.noise(ref[fin], "mad")
+        err = np.abs(got[fin] - ref[fin])
+        assert err.max() <= S_TOL * sig, (kernel, err.max(), sig)
+        # exact arithmetic: within a few float ulps of the true value, plus the
+        # fixed-point quantum (2^-f with f >= 30 here)
+        bound = 4.0 * np.spacing(np.abs(ref[fin]).astype(np.float32)).astype(np.float64) + 1e-9
+        worst = int(np.argmax(err / bound))
+        assert err[worst] <= bound[worst], (kernel, m_np is not None, got[fin][worst], ref[fin][worst], err[worst])
+
+
+# ---------------------------------------------------------------------------
+def test_small_cube_default(ctx):
+    m, sig, s0, ndiff = check_run(ctx, small_cube(), KERNELS_12)
+    assert m.sum().item() > 0
+    print(f"small cube: sigma0={s0:.7f} band disagreements={ndiff}")
+
+
+def test_small_cube_paper_kernels_and_wide(ctx):
+    check_run(ctx, small_cube(), [(0.0, 0), (5.0, 3), (10.0, 15), (10.0, 31), (6.0, 7)])
+
+
+def test_replacement_off(ctx):
+    check_run(ctx, small_cube(), KERNELS_12, n=0.0)
+
+
+def test_std_mode(ctx):
+    check_run(ctx, small_cube(), KERNELS_12, mode="std")
+
+
+def test_low_threshold(ctx):
+    check_run(ctx, small_cube(), KERNELS_12, t=2.5, n=1.5)
+
+
+def test_accumulate(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    cube = small_cube()
+    rng = np.random.default_rng(9)
+    mask0 = rng.random(tuple(cube.shape)) < 0.01
+    check_run(ctx, cube, KERNELS_12[3:], flags=sc.SC_FLAG_ACCUMULATE, mask0=mask0)
+
+
+def test_full_passes_identical(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    cube = small_cube().cuda()
+    a = ctx.run(cube, KERNELS_12, T, "mad", N_REPL)
+    b = ctx.run(cube, KERNELS_12, T, "mad", N_REPL, flags=sc.SC_FLAG_NO_FAST_SELECT)
+    assert a[1] == b[1] and a[2] == b[2]
+    assert torch.equal(a[0], b[0])
+
+
+def test_run_host_matches_device(ctx):
+    cube = small_cube()
+    a = ctx.run(cube.cuda(), KERNELS_12, T, "mad", N_REPL)
+    b = ctx.run_host(cube.contiguous(), KERNELS_12, T, "mad", N_REPL)
+    assert a[1] == b[1] and a[2] == b[2]
+    assert torch.equal(a[0].cpu(), b[0])
+
+
+@pytest.mark.parametrize("shape", [(19, 23, 37), (1, 50, 40), (30, 1, 1), (5, 3, 200), (200, 2, 3), (7, 9, 1),
+                                   (33, 65, 31), (2, 1, 1)])
+def test_ragged_shapes(ctx, shape):
+    rng = np.random.default_rng(sum(shape))
+    c = rng.standard_normal(shape)
+    for _ in range(4):
+        p = tuple(int(rng.integers(0, n)) for n in shape)
+        c[p] += rng.choice([-1, 1]) * 8.0
+    c[rng.random(shape) < 0.05] = np.nan
+    c = c.astype(np.float32)
+    if not np.isfinite(c).any():
+        c.flat[0] = 1.0
+    kernels = [(0.0, 0), (3.0, 3), (10.0, 15), (6.0, 1), (0.0, 31)]
+    check_run(ctx, torch.from_numpy(c), kernels, t=2.5)
+
+
+def test_errors(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    cube = torch.full((8, 8, 8), float("nan"), device="cuda")
+    mask = torch.full(cube.shape, 7, dtype=torch.uint8, device="cuda")
+    with pytest.raises(sc.ScError) as e:
+        ctx.run(cube, KERNELS_12, T, mask=mask)
+    assert e.value.code == sc.SC_ERR_ALLNAN
+    assert mask.sum().item() == 0
+    good = torch.randn(8, 8, 8, device="cuda")
+    for kernels, t, mode, code in (([(3.0, 4)], T, "mad", sc.SC_ERR_ARG), ([(-1.0, 3)], T, "mad", sc.SC_ERR_ARG),
+                                   ([(float("nan"), 3)], T, "mad", sc.SC_ERR_ARG), ([(3.0, 3)], 0.0, "mad", sc.SC_ERR_ARG),
+                                   ([(3.0, 3)], T, "gauss", sc.SC_ERR_UNSUPPORTED), ([(3.0, 3)] * 65, T, "mad", sc.SC_ERR_ARG),
+                                   ([(3.0, 129)], T, "mad", sc.SC_ERR_UNSUPPORTED)):
+        with pytest.raises(sc.ScError) as e:
+            ctx.run(good, kernels, t, mode)
+        assert e.value.code == code, (kernels, t, mode)
+    big = torch.empty((1, 1, ctx.max_voxels + 1), device="cuda")
+    with pytest.raises(sc.ScError) as e:
+        ctx.run(big, KERNELS_12, T)
+    assert e.value.code == sc.SC_ERR_BUDGET
+
+
+def test_stats_and_profiling(ctx):
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    ctx.run(small_cube().cuda(), KERNELS_12, T)
+    st = ctx.stats(reset=True)
+    ctx.set_profiling(False)
+    assert st["launches"] > 12 and st["runs"] == 1
+    assert st["ms_smooth"] > 0 and st["smooth_launches"] == 11
