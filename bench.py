@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 smooth-and-clip library (one JSON line on stdout).
+
+Metric: S+C voxel*kernels/s, i.e. cube voxels x kernel pairs processed per
+second, for plain float32 S+C on a WALLABY-shaped synthetic cube
+(1200 x 1200 x 1024, spatial {0,3,6} x spectral {0,3,7,15}, t = 3.5, MAD
+noise, replacement 2.0), cube resident in HBM, sigma copied to the host every
+step. The cube (5.9 GB) is larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas, one cube per rank (weak
+scaling; S+C of one cube needs no exchange between GPUs). --impl reference
+times the FP64 CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM roofline"
+UNIT = "voxel·kernels/s"
+SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
+WORKLOADS = ("wallaby", "medium", "small")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def smooth_traffic_record():
+    """DRAM bytes per voxel of the smoothing kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_2106_15789_gb300", "csrc", "sc_smooth.cu")
+    rec = os.path.join(ROOT, "profiles", "smooth_traffic.json")
+    try:
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(rec) as f:
+            r = json.load(f)
+        return r if r.get("source_sha256_16") == h else None
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples of one GPU while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_workload(name: str, rank: int, device: str):
+    import torch
+
+    from synth.cubes import SMALL, WALLABY, CubeSpec, make_cube
+
+    if name == "wallaby":
+        spec = WALLABY
+    elif name == "medium":
+        spec = CubeSpec(nx=512, ny=512, nz=512, seed=WALLABY.seed, n_gal=300, snr=WALLABY.snr, snr_log=True,
+                        fwhm_xy=WALLABY.fwhm_xy, fwhm_z=WALLABY.fwhm_z, ripple=0.1, nan_border=16,
+                        name="medium-512x512x512")
+    else:
+        spec = SMALL
+    if rank:
+        spec = CubeSpec(**{**spec.__dict__, "seed": spec.seed + 1000 * rank})
+    with torch.no_grad():
+        cube = make_cube(spec, device=device)
+    return spec, cube
+
+
+def cpu_baseline(cube_dev, kernels, t, n_repl):
+    """FP64 oracle (as it stands) on an interior 192 x 192 x 256 sub-cube."""
+    from oracle.sc_oracle import sc_filter
+
+    nz, ny, nx = cube_dev.shape
+    sz, sy, sx = min(256, nz), min(192, ny), min(192, nx)
+    z0, y0, x0 = (nz - sz) // 2, (ny - sy) // 2, (nx - sx) // 2
+    sub = cube_dev[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx].float().cpu().numpy()
+    t0 = time.perf_counter()
+    sc_filter(sub, kernels, t, "mad", n_repl)
+    dt = time.perf_counter() - t0
+    return {"value": sub.size * len(kernels) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"interior {sx}x{sy}x{sz} sub-cube of the same cube, {len(kernels)} pairs, numpy float64, "
+                      f"one thread, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores: each step is a bounded sample."""
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    from oracle.sc_oracle import sc_filter
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, WALLABY, CubeSpec, make_cube
+
+    # a 128 x 128 x 128 cube with the wallaby recipe (noise, ripple, galaxies, NaN border)
+    spec = CubeSpec(nx=128, ny=128, nz=128, seed=WALLABY.seed, n_gal=12, snr=WALLABY.snr, snr_log=True,
+                    fwhm_xy=WALLABY.fwhm_xy, fwhm_z=WALLABY.fwhm_z, ripple=0.1, nan_border=4, name="ref-sample")
+    c = make_cube(spec).numpy()
+    for _ in range(args.warmup):
+        sc_filter(c, KERNELS_12, SC_THRESHOLD, "mad", SC_REPLACEMENT)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sc_filter(c, KERNELS_12, SC_THRESHOLD, "mad", SC_REPLACEMENT)
+    dt = time.perf_counter() - t0
+    value = c.size * len(KERNELS_12) * args.steps / dt
+    sample = f"128x128x128 cube of the wallaby recipe per step, {len(KERNELS_12)} pairs, numpy float64, one thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args.workload, KERNELS_12),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(workload, kernels):
+    from synth.cubes import SC_REPLACEMENT, SC_THRESHOLD
+
+    names = {"wallaby": "wallaby-1200x1200x1024", "medium": "medium-512x512x512", "small": "small-64x64x128"}
+    return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
+            "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": "mad", "replacement": SC_REPLACEMENT,
+            "precision": "float32 cube, exact fixed-point smoothing", "l2": "inputs (cube 5.9 GB) larger than L2"
+            if workload == "wallaby" else "no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=WORKLOADS, default="wallaby")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()  # fails loudly when the CUDA library is missing
+    kernels = KERNELS_12
+    t, n_repl = SC_THRESHOLD, SC_REPLACEMENT
+    spec, cube = make_workload(args.workload, rank, str(dev))
+    nvox = cube.numel()
+    mask = torch.empty(cube.shape, dtype=torch.uint8, device=dev)
+    ctx = Context(local, nvox)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return ctx.run(cube, kernels, t, "mad", n_repl, mask=mask)
+
+    for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, sig, sig0 = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    ctx.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    if pg:
+        tm = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+        ms = float(tm.item())
+    st = ctx.stats(reset=True)
+    value = nvox * len(kernels) * args.steps * world / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the smoothing kernel), from the live events
+    peak, peak_kind = measured_hbm_peak()
+    avg_ms = st["ms_smooth"] / max(1, st["smooth_launches"])
+    vox_per_launch = st["smooth_voxels"] / max(1, st["smooth_launches"])
+    achieved = SMOOTH_BYTES_PER_VOXEL * vox_per_launch / (avg_ms * 1e-3) / 1e9
+    tr = smooth_traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tr["dram_bytes_per_voxel"] * vox_per_launch) if tr else None,
+                "kernel": "k_smooth (smoothing of one pair)", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL}
+
+    e2e = None
+    if not args.no_e2e:
+        cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+        cube_h.copy_(cube)
+        mask_h = torch.empty(cube.shape, dtype=torch.uint8, pin_memory=True)
+        ctx.run_host(cube_h, kernels, t, "mad", n_repl, mask_host=mask_h)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.run_host(cube_h, kernels, t, "mad", n_repl, mask_host=mask_h)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if pg:
+            tm = torch.tensor([dt], device=dev, dtype=torch.float64)
+            pg.all_reduce(tm, op=pg.ReduceOp.MAX)
+            dt = float(tm.item())
+        e2e = {"value": nvox * len(kernels) * args.e2e_steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1),
+               "steps": args.e2e_steps, "api": "sc_run_host (pinned host cube and mask)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cube, kernels, t, n_repl)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.workload, kernels),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(st["launches"]), "clocks": sampler.summary(),
+                "breakdown_ms_per_step": {"smooth": st["ms_smooth"] / args.steps,
+                                          "select": st["ms_select"] / args.steps,
+                                          "clip": st["ms_clip"] / args.steps},
+                "sigma0": sig0, "sigmas": sig, "mask_fraction": float(mask.float().mean().item()),
+                "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
