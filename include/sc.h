@@ -155,6 +155,23 @@ int sc_smooth(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, sc_kernel
 int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, double *sigma_host, uint32_t flags,
              void *cuda_stream);
 
+/* Noise level of a device float32 array, like sc_noise, for callers that
+ * cannot allocate device memory when they need it: processes whose device
+ * memory belongs to another allocator or a fixed pool, real-time pipelines
+ * that forbid allocation (and the device synchronisation it implies) once
+ * running, plug-ins that are handed only a stream and buffers. It needs no
+ * context and allocates nothing: its scratch (2,525,440 bytes) is one static
+ * device array that every GPU loading this library holds until the process
+ * exits. The paper has no counterpart; this is a library-level addition.
+ *   - n <= 4194304 (4 Mi values), else SC_ERR_BUDGET.
+ *   - Runs on the calling thread's current device; data_dev must live there.
+ *   - The first call on each device looks up the array's device address and
+ *     sets kernel attributes; make that first call before any stream capture.
+ *   - All calls on a device share the array (each clears what must start at
+ *     zero); calls that overlap on the GPU race and must be serialised.
+ *   - Synchronises cuda_stream to return *sigma_host. Other errors as sc_noise. */
+int sc_noise_static(const float *data_dev, int64_t n, int noise_mode, double *sigma_host, void *cuda_stream);
+
 /* Device-timed profiling of the library's kernels with CUDA events on the
  * launching stream (adds a few microseconds per launch). on = 0 / 1. */
 int sc_set_profiling(sc_ctx *ctx, int on);

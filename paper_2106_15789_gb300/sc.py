@@ -72,6 +72,7 @@ _SIGS = {
                               C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_set_profiling": (C.c_int, [_P, C.c_int]),
     "sc_get_stats": (C.c_int, [_P, C.POINTER(sc_stats), C.c_int]),
 }
@@ -208,6 +209,19 @@ def sc_noise(ctx, data: torch.Tensor, noise_mode="mad", flags: int = 0, stream=N
     code = lib().sc_noise(ctx, C.c_void_p(data.data_ptr()), int(data.numel()), int(mode), C.byref(out), int(flags),
                           _stream(data, stream))
     _check(code, "sc_noise")
+    return out.value
+
+
+def sc_noise_static(data: torch.Tensor, noise_mode="mad", stream=None) -> float:
+    """Noise level without a context or any allocation (scratch in a static
+    device array; at most 4 Mi values; calls must not overlap on the GPU)."""
+    _dev(data, torch.float32, "data")
+    out = C.c_double()
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    with torch.cuda.device(data.device):
+        code = lib().sc_noise_static(C.c_void_p(data.data_ptr()), int(data.numel()), int(mode), C.byref(out),
+                                     _stream(data, stream))
+    _check(code, "sc_noise_static")
     return out.value
 
 
