@@ -96,6 +96,11 @@ void sc_destroy(sc_ctx *ctx);
 /* Static description of a status code (never NULL). */
 const char *sc_strerror(int code);
 
+/* Text of the last CUDA failure behind an SC_ERR_CUDA returned on the calling
+ * host thread (CUDA's error string, code and the failing call), or "" if none.
+ * The buffer is thread-local and overwritten by the next failure. */
+const char *sc_last_cuda_error(void);
+
 /* Host helper: the 3 boxcar widths whose cascade approximates a Gaussian of
  * this FWHM (Kovesi 2010 construction; FWHM <= 0 gives widths {1,1,1}, the
  * identity). widths must hold 3 ints. Errors: SC_ERR_ARG (NULL, FWHM not

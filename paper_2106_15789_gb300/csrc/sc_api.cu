@@ -117,10 +117,18 @@ void flush_events(sc_ctx* c) {
   c->events.clear();
 }
 
-#define CK(x)                                  \
-  do {                                         \
-    cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return SC_ERR_CUDA; \
+thread_local char g_last_cuda_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what, int line) {
+  snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s (%d) at %s:%d", cudaGetErrorString(e), (int)e, what,
+           line);
+  return SC_ERR_CUDA;
+}
+
+#define CK(x)                                                   \
+  do {                                                          \
+    cudaError_t e_ = (x);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__);  \
   } while (0)
 
 int check_dims(const sc_ctx* c, const int64_t* dims, long long* n) {
@@ -280,6 +288,8 @@ int finish(sc_ctx* c, int nk, double* sigma_host, double* sigma0_host, cudaStrea
 }  // namespace
 
 extern "C" {
+
+const char* sc_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char* sc_strerror(int code) {
   switch (code) {

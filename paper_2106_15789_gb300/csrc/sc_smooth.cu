@@ -244,7 +244,17 @@ void choose_tiles(SmoothArgs* a) {
   a->tiles_y = (a->ny + a->ty - 1) / a->ty;
 }
 
+cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
+void init_tile_attrs();
+
 cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* launches) {
+  bool done = false;
+  cudaError_t et = launch_smooth_tile(a0, sms, s, &done);
+  if (et != cudaSuccess) return et;
+  if (done) {
+    if (launches) ++*launches;
+    return cudaSuccess;
+  }
   SmoothArgs a = a0;
   if (a.tx == 0) choose_tiles(&a);
   const size_t smem = smooth_smem_bytes(a);
@@ -272,6 +282,7 @@ void init_noise_attrs();
 // Raise the dynamic shared-memory limits once per device (called by sc_create).
 void init_kernel_attrs() {
   cudaFuncSetAttribute(k_smooth_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  init_tile_attrs();
   init_noise_attrs();
 }
 

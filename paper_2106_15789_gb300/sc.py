@@ -55,7 +55,14 @@ class sc_stats(C.Structure):
 class ScError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
-        super().__init__(f"{what}: {sc_strerror(code)} ({code})" if what else f"{sc_strerror(code)} ({code})")
+        msg = f"{what}: {sc_strerror(code)} ({code})" if what else f"{sc_strerror(code)} ({code})"
+        if code == SC_ERR_CUDA:
+            msg += f": {sc_last_cuda_error()}"
+        super().__init__(msg)
+
+
+def sc_last_cuda_error() -> str:
+    return lib().sc_last_cuda_error().decode()
 
 
 _lib = None
@@ -65,6 +72,7 @@ _SIGS = {
     "sc_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t]),
     "sc_destroy": (None, [_P]),
     "sc_strerror": (C.c_char_p, [C.c_int]),
+    "sc_last_cuda_error": (C.c_char_p, []),
     "sc_cascade_widths": (C.c_int, [C.c_float, C.POINTER(C.c_int32)]),
     "sc_run": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int, C.c_float,
                          _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),

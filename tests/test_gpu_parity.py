@@ -231,3 +231,21 @@ def test_stats_and_profiling(ctx):
     ctx.set_profiling(False)
     assert st["launches"] > 12 and st["runs"] == 1
     assert st["ms_smooth"] > 0 and st["smooth_launches"] == 11
+
+
+@pytest.mark.parametrize("shape", [(128, 64, 64), (37, 70, 131), (9, 33, 65), (3, 1, 200)])
+def test_specialised_kernels_equal_generic(ctx, shape):
+    """Exact fixed-point arithmetic: every smoothing kernel variant gives the
+    same floats, whatever its tiling."""
+    from paper_2106_15789_gb300 import sc
+
+    rng = np.random.default_rng(77)
+    c = rng.standard_normal(shape).astype(np.float32)
+    c[rng.random(shape) < 0.03] = np.nan
+    cube = torch.from_numpy(c).cuda()
+    mask = torch.from_numpy((rng.random(shape) < 0.05).astype(np.uint8)).cuda()
+    for kernel in [(0.0, 3), (0.0, 7), (3.0, 0), (3.0, 3), (5.0, 7), (6.0, 1), (6.0, 7), (10.0, 5), (6.0, 15)]:
+        for m, v in ((None, 0.0), (mask, 2.5)):
+            a = ctx.smooth(cube, kernel, mask=m, replacement_value=v)
+            b = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_FLAG_GENERIC)
+            assert torch.equal(torch.nan_to_num(a, nan=7e7), torch.nan_to_num(b, nan=7e7)), (shape, kernel, m is None)
