@@ -142,6 +142,7 @@ int check_dims(const sc_ctx* c, const int64_t* dims, long long* n) {
 }
 
 int status_to_code(const DevState& h) {
+  if (h.status & SC_ST_TIMEOUT) return SC_ERR_TIMEOUT;
   if (h.status & SC_ST_ALLNAN) return SC_ERR_ALLNAN;
   if (h.status & (SC_ST_INTERNAL | SC_ST_OVERFLOW)) return SC_ERR_INTERNAL;
   return SC_OK;
@@ -250,6 +251,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     a.hist = c->hist;
     a.win = 1;
     a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
+    a.repl_possible = replacement > 0.0f ? 1 : 0;
     {
       Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
       if (a.pd.h == 0 && a.pd.wz == 1) {
@@ -454,6 +456,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   a.repl_value = repl;
   a.hist = nullptr;
   a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
+  a.repl_possible = repl > 0.0f ? 1 : 0;
   {
     Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
     if (pd.h == 0 && pd.wz == 1) {

@@ -33,18 +33,14 @@ __host__ __device__ __forceinline__ BinCfg window_cfg(float sigma0) {
   return BinCfg{e, kWindowE, kWindowMB};
 }
 
-// Histogram bin of a non-NaN float (monotone in the value).
+// Histogram bin of a non-NaN float (monotone in the value): the magnitude's
+// top 9 + MB bits (exponent and MB mantissa bits), offset by the window base
+// and clamped to the underflow / overflow bins.
 __host__ __device__ __forceinline__ int bin_of_bits(unsigned int u, BinCfg c) {
-  unsigned int mag = u & 0x7fffffffu;
-  int e = (int)(mag >> 23);
-  int b;
-  if (e < c.e_base) {
-    b = 0;
-  } else if (e >= c.e_base + c.E) {
-    b = (c.E << c.MB) + 1;
-  } else {
-    b = 1 + ((e - c.e_base) << c.MB) + (int)((mag >> (23 - c.MB)) & ((1u << c.MB) - 1u));
-  }
+  const int key = (int)((u & 0x7fffffffu) >> (23 - c.MB));
+  int b = key - (c.e_base << c.MB) + 1;
+  b = b < 0 ? 0 : b;
+  b = b > (c.E << c.MB) + 1 ? (c.E << c.MB) + 1 : b;
   return (u >> 31) ? (kBinsPerSign - 1 - b) : (kBinsPerSign + b);
 }
 __device__ __forceinline__ int bin_of(float s, BinCfg c) { return bin_of_bits(__float_as_uint(s), c); }
@@ -80,47 +76,44 @@ __device__ __forceinline__ double bin_hi_value(int i, BinCfg c) {
   return i >= kBinsPerSign ? mag_hi(i - kBinsPerSign, c) : -mag_lo(kBinsPerSign - 1 - i, c);
 }
 
-// x * 2^f rounded to the nearest integer (halves away from zero), exactly,
-// built from the float's bits (the 64-bit cvt instructions run on the FP64
-// pipe). Requires |x| * 2^f < 2^62; zero and subnormal x give 0.
-__device__ __forceinline__ long long quantize(float x, int f) {
-  unsigned int u = __float_as_uint(x);
-  int e = (int)((u >> 23) & 0xffu);
-  unsigned int m = (u & 0x7fffffu) | 0x800000u;
-  int sh = e - 150 + f;
-  unsigned long long q;
-  if (e == 0) {
-    q = 0ull;
-  } else if (sh >= 0) {
-    q = (unsigned long long)m << sh;
-  } else if (sh >= -25) {
-    q = (unsigned long long)((m + (1u << (-sh - 1))) >> (-sh));
-  } else {
-    q = 0ull;
-  }
-  long long r = (long long)q;
-  return (u >> 31) ? -r : r;
+// rint(x * 2^f) (ties to even) as an exact int64, for |x| * 2^f < 2^62,
+// given scale = 2^f. Uses the FMA and conversion pipes rather than the
+// integer pipe (the 64-bit cvt instructions run on the FP64 pipe): with
+// y = |x| * 2^f (exact), hi = floor(y * 2^-32) and lo = y - hi * 2^32 (an
+// exact FMA, 0 <= lo < 2^32) each convert exactly, lo with the rounding.
+// NaN or infinite x give an unspecified value (callers blank them).
+__device__ __forceinline__ long long quantize(float x, float scale) {
+  const float y = __fmul_rn(fabsf(x), scale);
+  const float th = floorf(__fmul_rn(y, 2.3283064365386963e-10f));  // 2^-32
+  const float lo_f = __fmaf_rn(-th, 4294967296.0f, y);
+  const unsigned int hi = __float2uint_rz(th);
+  const unsigned int lo = __float2uint_rn(lo_f);
+  const long long r = (long long)(((unsigned long long)hi << 32) | lo);
+  return x < 0.0f ? -r : r;
 }
 
 // Correctly rounded (to nearest, ties to even) float of an unsigned 64-bit
 // integer, from integer operations (the 64-bit cvt runs on the FP64 pipe).
+// Branch-free.
 __device__ __forceinline__ float u64_to_float_rn(unsigned long long a) {
-  if (a == 0ull) return 0.0f;
-  const int lz = __clzll((long long)a);
-  const unsigned long long n = a << lz;             // leading one at bit 63
-  unsigned int mant = (unsigned int)(n >> 40);      // 24 significant bits
+  const int lz = __clzll((long long)a);                   // 64 for a == 0
+  const unsigned long long n = a << (lz & 63);            // leading one at bit 63
+  unsigned int mant = (unsigned int)(n >> 40);            // 24 significant bits
   const unsigned long long rest = n & 0xffffffffffull;
   const unsigned long long half = 0x8000000000ull;
-  if (rest > half || (rest == half && (mant & 1u))) mant += 1u;  // may carry to 2^24
+  mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;  // may carry to 2^24
   const unsigned int e = (unsigned int)(63 - lz + 127);
-  return __uint_as_float((e << 23) + (mant - 0x800000u));  // a carry moves into the exponent
+  const unsigned int bits = (e << 23) + (mant - 0x800000u);  // a carry moves into the exponent
+  return __uint_as_float(a == 0ull ? 0u : bits);
 }
 
-// float of q * inv: q rounded once to float, then one multiply (<= 1.5 ulp
-// of the exact product plus the rounding of inv).
+// float of q * inv from two 32-bit conversions of |q|'s halves, one FMA and
+// one multiply (within about 2 ulp of the exact product).
 __device__ __forceinline__ float dequantize(long long q, float inv) {
   const unsigned long long a = q < 0 ? (unsigned long long)0 - (unsigned long long)q : (unsigned long long)q;
-  const float v = __fmul_rn(u64_to_float_rn(a), inv);
+  const float hi = __uint2float_rn((unsigned int)(a >> 32));
+  const float lo = __uint2float_rn((unsigned int)(a & 0xffffffffull));
+  const float v = __fmul_rn(__fmaf_rn(hi, 4294967296.0f, lo), inv);
   return q < 0 ? -v : v;
 }
 

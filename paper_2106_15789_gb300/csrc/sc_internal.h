@@ -113,6 +113,7 @@ enum StatusBits : unsigned int {
   SC_ST_ALLNAN = 1u,
   SC_ST_INTERNAL = 2u,
   SC_ST_OVERFLOW = 4u,
+  SC_ST_TIMEOUT = 8u,   // a bounded device-side wait gave up
 };
 
 struct Caps {
@@ -151,6 +152,7 @@ struct SmoothArgs {
   int nx, ny, nz;
   int pair;               // index into DevState fixed-point arrays
   int use_fixed_repl;     // 1: replacement value below instead of DevState::repl
+  int repl_possible;      // 0: replacement is off for this pair (skip the mask entirely)
   float repl_value;
   DevState* st;
   unsigned long long* hist;  // null: no histogram

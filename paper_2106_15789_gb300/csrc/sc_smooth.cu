@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth_generic(SmoothArgs a)
   if (a.hist)
     for (int i = tid; i < kNumBins; i += blockDim.x) hist[i] = 0u;
   const BinCfg cfg = a.win ? a.st->win : kFullRange;
-  const int f = a.st->fx_shift[a.pair];
+  const float fscale = a.st->fx_scale[a.pair];
   const float inv = a.st->fx_inv[a.pair];
   const long long qrepl = a.st->fx_qrepl[a.pair];
   const bool do_repl = qrepl > 0 && a.mbits != nullptr;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth_generic(SmoothArgs a)
               if (do_repl && mask_bit(a.mbits, v)) {
                 q = (c >= 0.0f) ? qrepl : -qrepl;
               } else {
-                q = quantize(c, f);
+                q = quantize(c, fscale);
               }
             }
           }
@@ -245,11 +245,19 @@ void choose_tiles(SmoothArgs* a) {
 }
 
 cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
+cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 void init_tile_attrs();
+void init_z_attrs();
 
 cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* launches) {
   bool done = false;
-  cudaError_t et = launch_smooth_tile(a0, sms, s, &done);
+  cudaError_t et = launch_smooth_z(a0, sms, s, &done);
+  if (et != cudaSuccess) return et;
+  if (done) {
+    if (launches) ++*launches;
+    return cudaSuccess;
+  }
+  et = launch_smooth_tile(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
   if (done) {
     if (launches) ++*launches;
@@ -283,6 +291,7 @@ void init_noise_attrs();
 void init_kernel_attrs() {
   cudaFuncSetAttribute(k_smooth_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   init_tile_attrs();
+  init_z_attrs();
   init_noise_attrs();
 }
 

@@ -1,21 +1,34 @@
-// Specialised smoothing kernel: compile-time boxcar widths, register-resident
-// box cascades, a 64 x 32 output tile per block.
+// Specialised smoothing kernel: compile-time boxcar widths, streamed register
+// box cascades, TMA tile loads, the spectral ring in Tensor Memory.
 //
 // Same arithmetic as the generic kernel (exact int64 fixed point, one final
-// rounding; see sc_smooth.cu), so both produce identical floats. Per plane:
-//   load   every thread fetches its share of the plane's halo'd tile
-//          ((32 + 2R) rows x (64 + 2R) columns) for the NEXT plane into
-//          registers while the current plane is processed, then quantises it
-//          (NaN -> 0, replacement of masked voxels) into shared memory;
-//   x pass (32 + 2R) rows x 4 segments of 16 outputs; each thread slides the
-//          three boxcars over its 16 + 2R inputs in registers;
-//   y pass 64 columns x 4 segments of 8 outputs, the same way down a column;
-//   z      the thread's 8 smoothed values enter a ring of wz planes in shared
-//          memory and a running int64 sum gives the spectral boxcar;
-//   out    the plane r = (wz - 1) / 2 behind is finished: scale to float, NaN
-//          where the input voxel is NaN (from a per-thread bit history), store,
-//          histogram.
+// rounding; see sc_smooth.cu), so both produce identical floats.
+//
+// A block (256 threads, one per SM) owns a 64 x 32 column tile and a chunk of
+// planes. Per plane:
+//   load    the plane's raw float tile with its halo ((32 + 2R) x (64 + 2RA)
+//           values, RA = R rounded up to 4 so the TMA x coordinate is 16-byte
+//           aligned) arrives by TMA into one of two shared buffers, one plane
+//           ahead, on an mbarrier (zero fill outside the cube is the padding);
+//           rows that are not a multiple of 16 bytes use cp.async instead.
+//           The mask words of the next plane are prefetched into registers.
+//   convert every halo'd value once: NaN -> 0, masked -> +-repl, else
+//           rint(x * 2^f), into an int64 tile.
+//   x pass  (32 + 2R) rows x 4 segments of 16 outputs; the three boxcars run
+//           as one interleaved stream of running sums (three independent
+//           dependency chains per step).
+//   y pass  64 columns x 4 segments of 8 outputs, the same way down a column.
+//   z       each thread's 8 values enter a ring of wz planes kept in TMEM
+//           (16 columns of the thread's lane per plane) and a running int64
+//           sum gives the spectral boxcar.
+//   out     plane r = (wz - 1)/2 behind is final: NaN where the input voxel is
+//           NaN (a per-thread bit history), else the scaled float; store and
+//           histogram.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <cstring>
 
 #include "sc_device.cuh"
 #include "sc_internal.h"
@@ -27,48 +40,97 @@ namespace tile {
 constexpr int kThreads = 256;
 constexpr int TX = 64, TY = 32;
 constexpr int SEGX = 16, SEGY = 8;
-constexpr int kMaxWzSmem = 7;  // spectral widths served by the shared-memory ring
+constexpr int kMaxWz = 15;                 // TMEM ring: 16 slots of 8 int64 per thread
+constexpr long long kMaxSpins = 1LL << 24;  // bound of every mbarrier wait
+constexpr int kStages = 3;                  // raw-tile buffers (loads run two planes ahead)
 
 template <int W1, int W2, int W3>
 struct Geo {
   static constexpr int R = (W1 - 1) / 2 + (W2 - 1) / 2 + (W3 - 1) / 2;
-  static constexpr int PX = TX + 2 * R;               // quantised tile width
-  static constexpr int PY = TY + 2 * R;               // quantised tile height
-  static constexpr int XP = PX | 1;                   // odd pitch (int64 units): conflict-free column access
-  static constexpr int BP = TX + 1;                   // odd pitch of the x-pass output
-  static constexpr int LOAD_SLOTS = (PX + 31) / 32;   // loads per row per lane
-  static constexpr int LOAD_ROWS = (PY + 7) / 8;      // rows per warp
-  static constexpr int NLOAD = LOAD_SLOTS * LOAD_ROWS;
+  static constexpr int RA = (R + 3) & ~3;  // halo of the raw tile in x, 16-byte aligned
+  static constexpr int BX = TX + 2 * RA;   // raw tile width
+  static constexpr int BY = TY + 2 * R;    // raw tile height = quantised tile height
+  static constexpr int PX = TX + 2 * R;    // quantised tile width
+  static constexpr int XP = PX | 1;        // odd pitch (8-byte words)
+  static constexpr int BP = TX + 1;        // odd pitch of the x-pass output
+  static constexpr int ROWS_PER_WARP = (BY + 7) / 8;
+  static constexpr int COL_SLOTS = (PX + 31) / 32;
 };
 
-// Sliding sum of W consecutive values of in[0..N) -> out[0..N-W+1), unrolled.
-template <int W, int N>
-__device__ __forceinline__ void box(const long long (&in)[N], long long (&out)[N - W + 1]) {
-  long long s = 0;
+struct Smem {
+  size_t raw[3], mw, x, b, hist, mbar, total;
+};
+
+__host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) & ~(size_t)127; }
+
+template <int W1, int W2, int W3>
+__host__ __device__ constexpr Smem smem_layout(bool hist) {
+  using G = Geo<W1, W2, W3>;
+  Smem s{};
+  size_t o = 0;
+  for (int b = 0; b < kStages; ++b) {
+    s.raw[b] = o;
+    o = al128(o + sizeof(float) * (size_t)G::BY * G::BX);
+  }
+  s.mw = o;
+  o = al128(o + sizeof(unsigned) * (size_t)G::BY * 5);
+  s.x = o;
+  o = al128(o + sizeof(long long) * (size_t)G::BY * G::XP);
+  s.b = o;
+  o = al128(o + sizeof(long long) * (size_t)G::BY * G::BP);
+  s.hist = o;
+  o = al128(o + (hist ? sizeof(unsigned) * kNumBins : 0));
+  s.mbar = o;
+  o = al128(o + kStages * sizeof(unsigned long long));
+  s.total = o + 128;  // room to align the dynamic base to 128 bytes at run time
+  return s;
+}
+
+// Streams NOUT + W1 + W2 + W3 - 3 inputs load(i) through the three boxcars
+// (all indices compile-time after unrolling); out(k, v) gets output k.
+template <int W1, int W2, int W3, int NOUT, class Load, class Out>
+__device__ __forceinline__ void cascade_stream(Load load, Out out) {
+  constexpr int N0 = NOUT + (W1 - 1) + (W2 - 1) + (W3 - 1);
+  long long h1[W1], h2[W2], h3[W3];
+  long long s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-  for (int k = 0; k < W; ++k) s += in[k];
-  out[0] = s;
-#pragma unroll
-  for (int i = 1; i < N - W + 1; ++i) {
-    s += in[i + W - 1] - in[i - 1];
-    out[i] = s;
+  for (int i = 0; i < N0; ++i) {
+    const long long x = load(i);
+    if (W1 == 1) {
+      s1 = x;
+    } else {
+      s1 += x;
+      if (i >= W1) s1 -= h1[i % W1];
+      h1[i % W1] = x;
+    }
+    if (i >= W1 - 1) {
+      const int i1 = i - (W1 - 1);
+      if (W2 == 1) {
+        s2 = s1;
+      } else {
+        s2 += s1;
+        if (i1 >= W2) s2 -= h2[i1 % W2];
+        h2[i1 % W2] = s1;
+      }
+      if (i1 >= W2 - 1) {
+        const int i2 = i1 - (W2 - 1);
+        if (W3 == 1) {
+          s3 = s2;
+        } else {
+          s3 += s2;
+          if (i2 >= W3) s3 -= h3[i2 % W3];
+          h3[i2 % W3] = s2;
+        }
+        if (i2 >= W3 - 1) out(i2 - (W3 - 1), s3);
+      }
+    }
   }
 }
 
-template <int W1, int W2, int W3, int N>
-__device__ __forceinline__ void cascade(const long long (&in)[N], long long (&out)[N - (W1 - 1) - (W2 - 1) - (W3 - 1)]) {
-  long long b1[N - W1 + 1];
-  box<W1, N>(in, b1);
-  long long b2[N - W1 + 1 - W2 + 1];
-  box<W2, N - W1 + 1>(b1, b2);
-  box<W3, N - W1 + 1 - W2 + 1>(b2, out);
-}
-
 // ---- Tensor Memory (TMEM) as ring storage --------------------------------
-// A block allocates all 512 columns of its SM's TMEM (one block per SM). Warp w
-// may touch lanes 32*(w%4) .. +31; warps 0-3 use columns 0..255, warps 4-7
-// columns 256..511, so every thread owns 256 32-bit words of one lane: 16 ring
-// slots of 8 int64 values.
+// The block allocates all 512 columns of its SM's TMEM. Warp w may touch
+// lanes 32*(w%4) .. +31; warps 0-3 use columns 0..255, warps 4-7 columns
+// 256..511, so each thread owns 256 32-bit words of one lane.
 constexpr int kTmemCols = 512;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -87,9 +149,7 @@ __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// 8 int64 values <-> 16 consecutive 32-bit columns of the thread's lane.
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[16]) {
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
@@ -97,268 +157,329 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[16]) {
       : "r"(taddr)
       : "memory");
 }
-__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[16]) {
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&v)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
       "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
       : "memory");
 }
-constexpr int kMaxWzTmem = 16;  // ring slots per thread in TMEM
 
-struct Smem {
-  size_t x, b, ring, hist, total;
-};
-
-template <int W1, int W2, int W3>
-__host__ __device__ constexpr Smem smem_layout(int wz, bool hist, bool tmem_ring) {
-  using G = Geo<W1, W2, W3>;
-  Smem s{};
-  size_t o = 0;
-  s.x = o;
-  o += sizeof(long long) * (size_t)G::PY * G::XP;
-  s.b = o;
-  o += sizeof(long long) * (size_t)G::PY * G::BP;
-  s.ring = o;
-  o += (tmem_ring || wz <= 1) ? 0 : sizeof(long long) * (size_t)wz * TX * TY;
-  s.hist = o;
-  o += hist ? sizeof(unsigned int) * kNumBins : 0;
-  s.total = o;
-  return s;
+// ---- mbarrier / TMA / cp.async --------------------------------------------
+__device__ __forceinline__ void mbar_init(unsigned addr) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+// Bounded wait for the barrier phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
+  for (long long it = 0; it < kMaxSpins; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one_pending() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace tile
 
-template <int W1, int W2, int W3, bool TMEM>
-__global__ void __launch_bounds__(tile::kThreads, 1) k_smooth_tile(SmoothArgs a) {
+template <int W1, int W2, int W3, bool TMA, bool REPL>
+__global__ void __launch_bounds__(tile::kThreads, 1)
+    k_smooth_tile(const __grid_constant__ CUtensorMap tmap, SmoothArgs a) {
   using namespace tile;
   using G = Geo<W1, W2, W3>;
-  constexpr int R = G::R;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int wz = a.pd.wz, r = (wz - 1) / 2;
-  const Smem L = smem_layout<W1, W2, W3>(wz, a.hist != nullptr, TMEM);
+  constexpr int R = G::R, RA = G::RA;
+  constexpr int NCONV = (G::BY * G::PX + kThreads - 1) / kThreads;  // conversions per thread
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  // 128-byte aligned base (TMA destinations, mbarriers)
+  unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+  const Smem L = smem_layout<W1, W2, W3>(a.hist != nullptr);
+  float* const raw0 = reinterpret_cast<float*>(smem + L.raw[0]);
+  constexpr size_t kRawStride = al128(sizeof(float) * (size_t)G::BY * G::BX) / sizeof(float);
+  unsigned* mw = reinterpret_cast<unsigned*>(smem + L.mw);  // [BY][4] mask words, then [BY] bit offsets
   long long* Xt = reinterpret_cast<long long*>(smem + L.x);
   long long* Bt = reinterpret_cast<long long*>(smem + L.b);
-  long long* ring = reinterpret_cast<long long*>(smem + L.ring);
-  unsigned int* hist = reinterpret_cast<unsigned int*>(smem + L.hist);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* hist = reinterpret_cast<unsigned*>(smem + L.hist);
+  const unsigned mbar0 = smem_u32(smem + L.mbar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int wz = a.pd.wz, r = (wz - 1) / 2;
   if (a.hist)
     for (int i = tid; i < kNumBins; i += kThreads) hist[i] = 0u;
   const BinCfg cfg = a.win ? a.st->win : kFullRange;
-  const int f = a.st->fx_shift[a.pair];
+  const float fscale = a.st->fx_scale[a.pair];
   const float inv = a.st->fx_inv[a.pair];
   const long long qrepl = a.st->fx_qrepl[a.pair];
-  const bool do_repl = qrepl > 0 && a.mbits != nullptr;
+  const bool do_repl = REPL && qrepl > 0;
   const long long nx = a.nx, ny = a.ny, nz = a.nz;
   const long long plane = nx * ny;
-  const long long n_items = (long long)a.tiles_x * a.tiles_y * a.zchunks;
-  // y pass / output ownership: column yc, rows ys*8 .. ys*8+7
-  const int yc = tid & (TX - 1), ys = tid / TX;
+  const long long n_tiles = (long long)a.tiles_x * a.tiles_y;
+  const long long n_items = n_tiles * a.zchunks;
+  const int yc = tid & (TX - 1), ys = tid / TX;  // y pass / output ownership
+
   __shared__ unsigned tmem_holder;
-  unsigned tbase = 0u;
-  if (TMEM) {
-    if (warp == 0) tmem_alloc(&tmem_holder);
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    tbase = tmem_holder;
+  if (warp == 0) tmem_alloc(&tmem_holder);
+  if (TMA && tid == 0) {
+    for (int b = 0; b < kStages; ++b) mbar_init(mbar0 + 8 * b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  // this thread's lane and first column in TMEM
-  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(256 * (warp >> 2));
+  tmem_fence_before();
   __syncthreads();
+  tmem_fence_after();
+  const unsigned tbase = tmem_holder;
+  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(256 * (warp >> 2));
+  bool timed_out = false;
 
+  auto item_geo = [&](long long it, int* x0, int* y0, int* z0, int* ns) {
+    const long long t = it % n_tiles;
+    const int zc = (int)(it / n_tiles);
+    *x0 = (int)(t % a.tiles_x) * TX;
+    *y0 = (int)(t / a.tiles_x) * TY;
+    *z0 = zc * a.lz;
+    *ns = (int)(min((long long)*z0 + a.lz, nz) - *z0) + 2 * r;
+  };
+  // raw tile of plane zp of tile (x0, y0) into stage b
+  auto issue = [&](int b, int x0, int y0, int zp) {
+    float* dst = raw0 + b * kRawStride;
+    if (TMA) {
+      if (tid == 0) {
+        mbar_expect_tx(mbar0 + 8 * b, (unsigned)(sizeof(float) * G::BX * G::BY));
+        tma_load_3d(smem_u32(dst), &tmap, x0 - RA, y0 - R, zp, mbar0 + 8 * b);
+      }
+    } else {
+      const bool zok = zp >= 0 && zp < nz;
+      for (int e = tid; e < G::BX * G::BY; e += kThreads) {
+        const int row = e / G::BX, col = e - row * G::BX;
+        const long long gx = (long long)x0 - RA + col, gy = (long long)y0 - R + row;
+        const bool ok = zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        cp_async4(smem_u32(dst + e), ok ? a.C + (long long)zp * plane + gy * nx + gx : a.C, ok);
+      }
+      cp_async_commit();
+    }
+  };
+  // lookahead cursor of the raw-tile loads (kStages - 1 planes ahead)
+  long long la_item = blockIdx.x;
+  int la_j = 0, la_x0 = 0, la_y0 = 0, la_z0 = 0, la_n = 0;
+  if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
+  long long issued = 0;
+  auto issue_next = [&]() {
+    if (la_item >= n_items) return;
+    issue((int)(issued % kStages), la_x0, la_y0, la_z0 - r + la_j);
+    ++issued;
+    if (++la_j == la_n) {
+      la_item += gridDim.x;
+      la_j = 0;
+      if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
+    }
+  };
+  // mask words of plane zp (4 words per halo'd row, bits of out-of-cube
+  // columns cleared; word 4 of a row's group is its bit offset)
+  auto fetch_mask = [&](int x0, int y0, int zp, unsigned* off_out) -> unsigned {
+    unsigned w = 0u;
+    *off_out = 0u;
+    if (do_repl && tid < 4 * G::BY) {
+      const int row = tid >> 2, k = tid & 3;
+      const long long gy = (long long)y0 - R + row;
+      const long long vb = (long long)zp * plane + gy * nx + ((long long)x0 - R);
+      const long long off = vb - ((vb >> 5) << 5);
+      *off_out = (unsigned)off;
+      if (zp >= 0 && zp < nz && gy >= 0 && gy < ny) {
+        const long long wi = (vb >> 5) + k;  // arithmetic shift: floor division
+        if (wi >= 0 && wi * 32 < (long long)nz * plane) w = __ldg(a.mbits + wi);
+        // keep bits whose column gx = x0 - R + (32k + bit - off) is in [0, nx)
+        const long long c_lo = 32LL * k - off + ((long long)x0 - R);  // gx of bit 0
+        long long lo = -c_lo, hi = nx - c_lo;                        // valid bit range [lo, hi)
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > 32 ? 32 : hi;
+        unsigned keep = 0u;
+        if (hi > lo) keep = (hi - lo >= 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
+        w &= keep;
+      }
+    }
+    return w;
+  };
+
+  for (int k = 0; k < kStages - 1; ++k) issue_next();
+  long long g = 0;  // plane steps consumed so far: stage g % kStages, parity (g / kStages) & 1
   for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const long long tile_id = item % ((long long)a.tiles_x * a.tiles_y);
-    const int zc = (int)(item / ((long long)a.tiles_x * a.tiles_y));
-    const int x0 = (int)(tile_id % a.tiles_x) * TX, y0 = (int)(tile_id / a.tiles_x) * TY;
-    const int z0 = zc * a.lz;
-    const int z1 = (int)min((long long)z0 + a.lz, nz);
-    const int n_steps = (z1 - z0) + 2 * r;
-
+    int x0, y0, z0, n_steps;
+    item_geo(item, &x0, &y0, &z0, &n_steps);
     long long zsum[SEGY];
 #pragma unroll
     for (int i = 0; i < SEGY; ++i) zsum[i] = 0;
     if (wz > 1) {
-      if (TMEM) {
-        unsigned zero[16];
+      unsigned zero[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) zero[i] = 0u;
-        for (int s = 0; s < wz; ++s) tmem_st8(tmine + 16u * s, zero);
-        tmem_wait_st();
-      } else {
-        for (int s = 0; s < wz; ++s)
-#pragma unroll
-          for (int i = 0; i < SEGY; ++i) ring[((size_t)s * TY + ys * SEGY + i) * TX + yc] = 0;
-      }
+      for (int i = 0; i < 16; ++i) zero[i] = 0u;
+      for (int s = 0; s < wz; ++s) tmem_st16(tmine + 16u * s, zero);
+      tmem_wait_st();
     }
-    unsigned long long nan_hist = 0ull;  // SEGY bits per plane, newest in the low byte
+    unsigned long long nan_hist = 0ull;
+    unsigned moff = 0u;
+    unsigned mword = fetch_mask(x0, y0, z0 - r, &moff);
 
-    // register prefetch of one plane's halo'd tile
-    static_assert(G::NLOAD <= 32, "mask prefetch bits fit one word");
-    float pre[G::NLOAD];
-    unsigned int prem = 0u;
-    auto fetch = [&](int zp) {
-      const bool zok = (zp >= 0 && zp < nz);
-      prem = 0u;
-#pragma unroll
-      for (int rr = 0; rr < G::LOAD_ROWS; ++rr) {
-        const int row = warp + 8 * rr;
-        const long long gy = (long long)y0 - R + row;
-#pragma unroll
-        for (int sl = 0; sl < G::LOAD_SLOTS; ++sl) {
-          const int col = lane + 32 * sl;
-          const long long gx = (long long)x0 - R + col;
-          float v = 0.0f;
-          unsigned int mb = 0u;
-          if (zok && row < G::PY && col < G::PX && gy >= 0 && gy < ny && gx >= 0 && gx < nx) {
-            const long long idx = (long long)zp * plane + gy * nx + gx;
-            v = __ldg(a.C + idx);
-            if (do_repl) mb = (__ldg(a.mbits + (idx >> 5)) >> (idx & 31)) & 1u;
-          }
-          pre[rr * G::LOAD_SLOTS + sl] = v;
-          prem |= mb << (rr * G::LOAD_SLOTS + sl);
-        }
-      }
-    };
-    auto commit = [&]() {
-#pragma unroll
-      for (int rr = 0; rr < G::LOAD_ROWS; ++rr) {
-        const int row = warp + 8 * rr;
-#pragma unroll
-        for (int sl = 0; sl < G::LOAD_SLOTS; ++sl) {
-          const int col = lane + 32 * sl;
-          if (row < G::PY && col < G::PX) {
-            const float v = pre[rr * G::LOAD_SLOTS + sl];
-            long long q = 0;
-            if (isfinite(v)) {
-              q = quantize(v, f);
-              if ((prem >> (rr * G::LOAD_SLOTS + sl)) & 1u) q = (v >= 0.0f) ? qrepl : -qrepl;
-            }
-            Xt[row * G::XP + col] = q;
-          }
-        }
-      }
-    };
-
-    fetch(z0 - r);
-    for (int j = 0; j < n_steps; ++j) {
+    for (int j = 0; j < n_steps; ++j, ++g) {
       const int zp = z0 - r + j;
-      const bool valid = (zp >= 0 && zp < nz);
-      // NaN flags of this thread's 8 output voxels in plane zp (center values)
-      unsigned int nanbits = 0u;
-      if (valid) {
-        commit();
+      const int b = (int)(g % kStages);
+      if (do_repl && tid < 4 * G::BY) {
+        mw[tid] = mword;
+        if ((tid & 3) == 0) mw[4 * G::BY + (tid >> 2)] = moff;
       }
-      if (j + 1 < n_steps) fetch(zp + 1);
-      long long P[SEGY];
-      if (valid) {
-        __syncthreads();
-        // x pass: items (row, segment), row fastest so a warp spans rows
-        for (int it = tid; it < G::PY * (TX / SEGX); it += kThreads) {
-          const int row = it % G::PY, seg = it / G::PY;
-          long long in[SEGX + 2 * R];
-#pragma unroll
-          for (int k = 0; k < SEGX + 2 * R; ++k) in[k] = Xt[row * G::XP + seg * SEGX + k];
-          long long out[SEGX];
-          cascade<W1, W2, W3, SEGX + 2 * R>(in, out);
-#pragma unroll
-          for (int k = 0; k < SEGX; ++k) Bt[row * G::BP + seg * SEGX + k] = out[k];
-        }
-        __syncthreads();
-        {
-          long long in[SEGY + 2 * R];
-#pragma unroll
-          for (int k = 0; k < SEGY + 2 * R; ++k) in[k] = Bt[(ys * SEGY + k) * G::BP + yc];
-          cascade<W1, W2, W3, SEGY + 2 * R>(in, P);
-        }
-        // NaN status of the output voxels' own inputs (tile centre)
-        {
-          const long long gx = (long long)x0 + yc;
-#pragma unroll
-          for (int i = 0; i < SEGY; ++i) {
-            const long long gy = (long long)y0 + ys * SEGY + i;
-            if (gx < nx && gy < ny) {
-              const float c = __ldg(a.C + (long long)zp * plane + gy * nx + gx);
-              if (!isfinite(c)) nanbits |= 1u << i;
-            }
-          }
-        }
+      if (TMA) {
+        if (!mbar_wait(mbar0 + 8 * b, (unsigned)((g / kStages) & 1))) timed_out = true;
       } else {
+        // groups complete in order: allow the newer one to stay in flight
+        if (issued > g + 1) cp_async_wait_one_pending();
+        else cp_async_wait_all();
+      }
+      __syncthreads();
+      issue_next();
+      if (j + 1 < n_steps) mword = fetch_mask(x0, y0, zp + 1, &moff);
+      // ring slot of this plane: load early, use after the passes
+      unsigned old[16];
+      const unsigned ta = tmine + 16u * (unsigned)(j % (wz > 1 ? wz : 1));
+      if (wz > 1) tmem_ld16(ta, old);
+      const float* rb = raw0 + b * kRawStride;
+      // convert the halo'd tile once (flattened, branch-free per element)
 #pragma unroll
-        for (int i = 0; i < SEGY; ++i) P[i] = 0;
+      for (int k = 0; k < NCONV; ++k) {
+        const int e = tid + k * kThreads;
+        if (k + 1 < NCONV || e < G::BY * G::PX) {
+          const int row = e / G::PX, col = e - row * G::PX;
+          const float v = rb[row * G::BX + col + (RA - R)];
+          const bool fin = (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+          long long q = quantize(v, fscale);
+          if (do_repl) {
+            const int bi = (int)mw[4 * G::BY + row] + col;
+            const unsigned word = mw[row * 4 + (bi >> 5)];
+            const long long qr = v >= 0.0f ? qrepl : -qrepl;
+            q = ((word >> (bi & 31)) & 1u) ? qr : q;
+          }
+          Xt[row * G::XP + col] = fin ? q : 0ll;
+        }
+      }
+      __syncthreads();
+      // x pass
+      for (int it = tid; it < G::BY * (TX / SEGX); it += kThreads) {
+        const int row = it % G::BY, seg = it / G::BY;
+        const long long* src = Xt + row * G::XP + seg * SEGX;
+        long long* dst = Bt + row * G::BP + seg * SEGX;
+        cascade_stream<W1, W2, W3, SEGX>([&](int i) { return src[i]; }, [&](int k, long long v) { dst[k] = v; });
+      }
+      __syncthreads();
+      // y pass
+      long long P[SEGY];
+      {
+        const long long* src = Bt + (ys * SEGY) * G::BP + yc;
+        cascade_stream<W1, W2, W3, SEGY>([&](int i) { return src[i * G::BP]; }, [&](int k, long long v) { P[k] = v; });
+      }
+      unsigned nanbits = 0u;
+#pragma unroll
+      for (int i = 0; i < SEGY; ++i) {
+        const float c = rb[(ys * SEGY + i + R) * G::BX + yc + RA];
+        nanbits |= ((__float_as_uint(c) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
       }
       nan_hist = (nan_hist << SEGY) | nanbits;
-      // spectral boxcar: running sum over the last wz planes
+      // spectral boxcar
       if (wz > 1) {
-        const int slot = j % wz;
-        if (TMEM) {
-          unsigned old[16], nw[16];
-          tmem_ld8(tmine + 16u * slot, old);
-          tmem_wait_ld();
+        unsigned nw[16];
+        tmem_wait_ld();
 #pragma unroll
-          for (int i = 0; i < SEGY; ++i) {
-            const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
-            zsum[i] += P[i] - o;
-            nw[2 * i] = (unsigned)((unsigned long long)P[i] & 0xffffffffull);
-            nw[2 * i + 1] = (unsigned)((unsigned long long)P[i] >> 32);
-          }
-          tmem_st8(tmine + 16u * slot, nw);
-          tmem_wait_st();
-        } else {
-#pragma unroll
-          for (int i = 0; i < SEGY; ++i) {
-            long long* rp = ring + ((size_t)slot * TY + ys * SEGY + i) * TX + yc;
-            zsum[i] += P[i] - *rp;
-            *rp = P[i];
-          }
+        for (int i = 0; i < SEGY; ++i) {
+          const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
+          zsum[i] += P[i] - o;
+          nw[2 * i] = (unsigned)((unsigned long long)P[i] & 0xffffffffull);
+          nw[2 * i + 1] = (unsigned)((unsigned long long)P[i] >> 32);
         }
+        tmem_st16(ta, nw);
       } else {
 #pragma unroll
         for (int i = 0; i < SEGY; ++i) zsum[i] = P[i];
       }
-      const int zo = zp - r;
       if (j >= 2 * r) {
-        const unsigned int nb = (unsigned int)(nan_hist >> (SEGY * r)) & ((1u << SEGY) - 1u);
+        const int zo = zp - r;
+        const unsigned nb = (unsigned)(nan_hist >> (SEGY * r)) & ((1u << SEGY) - 1u);
         const long long gx = (long long)x0 + yc;
+        float* out = a.S + (long long)zo * plane + ((long long)y0 + ys * SEGY) * nx + gx;
 #pragma unroll
         for (int i = 0; i < SEGY; ++i) {
-          const long long gy = (long long)y0 + ys * SEGY + i;
-          if (gx < nx && gy < ny) {
-            float s;
-            if ((nb >> i) & 1u) {
-              s = __int_as_float(0x7fc00000);
-            } else {
-              s = dequantize(zsum[i], inv);
-              if (a.hist) atomicAdd(&hist[bin_of(s, cfg)], 1u);
-            }
-            a.S[(long long)zo * plane + gy * nx + gx] = s;
+          const bool inb = gx < nx && (long long)y0 + ys * SEGY + i < ny;
+          const bool isnan_out = (nb >> i) & 1u;
+          const float sv = dequantize(zsum[i], inv);
+          const float s = isnan_out ? __int_as_float(0x7fc00000) : sv;
+          if (inb) {
+            out[i * nx] = s;
+            if (a.hist && !isnan_out) atomicAdd(&hist[bin_of(s, cfg)], 1u);
           }
         }
       }
+      if (wz > 1) tmem_wait_st();
       __syncthreads();
     }
   }
-  if (TMEM) {
-    tmem_fence_before();
-    __syncthreads();
-    tmem_fence_after();
-    if (warp == 0) tmem_dealloc(tbase);
-  }
-  if (a.hist) {
-    __syncthreads();
+  if (!TMA) cp_async_wait_all();
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tbase);
+  if (timed_out && (tid & 31) == 0) atomicOr(&a.st->status, (unsigned)SC_ST_TIMEOUT);
+  if (a.hist)
     for (int i = tid; i < kNumBins; i += kThreads)
       if (hist[i]) atomicAdd(a.hist + i, (unsigned long long)hist[i]);
-  }
 }
 
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int W1, int W2, int W3, bool TMEM>
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+template <typename K>
+void set_dyn_smem_limit(K kernel) {
+  cudaFuncAttributes fa{};
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <int W1, int W2, int W3>
 cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done) {
   using namespace tile;
+  using G = Geo<W1, W2, W3>;
   SmoothArgs a = a0;
-  const Smem L = smem_layout<W1, W2, W3>(a.pd.wz, a.hist != nullptr, TMEM);
+  const Smem L = smem_layout<W1, W2, W3>(a.hist != nullptr);
   if (L.total + 1024 > 227 * 1024) return cudaSuccess;  // not served: caller falls back
   a.tx = TX;
   a.ty = TY;
@@ -373,33 +494,46 @@ cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* don
   a.zchunks = (a.nz + a.lz - 1) / a.lz;
   const long long items = tiles * a.zchunks;
   const int grid = (int)(items < sms ? items : sms);
-  k_smooth_tile<W1, W2, W3, TMEM><<<grid, kThreads, L.total, s>>>(a);
+  // TMA needs 16-byte aligned rows and base address
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  bool tma = (a.nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tma ? tensor_map_encoder() : nullptr;
+  if (enc) {
+    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 4, (cuuint64_t)a.nx * a.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)G::BX, (cuuint32_t)G::BY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a.C), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    tma = (cr == CUDA_SUCCESS);
+  } else {
+    tma = false;
+  }
+  const bool repl = a.mbits != nullptr && a.repl_possible;
+  // one block per SM (it holds all of the SM's TMEM): at least half the shared memory
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t smem_req = L.total > (size_t)per_sm / 2 + 1024 ? L.total : (size_t)per_sm / 2 + 1024;
+  if (tma) {
+    if (repl) k_smooth_tile<W1, W2, W3, true, true><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_tile<W1, W2, W3, true, false><<<grid, kThreads, smem_req, s>>>(map, a);
+  } else {
+    if (repl) k_smooth_tile<W1, W2, W3, false, true><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_tile<W1, W2, W3, false, false><<<grid, kThreads, smem_req, s>>>(map, a);
+  }
   *done = true;
   return cudaGetLastError();
 }
 
-// Dynamic shared memory limit = the per-block maximum minus the kernel's
-// static shared memory.
-template <typename K>
-void set_dyn_smem_limit(K kernel) {
-  cudaFuncAttributes fa{};
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-}
-
 template <int W1, int W2, int W3>
 void set_attr() {
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false>);
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true>);
-}
-
-template <int W1, int W2, int W3>
-cudaError_t launch_tile_any(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
-  if (a.pd.wz <= tile::kMaxWzSmem) return launch_tile<W1, W2, W3, false>(a, sms, s, done);
-  return launch_tile<W1, W2, W3, true>(a, sms, s, done);
+  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, false>);
+  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, false>);
+  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, true>);
+  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, true>);
 }
 
 }  // namespace
@@ -413,17 +547,16 @@ void init_tile_attrs() {
 }
 
 // Specialised kernel for the common cascades (FWHM 0, 3, 5, 6, 10 px) with
-// spectral widths up to 7 (ring in shared memory) or 15 (ring in TMEM);
-// *done = false when the pair is not served.
+// spectral widths up to 15; *done = false when the pair is not served.
 cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
-  if (a.generic || a.pd.wz > tile::kMaxWzTmem) return cudaSuccess;
+  if (a.generic || a.pd.wz > tile::kMaxWz) return cudaSuccess;
   const int* w = a.pd.w;
-  if (w[0] == 1 && w[1] == 1 && w[2] == 1) return launch_tile_any<1, 1, 1>(a, sms, s, done);
-  if (w[0] == 1 && w[1] == 3 && w[2] == 3) return launch_tile_any<1, 3, 3>(a, sms, s, done);
-  if (w[0] == 3 && w[1] == 5 && w[2] == 5) return launch_tile_any<3, 5, 5>(a, sms, s, done);
-  if (w[0] == 5 && w[1] == 5 && w[2] == 5) return launch_tile_any<5, 5, 5>(a, sms, s, done);
-  if (w[0] == 7 && w[1] == 9 && w[2] == 9) return launch_tile_any<7, 9, 9>(a, sms, s, done);
+  if (w[0] == 1 && w[1] == 1 && w[2] == 1) return launch_tile<1, 1, 1>(a, sms, s, done);
+  if (w[0] == 1 && w[1] == 3 && w[2] == 3) return launch_tile<1, 3, 3>(a, sms, s, done);
+  if (w[0] == 3 && w[1] == 5 && w[2] == 5) return launch_tile<3, 5, 5>(a, sms, s, done);
+  if (w[0] == 5 && w[1] == 5 && w[2] == 5) return launch_tile<5, 5, 5>(a, sms, s, done);
+  if (w[0] == 7 && w[1] == 9 && w[2] == 9) return launch_tile<7, 9, 9>(a, sms, s, done);
   return cudaSuccess;
 }
 

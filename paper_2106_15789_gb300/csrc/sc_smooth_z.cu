@@ -1,0 +1,328 @@
+// Spectral-only smoothing (spatial FWHM 0, boxcar of wz channels), SoFiA 2
+// Sect. 4.2 / 5, with the replacement of Sect. 6.2.
+//
+// With no spatial kernel, S(v) = (1/wz) * sum_{|d|<=r} X(v + d * plane) on the
+// flattened plane, so no tiles, halos or block barriers are needed: each
+// thread owns VPT consecutive voxels of the plane and walks through z, with
+// the wz most recent quantised values of its voxels in Tensor Memory (the
+// ring of the running sum) and the next plane's values prefetched into
+// registers. Same exact fixed-point arithmetic as the other smoothing kernels,
+// hence identical floats.
+#include <cstdint>
+
+#include "sc_device.cuh"
+#include "sc_internal.h"
+
+namespace sc {
+namespace zonly {
+
+constexpr int kThreads = 256;
+constexpr int kTmemCols = 512;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// 2*VPT consecutive 32-bit TMEM columns of the thread's lane <-> VPT int64.
+template <int VPT>
+struct Tm;
+template <>
+struct Tm<8> {
+  static __device__ __forceinline__ void ld(unsigned t, unsigned (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(t)
+        : "memory");
+  }
+  static __device__ __forceinline__ void st(unsigned t, const unsigned (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(t),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+  }
+};
+template <>
+struct Tm<4> {
+  static __device__ __forceinline__ void ld(unsigned t, unsigned (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(t)
+                 : "memory");
+  }
+  static __device__ __forceinline__ void st(unsigned t, const unsigned (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(t), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+  }
+};
+template <>
+struct Tm<1> {
+  static __device__ __forceinline__ void ld(unsigned t, unsigned (&v)[2]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(v[0]), "=r"(v[1]) : "r"(t) : "memory");
+  }
+  static __device__ __forceinline__ void st(unsigned t, const unsigned (&v)[2]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(t), "r"(v[0]), "r"(v[1]) : "memory");
+  }
+};
+
+constexpr int kDepth = 8;  // planes in flight per thread (cp.async ring in shared memory)
+
+__device__ __forceinline__ void cp16(unsigned dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp4(unsigned dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+}  // namespace zonly
+
+template <int VPT, bool VEC, bool REPL>
+__global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
+  using namespace zonly;
+  extern __shared__ __align__(16) unsigned char zsmem[];
+  float* const zring = reinterpret_cast<float*>(zsmem);  // [kDepth][kThreads * VPT]
+  unsigned long long* const zmask =
+      reinterpret_cast<unsigned long long*>(zsmem + sizeof(float) * kDepth * kThreads * VPT);  // [kDepth][kThreads]
+  unsigned int* const zhist =
+      reinterpret_cast<unsigned int*>(zsmem + sizeof(float) * kDepth * kThreads * VPT + 8 * kDepth * kThreads);
+  __shared__ unsigned tmem_holder;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (a.hist)
+    for (int i = tid; i < kNumBins; i += kThreads) zhist[i] = 0u;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tbase = tmem_holder;
+  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(256 * (warp >> 2));
+
+  const BinCfg cfg = a.win ? a.st->win : kFullRange;
+  const float fscale = a.st->fx_scale[a.pair];
+  const float inv = a.st->fx_inv[a.pair];
+  const long long qrepl = a.st->fx_qrepl[a.pair];
+  const bool do_repl = REPL && qrepl > 0;
+  const int wz = a.pd.wz, r = (wz - 1) / 2;
+  const long long nz = a.nz, P = (long long)a.nx * a.ny, N = P * nz;
+  const long long per_block = (long long)kThreads * VPT;
+  const long long groups = (P + per_block - 1) / per_block;
+  const long long n_items = groups * a.zchunks;
+  constexpr int W = 2 * VPT;  // TMEM columns per ring slot
+
+  for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const long long grp = item % groups;
+    const int zc = (int)(item / groups);
+    const long long p0 = grp * per_block + (long long)tid * VPT;
+    const int nv = (int)(P - p0 < 0 ? 0 : (P - p0 > VPT ? VPT : P - p0));  // voxels this thread owns
+    const int z0 = zc * a.lz;
+    const int z1 = (int)min((long long)z0 + a.lz, nz);
+    const int n_steps = (z1 - z0) + 2 * r;
+    long long zsum[VPT];
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) zsum[i] = 0;
+    {
+      unsigned zero[W];
+#pragma unroll
+      for (int i = 0; i < W; ++i) zero[i] = 0u;
+      for (int s = 0; s < wz; ++s) Tm<VPT>::st(tmine + (unsigned)(W * s), zero);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    unsigned long long nan_hist = 0ull;
+
+    // Per-thread ring of kDepth planes in shared memory, filled by cp.async:
+    // the thread's VPT values and the mask word(s) holding its bits. Each
+    // thread reads back only what it copied itself, so no barrier is needed.
+    float* my_vals = zring + (size_t)tid * VPT;                       // stage stride kThreads*VPT floats
+    unsigned long long* my_mask = zmask + tid;                        // stage stride kThreads
+    auto issue = [&](int zp, int stage) {
+      const bool zok = zp >= 0 && zp < nz;
+      const long long base = (long long)zp * P + p0;
+      float* dv = my_vals + (size_t)stage * kThreads * VPT;
+      if (VEC) {
+#pragma unroll
+        for (int q = 0; q < VPT / 4; ++q)
+          cp16(smem_u32(dv + 4 * q), zok && nv == VPT ? (const void*)(a.C + base + 4 * q) : (const void*)a.C,
+               zok && nv == VPT);
+      } else {
+#pragma unroll
+        for (int i = 0; i < VPT; ++i)
+          cp4(smem_u32(dv + i), zok && i < nv ? (const void*)(a.C + base + i) : (const void*)a.C, zok && i < nv);
+      }
+      if (do_repl) {
+        unsigned* dm = reinterpret_cast<unsigned*>(my_mask + (size_t)stage * kThreads);
+        const long long w = base >> 5;
+        const bool ok = zok && nv > 0;
+        cp4(smem_u32(dm), ok ? (const void*)(a.mbits + w) : (const void*)a.mbits, ok);
+        const bool ok2 = ok && ((base & 31) + VPT > 32) && (w + 1) * 32 < N;
+        cp4(smem_u32(dm + 1), ok2 ? (const void*)(a.mbits + w + 1) : (const void*)a.mbits, ok2);
+      }
+      cp_commit();
+    };
+    for (int k = 0; k < kDepth - 1; ++k) issue(z0 - r + k, k);  // plane index beyond n_steps: harmless zero fill
+    for (int j = 0; j < n_steps; ++j) {
+      const int zp = z0 - r + j;
+      issue(zp + kDepth - 1, (j + kDepth - 1) % kDepth);
+      cp_wait<kDepth - 1>();
+      const int st = j % kDepth;
+      float cur[VPT];
+      const float* sv = my_vals + (size_t)st * kThreads * VPT;
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) cur[i] = sv[i];
+      unsigned mcur = 0u;
+      if (do_repl && zp >= 0 && zp < nz && nv > 0) {
+        const unsigned* mm = reinterpret_cast<const unsigned*>(my_mask + (size_t)st * kThreads);
+        const unsigned long long two = (unsigned long long)mm[0] | ((unsigned long long)mm[1] << 32);
+        const long long base = (long long)zp * P + p0;
+        mcur = (unsigned)(two >> (base & 31)) & ((1u << VPT) - 1u);
+        mcur &= (nv >= 32 ? 0xffffffffu : ((1u << nv) - 1u));
+      }
+      const unsigned ta = tmine + (unsigned)(W * (j % wz));
+      unsigned old[W], nw[W];
+      Tm<VPT>::ld(ta, old);
+      unsigned nanbits = 0u;
+      long long Pq[VPT];
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) {
+        const float c = cur[i];
+        const bool fin = (__float_as_uint(c) & 0x7f800000u) != 0x7f800000u;
+        long long q = quantize(c, fscale);
+        if (do_repl) q = ((mcur >> i) & 1u) ? (c >= 0.0f ? qrepl : -qrepl) : q;
+        Pq[i] = fin ? q : 0ll;
+        nanbits |= (fin ? 0u : 1u) << i;
+      }
+      nan_hist = (nan_hist << VPT) | nanbits;
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) {
+        const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
+        zsum[i] += Pq[i] - o;
+        nw[2 * i] = (unsigned)((unsigned long long)Pq[i] & 0xffffffffull);
+        nw[2 * i + 1] = (unsigned)((unsigned long long)Pq[i] >> 32);
+      }
+      Tm<VPT>::st(ta, nw);
+      if (j >= 2 * r && nv > 0) {
+        const int zo = zp - r;
+        const unsigned nb = (unsigned)(nan_hist >> (VPT * r)) & ((1u << VPT) - 1u);
+        float s[VPT];
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+          const bool isn = (nb >> i) & 1u;
+          const float sv = dequantize(zsum[i], inv);
+          s[i] = isn ? __int_as_float(0x7fc00000) : sv;
+          if (a.hist && !isn && i < nv) atomicAdd(&zhist[bin_of(s[i], cfg)], 1u);
+        }
+        float* out = a.S + (long long)zo * P + p0;
+        if (VEC && nv == VPT) {
+#pragma unroll
+          for (int q = 0; q < VPT / 4; ++q)
+            reinterpret_cast<float4*>(out)[q] = make_float4(s[4 * q], s[4 * q + 1], s[4 * q + 2], s[4 * q + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < VPT; ++i)
+            if (i < nv) out[i] = s[i];
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    cp_wait<0>();  // drain the copies issued past the item's last plane
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
+  if (a.hist)
+    for (int i = tid; i < kNumBins; i += kThreads)
+      if (zhist[i]) atomicAdd(a.hist + i, (unsigned long long)zhist[i]);
+}
+
+namespace {
+
+size_t one_block_per_sm_smem(size_t need) {
+  int dev = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const size_t half = (size_t)per_sm / 2 + 1024;
+  return need > half ? need : half;
+}
+
+template <int VPT, bool VEC, bool REPL>
+void set_z_attr() {
+  cudaFuncAttributes fa{};
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaFuncGetAttributes(&fa, k_smooth_z<VPT, VEC, REPL>) != cudaSuccess) return;
+  cudaFuncSetAttribute(k_smooth_z<VPT, VEC, REPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       optin - (int)fa.sharedSizeBytes);
+}
+
+template <int VPT>
+void set_z_attrs() {
+  set_z_attr<VPT, false, false>();
+  set_z_attr<VPT, false, true>();
+  set_z_attr<VPT, true, false>();
+  set_z_attr<VPT, true, true>();
+}
+
+template <int VPT, bool VEC, bool REPL>
+cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
+  SmoothArgs a = a0;
+  const long long P = (long long)a.nx * a.ny;
+  const long long per_block = (long long)zonly::kThreads * VPT;
+  const long long groups = (P + per_block - 1) / per_block;
+  long long zch = (2LL * sms + groups - 1) / groups;
+  const long long max_ch = (a.nz + 15) / 16;
+  zch = zch < 1 ? 1 : (zch > max_ch ? max_ch : zch);
+  a.lz = (int)((a.nz + zch - 1) / zch);
+  a.zchunks = (a.nz + a.lz - 1) / a.lz;
+  const long long items = groups * a.zchunks;
+  const int grid = (int)(items < sms ? items : sms);
+  // one block per SM (it holds all of the SM's TMEM): request more than half
+  // of the shared memory
+  const size_t need = sizeof(float) * zonly::kDepth * zonly::kThreads * VPT + 8 * zonly::kDepth * zonly::kThreads +
+                      (a.hist ? sizeof(unsigned) * kNumBins : 0);
+  const size_t smem = one_block_per_sm_smem(need);
+  k_smooth_z<VPT, VEC, REPL><<<grid, zonly::kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int VPT>
+cudaError_t launch_z_vpt(const SmoothArgs& a, int sms, cudaStream_t s) {
+  const bool vec = VPT >= 4 && ((long long)a.nx * a.ny) % 4 == 0 && (reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(a.S) & 15u) == 0;
+  const bool repl = a.mbits != nullptr && a.repl_possible;
+  if (vec) return repl ? launch_z<VPT, true, true>(a, sms, s) : launch_z<VPT, true, false>(a, sms, s);
+  return repl ? launch_z<VPT, false, true>(a, sms, s) : launch_z<VPT, false, false>(a, sms, s);
+}
+
+}  // namespace
+
+void init_z_attrs() {
+  set_z_attrs<8>();
+  set_z_attrs<4>();
+  set_z_attrs<1>();
+}
+
+// Spectral-only pairs (no spatial smoothing, boxcar up to 127 channels).
+cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
+  *done = false;
+  if (a.generic || a.pd.h != 0 || a.pd.wz <= 1) return cudaSuccess;
+  *done = true;
+  if (a.pd.wz <= 15) return launch_z_vpt<8>(a, sms, s);
+  if (a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
+  return launch_z_vpt<1>(a, sms, s);
+}
+
+}  // namespace sc

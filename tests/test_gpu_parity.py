@@ -244,7 +244,8 @@ def test_specialised_kernels_equal_generic(ctx, shape):
     c[rng.random(shape) < 0.03] = np.nan
     cube = torch.from_numpy(c).cuda()
     mask = torch.from_numpy((rng.random(shape) < 0.05).astype(np.uint8)).cuda()
-    for kernel in [(0.0, 3), (0.0, 7), (3.0, 0), (3.0, 3), (5.0, 7), (6.0, 1), (6.0, 7), (10.0, 5), (6.0, 15)]:
+    for kernel in [(0.0, 3), (0.0, 7), (0.0, 15), (0.0, 31), (0.0, 63), (3.0, 0), (3.0, 3), (5.0, 7), (6.0, 1), (6.0, 7),
+                   (10.0, 5), (6.0, 15)]:
         for m, v in ((None, 0.0), (mask, 2.5)):
             a = ctx.smooth(cube, kernel, mask=m, replacement_value=v)
             b = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_FLAG_GENERIC)
