@@ -107,14 +107,15 @@ __device__ __forceinline__ float u64_to_float_rn(unsigned long long a) {
   return __uint_as_float(a == 0ull ? 0u : bits);
 }
 
-// float of q * inv from two 32-bit conversions of |q|'s halves, one FMA and
-// one multiply (within about 2 ulp of the exact product).
+// float of q * inv from two 32-bit conversions (signed high word, unsigned
+// low word), one FMA and one multiply. The low word's rounding costs at most
+// 2^7 units of q (|error| <= 2^7 * inv absolute, far below the float
+// resolution of any value above 2^31 * inv); above that the result is within
+// about 2 ulp of the exact product.
 __device__ __forceinline__ float dequantize(long long q, float inv) {
-  const unsigned long long a = q < 0 ? (unsigned long long)0 - (unsigned long long)q : (unsigned long long)q;
-  const float hi = __uint2float_rn((unsigned int)(a >> 32));
-  const float lo = __uint2float_rn((unsigned int)(a & 0xffffffffull));
-  const float v = __fmul_rn(__fmaf_rn(hi, 4294967296.0f, lo), inv);
-  return q < 0 ? -v : v;
+  const float hi = __int2float_rn((int)(q >> 32));
+  const float lo = __uint2float_rn((unsigned int)((unsigned long long)q & 0xffffffffull));
+  return __fmul_rn(__fmaf_rn(hi, 4294967296.0f, lo), inv);
 }
 
 __device__ __forceinline__ bool mask_bit(const uint32_t* mbits, long long v) {

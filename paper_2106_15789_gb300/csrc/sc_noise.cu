@@ -364,11 +364,25 @@ __device__ __forceinline__ void stage_push(bool pred, T val, T* stage, int& cnt)
   cnt += __popc(b);
 }
 
+// Smallest and largest order-preserving key of histogram bin b (the bins are
+// contiguous key ranges): found by bisection on bin_of over keys.
+__device__ unsigned int bin_key_lo(int b, BinCfg cfg) {
+  unsigned int lo = 0u, hi = 0xffffffffu;  // first key whose bin >= b
+  while (lo < hi) {
+    const unsigned int mid = lo + ((hi - lo) >> 1);
+    if (bin_of(fkey_inv(mid), cfg) >= b) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+constexpr int kPass2Unroll = 4;  // chunks of 128 values in flight per warp
+
 __global__ void __launch_bounds__(256) k_pass2(const float* __restrict__ src, long long n, uint32_t* mbits,
                                                DevState* st, Lists L, int win) {
   __shared__ float sh_med[8][kStage];
   __shared__ float sh_mad[8][kStage];
   __shared__ unsigned long long sh_amb[8][kStage];
+  __shared__ unsigned int s_keys[2];
   const NoisePlan p = st->plan;
   if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
   const BinCfg cfg = win ? st->win : kFullRange;
@@ -376,6 +390,13 @@ __global__ void __launch_bounds__(256) k_pass2(const float* __restrict__ src, lo
   const bool do_mad = !(p.flags & PLAN_MAD_FULL);
   const bool do_clip = (p.flags & PLAN_CLIP) && !(p.flags & PLAN_CLIP_FULL);
   if (!do_med && !do_mad && !do_clip) return;
+  // median candidates = keys in [key_lo, key_hi] (exact for -0 / +0)
+  if (threadIdx.x == 0) {
+    s_keys[0] = bin_key_lo(p.b_med_lo, cfg);
+    s_keys[1] = p.b_med_hi + 1 < kNumBins ? bin_key_lo(p.b_med_hi + 1, cfg) - 1u : 0xffffffffu;
+  }
+  __syncthreads();
+  const unsigned int key_lo = s_keys[0], key_hi = s_keys[1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* smed = sh_med[warp];
   float* smad = sh_mad[warp];
@@ -384,69 +405,67 @@ __global__ void __launch_bounds__(256) k_pass2(const float* __restrict__ src, lo
   unsigned long long below = 0;
   const long long nchunks = (n + 127) / 128;
   const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
-  const long long wstride = (long long)gridDim.x * 8;
-  for (long long ch = (long long)blockIdx.x * 8 + warp; ch < nchunks; ch += wstride) {
-    const long long v0 = ch * 128 + lane * 4;
-    float a[4];
-    if (vec && v0 + 3 < n) {
-      float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
-      a[0] = t4.x; a[1] = t4.y; a[2] = t4.z; a[3] = t4.w;
-    } else {
+  const long long wstride = (long long)gridDim.x * 8 * kPass2Unroll;
+  for (long long ch0 = ((long long)blockIdx.x * 8 + warp) * kPass2Unroll; ch0 < nchunks; ch0 += wstride) {
+    float a[kPass2Unroll][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) a[c] = (v0 + c < n) ? __ldg(src + v0 + c) : __int_as_float(0x7fc00000);
-    }
-    unsigned int sure_bits[4];
+    for (int u = 0; u < kPass2Unroll; ++u) {
+      const long long v0 = (ch0 + u) * 128 + lane * 4;
+      if (vec && v0 + 3 < n) {
+        const float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
+        a[u][0] = t4.x; a[u][1] = t4.y; a[u][2] = t4.z; a[u][3] = t4.w;
+      } else {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float s = a[c];
-      const bool fin = isfinite(s);
-      bool pm = false, pa = false, pamb = false, sure = false;
-      if (fin) {
-        if (do_med) {
-          const int b = bin_of(s, cfg);
-          pm = (b >= p.b_med_lo && b <= p.b_med_hi);
-        }
-        if (do_mad) {
-          if (p.has_B && s >= p.B_lo && s <= p.B_hi) {
-            ++below;
-          } else if (s >= p.A_lo && s <= p.A_hi) {
-            pa = true;
-          }
-        }
-        if (do_clip) {
-          const float as = fabsf(s);
-          if (as > p.thr_hi) sure = true;
-          else if (as > p.thr_lo) pamb = true;
-        }
+        for (int c = 0; c < 4; ++c) a[u][c] = (v0 + c < n) ? __ldg(src + v0 + c) : __int_as_float(0x7fc00000);
       }
-      stage_push(pm, s, smed, nmed);
-      stage_push(pa, s, smad, nmad);
-      stage_push(pamb, (unsigned long long)(v0 + c), samb, namb);
-      sure_bits[c] = __ballot_sync(0xffffffffu, sure);
     }
-    if (do_clip) {
-      if (lane < 4) {
+#pragma unroll
+    for (int u = 0; u < kPass2Unroll; ++u) {
+      const long long ch = ch0 + u;
+      if (ch >= nchunks) break;
+      const long long v0 = ch * 128 + lane * 4;
+      unsigned int sure_bits[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float s = a[u][c];
+        const bool fin = (__float_as_uint(s) & 0x7f800000u) != 0x7f800000u;
+        const unsigned int k = fkey(s);
+        const bool pm = do_med && fin && k >= key_lo && k <= key_hi;
+        const bool inB = do_mad && p.has_B && s >= p.B_lo && s <= p.B_hi;  // NaN compares false
+        const bool pa = do_mad && !inB && s >= p.A_lo && s <= p.A_hi && fin;
+        const float as = fabsf(s);
+        const bool sure = do_clip && fin && as > p.thr_hi;
+        const bool pamb = do_clip && fin && !sure && as > p.thr_lo;
+        const unsigned int bB = __ballot_sync(0xffffffffu, inB);
+        below += (lane == 0) ? (unsigned long long)__popc(bB) : 0ull;
+        if (__any_sync(0xffffffffu, pm || pa || pamb)) {
+          stage_push(pm, s, smed, nmed);
+          stage_push(pa, s, smad, nmad);
+          stage_push(pamb, (unsigned long long)(v0 + c), samb, namb);
+        }
+        sure_bits[c] = __ballot_sync(0xffffffffu, sure);
+      }
+      if (do_clip && lane < 4) {
         unsigned int w = 0u;
 #pragma unroll
         for (int c = 0; c < 4; ++c) w |= spread4(sure_bits[c] >> (8 * lane)) << c;
         const long long wi = ch * 4 + lane;
         if (w && wi * 32 < n) mbits[wi] |= w;
       }
+      if (nmed > kFlushAt) stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
+      if (nmad > kFlushAt) stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
+      if (namb > kFlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
     }
-    if (nmed > kFlushAt) stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
-    if (nmad > kFlushAt) stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
-    if (namb > kFlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
   }
   stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
   stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
   stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
-  below = warp_sum_u64(below);
-  if (lane == 0 && below) atomicAdd(&st->n_below, below);
+  if (lane == 0 && below) atomicAdd(&st->n_below, below);  // lane 0 counted the whole warp
 }
 
 cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int win, int sms,
                          cudaStream_t s) {
-  long long want = (n + 1023) / 1024;
+  long long want = (n + 1024 * kPass2Unroll - 1) / (1024 * kPass2Unroll);
   int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
   k_pass2<<<grid, 256, 0, s>>>(src, n, mbits, st, L, win);
   return cudaGetLastError();

@@ -37,10 +37,10 @@ namespace sc {
 
 namespace tile {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int TX = 64, TY = 32;
-constexpr int SEGX = 16, SEGY = 8;
-constexpr int kMaxWz = 15;                 // TMEM ring: 16 slots of 8 int64 per thread
+constexpr int SEGX = 8, SEGY = 4;
+constexpr int kMaxWz = 15;                 // TMEM ring: 16 slots of 4 int64 per thread
 constexpr long long kMaxSpins = 1LL << 24;  // bound of every mbarrier wait
 constexpr int kStages = 3;                  // raw-tile buffers (loads run two planes ahead)
 
@@ -129,8 +129,8 @@ __device__ __forceinline__ void cascade_stream(Load load, Out out) {
 
 // ---- Tensor Memory (TMEM) as ring storage --------------------------------
 // The block allocates all 512 columns of its SM's TMEM. Warp w may touch
-// lanes 32*(w%4) .. +31; warps 0-3 use columns 0..255, warps 4-7 columns
-// 256..511, so each thread owns 256 32-bit words of one lane.
+// lanes 32*(w%4) .. +31; the 16 warps take columns 128*(w/4) .. +127, so each
+// thread owns 128 32-bit words of one lane: 16 ring slots of 4 int64.
 constexpr int kTmemCols = 512;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -149,21 +149,18 @@ __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, unsigned (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr)
-      : "memory");
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
 }
-__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
 }
+constexpr int kSlotCols = 2 * SEGY;  // TMEM columns per ring slot
 
 // ---- mbarrier / TMA / cp.async --------------------------------------------
 __device__ __forceinline__ void mbar_init(unsigned addr) {
@@ -245,7 +242,7 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
   __syncthreads();
   tmem_fence_after();
   const unsigned tbase = tmem_holder;
-  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(256 * (warp >> 2));
+  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(128 * (warp >> 2));
   bool timed_out = false;
 
   auto item_geo = [&](long long it, int* x0, int* y0, int* z0, int* ns) {
@@ -290,25 +287,27 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
       if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
     }
   };
-  // mask words of plane zp (4 words per halo'd row, bits of out-of-cube
-  // columns cleared; word 4 of a row's group is its bit offset)
-  auto fetch_mask = [&](int x0, int y0, int zp, unsigned* off_out) -> unsigned {
+  // Mask bits of plane zp re-aligned to the quantised tile: word k of row
+  // `row` holds the bits of columns 32k .. 32k+31 (column c <-> gx = x0 - R + c),
+  // with bits of columns outside the cube cleared. One word per thread
+  // (tid < 4 * BY); the two source words straddling it are funnel-shifted.
+  auto fetch_mask = [&](int x0, int y0, int zp) -> unsigned {
     unsigned w = 0u;
-    *off_out = 0u;
     if (do_repl && tid < 4 * G::BY) {
       const int row = tid >> 2, k = tid & 3;
       const long long gy = (long long)y0 - R + row;
-      const long long vb = (long long)zp * plane + gy * nx + ((long long)x0 - R);
-      const long long off = vb - ((vb >> 5) << 5);
-      *off_out = (unsigned)off;
       if (zp >= 0 && zp < nz && gy >= 0 && gy < ny) {
-        const long long wi = (vb >> 5) + k;  // arithmetic shift: floor division
-        if (wi >= 0 && wi * 32 < (long long)nz * plane) w = __ldg(a.mbits + wi);
-        // keep bits whose column gx = x0 - R + (32k + bit - off) is in [0, nx)
-        const long long c_lo = 32LL * k - off + ((long long)x0 - R);  // gx of bit 0
-        long long lo = -c_lo, hi = nx - c_lo;                        // valid bit range [lo, hi)
-        lo = lo < 0 ? 0 : lo;
-        hi = hi > 32 ? 32 : hi;
+        const long long vb = (long long)zp * plane + gy * nx + ((long long)x0 - R) + 32 * k;  // flat index of bit 0
+        const long long wi = vb >> 5;                                                           // floor division
+        const unsigned off = (unsigned)(vb & 31);
+        const long long nwords = (plane * nz + 31) >> 5;
+        const unsigned w0 = (wi >= 0 && wi < nwords) ? __ldg(a.mbits + wi) : 0u;
+        const unsigned w1 = (wi + 1 >= 0 && wi + 1 < nwords) ? __ldg(a.mbits + wi + 1) : 0u;
+        w = __funnelshift_r(w0, w1, off);
+        // keep columns with gx = x0 - R + 32k + bit in [0, nx)
+        const int g0 = x0 - R + 32 * k;  // gx of bit 0
+        const int lo = g0 < 0 ? -g0 : 0;
+        const int hi = (long long)nx - g0 > 32 ? 32 : (int)((long long)nx - g0);
         unsigned keep = 0u;
         if (hi > lo) keep = (hi - lo >= 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
         w &= keep;
@@ -326,23 +325,19 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
 #pragma unroll
     for (int i = 0; i < SEGY; ++i) zsum[i] = 0;
     if (wz > 1) {
-      unsigned zero[16];
+      unsigned zero[kSlotCols];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) zero[i] = 0u;
-      for (int s = 0; s < wz; ++s) tmem_st16(tmine + 16u * s, zero);
+      for (int i = 0; i < kSlotCols; ++i) zero[i] = 0u;
+      for (int s = 0; s < wz; ++s) tmem_st8(tmine + (unsigned)(kSlotCols * s), zero);
       tmem_wait_st();
     }
     unsigned long long nan_hist = 0ull;
-    unsigned moff = 0u;
-    unsigned mword = fetch_mask(x0, y0, z0 - r, &moff);
+    unsigned mword = fetch_mask(x0, y0, z0 - r);
 
     for (int j = 0; j < n_steps; ++j, ++g) {
       const int zp = z0 - r + j;
       const int b = (int)(g % kStages);
-      if (do_repl && tid < 4 * G::BY) {
-        mw[tid] = mword;
-        if ((tid & 3) == 0) mw[4 * G::BY + (tid >> 2)] = moff;
-      }
+      if (do_repl && tid < 4 * G::BY) mw[tid] = mword;
       if (TMA) {
         if (!mbar_wait(mbar0 + 8 * b, (unsigned)((g / kStages) & 1))) timed_out = true;
       } else {
@@ -352,11 +347,11 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
       }
       __syncthreads();
       issue_next();
-      if (j + 1 < n_steps) mword = fetch_mask(x0, y0, zp + 1, &moff);
+      if (j + 1 < n_steps) mword = fetch_mask(x0, y0, zp + 1);
       // ring slot of this plane: load early, use after the passes
-      unsigned old[16];
-      const unsigned ta = tmine + 16u * (unsigned)(j % (wz > 1 ? wz : 1));
-      if (wz > 1) tmem_ld16(ta, old);
+      unsigned old[kSlotCols];
+      const unsigned ta = tmine + (unsigned)(kSlotCols * (j % (wz > 1 ? wz : 1)));
+      if (wz > 1) tmem_ld8(ta, old);
       const float* rb = raw0 + b * kRawStride;
       // convert the halo'd tile once (flattened, branch-free per element)
 #pragma unroll
@@ -368,10 +363,9 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
           const bool fin = (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
           long long q = quantize(v, fscale);
           if (do_repl) {
-            const int bi = (int)mw[4 * G::BY + row] + col;
-            const unsigned word = mw[row * 4 + (bi >> 5)];
+            const unsigned word = mw[row * 4 + (col >> 5)];
             const long long qr = v >= 0.0f ? qrepl : -qrepl;
-            q = ((word >> (bi & 31)) & 1u) ? qr : q;
+            q = ((word >> (col & 31)) & 1u) ? qr : q;
           }
           Xt[row * G::XP + col] = fin ? q : 0ll;
         }
@@ -400,7 +394,7 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
       nan_hist = (nan_hist << SEGY) | nanbits;
       // spectral boxcar
       if (wz > 1) {
-        unsigned nw[16];
+        unsigned nw[kSlotCols];
         tmem_wait_ld();
 #pragma unroll
         for (int i = 0; i < SEGY; ++i) {
@@ -409,7 +403,7 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
           nw[2 * i] = (unsigned)((unsigned long long)P[i] & 0xffffffffull);
           nw[2 * i + 1] = (unsigned)((unsigned long long)P[i] >> 32);
         }
-        tmem_st16(ta, nw);
+        tmem_st8(ta, nw);
       } else {
 #pragma unroll
         for (int i = 0; i < SEGY; ++i) zsum[i] = P[i];
