@@ -165,7 +165,7 @@ int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, doub
  * memory belongs to another allocator or a fixed pool, real-time pipelines
  * that forbid allocation (and the device synchronisation it implies) once
  * running, plug-ins that are handed only a stream and buffers. It needs no
- * context and allocates nothing: its scratch (2,525,440 bytes) is one static
+ * context and allocates nothing: its scratch (2,590,976 bytes) is one static
  * device array that every GPU loading this library holds until the process
  * exits. The paper has no counterpart; this is a library-level addition.
  *   - n <= 4194304 (4 Mi values), else SC_ERR_BUDGET.

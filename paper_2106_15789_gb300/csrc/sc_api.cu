@@ -161,7 +161,7 @@ int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip
       CK(launch_std_final(c->st, pair, s));
       c->stats.launches += 3;
     } else {
-      CK(launch_pass2(src, n, c->mbits, c->st, c->L, win, c->sms, s));
+      CK(launch_pass2(src, n, c->mbits, c->st, c->L, c->sms, s));
       CK(launch_select(c->st, 0, -1, c->sms, s));
       CK(launch_select(c->st, 1, pair, c->sms, s));
       c->stats.launches += 11;
@@ -224,7 +224,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   const long long nwords = (n + 31) / 32;
   if (flags & SC_FLAG_ACCUMULATE) {
-    CK(launch_pack(mask_dev, n, c->mbits, s));
+    CK(launch_pack(mask_dev, cube, n, c->mbits, s));
     c->stats.launches += 1;
   } else {
     CK(cudaMemsetAsync(c->mbits, 0, sizeof(uint32_t) * nwords, s));
@@ -268,7 +268,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   }
   {
     Phase ph(c, s, EV_CLIP);
-    CK(launch_expand(c->mbits, n, mask_dev, s));
+    CK(launch_expand(c->mbits, n, mask_dev, (flags & SC_FLAG_ACCUMULATE) ? 1 : 0, s));
     c->stats.launches += 1;
   }
   return SC_OK;
@@ -339,6 +339,7 @@ int sc_create(sc_ctx** out, int device, size_t max_voxels) {
             cudaMalloc(&c->L.med, sizeof(float) * c->L.cap.med) == cudaSuccess &&
             cudaMalloc(&c->L.mad, sizeof(float) * c->L.cap.mad) == cudaSuccess &&
             cudaMalloc(&c->L.amb, sizeof(unsigned long long) * c->L.cap.amb) == cudaSuccess &&
+            cudaMalloc(&c->L.cls, kClassTableBytes) == cudaSuccess &&
             cudaMalloc(&c->st, sizeof(DevState)) == cudaSuccess &&
             cudaHostAlloc(&c->st_host, sizeof(DevState), cudaHostAllocDefault) == cudaSuccess;
   if (!ok) {
@@ -371,6 +372,7 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->L.med);
   cudaFree(c->L.mad);
   cudaFree(c->L.amb);
+  cudaFree(c->L.cls);
   cudaFree(c->st);
   cudaFree(c->stage_cube);
   cudaFree(c->stage_mask);
@@ -438,7 +440,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   c->last = s;
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   if (mask_dev) {
-    CK(launch_pack(mask_dev, n, c->mbits, s));
+    CK(launch_pack(mask_dev, cube_dev, n, c->mbits, s));
     c->stats.launches += 1;
   }
   const float repl = replacement_value > 0.0f ? replacement_value : 0.0f;  // quantised exactly per pair

@@ -80,6 +80,9 @@ struct NoisePlan {
   float threshold;       // t
   float T1, T2;
   unsigned long long bound_med, bound_mad, bound_amb;  // candidate counts bounds from the histogram
+  int bA_lo, bA_hi;        // bins that may hold MAD candidates
+  int bB_lo, bB_hi;        // bins surely inside the MAD band (empty if bB_lo > bB_hi)
+  unsigned long long n_B;  // values in those bins
 };
 
 // Device-resident state of one sc_run (one context owns one).
@@ -120,11 +123,14 @@ struct Caps {
   unsigned long long med, mad, amb;
 };
 
+constexpr size_t kClassTableBytes = 1 << 16;  // one byte per 16-bit cell of the float encoding
+
 // Candidate lists owned by the context.
 struct Lists {
   float* med;
   float* mad;
   unsigned long long* amb;
+  unsigned char* cls;  // 65536-byte class table written by the plan (16-byte aligned)
   Caps cap;
 };
 
@@ -169,7 +175,7 @@ cudaError_t launch_hist(const float* x, long long n, DevState* st, unsigned long
                         int want_maxabs, int sms, cudaStream_t s);
 cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, const float* src, long long n_total,
                         Lists L, float threshold, int clip, int std_mode, unsigned int force_flags, cudaStream_t s);
-cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int win, int sms,
+cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int sms,
                          cudaStream_t s);
 // which: 0 median (result in DevState::m), 1 MAD (DevState::mad, sigma_cur, sigma[pair] if pair >= 0)
 cudaError_t launch_select(DevState* st, int which, int pair, int sms, cudaStream_t s);
@@ -181,8 +187,8 @@ cudaError_t launch_std_final(DevState* st, int pair, cudaStream_t s);
 cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,
                                cudaStream_t s);
 cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s);
-cudaError_t launch_pack(const uint8_t* m8, long long n, uint32_t* mbits, cudaStream_t s);
-cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, cudaStream_t s);
+cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s);
+cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s);
 cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s);
 cudaError_t launch_identity(const SmoothArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);

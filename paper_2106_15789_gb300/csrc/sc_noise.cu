@@ -143,6 +143,54 @@ __device__ unsigned long long f_sure(const PlanCtx& P, float T) {
   return cum_range(P, bin_of(lo, P.cfg) + 1, bin_of(hi, P.cfg) - 1);
 }
 
+// Class of a 16-bit cell of the float encoding (sign, 8 exponent bits, top
+// 7 mantissa bits). Every histogram bin is a union of whole cells (bins
+// resolve at most 7 mantissa bits), so the median and MAD classes are exact
+// functions of the cell. CLS_SURE marks cells wholly above thr_hi in |s| (all
+// their values are detected whatever sigma is); CLS_AMB marks cells that
+// overlap (thr_lo, thr_hi] and is refined per value by the candidate pass.
+constexpr int kClsCells = (int)kClassTableBytes;
+enum : unsigned int { CLS_MED = 1u, CLS_MAD = 2u, CLS_AMB = 4u, CLS_SURE = 8u };
+
+__device__ __forceinline__ unsigned int cell_class(unsigned int cell, const NoisePlan& p, BinCfg cfg, bool med,
+                                                   bool mad, bool amb) {
+  const unsigned int u = cell << 16;
+  if (((u >> 23) & 0xffu) == 0xffu) return 0u;  // Inf and NaN are never candidates
+  const int b = bin_of_bits(u, cfg);
+  unsigned int k = 0u;
+  if (med && b >= p.b_med_lo && b <= p.b_med_hi) k |= CLS_MED;
+  if (mad && b >= p.bA_lo && b <= p.bA_hi && !(b >= p.bB_lo && b <= p.bB_hi)) k |= CLS_MAD;
+  if (amb) {
+    const float lo = fabsf(__uint_as_float(u)), hi = fabsf(__uint_as_float(u | 0xffffu));
+    if (hi > p.thr_lo && lo <= p.thr_hi) k |= CLS_AMB;
+    if (lo > p.thr_hi) k |= CLS_SURE;
+  }
+  return k;
+}
+
+// All threads of the block write the 64 KiB class table (one byte per cell).
+__device__ void fill_class_table(const NoisePlan& p, BinCfg cfg, unsigned char* cls) {
+  const bool live = !(p.flags & (PLAN_EMPTY | PLAN_STD));
+  const bool med = live && !(p.flags & PLAN_MED_FULL);
+  const bool mad = live && !(p.flags & PLAN_MAD_FULL);
+  const bool amb = live && (p.flags & PLAN_CLIP) && !(p.flags & PLAN_CLIP_FULL);
+  for (int i = threadIdx.x; i < kClsCells / 16; i += blockDim.x) {
+    unsigned int w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      unsigned int x = 0u;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) x |= cell_class((unsigned)(i * 16 + j * 4 + b), p, cfg, med, mad, amb) << (8 * b);
+      w[j] = x;
+    }
+    reinterpret_cast<uint4*>(cls)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+__device__ __noinline__ NoisePlan plan_of(DevState* st, const unsigned long long* cum, int win, const float* src,
+                                          long long n_total, Lists L, float threshold, int clip, int std_mode,
+                                          unsigned int force_flags);
+
 __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long long* __restrict__ hist, int win,
                                                const float* src, long long n_total, Lists L, float threshold,
                                                int clip, int std_mode, unsigned int force_flags) {
@@ -189,8 +237,20 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
     (&st->sel_mad.hist[0][0])[i] = 0ull;
   }
   __syncthreads();
-  if (tid != 0) return;
+  __shared__ NoisePlan s_plan;
+  if (tid == 0) s_plan = plan_of(st, cum, win, src, n_total, L, threshold, clip, std_mode, force_flags);
+  __syncthreads();
+  if (L.cls != nullptr) {
+    BinCfg cfg = kFullRange;
+    if (win) cfg = st->win;
+    fill_class_table(s_plan, cfg, L.cls);
+  }
+}
 
+// The plan proper (one thread). Returns the plan it stored in st->plan.
+__device__ __noinline__ NoisePlan plan_of(DevState* st, const unsigned long long* cum, int win, const float* src,
+                                          long long n_total, Lists L, float threshold, int clip, int std_mode,
+                                          unsigned int force_flags) {
   NoisePlan p;
   p.flags = (int)force_flags;
   p.threshold = threshold;
@@ -204,6 +264,11 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
   p.T1 = 0.0f;
   p.T2 = INFINITY;
   p.bound_med = p.bound_mad = p.bound_amb = 0ull;
+  p.bA_lo = 0;
+  p.bA_hi = kNumBins - 1;
+  p.bB_lo = 1;
+  p.bB_hi = 0;
+  p.n_B = 0ull;
   const unsigned long long n = cum[kNumBins];
   p.n = n;
   st->n_cand_med = st->n_cand_mad = st->n_amb = st->n_below = 0ull;
@@ -225,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
     p.flags |= PLAN_EMPTY;
     st->status |= SC_ST_ALLNAN;
     st->plan = p;
-    return;
+    return p;
   }
   p.k_lo = (n - 1ull) / 2ull;
   p.k_hi = n / 2ull;
@@ -263,6 +328,12 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
         p.has_B = 1;
         p.B_lo = f_up(P.m_max - (double)p.T1);
         p.B_hi = f_down(P.m_min + (double)p.T1);
+        // B as whole bins strictly inside [B_lo, B_hi]: its count is exact
+        // from the histogram, so the candidate pass need not count it.
+        if (p.B_lo <= p.B_hi) {
+          p.bB_lo = bin_of(p.B_lo, cfg) + 1;
+          p.bB_hi = bin_of(p.B_hi, cfg) - 1;
+        }
       }
       // T2: smallest T with surely-within count >= k_hi + 1 (then MAD < T2)
       const unsigned int fmax_bits = 0x7f7fffffu;
@@ -277,12 +348,10 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
         p.A_hi = f_up(P.m_max + (double)p.T2);
       }
       // bound on the MAD candidates: values neither surely inside nor outside
-      const int bA0 = bin_of(p.A_lo, cfg), bA1 = bin_of(p.A_hi, cfg);
-      if (p.has_B && p.B_lo <= p.B_hi) {
-        p.bound_mad = cum_range(P, bA0, bin_of(p.B_lo, cfg)) + cum_range(P, bin_of(p.B_hi, cfg), bA1);
-      } else {
-        p.bound_mad = cum_range(P, bA0, bA1);
-      }
+      p.bA_lo = bin_of(p.A_lo, cfg);
+      p.bA_hi = bin_of(p.A_hi, cfg);
+      p.n_B = cum_range(P, p.bB_lo, p.bB_hi);  // B lies inside A: its values are within T1 < T2
+      p.bound_mad = cum_range(P, p.bA_lo, p.bA_hi) - p.n_B;
       if (p.bound_mad > L.cap.mad) p.flags |= PLAN_MAD_FULL;
       if (clip) {
         if (!p.has_B || !(p.T1 > 0.0f) || !isfinite(p.T2)) {
@@ -310,9 +379,11 @@ __global__ void __launch_bounds__(1024) k_plan(DevState* st, const unsigned long
   st->sel_mad.count_fixed = mad_full ? (unsigned long long)n_total : L.cap.mad;
   st->sel_mad.count_ptr = mad_full ? nullptr : &st->n_cand_mad;
   st->sel_mad.mode = SEL_ABSDEV;
-  st->sel_mad.rank_lo = p.k_lo;  // minus n_below (known after k_pass2) unless full
+  st->sel_mad.rank_lo = p.k_lo;  // minus n_below unless full
   st->sel_mad.rank_hi = p.k_hi;
+  st->n_below = mad_full ? 0ull : p.n_B;
   st->plan = p;
+  return p;
 }
 
 cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, const float* src, long long n_total,
@@ -324,18 +395,19 @@ cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, c
 }
 
 // ---------------------------------------------------------------------------
-// Candidate pass. Each warp handles chunks of 128 consecutive values (4 per
-// lane) and stages list entries in its own shared-memory region, flushing to
-// the global lists with one atomic per >= 64 entries.
-constexpr int kStage = 192;   // entries per warp and list
-constexpr int kFlushAt = 64;  // flush when more than this many are staged
-
-struct WarpStage {
-  float* med;
-  float* mad;
-  unsigned long long* amb;
-  int nmed, nmad, namb;
-};
+// Candidate pass. A warp takes chunks of 128 consecutive values; lane l reads
+// values l, l + 32, l + 64 and l + 96 of a chunk, so one ballot per read is
+// exactly one word of the bit mask. Each value costs a class-table lookup
+// (shared memory), whose SURE bit feeds the mask ballot; the few values whose
+// cell is a candidate cell take the slow path, which stages list entries in the warp's own
+// shared-memory region and flushes them with one atomic per batch.
+constexpr int kP2Threads = 512;
+constexpr int kP2Warps = kP2Threads / 32;
+constexpr int kP2Unroll = 4;                 // chunks in flight per warp
+constexpr int kP2FlushAt = 64;               // flush a list holding more than this after a chunk
+constexpr int kP2Stage = kP2FlushAt + 128;   // one chunk adds at most 128 entries per list
+constexpr size_t kP2Smem =
+    kClsCells + (size_t)kP2Warps * kP2Stage * (2 * sizeof(float) + sizeof(unsigned long long));
 
 template <typename T>
 __device__ __forceinline__ void stage_flush(T* stage, int& cnt, T* glob, unsigned long long* gcount,
@@ -354,120 +426,107 @@ __device__ __forceinline__ void stage_flush(T* stage, int& cnt, T* glob, unsigne
   cnt = 0;
 }
 
+// Appends val from the lanes whose bit is set in b (the warp's ballot of pred).
 template <typename T>
-__device__ __forceinline__ void stage_push(bool pred, T val, T* stage, int& cnt) {
-  const unsigned int b = __ballot_sync(0xffffffffu, pred);
-  if (pred) {
-    const int off = __popc(b & ((1u << (threadIdx.x & 31)) - 1u));
-    stage[cnt + off] = val;
-  }
+__device__ __forceinline__ void stage_push(unsigned int b, bool pred, unsigned int lanes_below, T val, T* stage,
+                                           int& cnt) {
+  if (pred) stage[cnt + __popc(b & lanes_below)] = val;
   cnt += __popc(b);
 }
 
-// Smallest and largest order-preserving key of histogram bin b (the bins are
-// contiguous key ranges): found by bisection on bin_of over keys.
-__device__ unsigned int bin_key_lo(int b, BinCfg cfg) {
-  unsigned int lo = 0u, hi = 0xffffffffu;  // first key whose bin >= b
-  while (lo < hi) {
-    const unsigned int mid = lo + ((hi - lo) >> 1);
-    if (bin_of(fkey_inv(mid), cfg) >= b) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
-constexpr int kPass2Unroll = 4;  // chunks of 128 values in flight per warp
-
-__global__ void __launch_bounds__(256) k_pass2(const float* __restrict__ src, long long n, uint32_t* mbits,
-                                               DevState* st, Lists L, int win) {
-  __shared__ float sh_med[8][kStage];
-  __shared__ float sh_mad[8][kStage];
-  __shared__ unsigned long long sh_amb[8][kStage];
-  __shared__ unsigned int s_keys[2];
+__global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict__ src, long long n,
+                                                         uint32_t* mbits, DevState* st, Lists L) {
+  extern __shared__ __align__(16) unsigned char p2_smem[];
   const NoisePlan p = st->plan;
   if (p.flags & (PLAN_EMPTY | PLAN_STD)) return;
-  const BinCfg cfg = win ? st->win : kFullRange;
-  const bool do_med = !(p.flags & PLAN_MED_FULL);
-  const bool do_mad = !(p.flags & PLAN_MAD_FULL);
-  const bool do_clip = (p.flags & PLAN_CLIP) && !(p.flags & PLAN_CLIP_FULL);
-  if (!do_med && !do_mad && !do_clip) return;
-  // median candidates = keys in [key_lo, key_hi] (exact for -0 / +0)
-  if (threadIdx.x == 0) {
-    s_keys[0] = bin_key_lo(p.b_med_lo, cfg);
-    s_keys[1] = p.b_med_hi + 1 < kNumBins ? bin_key_lo(p.b_med_hi + 1, cfg) - 1u : 0xffffffffu;
-  }
-  __syncthreads();
-  const unsigned int key_lo = s_keys[0], key_hi = s_keys[1];
+  const bool do_clip = (p.flags & PLAN_CLIP) && !(p.flags & PLAN_CLIP_FULL) && mbits != nullptr;
+  if ((p.flags & PLAN_MED_FULL) && (p.flags & PLAN_MAD_FULL) && !do_clip) return;
+  unsigned char* cls = p2_smem;
+  for (int i = threadIdx.x; i < kClsCells / 16; i += kP2Threads)
+    reinterpret_cast<uint4*>(cls)[i] = __ldg(reinterpret_cast<const uint4*>(L.cls) + i);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* smed = sh_med[warp];
-  float* smad = sh_mad[warp];
-  unsigned long long* samb = sh_amb[warp];
+  float* smed = reinterpret_cast<float*>(p2_smem + kClsCells) + warp * kP2Stage;
+  float* smad = reinterpret_cast<float*>(p2_smem + kClsCells) + (kP2Warps + warp) * kP2Stage;
+  unsigned long long* samb =
+      reinterpret_cast<unsigned long long*>(p2_smem + kClsCells + 2 * kP2Warps * kP2Stage * sizeof(float)) +
+      warp * kP2Stage;
+  __syncthreads();
+  const float thr_lo = p.thr_lo, thr_hi = p.thr_hi;
+  const unsigned int lanes_below = (1u << lane) - 1u;
   int nmed = 0, nmad = 0, namb = 0;
-  unsigned long long below = 0;
-  const long long nchunks = (n + 127) / 128;
-  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
-  const long long wstride = (long long)gridDim.x * 8 * kPass2Unroll;
-  for (long long ch0 = ((long long)blockIdx.x * 8 + warp) * kPass2Unroll; ch0 < nchunks; ch0 += wstride) {
-    float a[kPass2Unroll][4];
+  const long long nchunks = (n + 127) >> 7;
+  const long long wstride = (long long)gridDim.x * kP2Warps * kP2Unroll;
+  for (long long ch0 = ((long long)blockIdx.x * kP2Warps + warp) * kP2Unroll; ch0 < nchunks; ch0 += wstride) {
+    // values past n read as NaN: class 0, never sure, never listed
+    float a[kP2Unroll][4];
+    const float* base = src + ch0 * 128 + lane;
+    if ((ch0 + kP2Unroll) * 128 <= n) {
 #pragma unroll
-    for (int u = 0; u < kPass2Unroll; ++u) {
-      const long long v0 = (ch0 + u) * 128 + lane * 4;
-      if (vec && v0 + 3 < n) {
-        const float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
-        a[u][0] = t4.x; a[u][1] = t4.y; a[u][2] = t4.z; a[u][3] = t4.w;
-      } else {
+      for (int u = 0; u < kP2Unroll; ++u)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) a[u][c] = (v0 + c < n) ? __ldg(src + v0 + c) : __int_as_float(0x7fc00000);
-      }
+        for (int c = 0; c < 4; ++c) a[u][c] = __ldg(base + 128 * u + 32 * c);
+    } else {
+#pragma unroll
+      for (int u = 0; u < kP2Unroll; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const long long v = (ch0 + u) * 128 + 32 * c + lane;
+          a[u][c] = v < n ? __ldg(src + v) : __int_as_float(0x7fc00000);
+        }
     }
 #pragma unroll
-    for (int u = 0; u < kPass2Unroll; ++u) {
+    for (int u = 0; u < kP2Unroll; ++u) {
       const long long ch = ch0 + u;
-      if (ch >= nchunks) break;
-      const long long v0 = ch * 128 + lane * 4;
-      unsigned int sure_bits[4];
+      unsigned int k[4], sure_w[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) k[c] = cls[__float_as_uint(a[u][c]) >> 16];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sure_w[c] = __ballot_sync(0xffffffffu, (k[c] & CLS_SURE) != 0u);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const float s = a[u][c];
-        const bool fin = (__float_as_uint(s) & 0x7f800000u) != 0x7f800000u;
-        const unsigned int k = fkey(s);
-        const bool pm = do_med && fin && k >= key_lo && k <= key_hi;
-        const bool inB = do_mad && p.has_B && s >= p.B_lo && s <= p.B_hi;  // NaN compares false
-        const bool pa = do_mad && !inB && s >= p.A_lo && s <= p.A_hi && fin;
-        const float as = fabsf(s);
-        const bool sure = do_clip && fin && as > p.thr_hi;
-        const bool pamb = do_clip && fin && !sure && as > p.thr_lo;
-        const unsigned int bB = __ballot_sync(0xffffffffu, inB);
-        below += (lane == 0) ? (unsigned long long)__popc(bB) : 0ull;
-        if (__any_sync(0xffffffffu, pm || pa || pamb)) {
-          stage_push(pm, s, smed, nmed);
-          stage_push(pa, s, smad, nmad);
-          stage_push(pamb, (unsigned long long)(v0 + c), samb, namb);
+        if (__any_sync(0xffffffffu, (k[c] & ~CLS_SURE) != 0u)) {
+          const float s = a[u][c];
+          const float as = fabsf(s);
+          const bool pm = (k[c] & CLS_MED) != 0u, pa = (k[c] & CLS_MAD) != 0u;
+          const bool amb_cell = (k[c] & CLS_AMB) != 0u;  // finite: the cell is not Inf / NaN
+          const bool sure = amb_cell && as > thr_hi;
+          const bool pamb = amb_cell && as > thr_lo && !sure;
+          sure_w[c] |= __ballot_sync(0xffffffffu, sure);
+          const unsigned int bmed = __ballot_sync(0xffffffffu, pm);
+          const unsigned int bmad = __ballot_sync(0xffffffffu, pa);
+          const unsigned int bamb = __ballot_sync(0xffffffffu, pamb);
+          stage_push(bmad, pa, lanes_below, s, smad, nmad);
+          stage_push(bmed, pm, lanes_below, s, smed, nmed);
+          stage_push(bamb, pamb, lanes_below, (unsigned long long)(ch * 128 + 32 * c + lane), samb, namb);
         }
-        sure_bits[c] = __ballot_sync(0xffffffffu, sure);
       }
-      if (do_clip && lane < 4) {
-        unsigned int w = 0u;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) w |= spread4(sure_bits[c] >> (8 * lane)) << c;
-        const long long wi = ch * 4 + lane;
-        if (w && wi * 32 < n) mbits[wi] |= w;
+      {
+        // lane c owns mask word 4 * ch + c of this chunk (no SURE cells, so
+        // no words, without a clip)
+        unsigned int w = sure_w[0];
+        w = lane == 1 ? sure_w[1] : w;
+        w = lane == 2 ? sure_w[2] : w;
+        w = lane == 3 ? sure_w[3] : w;
+        if (do_clip && lane < 4 && w != 0u) atomicOr(mbits + ch * 4 + lane, w);
       }
-      if (nmed > kFlushAt) stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
-      if (nmad > kFlushAt) stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
-      if (namb > kFlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
+      if (max(nmad, max(nmed, namb)) > kP2FlushAt) {
+        if (nmad > kP2FlushAt) stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
+        if (nmed > kP2FlushAt) stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
+        if (namb > kP2FlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
+      }
     }
   }
   stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
   stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
   stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
-  if (lane == 0 && below) atomicAdd(&st->n_below, below);  // lane 0 counted the whole warp
 }
 
-cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int win, int sms,
+cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int sms,
                          cudaStream_t s) {
-  long long want = (n + 1024 * kPass2Unroll - 1) / (1024 * kPass2Unroll);
-  int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
-  k_pass2<<<grid, 256, 0, s>>>(src, n, mbits, st, L, win);
+  const long long chunks = (n + 127) / 128;
+  long long want = (chunks + kP2Warps * kP2Unroll - 1) / (kP2Warps * kP2Unroll);
+  int grid = (int)(want < 1 ? 1 : (want > 2LL * sms ? 2LL * sms : want));
+  k_pass2<<<grid, kP2Threads, kP2Smem, s>>>(src, n, mbits, st, L);
   return cudaGetLastError();
 }
 
@@ -855,26 +914,31 @@ cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeight
 
 // ---------------------------------------------------------------------------
 // uint8 mask <-> 1-bit working mask.
-__global__ void k_pack(const uint8_t* __restrict__ m8, long long n, uint32_t* __restrict__ mbits) {
+// Working mask from a caller's uint8 mask: a bit for every set voxel whose
+// cube value is finite (non-finite voxels are never replaced, and no clip
+// ever sets their bit, so the working mask holds finite voxels only).
+__global__ void k_pack(const uint8_t* __restrict__ m8, const float* __restrict__ cube, long long n,
+                       uint32_t* __restrict__ mbits) {
   const long long nw = (n + 31) / 32;
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (long long)gridDim.x * blockDim.x) {
     unsigned int bits = 0u;
     const long long v0 = w * 32;
     for (int i = 0; i < 32; ++i)
-      if (v0 + i < n && m8[v0 + i]) bits |= 1u << i;
+      if (v0 + i < n && m8[v0 + i] && isfinite(__ldg(cube + v0 + i))) bits |= 1u << i;
     mbits[w] = bits;
   }
 }
-
-cudaError_t launch_pack(const uint8_t* m8, long long n, uint32_t* mbits, cudaStream_t s) {
+cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s) {
   long long nw = (n + 31) / 32;
   long long want = (nw + 255) / 256;
   int grid = (int)(want < 1 ? 1 : (want > 4096 ? 4096 : want));
-  k_pack<<<grid, 256, 0, s>>>(m8, n, mbits);
+  k_pack<<<grid, 256, 0, s>>>(m8, cube, n, mbits);
   return cudaGetLastError();
 }
 
-__global__ void k_expand(const uint32_t* __restrict__ mbits, long long n, uint8_t* __restrict__ m8) {
+// uint8 mask from the working mask; with keep, OR-ed into the caller's mask
+// (whose set voxels at non-finite values the working mask does not hold).
+__global__ void k_expand(const uint32_t* __restrict__ mbits, long long n, uint8_t* __restrict__ m8, int keep) {
   // each thread writes 16 bytes
   const bool vec = ((reinterpret_cast<uintptr_t>(m8) & 15u) == 0);
   const long long ng = (n + 15) / 16;
@@ -882,33 +946,37 @@ __global__ void k_expand(const uint32_t* __restrict__ mbits, long long n, uint8_
     const long long v0 = g * 16;
     const unsigned int w = __ldg(mbits + (v0 >> 5)) >> (v0 & 31);
     if (vec && v0 + 16 <= n) {
-      uint4 o;
+      uint4 o = keep ? *reinterpret_cast<const uint4*>(m8 + v0) : make_uint4(0u, 0u, 0u, 0u);
       unsigned int* po = &o.x;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         unsigned int b = 0u;
 #pragma unroll
         for (int i = 0; i < 4; ++i) b |= ((w >> (4 * q + i)) & 1u) << (8 * i);
-        po[q] = b;
+        // 0x01 in every byte of the caller's word that is non-zero
+        const unsigned int t = po[q];
+        const unsigned int nz = ((((t & 0x7f7f7f7fu) + 0x7f7f7f7fu) | t) >> 7) & 0x01010101u;
+        po[q] = keep ? (b | nz) : b;
       }
       *reinterpret_cast<uint4*>(m8 + v0) = o;
     } else {
-      for (int i = 0; i < 16 && v0 + i < n; ++i) m8[v0 + i] = (uint8_t)((w >> i) & 1u);
+      for (int i = 0; i < 16 && v0 + i < n; ++i)
+        m8[v0 + i] = (uint8_t)((((w >> i) & 1u) != 0u || (keep && m8[v0 + i] != 0)) ? 1u : 0u);
     }
   }
 }
-
-cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, cudaStream_t s) {
+cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s) {
   long long ng = (n + 15) / 16;
   long long want = (ng + 255) / 256;
   int grid = (int)(want < 1 ? 1 : (want > 8192 ? 8192 : want));
-  k_expand<<<grid, 256, 0, s>>>(mbits, n, m8);
+  k_expand<<<grid, 256, 0, s>>>(mbits, n, m8, keep);
   return cudaGetLastError();
 }
 
 void init_noise_attrs() {
   cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((kNumBins + 1) * sizeof(unsigned long long)));
+  cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
 }
 
 }  // namespace sc

@@ -245,13 +245,21 @@ void choose_tiles(SmoothArgs* a) {
 }
 
 cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
+cudaError_t launch_smooth_ws(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 void init_tile_attrs();
+void init_ws_attrs();
 void init_z_attrs();
 
 cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* launches) {
   bool done = false;
   cudaError_t et = launch_smooth_z(a0, sms, s, &done);
+  if (et != cudaSuccess) return et;
+  if (done) {
+    if (launches) ++*launches;
+    return cudaSuccess;
+  }
+  et = launch_smooth_ws(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
   if (done) {
     if (launches) ++*launches;
@@ -291,6 +299,7 @@ void init_noise_attrs();
 void init_kernel_attrs() {
   cudaFuncSetAttribute(k_smooth_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   init_tile_attrs();
+  init_ws_attrs();
   init_z_attrs();
   init_noise_attrs();
 }

@@ -32,6 +32,7 @@
 
 #include "sc_device.cuh"
 #include "sc_internal.h"
+#include "sc_tile_common.cuh"
 
 namespace sc {
 
@@ -41,8 +42,8 @@ constexpr int kThreads = 512;
 constexpr int TX = 64, TY = 32;
 constexpr int SEGX = 8, SEGY = 4;
 constexpr int kMaxWz = 15;                 // TMEM ring: 16 slots of 4 int64 per thread
-constexpr long long kMaxSpins = 1LL << 24;  // bound of every mbarrier wait
 constexpr int kStages = 3;                  // raw-tile buffers (loads run two planes ahead)
+using namespace tc;
 
 template <int W1, int W2, int W3>
 struct Geo {
@@ -60,8 +61,6 @@ struct Geo {
 struct Smem {
   size_t raw[3], mw, x, b, hist, mbar, total;
 };
-
-__host__ __device__ constexpr size_t al128(size_t v) { return (v + 127) & ~(size_t)127; }
 
 template <int W1, int W2, int W3>
 __host__ __device__ constexpr Smem smem_layout(bool hist) {
@@ -86,115 +85,10 @@ __host__ __device__ constexpr Smem smem_layout(bool hist) {
   return s;
 }
 
-// Streams NOUT + W1 + W2 + W3 - 3 inputs load(i) through the three boxcars
-// (all indices compile-time after unrolling); out(k, v) gets output k.
-template <int W1, int W2, int W3, int NOUT, class Load, class Out>
-__device__ __forceinline__ void cascade_stream(Load load, Out out) {
-  constexpr int N0 = NOUT + (W1 - 1) + (W2 - 1) + (W3 - 1);
-  long long h1[W1], h2[W2], h3[W3];
-  long long s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-  for (int i = 0; i < N0; ++i) {
-    const long long x = load(i);
-    if (W1 == 1) {
-      s1 = x;
-    } else {
-      s1 += x;
-      if (i >= W1) s1 -= h1[i % W1];
-      h1[i % W1] = x;
-    }
-    if (i >= W1 - 1) {
-      const int i1 = i - (W1 - 1);
-      if (W2 == 1) {
-        s2 = s1;
-      } else {
-        s2 += s1;
-        if (i1 >= W2) s2 -= h2[i1 % W2];
-        h2[i1 % W2] = s1;
-      }
-      if (i1 >= W2 - 1) {
-        const int i2 = i1 - (W2 - 1);
-        if (W3 == 1) {
-          s3 = s2;
-        } else {
-          s3 += s2;
-          if (i2 >= W3) s3 -= h3[i2 % W3];
-          h3[i2 % W3] = s2;
-        }
-        if (i2 >= W3 - 1) out(i2 - (W3 - 1), s3);
-      }
-    }
-  }
-}
-
-// ---- Tensor Memory (TMEM) as ring storage --------------------------------
-// The block allocates all 512 columns of its SM's TMEM. Warp w may touch
-// lanes 32*(w%4) .. +31; the 16 warps take columns 128*(w/4) .. +127, so each
-// thread owns 128 32-bit words of one lane: 16 ring slots of 4 int64.
-constexpr int kTmemCols = 512;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void tmem_alloc(unsigned* holder) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
-               "r"(kTmemCols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(unsigned base) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(kTmemCols) : "memory");
-}
-__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, unsigned (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&v)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
-               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
-}
+// TMEM ring: 16 warps; warp w uses lanes 32*(w%4) and columns 128*(w/4) ..
+// +127, so each thread owns 128 32-bit words of one lane: 16 ring slots of
+// 4 int64.
 constexpr int kSlotCols = 2 * SEGY;  // TMEM columns per ring slot
-
-// ---- mbarrier / TMA / cp.async --------------------------------------------
-__device__ __forceinline__ void mbar_init(unsigned addr) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned addr, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
-}
-// Bounded wait for the barrier phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity) {
-  for (long long it = 0; it < kMaxSpins; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void cp_async4(unsigned dst, const float* src, bool valid) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one_pending() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 }  // namespace tile
 
@@ -234,7 +128,7 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
   __shared__ unsigned tmem_holder;
   if (warp == 0) tmem_alloc(&tmem_holder);
   if (TMA && tid == 0) {
-    for (int b = 0; b < kStages; ++b) mbar_init(mbar0 + 8 * b);
+    for (int b = 0; b < kStages; ++b) mbar_init(mbar0 + 8 * b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -443,31 +337,6 @@ __global__ void __launch_bounds__(tile::kThreads, 1)
 // ---------------------------------------------------------------------------
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    cudaGetLastError();
-  }
-  return fn;
-}
-
-template <typename K>
-void set_dyn_smem_limit(K kernel) {
-  cudaFuncAttributes fa{};
-  int dev = 0, optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-}
-
 template <int W1, int W2, int W3>
 cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done) {
   using namespace tile;
@@ -490,27 +359,10 @@ cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* don
   const int grid = (int)(items < sms ? items : sms);
   // TMA needs 16-byte aligned rows and base address
   CUtensorMap map;
-  memset(&map, 0, sizeof(map));
-  bool tma = (a.nx % 4 == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tma ? tensor_map_encoder() : nullptr;
-  if (enc) {
-    const cuuint64_t dims[3] = {(cuuint64_t)a.nx, (cuuint64_t)a.ny, (cuuint64_t)a.nz};
-    const cuuint64_t strides[2] = {(cuuint64_t)a.nx * 4, (cuuint64_t)a.nx * a.ny * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)G::BX, (cuuint32_t)G::BY, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a.C), dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    tma = (cr == CUDA_SUCCESS);
-  } else {
-    tma = false;
-  }
+  const bool tma = tc::encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY);
   const bool repl = a.mbits != nullptr && a.repl_possible;
-  // one block per SM (it holds all of the SM's TMEM): at least half the shared memory
-  int dev = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const size_t smem_req = L.total > (size_t)per_sm / 2 + 1024 ? L.total : (size_t)per_sm / 2 + 1024;
+  // one block per SM (it holds all of the SM's TMEM)
+  const size_t smem_req = tc::one_block_per_sm_smem(L.total);
   if (tma) {
     if (repl) k_smooth_tile<W1, W2, W3, true, true><<<grid, kThreads, smem_req, s>>>(map, a);
     else k_smooth_tile<W1, W2, W3, true, false><<<grid, kThreads, smem_req, s>>>(map, a);
@@ -524,10 +376,10 @@ cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* don
 
 template <int W1, int W2, int W3>
 void set_attr() {
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, false>);
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, false>);
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, true>);
-  set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, true>);
+  tc::set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, false>);
+  tc::set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, false>);
+  tc::set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, false, true>);
+  tc::set_dyn_smem_limit(k_smooth_tile<W1, W2, W3, true, true>);
 }
 
 }  // namespace

@@ -12,6 +12,7 @@
 
 #include "sc_device.cuh"
 #include "sc_internal.h"
+#include "sc_tile_common.cuh"
 
 namespace sc {
 namespace zonly {
@@ -249,13 +250,6 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
 
 namespace {
 
-size_t one_block_per_sm_smem(size_t need) {
-  int dev = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  const size_t half = (size_t)per_sm / 2 + 1024;
-  return need > half ? need : half;
-}
 
 template <int VPT, bool VEC, bool REPL>
 void set_z_attr() {
@@ -293,7 +287,7 @@ cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   // of the shared memory
   const size_t need = sizeof(float) * zonly::kDepth * zonly::kThreads * VPT + 8 * zonly::kDepth * zonly::kThreads +
                       (a.hist ? sizeof(unsigned) * kNumBins : 0);
-  const size_t smem = one_block_per_sm_smem(need);
+  const size_t smem = tc::one_block_per_sm_smem(need);
   k_smooth_z<VPT, VEC, REPL><<<grid, zonly::kThreads, smem, s>>>(a);
   return cudaGetLastError();
 }

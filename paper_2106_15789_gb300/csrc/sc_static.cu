@@ -36,7 +36,8 @@ constexpr size_t kOffState = 0;
 constexpr size_t kOffHist = align_up(kOffState + sizeof(DevState));
 constexpr size_t kOffMed = align_up(kOffHist + sizeof(unsigned long long) * kNumBins);
 constexpr size_t kOffMad = align_up(kOffMed + sizeof(float) * kStaticCapMed);
-constexpr size_t kStaticBytes = align_up(kOffMad + sizeof(float) * kStaticCapMad);
+constexpr size_t kOffCls = align_up(kOffMad + sizeof(float) * kStaticCapMad);
+constexpr size_t kStaticBytes = align_up(kOffCls + kClassTableBytes);
 
 // The scratch itself. In host code this name is a host-side stand-in, not a
 // device address: only the pointer from cudaGetSymbolAddress goes to kernels.
@@ -89,6 +90,7 @@ extern "C" int sc_noise_static(const float* data_dev, int64_t n, int noise_mode,
   L.med = reinterpret_cast<float*>(base + kOffMed);
   L.mad = reinterpret_cast<float*>(base + kOffMad);
   L.amb = nullptr;
+  L.cls = base + kOffCls;
   L.cap = Caps{kStaticCapMed, kStaticCapMad, 0ull};
   const int std_mode = (noise_mode == SC_NOISE_STD);
   // the previous call's contents stay in the array: clear state and histogram
@@ -100,7 +102,7 @@ extern "C" int sc_noise_static(const float* data_dev, int64_t n, int noise_mode,
     CKS(launch_std(data_dev, n, st, sms, s));
     CKS(launch_std_final(st, SC_MAX_KERNELS, s));
   } else {
-    CKS(launch_pass2(data_dev, n, nullptr, st, L, 0, sms, s));
+    CKS(launch_pass2(data_dev, n, nullptr, st, L, sms, s));
     CKS(launch_select(st, 0, -1, sms, s));
     CKS(launch_select(st, 1, SC_MAX_KERNELS, sms, s));
   }
