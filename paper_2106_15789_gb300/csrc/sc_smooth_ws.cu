@@ -141,6 +141,53 @@ __host__ __device__ constexpr Smem smem_layout(bool hist) {
   return s;
 }
 
+// Quantise the halo'd raw tile into X, in chunks of kConvChunk elements whose
+// loads are all issued before their stores (the pointers do not alias).
+constexpr int kConvChunk = 4;
+template <int W1, int W2, int W3, bool REPL>
+__device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const unsigned* __restrict__ mwb,
+                                             long long* __restrict__ X, int pt, float fscale, long long qrepl,
+                                             bool do_repl) {
+  using G = Geo<W1, W2, W3>;
+  constexpr int R = G::R, RA = G::RA;
+#pragma unroll
+  for (int k0 = 0; k0 < G::NCONV; k0 += kConvChunk) {
+    float v[kConvChunk];
+    unsigned word[kConvChunk];
+#pragma unroll
+    for (int i = 0; i < kConvChunk; ++i) {
+      const int k = k0 + i, e = pt + k * kPT;
+      const bool ok = k < G::NCONV && (k + 1 < G::NCONV || e < G::BY * G::PX);
+      const int row = e / G::PX, col = e - row * G::PX;
+      v[i] = ok ? rb[row * G::BX + col + (RA - R)] : 0.0f;
+      word[i] = (REPL && do_repl && ok) ? mwb[row * 4 + (col >> 5)] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < kConvChunk; ++i) {
+      const int k = k0 + i, e = pt + k * kPT;
+      if (k < G::NCONV && (k + 1 < G::NCONV || e < G::BY * G::PX)) {
+        const int row = e / G::PX, col = e - row * G::PX;
+        // v + (v - v) is NaN for NaN and Inf, whose quantised value is 0;
+        // the working mask holds finite voxels only
+        long long q = quantize(v[i] + (v[i] - v[i]), fscale);
+        if (REPL && do_repl) {
+          const long long qr = v[i] >= 0.0f ? qrepl : -qrepl;
+          q = ((word[i] >> (col & 31)) & 1u) ? qr : q;
+        }
+        X[row * G::XP + col] = q;
+      }
+    }
+  }
+}
+
+// x cascade of one row segment (SEGX outputs). The pointers do not alias, so
+// the stream's loads need not wait for its stores.
+template <int W1, int W2, int W3>
+__device__ __forceinline__ void xpass_item(const long long* __restrict__ src, long long* __restrict__ dst) {
+  using G = Geo<W1, W2, W3>;
+  cascade_stream<W1, W2, W3, G::SEGX>([&](int i) { return src[i]; }, [&](int k, long long v) { dst[k] = v; });
+}
+
 }  // namespace ws
 
 template <int W1, int W2, int W3, bool REPL>
@@ -271,23 +318,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const unsigned* mwb = mw + b * 4 * G::BY;
         long long* const X = Xt + (G::XBUF == 2 ? (size_t)b * G::BY * G::XP : 0);
         // quantise the halo'd tile once
-#pragma unroll
-        for (int k = 0; k < G::NCONV; ++k) {
-          const int e = pt + k * kPT;
-          if (k + 1 < G::NCONV || e < G::BY * G::PX) {
-            const int row = e / G::PX, col = e - row * G::PX;
-            const float v = rb[row * G::BX + col + (RA - R)];
-            // v + (v - v) is NaN for NaN and Inf, whose quantised value is 0;
-            // the working mask holds finite voxels only
-            long long q = quantize(v + (v - v), fscale);
-            if (do_repl) {
-              const unsigned word = mwb[row * 4 + (col >> 5)];
-              const long long qr = v >= 0.0f ? qrepl : -qrepl;
-              q = ((word >> (col & 31)) & 1u) ? qr : q;
-            }
-            X[row * G::XP + col] = q;
-          }
-        }
+        convert_tile<W1, W2, W3, REPL>(rb, mwb, X, pt, fscale, qrepl, do_repl);
         if (do_repl && j + 1 < n_steps && pt < 4 * G::BY) mw[((g + 1) & 1) * 4 * G::BY + pt] = mask_finish(x0, m_next);
         m_next = m_after;
         // quantised tile and next mask words done; with two tiles, also every
@@ -297,9 +328,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         // x pass into buffer b
         if (pt < G::XITEMS) {
           const int row = pt % G::BY, seg = pt / G::BY;
-          const long long* src = X + row * G::XP + seg * G::SEGX;
-          long long* dst = Bt + (size_t)b * G::BY * G::BP + row * G::BP + seg * G::SEGX;
-          cascade_stream<W1, W2, W3, G::SEGX>([&](int i) { return src[i]; }, [&](int k, long long v) { dst[k] = v; });
+          xpass_item<W1, W2, W3>(X + row * G::XP + seg * G::SEGX,
+                                 Bt + (size_t)b * G::BY * G::BP + row * G::BP + seg * G::SEGX);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(bt_full + 8 * b);
