@@ -48,19 +48,41 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
+SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_tile.cu", "sc_smooth_z.cu", "sc_tile_common.cuh",
+                  "sc_device.cuh", "sc_internal.h")
+
+
+def smooth_source_hash():
+    """First 16 hex digits of the SHA-256 of the smoothing kernels' sources."""
+    h = hashlib.sha256()
+    for name in SMOOTH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_15789_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def smooth_traffic_record():
-    """DRAM bytes per voxel of the smoothing kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2106_15789_gb300", "csrc", "sc_smooth.cu")
+    """DRAM bytes per voxel of each smoothing kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
     rec = os.path.join(ROOT, "profiles", "smooth_traffic.json")
     try:
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
         with open(rec) as f:
             r = json.load(f)
-        return r if r.get("source_sha256_16") == h else None
+        return r if r.get("source_sha256_16") == smooth_source_hash() else None
     except Exception:
         return None
+
+
+def smoothing_kernel_name(sc, pair):
+    """Name of the smoothing kernel the library runs for one kernel pair of a
+    TMA-addressable cube (the bench workloads are)."""
+    fwhm, wz = pair
+    w = list(sc.sc_cascade_widths(fwhm)) if fwhm > 0 else [1, 1, 1]
+    if w == [1, 1, 1]:
+        return "k_smooth_z" if wz > 1 else "k_identity"
+    if tuple(w) in ((1, 3, 3), (3, 5, 5), (5, 5, 5), (7, 9, 9)) and wz <= 15:
+        return "k_smooth_ws<%d,%d,%d>" % tuple(w)
+    return "k_smooth_generic"
 
 
 class ClockSampler:
@@ -265,16 +287,29 @@ def main():
     st = ctx.stats(reset=True)
     value = nvox * len(kernels) * args.steps * world / (ms * 1e-3)
 
-    # roofline of the dominant kernel (the smoothing kernel), from the live events
+    # roofline of the dominant kernel: the smoothing kernel with the largest
+    # share of device time in the timed region (live events, grouped by the
+    # kernel each pair runs)
     peak, peak_kind = measured_hbm_peak()
-    avg_ms = st["ms_smooth"] / max(1, st["smooth_launches"])
-    vox_per_launch = st["smooth_voxels"] / max(1, st["smooth_launches"])
-    achieved = SMOOTH_BYTES_PER_VOXEL * vox_per_launch / (avg_ms * 1e-3) / 1e9
+    groups = {}
+    for k, pair in enumerate(kernels):
+        n_l = st["smooth_launches_pair"][k]
+        if n_l == 0:
+            continue
+        g = groups.setdefault(smoothing_kernel_name(sc, pair), [0.0, 0])
+        g[0] += st["ms_smooth_pair"][k]
+        g[1] += n_l
+    dom = max(groups, key=lambda name: groups[name][0])
+    dom_ms, dom_launches = groups[dom]
+    avg_ms = dom_ms / dom_launches
+    achieved = SMOOTH_BYTES_PER_VOXEL * nvox / (avg_ms * 1e-3) / 1e9
     tr = smooth_traffic_record()
+    dram = tr["kernels"].get(dom) if tr else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (tr["dram_bytes_per_voxel"] * vox_per_launch) if tr else None,
-                "kernel": "k_smooth (smoothing of one pair)", "peak_kind": peak_kind,
-                "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL}
+                "traffic": dram * nvox if dram is not None else None,
+                "kernel": dom, "launch_ms": avg_ms, "share_of_smoothing": dom_ms / max(1e-9, st["ms_smooth"]),
+                "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL,
+                "smoothing_ms_by_kernel": {name: round(v[0] / args.steps, 3) for name, v in groups.items()}}
 
     e2e = None
     if not args.no_e2e:

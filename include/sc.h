@@ -70,6 +70,9 @@ typedef struct {
   int32_t boxcar_chan;
 } sc_kernel;
 
+/* Largest number of kernel pairs in one run. */
+#define SC_MAX_KERNELS 64
+
 /* Counters and timings of the context (cumulative unless reset). */
 typedef struct {
   uint64_t launches;      /* CUDA kernels this library launched */
@@ -81,6 +84,8 @@ typedef struct {
   double ms_clip;         /* device time of mask kernels */
   uint64_t smooth_launches; /* smoothing-kernel launches timed in ms_smooth */
   uint64_t smooth_voxels;   /* output voxels those launches produced */
+  double ms_smooth_pair[SC_MAX_KERNELS];          /* ms_smooth split by kernel-pair index of the run */
+  uint64_t smooth_launches_pair[SC_MAX_KERNELS];  /* smooth_launches split the same way */
 } sc_stats;
 
 /* Create a context on CUDA device `device` with workspace for cubes of up to
@@ -128,7 +133,6 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  * outside 1..SC_MAX_KERNELS, NULL pointers), SC_ERR_UNSUPPORTED
  * (SC_NOISE_GAUSS), SC_ERR_ALLNAN (no finite voxel; mask left zero),
  * SC_ERR_CUDA. */
-#define SC_MAX_KERNELS 64
 int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_kernel *kernels, int n_kernels,
            float threshold, int noise_mode, float replacement, uint8_t *mask_dev, double *sigma_host,
            double *sigma0_host, uint32_t flags, void *cuda_stream);

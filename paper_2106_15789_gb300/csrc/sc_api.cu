@@ -42,6 +42,7 @@ struct sc_ctx {
     cudaEvent_t a, b;
     int kind;
     unsigned long long voxels;
+    int pair;  // kernel-pair index for smoothing events, else -1
   };
   std::vector<Ev> events;     // recorded, not yet accumulated
   std::vector<cudaEvent_t> pool;
@@ -82,7 +83,9 @@ struct Phase {
   cudaEvent_t a = nullptr;
   int kind;
   unsigned long long vox;
-  Phase(sc_ctx* c_, cudaStream_t s_, int kind_, unsigned long long vox_ = 0) : c(c_), s(s_), kind(kind_), vox(vox_) {
+  int pair;
+  Phase(sc_ctx* c_, cudaStream_t s_, int kind_, unsigned long long vox_ = 0, int pair_ = -1)
+      : c(c_), s(s_), kind(kind_), vox(vox_), pair(pair_) {
     if (c->profiling) {
       a = take_event(c);
       cudaEventRecord(a, s);
@@ -92,7 +95,7 @@ struct Phase {
     if (c->profiling && a) {
       cudaEvent_t b = take_event(c);
       cudaEventRecord(b, s);
-      c->events.push_back({a, b, kind, vox});
+      c->events.push_back({a, b, kind, vox, pair});
     }
   }
 };
@@ -106,6 +109,10 @@ void flush_events(sc_ctx* c) {
       c->stats.ms_smooth += ms;
       c->stats.smooth_launches += 1;
       c->stats.smooth_voxels += e.voxels;
+      if (e.pair >= 0 && e.pair < SC_MAX_KERNELS) {
+        c->stats.ms_smooth_pair[e.pair] += ms;
+        c->stats.smooth_launches_pair[e.pair] += 1;
+      }
     } else if (e.kind == EV_SELECT) {
       c->stats.ms_select += ms;
     } else {
@@ -253,7 +260,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
     a.repl_possible = replacement > 0.0f ? 1 : 0;
     {
-      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
+      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
       if (a.pd.h == 0 && a.pd.wz == 1) {
         CK(launch_identity(a, c->sms, s));
         c->stats.launches += 1;
@@ -460,7 +467,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
   a.repl_possible = repl > 0.0f ? 1 : 0;
   {
-    Phase ph(c, s, EV_SMOOTH, (unsigned long long)n);
+    Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, 0);
     if (pd.h == 0 && pd.wz == 1) {
       CK(launch_identity(a, c->sms, s));
       c->stats.launches += 1;

@@ -49,7 +49,8 @@ class sc_kernel(C.Structure):
 class sc_stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("runs", C.c_uint64), ("warnings", C.c_uint32), ("reserved", C.c_uint32),
                 ("ms_smooth", C.c_double), ("ms_select", C.c_double), ("ms_clip", C.c_double),
-                ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64)]
+                ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64),
+                ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS)]
 
 
 class ScError(RuntimeError):
@@ -240,7 +241,13 @@ def sc_set_profiling(ctx, on: bool) -> None:
 def sc_get_stats(ctx, reset: bool = False) -> dict:
     st = sc_stats()
     _check(lib().sc_get_stats(ctx, C.byref(st), 1 if reset else 0), "sc_get_stats")
-    return {name: getattr(st, name) for name, _ in sc_stats._fields_ if name != "reserved"}
+    out = {}
+    for name, _ in sc_stats._fields_:
+        if name == "reserved":
+            continue
+        v = getattr(st, name)
+        out[name] = list(v) if name.endswith("_pair") else v
+    return out
 
 
 class Context:
