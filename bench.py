@@ -39,6 +39,24 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, pg, device=None):
+    """The maximum of x over all ranks (x itself without a process group).
+    Works with gloo (CPU tensors) and NCCL (tensors on `device`)."""
+    if pg is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(voxels_per_rank, n_pairs, steps, world, seconds):
+    """Whole-job S+C throughput: every rank runs its own cube (replicas), so
+    the job processes world x voxels x pairs per step in the slowest rank's time."""
+    return voxels_per_rank * n_pairs * steps * world / seconds
+
+
 def measured_hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -279,13 +297,9 @@ def main():
         pg.barrier()
     sampler.stop()
     ctx.set_profiling(False)
-    ms = e0.elapsed_time(e1)
-    if pg:
-        tm = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-        ms = float(tm.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
     st = ctx.stats(reset=True)
-    value = nvox * len(kernels) * args.steps * world / (ms * 1e-3)
+    value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
 
     # roofline of the dominant kernel: the smoothing kernel with the largest
     # share of device time in the timed region (live events, grouped by the
@@ -324,12 +338,8 @@ def main():
         for _ in range(args.e2e_steps):
             ctx.run_host(cube_h, kernels, t, "mad", n_repl, mask_host=mask_h)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if pg:
-            tm = torch.tensor([dt], device=dev, dtype=torch.float64)
-            pg.all_reduce(tm, op=pg.ReduceOp.MAX)
-            dt = float(tm.item())
-        e2e = {"value": nvox * len(kernels) * args.e2e_steps * world / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+        e2e = {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1),
                "steps": args.e2e_steps, "api": "sc_run_host (pinned host cube and mask)"}
 
