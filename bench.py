@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM roofline"
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
-WORKLOADS = ("wallaby", "medium", "small")
+WORKLOADS = ("wallaby", "medium", "small", "batch64")
 
 
 def dist_env():
@@ -228,11 +228,145 @@ def run_reference(args, rank, world):
 def config_dict(workload, kernels):
     from synth.cubes import SC_REPLACEMENT, SC_THRESHOLD
 
-    names = {"wallaby": "wallaby-1200x1200x1024", "medium": "medium-512x512x512", "small": "small-64x64x128"}
+    names = {"wallaby": "wallaby-1200x1200x1024", "medium": "medium-512x512x512", "small": "small-64x64x128",
+             "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
             "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": "mad", "replacement": SC_REPLACEMENT,
             "precision": "float32 cube, exact fixed-point smoothing", "l2": "inputs (cube 5.9 GB) larger than L2"
-            if workload == "wallaby" else "no flush"}
+            if workload == "wallaby" else ("inputs (10.9 GB of sub-cubes) larger than L2" if workload == "batch64"
+                                           else "no flush")}
+
+
+def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
+    """Roofline object of the smoothing kernel with the largest share of the
+    profiled smoothing time (per-pair CUDA events recorded by the library)."""
+    groups = {}
+    for k, pair in enumerate(kernels):
+        n_l = st["smooth_launches_pair"][k]
+        if n_l == 0:
+            continue
+        g = groups.setdefault(smoothing_kernel_name(sc, pair), [0.0, 0])
+        g[0] += st["ms_smooth_pair"][k]
+        g[1] += n_l
+    dom = max(groups, key=lambda name: groups[name][0])
+    dom_ms, dom_launches = groups[dom]
+    avg_ms = dom_ms / dom_launches
+    achieved = SMOOTH_BYTES_PER_VOXEL * voxels_per_launch / (avg_ms * 1e-3) / 1e9
+    tr = smooth_traffic_record()
+    dram = tr["kernels"].get(dom) if tr else None
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": dram * voxels_per_launch if dram is not None else None,
+            "kernel": dom, "launch_ms": avg_ms, "share_of_smoothing": dom_ms / max(1e-9, st["ms_smooth"]),
+            "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL,
+            "smoothing_ms_by_kernel": {name: round(v[0] / steps, 3) for name, v in groups.items()}}
+
+
+def run_batch_bench(args, rank, world, local):
+    """The batched form: 64 uneven sub-cubes per rank in one graph-captured
+    sc_run_batch call per step, after autotuning every sub-cube shape."""
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, batch_specs, make_cube
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    kernels, t, n_repl = KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT
+    with torch.no_grad():
+        cubes = [make_cube(spec, device=str(dev)) for spec in batch_specs(64, first_seed=64 * rank)]
+    masks = [torch.empty(c.shape, dtype=torch.uint8, device=dev) for c in cubes]
+    nvox = sum(c.numel() for c in cubes)
+    ctx = Context(local, max(c.numel() for c in cubes))
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    for shape in sorted({tuple(c.shape) for c in cubes}):
+        ctx.autotune(shape, kernels)
+    tune_s = time.perf_counter() - t0
+
+    def step():
+        return ctx.run_batch(cubes, kernels, t, "mad", n_repl, masks=masks, flags=sc.SC_FLAG_GRAPH)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    launches = int(ctx.stats(reset=True)["launches"])
+    value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
+
+    # roofline: one more batch without the graph, with per-pair CUDA events
+    ctx.set_profiling(True)
+    ctx.run_batch(cubes, kernels, t, "mad", n_repl, masks=masks)
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
+    st = ctx.stats(reset=True)
+    peak, peak_kind = measured_hbm_peak()
+    roofline = dominant_kernel(sc, kernels, st, nvox / len(cubes), 1, peak, peak_kind)
+    roofline["measured_in"] = "one profiled batch after the timed region (events per pair, no graph)"
+
+    e2e = None
+    if not args.no_e2e:
+        hosts = [torch.empty(c.shape, dtype=torch.float32, pin_memory=True) for c in cubes]
+        for h, c in zip(hosts, cubes):
+            h.copy_(c)
+        mask_h = [torch.empty(c.shape, dtype=torch.uint8, pin_memory=True) for c in cubes]
+        work = [torch.empty_like(c) for c in cubes]
+
+        def e2e_step():
+            for w, h in zip(work, hosts):
+                w.copy_(h, non_blocking=True)
+            m, _, _ = ctx.run_batch(work, kernels, t, "mad", n_repl, masks=masks, flags=sc.SC_FLAG_GRAPH)
+            for mh, md in zip(mask_h, m):
+                mh.copy_(md, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_step()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+        e2e = {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * nvox, "d2h_bytes_per_step": nvox + 8 * len(cubes) * (len(kernels) + 1),
+               "steps": args.e2e_steps,
+               "api": "sc_run_batch on device copies of pinned host sub-cubes, masks copied back, per step"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {**config_dict("batch64", kernels), "n_cubes": len(cubes), "voxels": nvox,
+                           "graph": True, "autotune_s": round(tune_s, 2)},
+                "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches,
+                "clocks": sampler.summary(),
+                "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
 
 
 def main():
@@ -249,6 +383,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch64":
+        return run_batch_bench(args, rank, world, local)
 
     import torch
 
@@ -305,25 +441,7 @@ def main():
     # share of device time in the timed region (live events, grouped by the
     # kernel each pair runs)
     peak, peak_kind = measured_hbm_peak()
-    groups = {}
-    for k, pair in enumerate(kernels):
-        n_l = st["smooth_launches_pair"][k]
-        if n_l == 0:
-            continue
-        g = groups.setdefault(smoothing_kernel_name(sc, pair), [0.0, 0])
-        g[0] += st["ms_smooth_pair"][k]
-        g[1] += n_l
-    dom = max(groups, key=lambda name: groups[name][0])
-    dom_ms, dom_launches = groups[dom]
-    avg_ms = dom_ms / dom_launches
-    achieved = SMOOTH_BYTES_PER_VOXEL * nvox / (avg_ms * 1e-3) / 1e9
-    tr = smooth_traffic_record()
-    dram = tr["kernels"].get(dom) if tr else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": dram * nvox if dram is not None else None,
-                "kernel": dom, "launch_ms": avg_ms, "share_of_smoothing": dom_ms / max(1e-9, st["ms_smooth"]),
-                "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL,
-                "smoothing_ms_by_kernel": {name: round(v[0] / args.steps, 3) for name, v in groups.items()}}
+    roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
 
     e2e = None
     if not args.no_e2e:

@@ -54,6 +54,7 @@ extern "C" {
 #define SC_FLAG_ACCUMULATE 0x1u /* start from the caller's mask (nonzero = detected) instead of an empty one */
 #define SC_FLAG_GENERIC 0x2u    /* use the generic (any-width) smoothing kernels even where a specialised one exists */
 #define SC_FLAG_NO_FAST_SELECT 0x4u /* skip the one-pass candidate selection; select by full passes (slow, for tests) */
+#define SC_FLAG_GRAPH 0x8u          /* sc_run_batch: capture the batch once into a CUDA graph and replay it */
 
 /* ---- warning bits (sc_stats.warnings, set per run) -------------------- */
 #define SC_WARN_ZERO_SIGMA 0x1u     /* some pair had sigma == 0 and added nothing to the mask */
@@ -136,6 +137,39 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
 int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_kernel *kernels, int n_kernels,
            float threshold, int noise_mode, float replacement, uint8_t *mask_dev, double *sigma_host,
            double *sigma0_host, uint32_t flags, void *cuda_stream);
+
+/* S+C over many independent cubes (the sub-regions SoFiA-X splits a survey
+ * into, Sect. 3): each cube gets its own sigma_0 and sigma_k, all with the
+ * same kernel list and parameters as sc_run.
+ *   n_cubes      >= 1.
+ *   cubes        n_cubes device pointers, cube i float32 [nz][ny][nx] with
+ *                dims[3*i .. 3*i+2] = {nx, ny, nz}, each <= max_voxels voxels.
+ *   masks        n_cubes device uint8 masks of the same shapes (output; zeroed
+ *                unless SC_FLAG_ACCUMULATE).
+ *   sigma_host   NULL or double[n_cubes * n_kernels], row i = cube i.
+ *   sigma0_host  NULL or double[n_cubes].
+ * The cubes run back to back on the stream with no host synchronisation
+ * between them, sharing the context's workspace. With SC_FLAG_GRAPH the whole
+ * batch is captured once into a CUDA graph (kept in the context and replayed
+ * while the cube and mask pointers, shapes, kernels, parameters and tuning
+ * are unchanged) and launched as one graph; do not make the first such call
+ * inside a caller's own stream capture. Returns after the stream has finished
+ * when sigma is wanted. Errors: as sc_run for any cube (nothing is enqueued
+ * when an argument is invalid); the first failing cube's status when a cube
+ * fails on the device (its sigma row is 0). */
+int sc_run_batch(sc_ctx *ctx, int n_cubes, const float *const *cubes, const int64_t *dims, const sc_kernel *kernels,
+                 int n_kernels, float threshold, int noise_mode, float replacement, uint8_t *const *masks,
+                 double *sigma_host, double *sigma0_host, uint32_t flags, void *cuda_stream);
+
+/* Choose, for a cube shape and each kernel pair, the smoothing kernel variant
+ * and z-chunking that run fastest, by timing the candidates on a synthetic
+ * noise cube of that shape (in the context's staging buffer) on this GPU.
+ * The choices are kept in the context and used by sc_run / sc_run_batch /
+ * sc_run_host for cubes of exactly that shape; results are identical for
+ * every choice (exact arithmetic), only the time differs. Uses the working
+ * mask and device state (no run may be in flight on another stream).
+ * Synchronises. Errors: SC_ERR_ARG, SC_ERR_BUDGET, SC_ERR_NOMEM, SC_ERR_CUDA. */
+int sc_autotune(sc_ctx *ctx, const int64_t *dims, const sc_kernel *kernels, int n_kernels, void *cuda_stream);
 
 /* sc_run on host buffers: copies cube_host to a device staging cube owned by
  * the context (allocated on first use, max_voxels floats), runs S+C and copies

@@ -10,9 +10,11 @@
 //                candidate pass over S (also sets the certain mask bits),
 //                selections of median and MAD, clip of the undecided voxels.
 //   end          1-bit working mask -> caller's uint8 mask; sigmas to host.
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -47,6 +49,19 @@ struct sc_ctx {
   std::vector<Ev> events;     // recorded, not yet accumulated
   std::vector<cudaEvent_t> pool;
   cudaStream_t last = nullptr;
+  // kernel choices fixed by sc_autotune: (nx, ny, nz, w1, w2, w3, wz) -> (kind, items per SM)
+  std::map<std::array<long long, 7>, std::array<int, 2>> tune;
+  // sc_run_batch: per-cube results on the device and their pinned host mirror
+  unsigned char* batch_res = nullptr;
+  unsigned char* batch_res_host = nullptr;
+  size_t batch_res_cap = 0;
+  // sc_run_batch with SC_FLAG_GRAPH: the captured batch and its signature
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  unsigned long long graph_key = 0;
+  unsigned long long graph_launches = 0;
+  bool capturing = false;  // no profiling events inside a capture
 };
 
 namespace {
@@ -86,13 +101,13 @@ struct Phase {
   int pair;
   Phase(sc_ctx* c_, cudaStream_t s_, int kind_, unsigned long long vox_ = 0, int pair_ = -1)
       : c(c_), s(s_), kind(kind_), vox(vox_), pair(pair_) {
-    if (c->profiling) {
+    if (c->profiling && !c->capturing) {
       a = take_event(c);
       cudaEventRecord(a, s);
     }
   }
   ~Phase() {
-    if (c->profiling && a) {
+    if (c->profiling && !c->capturing && a) {
       cudaEvent_t b = take_event(c);
       cudaEventRecord(b, s);
       c->events.push_back({a, b, kind, vox, pair});
@@ -203,6 +218,19 @@ int validate_common(sc_ctx* c, const float* cube, const int64_t* dims, const sc_
   return SC_OK;
 }
 
+std::array<long long, 7> tune_key(const int64_t* dims, const PairDesc& pd) {
+  return {dims[0], dims[1], dims[2], pd.w[0], pd.w[1], pd.w[2], pd.wz};
+}
+
+// Kernel choice of sc_autotune for this cube shape and pair, if any.
+void apply_tuning(sc_ctx* c, const int64_t* dims, SmoothArgs* a) {
+  if (c->tune.empty()) return;
+  auto it = c->tune.find(tune_key(dims, a->pd));
+  if (it == c->tune.end()) return;
+  a->tune_kind = it->second[0];
+  a->tune_zfactor = it->second[1];
+}
+
 SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims) {
   SmoothArgs a;
   memset(&a, 0, sizeof(a));
@@ -255,6 +283,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     SmoothArgs a = base_args(c, cube, dims);
     a.pd = pds[k];
     a.pair = k;
+    apply_tuning(c, dims, &a);
     a.hist = c->hist;
     a.win = 1;
     a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
@@ -384,6 +413,11 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->stage_cube);
   cudaFree(c->stage_mask);
   if (c->st_host) cudaFreeHost(c->st_host);
+  cudaFree(c->batch_res);
+  if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaGetLastError();
   delete c;
 }
@@ -402,6 +436,248 @@ int sc_run(sc_ctx* c, const float* cube_dev, const int64_t* dims, const sc_kerne
   return rc;
 }
 
+namespace {
+
+// Device staging cube and mask of max_voxels elements (allocated on first use).
+int ensure_stage(sc_ctx* c) {
+  if (c->stage_cube) return SC_OK;
+  if (cudaMalloc(&c->stage_cube, sizeof(float) * c->max_voxels) != cudaSuccess ||
+      cudaMalloc(&c->stage_mask, c->max_voxels) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->stage_cube);
+    cudaFree(c->stage_mask);
+    c->stage_cube = nullptr;
+    c->stage_mask = nullptr;
+    return SC_ERR_NOMEM;
+  }
+  return SC_OK;
+}
+
+// Per-cube results of a batch, copied out of DevState after each cube.
+struct BatchRes {
+  unsigned int status, warn;
+  float sigma0;
+  float sigma[SC_MAX_KERNELS];
+};
+static_assert(offsetof(DevState, status) == 0 && offsetof(DevState, warn) == 4 && offsetof(DevState, sigma0) == 8,
+              "status, warn and sigma_0 lead DevState");
+
+unsigned long long fnv1a(unsigned long long h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  return h;
+}
+
+int status_code(unsigned int status) {
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.status = status;
+  return status_to_code(h);
+}
+
+}  // namespace
+
+int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_t* dims, const sc_kernel* kernels,
+                 int n_kernels, float threshold, int noise_mode, float replacement, uint8_t* const* masks,
+                 double* sigma_host, double* sigma0_host, uint32_t flags, void* cuda_stream) {
+  if (!c || n_cubes < 1 || !cubes || !dims || !masks || !kernels) return SC_ERR_ARG;
+  if (n_kernels < 1 || n_kernels > SC_MAX_KERNELS || !std::isfinite(replacement)) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  // validate every cube before anything is enqueued
+  for (int i = 0; i < n_cubes; ++i) {
+    if (!cubes[i] || !masks[i]) return SC_ERR_ARG;
+    long long n = 0;
+    std::vector<PairDesc> pds;
+    const int rc = validate_common(c, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, &n, &pds);
+    if (rc) return rc;
+  }
+  const size_t need = sizeof(BatchRes) * (size_t)n_cubes;
+  if (need > c->batch_res_cap) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    cudaFree(c->batch_res);
+    if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
+    c->batch_res = c->batch_res_host = nullptr;
+    c->batch_res_cap = 0;
+    if (cudaMalloc(&c->batch_res, need) != cudaSuccess ||
+        cudaHostAlloc(&c->batch_res_host, need, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    c->batch_res_cap = need;
+  }
+  BatchRes* res = reinterpret_cast<BatchRes*>(c->batch_res);
+  const uint32_t rflags = flags & ~(uint32_t)SC_FLAG_GRAPH;
+  auto enqueue = [&](cudaStream_t q) -> int {
+    for (int i = 0; i < n_cubes; ++i) {
+      const int rc = run_device(c, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, replacement,
+                                masks[i], rflags, q);
+      if (rc) return rc;
+      CK(cudaMemcpyAsync(&res[i], c->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToDevice, q));
+      CK(cudaMemcpyAsync(res[i].sigma, c->st->sigma, sizeof(float) * n_kernels, cudaMemcpyDeviceToDevice, q));
+    }
+    return SC_OK;
+  };
+  if (flags & SC_FLAG_GRAPH) {
+    unsigned long long key = 1469598103934665603ull;
+    key = fnv1a(key, &n_cubes, sizeof(n_cubes));
+    key = fnv1a(key, cubes, sizeof(*cubes) * n_cubes);
+    key = fnv1a(key, dims, sizeof(*dims) * 3 * n_cubes);
+    key = fnv1a(key, masks, sizeof(*masks) * n_cubes);
+    key = fnv1a(key, kernels, sizeof(*kernels) * n_kernels);
+    key = fnv1a(key, &n_kernels, sizeof(n_kernels));
+    key = fnv1a(key, &threshold, sizeof(threshold));
+    key = fnv1a(key, &noise_mode, sizeof(noise_mode));
+    key = fnv1a(key, &replacement, sizeof(replacement));
+    key = fnv1a(key, &rflags, sizeof(rflags));
+    key = fnv1a(key, &c->batch_res, sizeof(c->batch_res));
+    for (const auto& kv : c->tune) {
+      key = fnv1a(key, kv.first.data(), sizeof(long long) * kv.first.size());
+      key = fnv1a(key, kv.second.data(), sizeof(int) * kv.second.size());
+    }
+    if (!c->graph_exec || key != c->graph_key) {
+      if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+      if (c->graph) cudaGraphDestroy(c->graph);
+      c->graph_exec = nullptr;
+      c->graph = nullptr;
+      if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      const unsigned long long l0 = c->stats.launches;
+      CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      c->capturing = true;
+      const int rc = enqueue(c->cap_stream);
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &gr);
+      c->capturing = false;
+      if (rc != SC_OK || ec != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        return rc != SC_OK ? rc : cuda_fail(ec, "cudaStreamEndCapture", __LINE__);
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, gr, 0);
+      if (ei != cudaSuccess) {
+        cudaGraphDestroy(gr);
+        c->graph_exec = nullptr;
+        return cuda_fail(ei, "cudaGraphInstantiate", __LINE__);
+      }
+      c->graph = gr;
+      c->graph_key = key;
+      c->graph_launches = c->stats.launches - l0;
+      c->stats.launches = l0;  // counted per replay
+    }
+    CK(cudaGraphLaunch(c->graph_exec, s));
+    c->stats.launches += c->graph_launches;
+  } else {
+    const int rc = enqueue(s);
+    if (rc) return rc;
+  }
+  if (!sigma_host && !sigma0_host) return SC_OK;
+  CK(cudaMemcpyAsync(c->batch_res_host, res, need, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const BatchRes* h = reinterpret_cast<const BatchRes*>(c->batch_res_host);
+  int first = SC_OK;
+  c->stats.warnings = 0;
+  for (int i = 0; i < n_cubes; ++i) {
+    const int code = status_code(h[i].status);
+    if (code != SC_OK && first == SC_OK) first = code;
+    c->stats.warnings |= h[i].warn;
+    if (sigma0_host) sigma0_host[i] = code == SC_OK ? (double)h[i].sigma0 : 0.0;
+    if (sigma_host)
+      for (int k = 0; k < n_kernels; ++k) sigma_host[(size_t)i * n_kernels + k] = code == SC_OK ? (double)h[i].sigma[k] : 0.0;
+  }
+  if (first == SC_OK) c->stats.runs += (unsigned long long)n_cubes;
+  return first;
+}
+
+int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_kernels, void* cuda_stream) {
+  if (!c || !dims || !kernels || n_kernels < 1 || n_kernels > SC_MAX_KERNELS) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  long long n = 0;
+  int rc = check_dims(c, dims, &n);
+  if (rc) return rc;
+  std::vector<PairDesc> pds(n_kernels);
+  for (int k = 0; k < n_kernels; ++k) {
+    rc = make_pair(kernels[k], &pds[k]);
+    if (rc) return rc;
+  }
+  rc = ensure_stage(c);
+  if (rc) return rc;
+  // a synthetic cube of the requested shape (uniform noise) and an empty mask
+  CK(launch_fill_noise(c->stage_cube, n, 20210630u, c->sms, s));
+  CK(cudaMemsetAsync(c->mbits, 0, sizeof(uint32_t) * ((n + 31) / 32), s));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  struct Cand {
+    int kind, zf;
+  };
+  std::map<std::array<long long, 7>, std::array<int, 2>> done;
+  int out = SC_OK;
+  for (int k = 0; k < n_kernels && out == SC_OK; ++k) {
+    const PairDesc& pd = pds[k];
+    if (pd.h == 0 && pd.wz <= 1) continue;  // identity: nothing to choose
+    const auto key = tune_key(dims, pd);
+    if (done.count(key)) continue;
+    std::vector<Cand> cands;
+    for (int zf : {1, 2, 4}) {
+      if (pd.h > 0) {
+        cands.push_back({TUNE_WS, zf});
+        cands.push_back({TUNE_TILE, zf});
+      } else {
+        cands.push_back({TUNE_Z8, zf});
+        cands.push_back({TUNE_Z4, zf});
+      }
+    }
+    // fixed-point scales of this pair on the synthetic cube, replacement value 1
+    PairWeights W{};
+    W.w[0] = pd.W;
+    if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess ||
+        launch_maxabs(c->stage_cube, n, c->st, c->sms, s) != cudaSuccess ||
+        launch_fx_setup(c->st, 1.0f, W, 1, s) != cudaSuccess) {
+      out = cuda_fail(cudaGetLastError(), "autotune setup", __LINE__);
+      break;
+    }
+    float best = 1e30f;
+    std::array<int, 2> choice{TUNE_AUTO, 0};
+    for (const Cand& cd : cands) {
+      SmoothArgs a = base_args(c, c->stage_cube, dims);
+      a.pd = pd;
+      a.pair = 0;
+      a.hist = c->hist;
+      a.win = 0;
+      a.repl_possible = 1;
+      a.tune_kind = cd.kind;
+      a.tune_zfactor = cd.zf;
+      cudaError_t e = launch_smooth(a, c->sms, s, nullptr);  // warm-up
+      e = e == cudaSuccess ? cudaEventRecord(e0, s) : e;
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_smooth(a, c->sms, s, nullptr);
+      e = e == cudaSuccess ? cudaEventRecord(e1, s) : e;
+      e = e == cudaSuccess ? cudaEventSynchronize(e1) : e;
+      float ms = 0.0f;
+      e = e == cudaSuccess ? cudaEventElapsedTime(&ms, e0, e1) : e;
+      if (e != cudaSuccess) {
+        out = cuda_fail(e, "autotune candidate", __LINE__);
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        choice = {cd.kind, cd.zf};
+      }
+    }
+    done[key] = choice;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out == SC_OK)
+    for (const auto& kv : done) c->tune[kv.first] = kv.second;
+  return out;
+}
+
 int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc_kernel* kernels, int n_kernels,
                 float threshold, int noise_mode, float replacement, uint8_t* mask_host, double* sigma_host,
                 double* sigma0_host, uint32_t flags, void* cuda_stream) {
@@ -410,15 +686,8 @@ int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc
   long long n = 0;
   int rc = check_dims(c, dims, &n);
   if (rc) return rc;
-  if (!c->stage_cube) {
-    if (cudaMalloc(&c->stage_cube, sizeof(float) * c->max_voxels) != cudaSuccess ||
-        cudaMalloc(&c->stage_mask, c->max_voxels) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(c->stage_cube);
-      c->stage_cube = nullptr;
-      return SC_ERR_NOMEM;
-    }
-  }
+  rc = ensure_stage(c);
+  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   c->last = s;
   CK(cudaMemcpyAsync(c->stage_cube, cube_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));

@@ -167,7 +167,13 @@ struct SmoothArgs {
   int tx, ty, lz;            // tile and z-chunk sizes
   int tiles_x, tiles_y, zchunks;
   int generic;               // force the generic FIR path
+  int tune_kind;             // TUNE_* kernel choice (TUNE_AUTO: the dispatcher decides)
+  int tune_zfactor;          // work items per SM targeted by the z chunking (0: 2)
 };
+
+// Kernel choices the autotuner may fix for a (dims, kernel pair).
+enum TuneKind : int { TUNE_AUTO = 0, TUNE_WS = 1, TUNE_TILE = 2, TUNE_GENERIC = 3, TUNE_Z8 = 4, TUNE_Z4 = 5 };
+inline long long tune_items_per_sm(const SmoothArgs& a) { return a.tune_zfactor > 0 ? a.tune_zfactor : 2; }
 
 // ---------------------------------------------------------------------------
 // Launchers (all enqueue on `s`, return cudaError_t of the launch).
@@ -190,6 +196,9 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
 cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s);
 cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s);
 cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s);
+// x[i] = uniform pseudo-random value in [-1, 1) from (i, seed) (autotuning input)
+cudaError_t launch_fill_noise(float* x, long long n, unsigned int seed, int sms, cudaStream_t s);
+cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);
 cudaError_t launch_identity(const SmoothArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);
 

@@ -276,7 +276,7 @@ cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   const long long P = (long long)a.nx * a.ny;
   const long long per_block = (long long)zonly::kThreads * VPT;
   const long long groups = (P + per_block - 1) / per_block;
-  long long zch = (2LL * sms + groups - 1) / groups;
+  long long zch = (tune_items_per_sm(a) * sms + groups - 1) / groups;
   const long long max_ch = (a.nz + 15) / 16;
   zch = zch < 1 ? 1 : (zch > max_ch ? max_ch : zch);
   a.lz = (int)((a.nz + zch - 1) / zch);
@@ -314,6 +314,7 @@ cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* 
   *done = false;
   if (a.generic || a.pd.h != 0 || a.pd.wz <= 1) return cudaSuccess;
   *done = true;
+  if (a.tune_kind == TUNE_Z4 && a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   if (a.pd.wz <= 15) return launch_z_vpt<8>(a, sms, s);
   if (a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   return launch_z_vpt<1>(a, sms, s);

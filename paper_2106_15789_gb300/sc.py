@@ -33,6 +33,7 @@ NOISE_MODES = {"mad": SC_NOISE_MAD, "std": SC_NOISE_STD, "gauss": SC_NOISE_GAUSS
 SC_FLAG_ACCUMULATE = 0x1
 SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
+SC_FLAG_GRAPH = 0x8
 
 SC_WARN_ZERO_SIGMA = 0x1
 SC_WARN_FULL_SELECT = 0x2
@@ -79,6 +80,10 @@ _SIGS = {
                          _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_run_host": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int,
                               C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_run_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int,
+                               C.c_float, C.c_int, C.c_float, C.POINTER(_P), C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_autotune": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, _P]),
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
@@ -171,6 +176,47 @@ def sc_run(ctx, cube: torch.Tensor, kernels, threshold: float, noise_mode="mad",
     if not want_sigma:
         return mask, None, None
     return mask, [float(x) for x in sig], float(sig0[0])
+
+
+def sc_run_batch(ctx, cubes, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0, masks=None,
+                 flags: int = 0, stream=None, want_sigma: bool = True):
+    """S+C over a list of CUDA cubes (each (nz, ny, nx) float32). Returns
+    (masks, sigmas [n_cubes][n_kernels], sigma0s [n_cubes])."""
+    n = len(cubes)
+    if n < 1:
+        raise ScError(SC_ERR_ARG, "sc_run_batch: no cubes")
+    for c in cubes:
+        _dev(c, torch.float32, "cube")
+    if masks is None:
+        masks = [torch.empty(c.shape, dtype=torch.uint8, device=c.device) for c in cubes]
+    for m in masks:
+        _dev(m, torch.uint8, "mask")
+    kk, nk = _kernels(kernels)
+    cp = (_P * n)(*[C.c_void_p(c.data_ptr()) for c in cubes])
+    mp = (_P * n)(*[C.c_void_p(m.data_ptr()) for m in masks])
+    dims = (C.c_int64 * (3 * n))()
+    for i, c in enumerate(cubes):
+        nz, ny, nx = c.shape
+        dims[3 * i], dims[3 * i + 1], dims[3 * i + 2] = nx, ny, nz
+    sig = (C.c_double * (n * nk))() if want_sigma else None
+    sig0 = (C.c_double * n)() if want_sigma else None
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    code = lib().sc_run_batch(ctx, n, cp, dims, kk, nk, float(threshold), int(mode), float(replacement), mp, sig, sig0,
+                              int(flags), _stream(cubes[0], stream))
+    _check(code, "sc_run_batch")
+    if not want_sigma:
+        return masks, None, None
+    return masks, [[float(sig[i * nk + k]) for k in range(nk)] for i in range(n)], [float(x) for x in sig0]
+
+
+def sc_autotune(ctx, shape, kernels, device: int = 0, stream=None) -> None:
+    """Time the smoothing variants for cubes of this (nz, ny, nx) shape and keep
+    the fastest per kernel pair in the context (synchronises)."""
+    kk, nk = _kernels(kernels)
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().sc_autotune(ctx, _dims(shape), kk, nk, s), "sc_autotune")
 
 
 def sc_run_host(ctx, cube_host: torch.Tensor, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0,
@@ -278,6 +324,14 @@ class Context:
     def run(self, cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, flags=0, stream=None,
             want_sigma=True):
         return sc_run(self.handle, cube, kernels, threshold, noise_mode, replacement, mask, flags, stream, want_sigma)
+
+    def run_batch(self, cubes, kernels, threshold, noise_mode="mad", replacement=2.0, masks=None, flags=0, stream=None,
+                  want_sigma=True):
+        return sc_run_batch(self.handle, cubes, kernels, threshold, noise_mode, replacement, masks, flags, stream,
+                            want_sigma)
+
+    def autotune(self, shape, kernels, stream=None):
+        sc_autotune(self.handle, shape, kernels, self.device, stream)
 
     def run_host(self, cube_host, kernels, threshold, noise_mode="mad", replacement=2.0, mask_host=None, flags=0,
                  stream=None):
