@@ -9,8 +9,11 @@
 // double buffers guarded by mbarriers, so neither group waits for the other
 // at a block-wide barrier:
 //
-//   producers (8 warps)  wait for the plane's raw halo'd tile (TMA, two planes
-//                        ahead, four buffers), quantise it into an int64 tile
+//   producers (8 warps)  wait for the plane's raw halo'd tile (loaded two
+//                        planes ahead into four buffers: by TMA, issued by
+//                        one producer, or, for cubes whose rows are not
+//                        16-byte multiples, by the consumers with 4-byte
+//                        cp.async copies), quantise it into an int64 tile
 //                        (NaN -> 0, masked -> +-replacement; mask words are
 //                        loaded two planes ahead), then run the x cascade of
 //                        every row into buffer g % 2. With two quantised tiles
@@ -190,7 +193,7 @@ __device__ __forceinline__ void xpass_item(const long long* __restrict__ src, lo
 
 }  // namespace ws
 
-template <int W1, int W2, int W3, bool REPL>
+template <int W1, int W2, int W3, bool REPL, bool TMA>
 __global__ void __launch_bounds__(ws::kThreads, 1)
     k_smooth_ws(const __grid_constant__ CUtensorMap tmap, SmoothArgs a) {
   using namespace ws;
@@ -218,7 +221,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
   __shared__ unsigned tmem_holder;
   if (warp == 0) tmem_alloc(&tmem_holder);
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(raw_full + 8 * s, 1);
+    // TMA: one arrival with the byte count; cp.async: one arrival per consumer
+    for (int s = 0; s < kStages; ++s) mbar_init(raw_full + 8 * s, TMA ? 1u : (unsigned)kCT);
     for (int b = 0; b < 2; ++b) {
       mbar_init(bt_full + 8 * b, kPW);
       mbar_init(bt_empty + 8 * b, kCW);
@@ -241,29 +245,53 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     *ns = (int)(min((long long)*z0 + a.lz, nz) - *z0) + 2 * r;
   };
 
+  // Lookahead cursor over the block's planes (its items in order, n_steps
+  // planes each): the next raw tile to load and its buffer.
+  long long la_item = blockIdx.x;
+  int la_j = 0, la_x0 = 0, la_y0 = 0, la_z0 = 0, la_n = 0;
+  if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
+  long long issued = 0;
+  auto advance = [&]() {
+    ++issued;
+    if (++la_j == la_n) {
+      la_item += gridDim.x;
+      la_j = 0;
+      if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
+    }
+  };
+  // TMA load of the next raw tile (one thread)
+  auto issue_tma = [&]() {
+    if (la_item >= n_items) return;
+    const int s = (int)(issued % kStages);
+    mbar_expect_tx(raw_full + 8 * s, (unsigned)(sizeof(float) * G::BX * G::BY));
+    tma_load_3d(smem_u32(raw0 + s * kRawStride), &tmap, la_x0 - RA, la_y0 - R, la_z0 - r + la_j, raw_full + 8 * s);
+    advance();
+  };
+  // cp.async load of the next raw tile by the consumers (thread ct copies
+  // elements ct, ct + kCT, ...; zero fill outside the cube), completing on the
+  // buffer's barrier once each thread's copies have landed
+  auto issue_async = [&](int ct) {
+    if (la_item >= n_items) return;
+    const int s = (int)(issued % kStages);
+    float* dst = raw0 + s * kRawStride;
+    const long long zp = (long long)la_z0 - r + la_j;
+    const bool zok = zp >= 0 && zp < nz;
+    for (int e = ct; e < G::BY * G::BX; e += kCT) {
+      const int row = e / G::BX, col = e - row * G::BX;
+      const long long gx = (long long)la_x0 - RA + col, gy = (long long)la_y0 - R + row;
+      const bool ok = zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      cp_async4(smem_u32(dst + e), ok ? a.C + zp * plane + gy * nx + gx : a.C, ok);
+    }
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(raw_full + 8 * s) : "memory");
+    advance();
+  };
+
   if (warp < kPW) {
     // ======================= producers =======================
     const int pt = tid;
     const float fscale = a.st->fx_scale[a.pair];
     const long long qrepl = a.st->fx_qrepl[a.pair];
     const bool do_repl = REPL && qrepl > 0;
-    // TMA lookahead cursor (thread 0 issues)
-    long long la_item = blockIdx.x;
-    int la_j = 0, la_x0 = 0, la_y0 = 0, la_z0 = 0, la_n = 0;
-    if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
-    long long issued = 0;
-    auto issue_next = [&]() {
-      if (la_item >= n_items) return;
-      const int s = (int)(issued % kStages);
-      mbar_expect_tx(raw_full + 8 * s, (unsigned)(sizeof(float) * G::BX * G::BY));
-      tma_load_3d(smem_u32(raw0 + s * kRawStride), &tmap, la_x0 - RA, la_y0 - R, la_z0 - r + la_j, raw_full + 8 * s);
-      ++issued;
-      if (++la_j == la_n) {
-        la_item += gridDim.x;
-        la_j = 0;
-        if (la_item < n_items) item_geo(la_item, &la_x0, &la_y0, &la_z0, &la_n);
-      }
-    };
     // Mask word k of row `row` of plane zp, aligned to the quantised tile:
     // bit c <-> column 32k + c (gx = x0 - R + 32k + c); bits outside the cube
     // clear. Issued as two loads (MaskLd) and finished once they have arrived.
@@ -295,8 +323,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       if (hi > lo) keep = (hi - lo >= 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
       return w & keep;
     };
-    if (pt == 0)
-      for (int k = 0; k < kLookahead; ++k) issue_next();
+    if (TMA && pt == 0)
+      for (int k = 0; k < kLookahead; ++k) issue_tma();
     long long g = 0;
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
       int x0, y0, z0, n_steps;
@@ -324,7 +352,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         // quantised tile and next mask words done; with two tiles, also every
         // producer's x pass of the plane before, so its tile may be refilled
         named_bar_sync(kBarProducers, kPT);
-        if (pt == 0) issue_next();  // into the buffer of plane g - 2, released by the consumers
+        if (TMA && pt == 0) issue_tma();  // into the buffer of plane g - 2, released by the consumers
         // x pass into buffer b
         if (pt < G::XITEMS) {
           const int row = pt % G::BY, seg = pt / G::BY;
@@ -344,6 +372,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const float inv = a.st->fx_inv[a.pair];
     const unsigned tmine =
         tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((kTmemCols / 2) * ((warp - kPW) >> 2));
+    if (!TMA)
+      for (int k = 0; k < kLookahead; ++k) issue_async(ct);
     long long g = 0;
     for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
       int x0, y0, z0, n_steps;
@@ -390,6 +420,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(bt_empty + 8 * b);
+        // The buffer of plane g - 2 is free: every consumer warp released that
+        // plane before the producers could finish plane g, whose hand-off this
+        // thread has passed. Refill it with plane g + 2.
+        if (!TMA) issue_async(ct);
         nan_hist = (nan_hist << SEGY) | nbyte;
         if (wz > 1) {
           unsigned nw[kSlotCols];
@@ -446,7 +480,7 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
   const Smem L = smem_layout<W1, W2, W3>(a.hist != nullptr);
   if (L.total + 1024 > 227 * 1024) return cudaSuccess;  // not served: the caller falls back
   CUtensorMap map;
-  if (!encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY)) return cudaSuccess;
+  const bool tma = encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY);  // else the cp.async variant
   a.tx = TX;
   a.ty = TY;
   a.tiles_x = (a.nx + TX - 1) / TX;
@@ -462,16 +496,23 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
   const int grid = (int)(items < sms ? items : sms);
   const bool repl = a.mbits != nullptr && a.repl_possible;
   const size_t smem_req = one_block_per_sm_smem(L.total);
-  if (repl) k_smooth_ws<W1, W2, W3, true><<<grid, kThreads, smem_req, s>>>(map, a);
-  else k_smooth_ws<W1, W2, W3, false><<<grid, kThreads, smem_req, s>>>(map, a);
+  if (tma) {
+    if (repl) k_smooth_ws<W1, W2, W3, true, true><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_ws<W1, W2, W3, false, true><<<grid, kThreads, smem_req, s>>>(map, a);
+  } else {
+    if (repl) k_smooth_ws<W1, W2, W3, true, false><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_ws<W1, W2, W3, false, false><<<grid, kThreads, smem_req, s>>>(map, a);
+  }
   *done = true;
   return cudaGetLastError();
 }
 
 template <int W1, int W2, int W3>
 void set_ws_attr() {
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, true>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, true>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, false>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, false>);
 }
 
 }  // namespace
@@ -484,7 +525,8 @@ void init_ws_attrs() {
 }
 
 // The warp-specialised kernel for the cascades of FWHM 3, 5, 6 and 10 px with
-// spectral widths up to 15 on TMA-addressable cubes; *done = false otherwise.
+// spectral widths up to 15 (TMA loads where the cube allows them, cp.async
+// otherwise); *done = false for other pairs.
 cudaError_t launch_smooth_ws(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
   if (a.generic || a.pd.wz > ws::kMaxWz) return cudaSuccess;
