@@ -148,8 +148,11 @@ int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_ker
  *                unless SC_FLAG_ACCUMULATE).
  *   sigma_host   NULL or double[n_cubes * n_kernels], row i = cube i.
  *   sigma0_host  NULL or double[n_cubes].
- * The cubes run back to back on the stream with no host synchronisation
- * between them, sharing the context's workspace. With SC_FLAG_GRAPH the whole
+ * The cubes run with no host synchronisation between them on four
+ * concurrent lanes (the context's workspace and three more of the same size,
+ * created on first use, each with its own stream forked from and joined back
+ * into cuda_stream), so one cube's selection overlaps another's smoothing.
+ * With SC_FLAG_GRAPH the whole
  * batch is captured once into a CUDA graph (kept in the context and replayed
  * while the cube and mask pointers, shapes, kernels, parameters and tuning
  * are unchanged) and launched as one graph; do not make the first such call

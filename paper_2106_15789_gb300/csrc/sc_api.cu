@@ -10,6 +10,7 @@
 //                candidate pass over S (also sets the certain mask bits),
 //                selections of median and MAD, clip of the undecided voxels.
 //   end          1-bit working mask -> caller's uint8 mask; sigmas to host.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -62,7 +63,17 @@ struct sc_ctx {
   unsigned long long graph_key = 0;
   unsigned long long graph_launches = 0;
   bool capturing = false;  // no profiling events inside a capture
+  // sc_run_batch: extra workspaces ("lanes", full contexts of their own) that
+  // run other cubes of the batch concurrently on their own streams
+  std::vector<sc_ctx*> lanes;
+  std::vector<cudaStream_t> lane_streams;
+  std::vector<cudaEvent_t> lane_done;
+  cudaEvent_t fork = nullptr;
 };
+
+namespace {
+constexpr int kBatchLanes = 4;  // concurrent cubes of a batch (the context itself and 3 lanes)
+}
 
 namespace {
 
@@ -418,6 +429,11 @@ void sc_destroy(sc_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (sc_ctx* l : c->lanes)
+    if (l != c) sc_destroy(l);  // lane 0 is the context itself
+  for (cudaStream_t ls : c->lane_streams) cudaStreamDestroy(ls);
+  for (cudaEvent_t e : c->lane_done) cudaEventDestroy(e);
+  if (c->fork) cudaEventDestroy(c->fork);
   cudaGetLastError();
   delete c;
 }
@@ -449,6 +465,31 @@ int ensure_stage(sc_ctx* c) {
     c->stage_cube = nullptr;
     c->stage_mask = nullptr;
     return SC_ERR_NOMEM;
+  }
+  return SC_OK;
+}
+
+// The batch lanes (created on first use, same workspace size as the context).
+int ensure_lanes(sc_ctx* c) {
+  if (!c->lanes.empty()) return SC_OK;
+  if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) return SC_ERR_CUDA;
+  for (int l = 0; l < kBatchLanes; ++l) {
+    sc_ctx* lc = nullptr;
+    if (l > 0) {
+      const int rc = sc_create(&lc, c->device, c->max_voxels);
+      if (rc) return rc;
+    }
+    cudaStream_t ls = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      if (lc) sc_destroy(lc);
+      cudaGetLastError();
+      return SC_ERR_CUDA;
+    }
+    c->lanes.push_back(l == 0 ? c : lc);
+    c->lane_streams.push_back(ls);
+    c->lane_done.push_back(ev);
   }
   return SC_OK;
 }
@@ -512,13 +553,42 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
   }
   BatchRes* res = reinterpret_cast<BatchRes*>(c->batch_res);
   const uint32_t rflags = flags & ~(uint32_t)SC_FLAG_GRAPH;
+  int rc_lanes = ensure_lanes(c);
+  if (rc_lanes) return rc_lanes;
+  const int n_lanes = (int)std::min<size_t>(c->lanes.size(), (size_t)n_cubes);
+  // Cube i runs on lane i % n_lanes; the lanes' streams fork from q and join
+  // back into it, so cubes on different lanes overlap.
   auto enqueue = [&](cudaStream_t q) -> int {
+    CK(cudaEventRecord(c->fork, q));
+    for (int l = 0; l < n_lanes; ++l) {
+      sc_ctx* lc = c->lanes[l];
+      if (lc != c) {
+        lc->tune = c->tune;
+        lc->profiling = c->profiling;
+        lc->capturing = c->capturing;
+      }
+      CK(cudaStreamWaitEvent(c->lane_streams[l], c->fork, 0));
+    }
     for (int i = 0; i < n_cubes; ++i) {
-      const int rc = run_device(c, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, replacement,
-                                masks[i], rflags, q);
+      const int l = i % n_lanes;
+      sc_ctx* lc = c->lanes[l];
+      cudaStream_t ls = c->lane_streams[l];
+      const int rc = run_device(lc, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, replacement,
+                                masks[i], rflags, ls);
       if (rc) return rc;
-      CK(cudaMemcpyAsync(&res[i], c->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToDevice, q));
-      CK(cudaMemcpyAsync(res[i].sigma, c->st->sigma, sizeof(float) * n_kernels, cudaMemcpyDeviceToDevice, q));
+      CK(cudaMemcpyAsync(&res[i], lc->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToDevice, ls));
+      CK(cudaMemcpyAsync(res[i].sigma, lc->st->sigma, sizeof(float) * n_kernels, cudaMemcpyDeviceToDevice, ls));
+    }
+    for (int l = 0; l < n_lanes; ++l) {
+      CK(cudaEventRecord(c->lane_done[l], c->lane_streams[l]));
+      CK(cudaStreamWaitEvent(q, c->lane_done[l], 0));
+      sc_ctx* lc = c->lanes[l];
+      if (lc != c) {  // the lanes' launch counts and timing events belong to the context
+        c->stats.launches += lc->stats.launches;
+        lc->stats.launches = 0;
+        c->events.insert(c->events.end(), lc->events.begin(), lc->events.end());
+        lc->events.clear();
+      }
     }
     return SC_OK;
   };
