@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM roofline"
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
-WORKLOADS = ("wallaby", "medium", "small", "batch64")
+WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16")
 
 
 def dist_env():
@@ -229,6 +229,10 @@ def config_dict(workload, kernels):
     from synth.cubes import SC_REPLACEMENT, SC_THRESHOLD
 
     names = {"wallaby": "wallaby-1200x1200x1024", "medium": "medium-512x512x512", "small": "small-64x64x128",
+             "small-bf16": "small-64x64x128 stored as BF16 + per-channel float32 scales",
+             "small-fp16": "small-64x64x128 stored as FP16 + per-channel float32 scales",
+             "wallaby-bf16": "wallaby-1200x1200x1024 stored as BF16 + per-channel float32 scales",
+             "wallaby-fp16": "wallaby-1200x1200x1024 stored as FP16 + per-channel float32 scales",
              "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
             "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": "mad", "replacement": SC_REPLACEMENT,
@@ -369,6 +373,100 @@ def run_batch_bench(args, rank, world, local):
     return 0
 
 
+def run_half_bench(args, rank, world, local):
+    """The precision form: the cube stored in 16 bits with per-channel float32
+    scales, run through sc_run_half; reports throughput and the sigma / mask
+    differences against plain float32 (and against the FP64 oracle for the
+    small cube)."""
+    import numpy as np
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, decode_half, encode_half
+
+    base, fmt = args.workload.split("-")
+    bf16 = fmt == "bf16"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    kernels, t, n_repl = KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT
+    spec, cube = make_workload(base, rank, str(dev))
+    bits, scale = encode_half(cube, bf16)
+    nvox = cube.numel()
+    mask = torch.empty(cube.shape, dtype=torch.uint8, device=dev)
+    ctx = Context(local, nvox)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        return ctx.run_half(bits, bf16, scale, kernels, t, "mad", n_repl, mask=mask)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if pg:
+        pg.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        m_h, sig_h, s0_h = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    ctx.set_profiling(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    st = ctx.stats(reset=True)
+    value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
+    peak, peak_kind = measured_hbm_peak()
+    roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
+
+    # precision: the same cube in float32 on the GPU, and (small cube) the oracle
+    m_h = m_h.clone()
+    m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
+    prec = {"format": fmt, "sigma_rel_err_vs_float32": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h],
+                                                                                            sig_f + [s0_f])),
+            "mask_disagreement_vs_float32": int((m_h != m_f).sum().item()),
+            "mask_disagreement_frac_vs_float32": float((m_h != m_f).sum().item()) / nvox}
+    if base == "small":
+        from oracle.sc_oracle import sc_filter
+
+        m_o, s_o, s0_o = sc_filter(cube.cpu().numpy(), kernels, t, "mad", n_repl)
+        dec = decode_half(bits.cpu().numpy(), scale.cpu().numpy(), bf16)
+        m_d, s_d, s0_d = sc_filter(dec, kernels, t, "mad", n_repl)
+        mh = m_h.cpu().numpy()
+        prec.update({"sigma_rel_err_vs_oracle_fp64": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h], s_o + [s0_o])),
+                     "mask_disagreement_vs_oracle_fp64": int((mh != m_o).sum()),
+                     "sigma_rel_err_vs_oracle_on_decoded": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h],
+                                                                                               s_d + [s0_d])),
+                     "mask_disagreement_vs_oracle_on_decoded": int((mh != m_d).sum())})
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": fmt, "data": "synthetic",
+                "config": {**config_dict(args.workload, kernels), "storage_bytes_per_voxel": 2},
+                "roofline": roofline, "cpu_baseline": None, "e2e": None, "gpu_launches": int(st["launches"]),
+                "clocks": sampler.summary(), "precision": prec,
+                "breakdown_ms_per_step": {"smooth": st["ms_smooth"] / args.steps,
+                                          "select": st["ms_select"] / args.steps,
+                                          "decode_and_mask": st["ms_clip"] / args.steps}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,6 +483,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch64":
         return run_batch_bench(args, rank, world, local)
+    if args.workload.endswith(("-bf16", "-fp16")):
+        return run_half_bench(args, rank, world, local)
 
     import torch
 

@@ -82,7 +82,7 @@ typedef struct {
   uint32_t reserved;
   double ms_smooth;       /* device time of smoothing kernels (only while profiling is on) */
   double ms_select;       /* device time of histogram/plan/candidate/select kernels */
-  double ms_clip;         /* device time of mask kernels */
+  double ms_clip;         /* device time of mask kernels and of the 16-bit decode (sc_run_half) */
   uint64_t smooth_launches; /* smoothing-kernel launches timed in ms_smooth */
   uint64_t smooth_voxels;   /* output voxels those launches produced */
   double ms_smooth_pair[SC_MAX_KERNELS];          /* ms_smooth split by kernel-pair index of the run */
@@ -173,6 +173,21 @@ int sc_run_batch(sc_ctx *ctx, int n_cubes, const float *const *cubes, const int6
  * mask and device state (no run may be in flight on another stream).
  * Synchronises. Errors: SC_ERR_ARG, SC_ERR_BUDGET, SC_ERR_NOMEM, SC_ERR_CUDA. */
 int sc_autotune(sc_ctx *ctx, const int64_t *dims, const sc_kernel *kernels, int n_kernels, void *cuda_stream);
+
+/* S+C on a cube stored in 16 bits with one float32 scale per channel (the
+ * precision form: half the bytes of storage and host-to-device transfer).
+ *   cube_dev        uint16 [nz][ny][nx]: BF16 bit patterns if is_bf16 != 0,
+ *                   else IEEE FP16; read only.
+ *   chan_scale_dev  float32 [nz] device array; the cube value of voxel
+ *                   (x, y, z) is the float32 product decode(x) * scale[z]
+ *                   (rounded once; NaN and Inf decode as such).
+ * The cube is decoded once per call into the context's float32 staging cube
+ * (allocated on first use, max_voxels floats), and S+C then runs exactly as
+ * sc_run on those values (same arguments, outputs and errors). */
+int sc_run_half(sc_ctx *ctx, const uint16_t *cube_dev, int is_bf16, const float *chan_scale_dev,
+                const int64_t *dims, const sc_kernel *kernels, int n_kernels, float threshold, int noise_mode,
+                float replacement, uint8_t *mask_dev, double *sigma_host, double *sigma0_host, uint32_t flags,
+                void *cuda_stream);
 
 /* sc_run on host buffers: copies cube_host to a device staging cube owned by
  * the context (allocated on first use, max_voxels floats), runs S+C and copies

@@ -748,6 +748,31 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
   return out;
 }
 
+int sc_run_half(sc_ctx* c, const uint16_t* cube_dev, int is_bf16, const float* chan_scale_dev, const int64_t* dims,
+                const sc_kernel* kernels, int n_kernels, float threshold, int noise_mode, float replacement,
+                uint8_t* mask_dev, double* sigma_host, double* sigma0_host, uint32_t flags, void* cuda_stream) {
+  if (!c || !cube_dev || !chan_scale_dev || !mask_dev) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  long long n = 0;
+  int rc = check_dims(c, dims, &n);
+  if (rc) return rc;
+  rc = ensure_stage(c);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  {
+    Phase ph(c, s, EV_CLIP);
+    CK(launch_decode_half(cube_dev, chan_scale_dev, (long long)dims[0] * dims[1], n, is_bf16 ? 1 : 0,
+                          c->stage_cube, c->sms, s));
+    c->stats.launches += 1;
+  }
+  rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, s);
+  if (rc) return rc;
+  rc = finish(c, n_kernels, sigma_host, sigma0_host, s, false);
+  if (rc == SC_OK) c->stats.runs += 1;
+  return rc;
+}
+
 int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc_kernel* kernels, int n_kernels,
                 float threshold, int noise_mode, float replacement, uint8_t* mask_host, double* sigma_host,
                 double* sigma0_host, uint32_t flags, void* cuda_stream) {

@@ -196,6 +196,9 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
 cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s);
 cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s);
 cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s);
+// out[i] = float(x[i]) * scale[i / plane], x BF16 (bf16 != 0) or FP16 bits
+cudaError_t launch_decode_half(const uint16_t* x, const float* scale, long long plane, long long n, int bf16,
+                               float* out, int sms, cudaStream_t s);
 // x[i] = uniform pseudo-random value in [-1, 1) from (i, seed) (autotuning input)
 cudaError_t launch_fill_noise(float* x, long long n, unsigned int seed, int sms, cudaStream_t s);
 cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);

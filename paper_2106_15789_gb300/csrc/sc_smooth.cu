@@ -19,6 +19,8 @@
 // plane into a ring of wz planes that keeps the running spectral sum.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "sc_device.cuh"
 #include "sc_internal.h"
 
@@ -261,6 +263,24 @@ __global__ void k_fill_noise(float* __restrict__ x, long long n, unsigned int se
     z ^= z >> 31;
     x[i] = (float)(z >> 40) * 0x1p-23f - 1.0f;
   }
+}
+
+// C = float(x) * scale[z] for a cube stored as BF16 (bf16 != 0) or FP16 bit
+// patterns with one float32 scale per channel (plane of `plane` voxels); the
+// product is rounded once to float32.
+__global__ void k_decode_half(const uint16_t* __restrict__ x, const float* __restrict__ scale, long long plane,
+                              long long n, int bf16, float* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned short h = __ldg(x + i);
+    const float v = bf16 ? __uint_as_float((unsigned)h << 16) : __half2float(__ushort_as_half(h));
+    out[i] = __fmul_rn(v, __ldg(scale + i / plane));
+  }
+}
+
+cudaError_t launch_decode_half(const uint16_t* x, const float* scale, long long plane, long long n, int bf16,
+                               float* out, int sms, cudaStream_t s) {
+  k_decode_half<<<8 * sms, 256, 0, s>>>(x, scale, plane, n, bf16, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fill_noise(float* x, long long n, unsigned int seed, int sms, cudaStream_t s) {

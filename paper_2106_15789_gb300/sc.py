@@ -84,6 +84,8 @@ _SIGS = {
                                C.c_float, C.c_int, C.c_float, C.POINTER(_P), C.POINTER(C.c_double),
                                C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_autotune": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, _P]),
+    "sc_run_half": (C.c_int, [_P, _P, C.c_int, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float,
+                              C.c_int, C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
@@ -209,6 +211,34 @@ def sc_run_batch(ctx, cubes, kernels, threshold: float, noise_mode="mad", replac
     return masks, [[float(sig[i * nk + k]) for k in range(nk)] for i in range(n)], [float(x) for x in sig0]
 
 
+def sc_run_half(ctx, cube16: torch.Tensor, bf16: bool, chan_scale: torch.Tensor, kernels, threshold: float,
+                noise_mode="mad", replacement: float = 2.0, mask: torch.Tensor | None = None, flags: int = 0,
+                stream=None, want_sigma: bool = True):
+    """S+C on a CUDA cube of 16-bit patterns (torch.int16 / uint16 storage of
+    BF16 or FP16 values, shape (nz, ny, nx)) with float32 per-channel scales
+    chan_scale [nz]. Returns (mask uint8, sigmas, sigma0)."""
+    if not isinstance(cube16, torch.Tensor) or not cube16.is_cuda or cube16.element_size() != 2 or \
+            cube16.is_floating_point() or not cube16.is_contiguous():
+        raise ScError(SC_ERR_ARG, "cube16 must be a contiguous CUDA tensor of 16-bit integers (bit patterns)")
+    _dev(chan_scale, torch.float32, "chan_scale")
+    if chan_scale.numel() != cube16.shape[0]:
+        raise ScError(SC_ERR_ARG, "chan_scale needs one value per channel")
+    if mask is None:
+        mask = torch.empty(cube16.shape, dtype=torch.uint8, device=cube16.device)
+    _dev(mask, torch.uint8, "mask")
+    kk, nk = _kernels(kernels)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    sig = (C.c_double * nk)() if want_sigma else None
+    sig0 = (C.c_double * 1)() if want_sigma else None
+    code = lib().sc_run_half(ctx, C.c_void_p(cube16.data_ptr()), 1 if bf16 else 0, C.c_void_p(chan_scale.data_ptr()),
+                             _dims(cube16.shape), kk, nk, float(threshold), int(mode), float(replacement),
+                             C.c_void_p(mask.data_ptr()), sig, sig0, int(flags), _stream(cube16, stream))
+    _check(code, "sc_run_half")
+    if not want_sigma:
+        return mask, None, None
+    return mask, [float(x) for x in sig], float(sig0[0])
+
+
 def sc_autotune(ctx, shape, kernels, device: int = 0, stream=None) -> None:
     """Time the smoothing variants for cubes of this (nz, ny, nx) shape and keep
     the fastest per kernel pair in the context (synchronises)."""
@@ -329,6 +359,11 @@ class Context:
                   want_sigma=True):
         return sc_run_batch(self.handle, cubes, kernels, threshold, noise_mode, replacement, masks, flags, stream,
                             want_sigma)
+
+    def run_half(self, cube16, bf16, chan_scale, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None,
+                 flags=0, stream=None, want_sigma=True):
+        return sc_run_half(self.handle, cube16, bf16, chan_scale, kernels, threshold, noise_mode, replacement, mask,
+                           flags, stream, want_sigma)
 
     def autotune(self, shape, kernels, stream=None):
         sc_autotune(self.handle, shape, kernels, self.device, stream)

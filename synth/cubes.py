@@ -188,5 +188,26 @@ def batch_specs(n_cubes: int = 64, first_seed: int = 0) -> list[CubeSpec]:
     return out
 
 
+def encode_half(cube: torch.Tensor, bf16: bool) -> tuple[torch.Tensor, torch.Tensor]:
+    """A cube's 16-bit storage form with one float32 scale per channel: BF16
+    with scale = max|C_c| / 256, or FP16 with scale = max|C_c| / 2^14 (finite
+    values; 1 for an all-zero or all-NaN channel). Returns (int16 bit patterns,
+    float32 scales [nz]) on the cube's device."""
+    a = torch.nan_to_num(cube.abs(), nan=0.0, posinf=0.0, neginf=0.0)
+    mx = a.reshape(cube.shape[0], -1).amax(dim=1)
+    scale = torch.where(mx > 0, mx / (256.0 if bf16 else 16384.0), torch.ones_like(mx)).to(torch.float32)
+    x = cube / scale[:, None, None]
+    half = x.to(torch.bfloat16 if bf16 else torch.float16)
+    return half.view(torch.int16).contiguous(), scale.contiguous()
+
+
+def decode_half(bits: np.ndarray, scale: np.ndarray, bf16: bool) -> np.ndarray:
+    """float32 cube of a 16-bit storage form: float32(value) * scale[z], one
+    float32 rounding (numpy, for test and benchmark references)."""
+    b = np.ascontiguousarray(bits).view(np.uint16)
+    v = (b.astype(np.uint32) << 16).view(np.float32) if bf16 else b.view(np.float16).astype(np.float32)
+    return (v * np.asarray(scale, dtype=np.float32)[:, None, None]).astype(np.float32)
+
+
 def to_numpy(cube: torch.Tensor) -> np.ndarray:
     return cube.detach().to("cpu").numpy()
