@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM roofline"
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
-WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16")
+WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
+             "stream512")
 
 
 def dist_env():
@@ -467,6 +468,97 @@ def run_half_bench(args, rank, world, local):
     return 0
 
 
+def run_stream_bench(args, rank, world, local):
+    """A stream of 512 sub-cubes (batch size distribution) arriving as a
+    Poisson process at 50 cubes/s, admitted by sc_submit under a 120 GB budget
+    with the masks kept on the device; once with BF16 storage and once with
+    plain float32. Reports the throughput over the makespan and the p50 / p99
+    latency (submission to completion) of both."""
+    import numpy as np
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_20, SC_REPLACEMENT, batch_specs, encode_half, make_cube
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc.lib()
+    kernels, t, n_repl, n_cubes, rate, budget = KERNELS_20, 4.0, SC_REPLACEMENT, 512, 50.0, 120e9
+    specs = batch_specs(n_cubes, first_seed=n_cubes * rank)
+    with torch.no_grad():
+        cubes = [make_cube(sp, device=str(dev)) for sp in specs]
+        halves = [encode_half(c, True) for c in cubes]
+    masks = [torch.empty(c.shape, dtype=torch.uint8, device=dev) for c in cubes]
+    nvox = sum(c.numel() for c in cubes)
+    ctx = Context(local, max(c.numel() for c in cubes))
+    ctx.set_budget(int(budget))
+    arrivals = np.cumsum(np.random.default_rng(5 + rank).exponential(1.0 / rate, n_cubes))
+
+    def submit(i, storage):
+        if storage == sc.SC_STORE_F32:
+            return ctx.submit(cubes[i], kernels, t, "mad", n_repl, mask=masks[i])[0]
+        bits, scale = halves[i]
+        return ctx.submit(bits, kernels, t, "mad", n_repl, mask=masks[i], storage=storage, chan_scale=scale)[0]
+
+    def run(storage):
+        lat, waits, i, pending, refused = {}, 0, 0, 0, 0
+        t0 = time.perf_counter()
+        while i < n_cubes or pending:
+            now = time.perf_counter() - t0
+            if i < n_cubes and now >= arrivals[i]:
+                try:
+                    submit(i, storage)
+                    i += 1
+                    pending += 1
+                except sc.ScError as e:
+                    if e.code != sc.SC_ERR_BUDGET:
+                        raise
+                    refused += 1
+                    r = ctx.poll(len(kernels), wait=True)
+                    lat[r[0]] = r[2]
+                    pending -= 1
+                continue
+            r = ctx.poll(len(kernels), wait=(i >= n_cubes))
+            if r is not None:
+                assert r[1] == sc.SC_OK, r
+                lat[r[0]] = r[2]
+                pending -= 1
+            elif i < n_cubes:
+                time.sleep(min(max(arrivals[i] - now, 0.0), 5e-4))
+        makespan = time.perf_counter() - t0
+        ls = np.sort(np.array(list(lat.values())))
+        return {"value": nvox * len(kernels) / makespan, "makespan_s": makespan,
+                "latency_p50_ms": 1e3 * float(np.percentile(ls, 50)), "latency_p99_ms": 1e3 * float(np.percentile(ls, 99)),
+                "latency_max_ms": 1e3 * float(ls[-1]), "refused_by_budget": refused}
+
+    # warm-up: a few jobs of each storage (lanes, kernels, first-use allocations)
+    for storage in (sc.SC_STORE_BF16, sc.SC_STORE_F32):
+        for i in range(4):
+            submit(i, storage)
+        while ctx.poll(len(kernels), wait=True) is not None:
+            pass
+    sampler = ClockSampler(local)
+    sampler.start()
+    res_bf16 = run(sc.SC_STORE_BF16)
+    res_f32 = run(sc.SC_STORE_F32)
+    sampler.stop()
+    if rank == 0:
+        line = {"metric": METRIC, "value": res_bf16["value"], "unit": UNIT, "n_gpus": world, "steps": 1,
+                "warmup": 1, "ms_per_step": 1e3 * res_bf16["makespan_s"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": "stream-512-subcubes-poisson-50-per-s", "n_cubes": n_cubes, "voxels": nvox,
+                           "kernels": "spatial {0,3,6,10} px x spectral {0,3,7,15,31} ch", "n_pairs": len(kernels),
+                           "threshold": t, "noise": "mad", "replacement": n_repl, "arrival_rate_per_s": rate,
+                           "budget_bytes": budget, "masks": "kept on the device"},
+                "stream_bf16": res_bf16, "stream_float32": res_f32, "roofline": None, "cpu_baseline": None,
+                "e2e": None, "clocks": sampler.summary(),
+                "note": "throughput over the makespan of a Poisson stream: bounded by the offered load when the "
+                        "GPU keeps up"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -485,6 +577,8 @@ def main():
         return run_batch_bench(args, rank, world, local)
     if args.workload.endswith(("-bf16", "-fp16")):
         return run_half_bench(args, rank, world, local)
+    if args.workload == "stream512":
+        return run_stream_bench(args, rank, world, local)
 
     import torch
 

@@ -189,6 +189,43 @@ int sc_run_half(sc_ctx *ctx, const uint16_t *cube_dev, int is_bf16, const float 
                 float replacement, uint8_t *mask_dev, double *sigma_host, double *sigma0_host, uint32_t flags,
                 void *cuda_stream);
 
+/* ---- stream of sub-cubes: asynchronous submission with admission -------
+ * Storage of a submitted cube: float32, or 16-bit with per-channel scales
+ * (as sc_run_half). */
+#define SC_STORE_F32 0
+#define SC_STORE_BF16 1
+#define SC_STORE_FP16 2
+
+/* Admission budget of sc_submit in bytes (0 = no limit): the cube and mask
+ * bytes of the jobs submitted and not yet returned by sc_poll never exceed it. */
+int sc_set_budget(sc_ctx *ctx, uint64_t bytes);
+
+/* Enqueue S+C of one cube and return at once with *job_id (> 0). The job runs
+ * on one of the context's three job lanes (workspaces of max_voxels voxels
+ * with their own streams, shared with sc_run_batch: do not run a batch while
+ * jobs are in flight), round robin, after the lane's earlier jobs; 16-bit
+ * storage is decoded into the lane's staging cube first. The caller keeps
+ * cube_dev, chan_scale_dev (16-bit storage only) and mask_dev alive and
+ * untouched until sc_poll returns the job. The job starts after the work
+ * enqueued on cuda_stream before the call (whatever produced the cube); once
+ * sc_poll has returned it, its mask may be read from any stream. Arguments as
+ * sc_run otherwise.
+ * Errors: SC_ERR_BUDGET when admitting the job would exceed the budget
+ * (nothing is enqueued; poll and retry), the argument errors of sc_run,
+ * SC_ERR_NOMEM, SC_ERR_CUDA. */
+int sc_submit(sc_ctx *ctx, const void *cube_dev, int storage, const float *chan_scale_dev, const int64_t *dims,
+              const sc_kernel *kernels, int n_kernels, float threshold, int noise_mode, float replacement,
+              uint8_t *mask_dev, uint32_t flags, int64_t *job_id, void *cuda_stream);
+
+/* Return one finished job, if any: 1 with *job_id, *status (SC_OK or the
+ * job's error code), *latency_s (host time of the device's completion minus
+ * the host time of sc_submit) and the job's sigmas (sigma_host must hold its
+ * n_kernels values; either pointer may be NULL); 0 when no job has finished
+ * (wait = 0) or none is in flight. wait != 0 blocks until the oldest job
+ * finishes when none has. Negative on a CUDA error. */
+int sc_poll(sc_ctx *ctx, int wait, int64_t *job_id, int *status, double *latency_s, double *sigma_host,
+            double *sigma0_host);
+
 /* sc_run on host buffers: copies cube_host to a device staging cube owned by
  * the context (allocated on first use, max_voxels floats), runs S+C and copies
  * the mask back to mask_host. Pinned (cudaHostAlloc'd / registered) host

@@ -12,7 +12,9 @@
 //   end          1-bit working mask -> caller's uint8 mask; sigmas to host.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
+#include <deque>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -69,6 +71,25 @@ struct sc_ctx {
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_done;
   cudaEvent_t fork = nullptr;
+  // sc_submit / sc_poll: jobs in flight, their admission budget and the clock
+  // reference that maps device completion times to host time
+  struct Job {
+    long long id;
+    int lane;
+    int n_kernels;
+    cudaEvent_t done;
+    double t_submit;
+    unsigned long long bytes;
+    unsigned char* slot;  // pinned per-job results (status, warnings, sigmas)
+  };
+  std::deque<Job> jobs;
+  long long next_job = 1;
+  unsigned long long budget = 0;  // 0: no limit
+  unsigned long long in_flight = 0;
+  std::vector<cudaEvent_t> job_events;
+  std::vector<unsigned char*> job_slots;
+  cudaEvent_t clock_ev = nullptr;
+  double clock_host = 0.0;
 };
 
 namespace {
@@ -434,6 +455,13 @@ void sc_destroy(sc_ctx* c) {
   for (cudaStream_t ls : c->lane_streams) cudaStreamDestroy(ls);
   for (cudaEvent_t e : c->lane_done) cudaEventDestroy(e);
   if (c->fork) cudaEventDestroy(c->fork);
+  for (auto& j : c->jobs) {
+    cudaEventDestroy(j.done);
+    cudaFreeHost(j.slot);
+  }
+  for (cudaEvent_t e : c->job_events) cudaEventDestroy(e);
+  for (unsigned char* p : c->job_slots) cudaFreeHost(p);
+  if (c->clock_ev) cudaEventDestroy(c->clock_ev);
   cudaGetLastError();
   delete c;
 }
@@ -660,6 +688,138 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
   }
   if (first == SC_OK) c->stats.runs += (unsigned long long)n_cubes;
   return first;
+}
+
+namespace {
+
+double host_seconds() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+int sc_set_budget(sc_ctx* c, uint64_t bytes) {
+  if (!c) return SC_ERR_ARG;
+  c->budget = bytes;
+  return SC_OK;
+}
+
+int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_scale_dev, const int64_t* dims,
+              const sc_kernel* kernels, int n_kernels, float threshold, int noise_mode, float replacement,
+              uint8_t* mask_dev, uint32_t flags, int64_t* job_id, void* cuda_stream) {
+  if (!c || !cube_dev || !mask_dev || !job_id) return SC_ERR_ARG;
+  if (storage != SC_STORE_F32 && storage != SC_STORE_BF16 && storage != SC_STORE_FP16) return SC_ERR_ARG;
+  if (storage != SC_STORE_F32 && !chan_scale_dev) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  long long n = 0;
+  std::vector<PairDesc> pds;
+  int rc = validate_common(c, storage == SC_STORE_F32 ? (const float*)cube_dev : c->S, dims, kernels, n_kernels,
+                           threshold, noise_mode, &n, &pds);
+  if (rc) return rc;
+  if (!std::isfinite(replacement)) return SC_ERR_ARG;
+  const unsigned long long bytes = (unsigned long long)n * ((storage == SC_STORE_F32 ? 4u : 2u) + 1u);
+  if (c->budget && c->in_flight + bytes > c->budget) return SC_ERR_BUDGET;
+  rc = ensure_lanes(c);
+  if (rc) return rc;
+  if (!c->clock_ev) {
+    // device-to-host clock reference: an event completed at a known host time
+    if (cudaEventCreate(&c->clock_ev) != cudaSuccess || cudaEventRecord(c->clock_ev, c->lane_streams[0]) != cudaSuccess ||
+        cudaEventSynchronize(c->clock_ev) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_CUDA;
+    }
+    c->clock_host = host_seconds();
+  }
+  // jobs use the lanes other than the context itself, round robin
+  const int n_job_lanes = (int)c->lanes.size() - 1;
+  const int l = 1 + (int)((c->next_job - 1) % n_job_lanes);
+  sc_ctx* lc = c->lanes[l];
+  cudaStream_t ls = c->lane_streams[l];
+  lc->tune = c->tune;
+  lc->profiling = 0;
+  // the job starts after the work already enqueued on the caller's stream
+  CK(cudaEventRecord(c->fork, (cudaStream_t)cuda_stream));
+  CK(cudaStreamWaitEvent(ls, c->fork, 0));
+  cudaEvent_t done = nullptr;
+  if (!c->job_events.empty()) {
+    done = c->job_events.back();
+    c->job_events.pop_back();
+  } else {
+    CK(cudaEventCreate(&done));
+  }
+  unsigned char* slot = nullptr;
+  if (!c->job_slots.empty()) {
+    slot = c->job_slots.back();
+    c->job_slots.pop_back();
+  } else if (cudaHostAlloc(&slot, sizeof(BatchRes), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    c->job_events.push_back(done);
+    return SC_ERR_NOMEM;
+  }
+  const double t_submit = host_seconds();
+  const float* src = (const float*)cube_dev;
+  if (storage != SC_STORE_F32) {
+    rc = ensure_stage(lc);
+    if (rc == SC_OK && launch_decode_half((const uint16_t*)cube_dev, chan_scale_dev, (long long)dims[0] * dims[1], n,
+                                         storage == SC_STORE_BF16 ? 1 : 0, lc->stage_cube, lc->sms, ls) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "launch_decode_half", __LINE__);
+    src = lc->stage_cube;
+  }
+  if (rc == SC_OK)
+    rc = run_device(lc, src, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, ls);
+  if (rc == SC_OK) {
+    BatchRes* r = reinterpret_cast<BatchRes*>(slot);
+    if (cudaMemcpyAsync(r, lc->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ls) != cudaSuccess ||
+        cudaMemcpyAsync(r->sigma, lc->st->sigma, sizeof(float) * n_kernels, cudaMemcpyDeviceToHost, ls) !=
+            cudaSuccess ||
+        cudaEventRecord(done, ls) != cudaSuccess)
+      rc = cuda_fail(cudaGetLastError(), "sc_submit", __LINE__);
+  }
+  c->stats.launches += lc->stats.launches + (storage != SC_STORE_F32 ? 1 : 0);
+  lc->stats.launches = 0;
+  if (rc) {
+    c->job_events.push_back(done);
+    c->job_slots.push_back(slot);
+    return rc;
+  }
+  c->jobs.push_back({c->next_job, l, n_kernels, done, t_submit, bytes, slot});
+  c->in_flight += bytes;
+  *job_id = c->next_job++;
+  return SC_OK;
+}
+
+int sc_poll(sc_ctx* c, int wait, int64_t* job_id, int* status, double* latency_s, double* sigma_host,
+            double* sigma0_host) {
+  if (!c || !job_id) return SC_ERR_ARG;
+  if (c->jobs.empty()) return 0;
+  DeviceGuard g(c->device);
+  for (;;) {
+    for (auto it = c->jobs.begin(); it != c->jobs.end(); ++it) {
+      const cudaError_t q = cudaEventQuery(it->done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery", __LINE__);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, c->clock_ev, it->done);
+      const BatchRes* r = reinterpret_cast<const BatchRes*>(it->slot);
+      const int code = status_code(r->status);
+      *job_id = it->id;
+      if (status) *status = code;
+      if (latency_s) *latency_s = c->clock_host + 1e-3 * ms - it->t_submit;
+      if (sigma0_host) *sigma0_host = code == SC_OK ? (double)r->sigma0 : 0.0;
+      if (sigma_host)
+        for (int k = 0; k < it->n_kernels; ++k) sigma_host[k] = code == SC_OK ? (double)r->sigma[k] : 0.0;
+      c->stats.warnings = r->warn;
+      if (code == SC_OK) c->stats.runs += 1;
+      c->in_flight -= it->bytes;
+      c->job_events.push_back(it->done);
+      c->job_slots.push_back(it->slot);
+      c->jobs.erase(it);
+      return 1;
+    }
+    if (!wait) return 0;
+    const cudaError_t e = cudaEventSynchronize(c->jobs.front().done);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize", __LINE__);
+  }
 }
 
 int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_kernels, void* cuda_stream) {

@@ -34,6 +34,7 @@ SC_FLAG_ACCUMULATE = 0x1
 SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
+SC_STORE_F32, SC_STORE_BF16, SC_STORE_FP16 = 0, 1, 2
 
 SC_WARN_ZERO_SIGMA = 0x1
 SC_WARN_FULL_SELECT = 0x2
@@ -84,6 +85,11 @@ _SIGS = {
                                C.c_float, C.c_int, C.c_float, C.POINTER(_P), C.POINTER(C.c_double),
                                C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_autotune": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, _P]),
+    "sc_set_budget": (C.c_int, [_P, C.c_uint64]),
+    "sc_submit": (C.c_int, [_P, _P, C.c_int, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int,
+                            C.c_float, _P, C.c_uint32, C.POINTER(C.c_int64), _P]),
+    "sc_poll": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "sc_run_half": (C.c_int, [_P, _P, C.c_int, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float,
                               C.c_int, C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
@@ -239,6 +245,50 @@ def sc_run_half(ctx, cube16: torch.Tensor, bf16: bool, chan_scale: torch.Tensor,
     return mask, [float(x) for x in sig], float(sig0[0])
 
 
+def sc_set_budget(ctx, nbytes: int) -> None:
+    _check(lib().sc_set_budget(ctx, int(nbytes)), "sc_set_budget")
+
+
+def sc_submit(ctx, cube: torch.Tensor, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0,
+              mask: torch.Tensor | None = None, storage: int = SC_STORE_F32, chan_scale: torch.Tensor | None = None,
+              flags: int = 0, stream=None):
+    """Enqueue S+C of one CUDA cube (float32, or 16-bit bit patterns with
+    chan_scale for SC_STORE_BF16 / SC_STORE_FP16). Returns (job_id, mask); the
+    caller keeps cube, chan_scale and mask alive until sc_poll returns the job.
+    Raises ScError with code SC_ERR_BUDGET when the job is not admitted."""
+    if storage == SC_STORE_F32:
+        _dev(cube, torch.float32, "cube")
+        sp = None
+    else:
+        if not (isinstance(cube, torch.Tensor) and cube.is_cuda and cube.element_size() == 2 and
+                not cube.is_floating_point() and cube.is_contiguous()):
+            raise ScError(SC_ERR_ARG, "cube must hold 16-bit bit patterns")
+        _dev(chan_scale, torch.float32, "chan_scale")
+        sp = C.c_void_p(chan_scale.data_ptr())
+    if mask is None:
+        mask = torch.empty(cube.shape, dtype=torch.uint8, device=cube.device)
+    _dev(mask, torch.uint8, "mask")
+    kk, nk = _kernels(kernels)
+    jid = C.c_int64(0)
+    code = lib().sc_submit(ctx, C.c_void_p(cube.data_ptr()), int(storage), sp, _dims(cube.shape), kk, nk,
+                           float(threshold), int(NOISE_MODES.get(noise_mode, noise_mode)), float(replacement),
+                           C.c_void_p(mask.data_ptr()), int(flags), C.byref(jid), _stream(cube, stream))
+    _check(code, "sc_submit")
+    return int(jid.value), mask
+
+
+def sc_poll(ctx, n_kernels: int, wait: bool = False):
+    """One finished job as (job_id, status, latency_s, sigmas, sigma0), or None."""
+    jid, st, lat = C.c_int64(0), C.c_int(0), C.c_double(0.0)
+    sig, sig0 = (C.c_double * max(1, n_kernels))(), C.c_double(0.0)
+    code = lib().sc_poll(ctx, 1 if wait else 0, C.byref(jid), C.byref(st), C.byref(lat), sig, C.byref(sig0))
+    if code < 0:
+        _check(code, "sc_poll")
+    if code == 0:
+        return None
+    return int(jid.value), int(st.value), float(lat.value), [float(sig[k]) for k in range(n_kernels)], float(sig0.value)
+
+
 def sc_autotune(ctx, shape, kernels, device: int = 0, stream=None) -> None:
     """Time the smoothing variants for cubes of this (nz, ny, nx) shape and keep
     the fastest per kernel pair in the context (synchronises)."""
@@ -364,6 +414,17 @@ class Context:
                  flags=0, stream=None, want_sigma=True):
         return sc_run_half(self.handle, cube16, bf16, chan_scale, kernels, threshold, noise_mode, replacement, mask,
                            flags, stream, want_sigma)
+
+    def set_budget(self, nbytes):
+        sc_set_budget(self.handle, nbytes)
+
+    def submit(self, cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, storage=SC_STORE_F32,
+               chan_scale=None, flags=0, stream=None):
+        return sc_submit(self.handle, cube, kernels, threshold, noise_mode, replacement, mask, storage, chan_scale,
+                         flags, stream)
+
+    def poll(self, n_kernels, wait=False):
+        return sc_poll(self.handle, n_kernels, wait)
 
     def autotune(self, shape, kernels, stream=None):
         sc_autotune(self.handle, shape, kernels, self.device, stream)
