@@ -302,10 +302,17 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
   {
     Phase ph(c, s, EV_SELECT);
-    CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));
+    CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));  // full range, and max |C|
     c->stats.launches += 1;
+    if (!std_mode) {
+      // a second, windowed histogram around the median |C|: a fine plan
+      CK(launch_window_from_hist(c->st, c->hist, s));
+      CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
+      CK(launch_hist(cube, n, c->st, c->hist, 1, 0, c->sms, s));
+      c->stats.launches += 2;
+    }
   }
-  rc = measure(c, cube, n, 0, t, first_identity ? 1 : 0, std_mode, first_identity ? 0 : -1, force, s);
+  rc = measure(c, cube, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, std_mode, first_identity ? 0 : -1, force, s);
   if (rc) return rc;
   CK(launch_sigma0_done(c->st, replacement, W, nk, s));
   c->stats.launches += 1;

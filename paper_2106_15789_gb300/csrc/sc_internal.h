@@ -190,6 +190,8 @@ cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, Dev
                              cudaStream_t s);
 cudaError_t launch_std(const float* src, long long n, DevState* st, int sms, cudaStream_t s);
 cudaError_t launch_std_final(DevState* st, int pair, cudaStream_t s);
+// DevState::win from the full-range histogram of a raw cube (median of |x|)
+cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s);
 cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,
                                cudaStream_t s);
 cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s);

@@ -895,6 +895,32 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
   return cudaGetLastError();
 }
 
+// Window of the fine histogram of the raw cube from its full-range one: the
+// bin of the median of |x| gives the scale, and the window spans 2^-20 .. 2^12
+// of it (as for the smoothed cubes), so the plan of the sigma_0 measurement
+// resolves 128 bins per octave instead of 16.
+__global__ void k_window_from_hist(DevState* st, const unsigned long long* __restrict__ hist) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const BinCfg full = kFullRange;
+  unsigned long long n = 0;
+  for (int i = 0; i < kNumBins; ++i) n += hist[i];
+  unsigned long long acc = 0;
+  float scale = 0.0f;
+  for (int mb = 0; mb < kBinsPerSign && n > 0; ++mb) {
+    acc += hist[kBinsPerSign + mb] + hist[kBinsPerSign - 1 - mb];  // both signs, magnitude bin mb
+    if (2 * acc > n) {
+      scale = (float)mag_hi(mb, full);
+      break;
+    }
+  }
+  st->win = window_cfg(isfinite(scale) ? scale : 3.0e38f);
+}
+
+cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s) {
+  k_window_from_hist<<<1, 1, 0, s>>>(st, hist);
+  return cudaGetLastError();
+}
+
 __global__ void k_sigma0_done(DevState* st, float replacement, PairWeights W, int n_pairs) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const float s0 = st->sigma_cur;

@@ -197,11 +197,14 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
 #pragma unroll
       for (int i = 0; i < VPT; ++i) {
         const float c = cur[i];
-        const bool fin = (__float_as_uint(c) & 0x7f800000u) != 0x7f800000u;
-        long long q = quantize(c, fscale);
-        if (do_repl) q = ((mcur >> i) & 1u) ? (c >= 0.0f ? qrepl : -qrepl) : q;
-        Pq[i] = fin ? q : 0ll;
-        nanbits |= (fin ? 0u : 1u) << i;
+        // c + (c - c) is NaN for NaN and Inf, whose quantised value is 0
+        Pq[i] = quantize(c + (c - c), fscale);
+        nanbits |= ((__float_as_uint(c) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
+      }
+      if (do_repl && mcur != 0u) {  // masked voxels are finite (the working mask holds no others)
+#pragma unroll
+        for (int i = 0; i < VPT; ++i)
+          if ((mcur >> i) & 1u) Pq[i] = cur[i] >= 0.0f ? qrepl : -qrepl;
       }
       nan_hist = (nan_hist << VPT) | nanbits;
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
