@@ -86,20 +86,30 @@ namespace ws {
 
 using namespace tc;
 
-constexpr int kPW = 8, kCW = 8;                // producer / consumer warps
-constexpr int kPT = 32 * kPW, kCT = 32 * kCW;  // threads per group
-constexpr int kThreads = kPT + kCT;
-constexpr int TX = 64, TY = 32;
+constexpr int kPW = 8;               // producer warps
+constexpr int kPT = 32 * kPW;        // producer threads
+constexpr int TX = 64;               // tile width
 constexpr int SEGY = 8;              // consecutive rows per consumer thread
 constexpr int kStages = 4;           // raw-tile buffers: being read by consumers, converted, two in flight
 constexpr int kLookahead = 2;        // planes loaded ahead of the one being converted
-constexpr int kMaxWz = 15;           // ring of wz slots; 8-bit NaN history per plane in 64 bits
 constexpr int kSlotCols = 2 * SEGY;  // TMEM columns per ring slot (8 int64)
 constexpr unsigned kBarProducers = 1;
-static_assert(kCT == TX * (TY / SEGY), "one consumer thread per column segment");
-static_assert(kMaxWz * kSlotCols <= kTmemCols / 2, "two consumer warps share each TMEM lane quarter");
 
-template <int W1, int W2, int W3>
+// Tile height TY: one consumer thread per 8-row column segment, so TY/4
+// consumer warps; a consumer warp's TMEM lane quarter is shared by TY/16
+// warps, which bounds the ring to kMaxWz planes (15 for TY = 32, 31 for 16).
+template <int TY>
+struct Tile {
+  static constexpr int kCW = TY / 4;
+  static constexpr int kCT = 32 * kCW;
+  static constexpr int kThreads = kPT + kCT;
+  static constexpr int kColsPerWarp = kTmemCols / (kCW / 4);
+  static constexpr int kMaxWz = ((kColsPerWarp / kSlotCols) - 1) | 1;
+  static_assert(kCT == TX * (TY / SEGY), "one consumer thread per column segment");
+  static_assert(kCW % 4 == 0, "consumer warps cover the four TMEM lane quarters evenly");
+};
+
+template <int W1, int W2, int W3, int TY>
 struct Geo {
   static constexpr int R = (W1 - 1) / 2 + (W2 - 1) / 2 + (W3 - 1) / 2;
   static constexpr int RA = (R + 3) & ~3;  // x halo of the raw tile (16-byte aligned TMA x coordinate)
@@ -111,7 +121,7 @@ struct Geo {
   static constexpr int SEGX = BY * (TX / 8) <= kPT ? 8 : 16;  // x outputs per producer item
   static constexpr int XITEMS = BY * (TX / SEGX);
   static constexpr int NCONV = (BY * PX + kPT - 1) / kPT;
-  static constexpr int XBUF = R <= 8 ? 2 : 1;  // quantised tiles (two fit in shared memory up to R = 8)
+  static constexpr int XBUF = (R <= 8 || TY <= 16) ? 2 : 1;  // quantised tiles (two if they fit)
   static_assert(XITEMS <= kPT, "one x-pass item per producer thread");
   static_assert(4 * BY <= kPT, "one mask word per producer thread");
   static_assert(PX <= 128, "four mask words per row");
@@ -121,9 +131,9 @@ struct Smem {
   size_t raw[kStages], mw, x, b, hist, mbar, total;
 };
 
-template <int W1, int W2, int W3>
+template <int W1, int W2, int W3, int TY>
 __host__ __device__ constexpr Smem smem_layout(bool hist) {
-  using G = Geo<W1, W2, W3>;
+  using G = Geo<W1, W2, W3, TY>;
   Smem s{};
   size_t o = 0;
   for (int b = 0; b < kStages; ++b) {
@@ -147,11 +157,11 @@ __host__ __device__ constexpr Smem smem_layout(bool hist) {
 // Quantise the halo'd raw tile into X, in chunks of kConvChunk elements whose
 // loads are all issued before their stores (the pointers do not alias).
 constexpr int kConvChunk = 4;
-template <int W1, int W2, int W3, bool REPL>
+template <int W1, int W2, int W3, int TY, bool REPL>
 __device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const unsigned* __restrict__ mwb,
                                              long long* __restrict__ X, int pt, float fscale, long long qrepl,
                                              bool do_repl) {
-  using G = Geo<W1, W2, W3>;
+  using G = Geo<W1, W2, W3, TY>;
   constexpr int R = G::R, RA = G::RA;
 #pragma unroll
   for (int k0 = 0; k0 < G::NCONV; k0 += kConvChunk) {
@@ -185,23 +195,25 @@ __device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const
 
 // x cascade of one row segment (SEGX outputs). The pointers do not alias, so
 // the stream's loads need not wait for its stores.
-template <int W1, int W2, int W3>
+template <int W1, int W2, int W3, int TY>
 __device__ __forceinline__ void xpass_item(const long long* __restrict__ src, long long* __restrict__ dst) {
-  using G = Geo<W1, W2, W3>;
+  using G = Geo<W1, W2, W3, TY>;
   cascade_stream<W1, W2, W3, G::SEGX>([&](int i) { return src[i]; }, [&](int k, long long v) { dst[k] = v; });
 }
 
 }  // namespace ws
 
-template <int W1, int W2, int W3, bool REPL, bool TMA>
-__global__ void __launch_bounds__(ws::kThreads, 1)
+template <int W1, int W2, int W3, bool REPL, bool TMA, int TY>
+__global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
     k_smooth_ws(const __grid_constant__ CUtensorMap tmap, SmoothArgs a) {
   using namespace ws;
-  using G = Geo<W1, W2, W3>;
+  using G = Geo<W1, W2, W3, TY>;
+  using T = Tile<TY>;
+  constexpr int kCW = T::kCW, kCT = T::kCT, kThreads = T::kThreads;
   constexpr int R = G::R, RA = G::RA;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-  const Smem L = smem_layout<W1, W2, W3>(a.hist != nullptr);
+  const Smem L = smem_layout<W1, W2, W3, TY>(a.hist != nullptr);
   float* const raw0 = reinterpret_cast<float*>(smem + L.raw[0]);
   constexpr size_t kRawStride = al128(sizeof(float) * (size_t)G::BY * G::BX) / sizeof(float);
   unsigned* const mw = reinterpret_cast<unsigned*>(smem + L.mw);
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const unsigned* mwb = mw + b * 4 * G::BY;
         long long* const X = Xt + (G::XBUF == 2 ? (size_t)b * G::BY * G::XP : 0);
         // quantise the halo'd tile once
-        convert_tile<W1, W2, W3, REPL>(rb, mwb, X, pt, fscale, qrepl, do_repl);
+        convert_tile<W1, W2, W3, TY, REPL>(rb, mwb, X, pt, fscale, qrepl, do_repl);
         if (do_repl && j + 1 < n_steps && pt < 4 * G::BY) mw[((g + 1) & 1) * 4 * G::BY + pt] = mask_finish(x0, m_next);
         m_next = m_after;
         // quantised tile and next mask words done; with two tiles, also every
@@ -356,7 +368,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         // x pass into buffer b
         if (pt < G::XITEMS) {
           const int row = pt % G::BY, seg = pt / G::BY;
-          xpass_item<W1, W2, W3>(X + row * G::XP + seg * G::SEGX,
+          xpass_item<W1, W2, W3, TY>(X + row * G::XP + seg * G::SEGX,
                                  Bt + (size_t)b * G::BY * G::BP + row * G::BP + seg * G::SEGX);
         }
         __syncwarp();
@@ -371,7 +383,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const BinCfg cfg = a.win ? a.st->win : kFullRange;
     const float inv = a.st->fx_inv[a.pair];
     const unsigned tmine =
-        tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((kTmemCols / 2) * ((warp - kPW) >> 2));
+        tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(T::kColsPerWarp * ((warp - kPW) >> 2));
     if (!TMA)
       for (int k = 0; k < kLookahead; ++k) issue_async(ct);
     long long g = 0;
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         for (int s = 0; s < wz; ++s) tmem_st16(tmine + (unsigned)(kSlotCols * s), zero);
         tmem_wait_st();
       }
-      unsigned long long nan_hist = 0ull;
+      unsigned long long nan_lo = 0ull, nan_hi = 0ull;  // NaN bytes of the last 16 planes, newest lowest
       const long long gx = (long long)x0 + xc;
       const long long gy0 = (long long)y0 + grp * SEGY;
       unsigned rows_in = 0u;  // rows of this thread inside the cube
@@ -424,7 +436,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         // plane before the producers could finish plane g, whose hand-off this
         // thread has passed. Refill it with plane g + 2.
         if (!TMA) issue_async(ct);
-        nan_hist = (nan_hist << SEGY) | nbyte;
+        nan_hi = (nan_hi << SEGY) | (nan_lo >> (64 - SEGY));
+        nan_lo = (nan_lo << SEGY) | nbyte;
         if (wz > 1) {
           unsigned nw[kSlotCols];
           tmem_wait_ld();
@@ -442,7 +455,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
         if (j >= 2 * r) {
           const long long zo = zp - r;
-          const unsigned nb = (unsigned)(nan_hist >> (SEGY * r)) & ((1u << SEGY) - 1u);
+          const unsigned nb =
+              (unsigned)((r < 8 ? nan_lo >> (SEGY * r) : nan_hi >> (SEGY * (r - 8))) & ((1ull << SEGY) - 1ull));
           float* out = a.S + zo * plane + gy0 * nx + gx;
 #pragma unroll
           for (int i = 0; i < SEGY; ++i) {
@@ -472,12 +486,13 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 // ---------------------------------------------------------------------------
 namespace {
 
-template <int W1, int W2, int W3>
+template <int W1, int W2, int W3, int TY>
 cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done) {
   using namespace ws;
-  using G = Geo<W1, W2, W3>;
+  using G = Geo<W1, W2, W3, TY>;
+  constexpr int kThreads = Tile<TY>::kThreads;
   SmoothArgs a = a0;
-  const Smem L = smem_layout<W1, W2, W3>(a.hist != nullptr);
+  const Smem L = smem_layout<W1, W2, W3, TY>(a.hist != nullptr);
   if (L.total + 1024 > 227 * 1024) return cudaSuccess;  // not served: the caller falls back
   CUtensorMap map;
   const bool tma = encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY);  // else the cp.async variant
@@ -497,22 +512,37 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
   const bool repl = a.mbits != nullptr && a.repl_possible;
   const size_t smem_req = one_block_per_sm_smem(L.total);
   if (tma) {
-    if (repl) k_smooth_ws<W1, W2, W3, true, true><<<grid, kThreads, smem_req, s>>>(map, a);
-    else k_smooth_ws<W1, W2, W3, false, true><<<grid, kThreads, smem_req, s>>>(map, a);
+    if (repl) k_smooth_ws<W1, W2, W3, true, true, TY><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_ws<W1, W2, W3, false, true, TY><<<grid, kThreads, smem_req, s>>>(map, a);
   } else {
-    if (repl) k_smooth_ws<W1, W2, W3, true, false><<<grid, kThreads, smem_req, s>>>(map, a);
-    else k_smooth_ws<W1, W2, W3, false, false><<<grid, kThreads, smem_req, s>>>(map, a);
+    if (repl) k_smooth_ws<W1, W2, W3, true, false, TY><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_ws<W1, W2, W3, false, false, TY><<<grid, kThreads, smem_req, s>>>(map, a);
   }
   *done = true;
   return cudaGetLastError();
 }
 
+// Tile height for a spectral width: 32 rows while the ring of w planes fits
+// two consumer warps per TMEM lane quarter, else 16 rows.
+template <int W1, int W2, int W3>
+cudaError_t launch_ws_for_wz(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
+  if (a.pd.wz <= ws::Tile<32>::kMaxWz) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
+  if (a.pd.wz <= ws::Tile<16>::kMaxWz) return launch_ws<W1, W2, W3, 16>(a, sms, s, done);
+  return cudaSuccess;
+}
+
+template <int W1, int W2, int W3, int TY>
+void set_ws_attr_ty() {
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, true, TY>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, true, TY>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, false, TY>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, false, TY>);
+}
+
 template <int W1, int W2, int W3>
 void set_ws_attr() {
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, true>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, true>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, false>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, false>);
+  set_ws_attr_ty<W1, W2, W3, 32>();
+  set_ws_attr_ty<W1, W2, W3, 16>();
 }
 
 }  // namespace
@@ -525,16 +555,17 @@ void init_ws_attrs() {
 }
 
 // The warp-specialised kernel for the cascades of FWHM 3, 5, 6 and 10 px with
-// spectral widths up to 15 (TMA loads where the cube allows them, cp.async
-// otherwise); *done = false for other pairs.
+// spectral widths up to 31 (64 x 32 tiles up to 15, 64 x 16 tiles beyond; TMA
+// loads where the cube allows them, cp.async otherwise); *done = false for
+// other pairs.
 cudaError_t launch_smooth_ws(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
-  if (a.generic || a.pd.wz > ws::kMaxWz) return cudaSuccess;
+  if (a.generic || a.pd.wz > ws::Tile<16>::kMaxWz) return cudaSuccess;
   const int* w = a.pd.w;
-  if (w[0] == 1 && w[1] == 3 && w[2] == 3) return launch_ws<1, 3, 3>(a, sms, s, done);
-  if (w[0] == 3 && w[1] == 5 && w[2] == 5) return launch_ws<3, 5, 5>(a, sms, s, done);
-  if (w[0] == 5 && w[1] == 5 && w[2] == 5) return launch_ws<5, 5, 5>(a, sms, s, done);
-  if (w[0] == 7 && w[1] == 9 && w[2] == 9) return launch_ws<7, 9, 9>(a, sms, s, done);
+  if (w[0] == 1 && w[1] == 3 && w[2] == 3) return launch_ws_for_wz<1, 3, 3>(a, sms, s, done);
+  if (w[0] == 3 && w[1] == 5 && w[2] == 5) return launch_ws_for_wz<3, 5, 5>(a, sms, s, done);
+  if (w[0] == 5 && w[1] == 5 && w[2] == 5) return launch_ws_for_wz<5, 5, 5>(a, sms, s, done);
+  if (w[0] == 7 && w[1] == 9 && w[2] == 9) return launch_ws_for_wz<7, 9, 9>(a, sms, s, done);
   return cudaSuccess;
 }
 
