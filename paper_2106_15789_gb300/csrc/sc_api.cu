@@ -864,6 +864,7 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
     for (int zf : {1, 2, 4}) {
       if (pd.h > 0) {
         cands.push_back({TUNE_WS, zf});
+        cands.push_back({TUNE_WS16, zf});
         cands.push_back({TUNE_TILE, zf});
       } else {
         cands.push_back({TUNE_Z8, zf});

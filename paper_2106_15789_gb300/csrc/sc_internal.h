@@ -172,7 +172,15 @@ struct SmoothArgs {
 };
 
 // Kernel choices the autotuner may fix for a (dims, kernel pair).
-enum TuneKind : int { TUNE_AUTO = 0, TUNE_WS = 1, TUNE_TILE = 2, TUNE_GENERIC = 3, TUNE_Z8 = 4, TUNE_Z4 = 5 };
+enum TuneKind : int {
+  TUNE_AUTO = 0,     // the dispatcher decides
+  TUNE_WS = 1,       // warp-specialised kernel, default tile height
+  TUNE_TILE = 2,     // single-group tile kernel
+  TUNE_GENERIC = 3,  // generic FIR kernel
+  TUNE_Z8 = 4,       // spectral-only kernel, 8 voxels per thread
+  TUNE_Z4 = 5,       // spectral-only kernel, 4 voxels per thread
+  TUNE_WS16 = 6      // warp-specialised kernel with 64 x 16 tiles
+};
 inline long long tune_items_per_sm(const SmoothArgs& a) { return a.tune_zfactor > 0 ? a.tune_zfactor : 2; }
 
 // ---------------------------------------------------------------------------

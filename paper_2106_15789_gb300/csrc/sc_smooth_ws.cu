@@ -523,10 +523,11 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
 }
 
 // Tile height for a spectral width: 32 rows while the ring of w planes fits
-// two consumer warps per TMEM lane quarter, else 16 rows.
+// two consumer warps per TMEM lane quarter, else (or when the autotuner chose
+// it) 16 rows.
 template <int W1, int W2, int W3>
 cudaError_t launch_ws_for_wz(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
-  if (a.pd.wz <= ws::Tile<32>::kMaxWz) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
+  if (a.pd.wz <= ws::Tile<32>::kMaxWz && a.tune_kind != TUNE_WS16) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
   if (a.pd.wz <= ws::Tile<16>::kMaxWz) return launch_ws<W1, W2, W3, 16>(a, sms, s, done);
   return cudaSuccess;
 }
