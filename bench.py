@@ -266,6 +266,61 @@ def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
             "smoothing_ms_by_kernel": {name: round(v[0] / steps, 3) for name, v in groups.items()}}
 
 
+def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world):
+    """End to end through sc_run from pinned host memory: every step copies its
+    cube host -> device and its mask device -> host; with two device buffers
+    the next cube's copy and the previous mask's copy run on a copy stream
+    while the current step computes. The sigmas come back synchronously."""
+    import torch
+
+    cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+    cube_h.copy_(cube)
+    mask_h = [torch.empty(cube.shape, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    bufs = [torch.empty_like(cube) for _ in range(2)]
+    masks = [torch.empty(cube.shape, dtype=torch.uint8, device=dev) for _ in range(2)]
+    compute = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    loaded = [torch.cuda.Event() for _ in range(2)]
+    computed = [torch.cuda.Event() for _ in range(2)]
+    sent = [torch.cuda.Event() for _ in range(2)]
+
+    def run(steps):
+        with torch.cuda.stream(copy):
+            bufs[0].copy_(cube_h, non_blocking=True)
+            loaded[0].record(copy)
+        for i in range(steps):
+            b, nb = i % 2, (i + 1) % 2
+            if i + 1 < steps:
+                with torch.cuda.stream(copy):
+                    if i >= 1:
+                        copy.wait_event(computed[nb])  # step i - 1 is done with that buffer
+                    bufs[nb].copy_(cube_h, non_blocking=True)
+                    loaded[nb].record(copy)
+            compute.wait_event(loaded[b])
+            if i >= 2:
+                compute.wait_event(sent[b])  # its mask of step i - 2 has left the device
+            ctx.run(bufs[b], kernels, t, "mad", n_repl, mask=masks[b])  # sigmas: synchronous
+            computed[b].record(compute)
+            with torch.cuda.stream(copy):
+                copy.wait_event(computed[b])
+                mask_h[b].copy_(masks[b], non_blocking=True)
+                sent[b].record(copy)
+        torch.cuda.synchronize(dev)
+
+    run(2)
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    run(args.e2e_steps)
+    dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
+    nvox = cube.numel()
+    return {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
+            "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1),
+            "steps": args.e2e_steps,
+            "api": "sc_run on device copies of a pinned host cube; next cube's H2D and previous mask's D2H overlap "
+                   "the current step on a copy stream (two device buffers); sigmas read back synchronously"}
+
+
 def run_batch_bench(args, rank, world, local):
     """The batched form: 64 uneven sub-cubes per rank in one graph-captured
     sc_run_batch call per step, after autotuning every sub-cube shape."""
@@ -332,31 +387,57 @@ def run_batch_bench(args, rank, world, local):
 
     e2e = None
     if not args.no_e2e:
+        # pinned host sub-cubes; two device buffer sets so that the next
+        # batch's H2D copies and the previous batch's mask D2H copies run on a
+        # copy stream while the current batch computes
         hosts = [torch.empty(c.shape, dtype=torch.float32, pin_memory=True) for c in cubes]
         for h, c in zip(hosts, cubes):
             h.copy_(c)
-        mask_h = [torch.empty(c.shape, dtype=torch.uint8, pin_memory=True) for c in cubes]
-        work = [torch.empty_like(c) for c in cubes]
+        mask_h = [[torch.empty(c.shape, dtype=torch.uint8, pin_memory=True) for c in cubes] for _ in range(2)]
+        work = [[torch.empty_like(c) for c in cubes] for _ in range(2)]
+        wmask = [masks, [torch.empty_like(m) for m in masks]]
+        copy = torch.cuda.Stream(dev)
+        loaded = [torch.cuda.Event() for _ in range(2)]
+        computed = [torch.cuda.Event() for _ in range(2)]
+        sent = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step():
-            for w, h in zip(work, hosts):
-                w.copy_(h, non_blocking=True)
-            m, _, _ = ctx.run_batch(work, kernels, t, "mad", n_repl, masks=masks, flags=sc.SC_FLAG_GRAPH)
-            for mh, md in zip(mask_h, m):
-                mh.copy_(md, non_blocking=True)
-            torch.cuda.synchronize()
+        def e2e_run(steps):
+            with torch.cuda.stream(copy):
+                for w, h in zip(work[0], hosts):
+                    w.copy_(h, non_blocking=True)
+                loaded[0].record(copy)
+            for i in range(steps):
+                b, nb = i % 2, (i + 1) % 2
+                if i + 1 < steps:
+                    with torch.cuda.stream(copy):
+                        if i >= 1:
+                            copy.wait_event(computed[nb])
+                        for w, h in zip(work[nb], hosts):
+                            w.copy_(h, non_blocking=True)
+                        loaded[nb].record(copy)
+                stream.wait_event(loaded[b])
+                if i >= 2:
+                    stream.wait_event(sent[b])
+                ctx.run_batch(work[b], kernels, t, "mad", n_repl, masks=wmask[b])  # sigmas: synchronous
+                computed[b].record(stream)
+                with torch.cuda.stream(copy):
+                    copy.wait_event(computed[b])
+                    for mh, md in zip(mask_h[b], wmask[b]):
+                        mh.copy_(md, non_blocking=True)
+                    sent[b].record(copy)
+            torch.cuda.synchronize(dev)
 
-        e2e_step()
+        e2e_run(2)
         if pg:
             pg.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
+        e2e_run(args.e2e_steps)
         dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
         e2e = {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * nvox, "d2h_bytes_per_step": nvox + 8 * len(cubes) * (len(kernels) + 1),
                "steps": args.e2e_steps,
-               "api": "sc_run_batch on device copies of pinned host sub-cubes, masks copied back, per step"}
+               "api": "sc_run_batch on device copies of pinned host sub-cubes; next batch's H2D and previous masks' "
+                      "D2H overlap the current batch on a copy stream (two buffer sets); sigmas read back synchronously"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -566,7 +647,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=WORKLOADS, default="wallaby")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -642,21 +723,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
-        cube_h.copy_(cube)
-        mask_h = torch.empty(cube.shape, dtype=torch.uint8, pin_memory=True)
-        ctx.run_host(cube_h, kernels, t, "mad", n_repl, mask_host=mask_h)
-        torch.cuda.synchronize()
-        if pg:
-            pg.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            ctx.run_host(cube_h, kernels, t, "mad", n_repl, mask_host=mask_h)
-        torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
-        e2e = {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
-               "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1),
-               "steps": args.e2e_steps, "api": "sc_run_host (pinned host cube and mask)"}
+        e2e = pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
