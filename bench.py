@@ -92,16 +92,75 @@ def smooth_traffic_record():
         return None
 
 
-def smoothing_kernel_name(sc, pair):
-    """Name of the smoothing kernel the library runs for one kernel pair of a
-    TMA-addressable cube (the bench workloads are)."""
-    fwhm, wz = pair
-    w = list(sc.sc_cascade_widths(fwhm)) if fwhm > 0 else [1, 1, 1]
-    if w == [1, 1, 1]:
-        return "k_smooth_z" if wz > 1 else "k_identity"
-    if tuple(w) in ((1, 3, 3), (3, 5, 5), (5, 5, 5), (7, 9, 9)) and wz <= 15:
-        return "k_smooth_ws<%d,%d,%d>" % tuple(w)
-    return "k_smooth_generic"
+TRAFFIC_WORKLOAD_VOXELS = 512 ** 3  # the medium workload, whose every smoothing launch covers the whole cube
+
+
+def ncu_kernel_key(name):
+    """Key of an ncu kernel name in the traffic record (the names
+    smoothing_kernel_name gives), or None for other kernels."""
+    import re
+
+    m = re.search(r"k_smooth_ws<(\d+), (\d+), (\d+), [^,]+, [^,]+, (\d+)>", name)
+    if m:
+        return "k_smooth_ws<%s,%s,%s>" % m.group(1, 2, 3) + ("/16" if m.group(4) == "16" else "")
+    m = re.search(r"k_smooth_tile<(\d+), (\d+), (\d+),", name)
+    if m:
+        return "k_smooth_tile<%s,%s,%s>" % m.group(1, 2, 3)
+    for k in ("k_smooth_z", "k_smooth_generic", "k_identity"):
+        if k + "<" in name or k + "(" in name:
+            return k
+    return None
+
+
+def record_traffic(csv_path, command):
+    """Write profiles/smooth_traffic.json from an ncu --csv log of
+    dram__bytes_read.sum + dram__bytes_write.sum per smoothing launch on the
+    medium workload: mean DRAM bytes per output voxel of each kernel, keyed by
+    the current smoothing-source hash."""
+    import csv
+
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per_launch = {}
+    with open(csv_path) as f:
+        rows = [r for r in csv.reader(f) if len(r) >= 15]
+    head = rows[0]
+    ci = {k: head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    for r in rows[1:]:
+        key = ncu_kernel_key(r[ci["Kernel Name"]])
+        if key is None or r[ci["Metric Name"]] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        b = float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
+        d = per_launch.setdefault((key, r[ci["ID"]]), [0.0])
+        d[0] += b
+    sums = {}
+    for (key, _), (b,) in per_launch.items():
+        acc = sums.setdefault(key, [0.0, 0])
+        acc[0] += b / TRAFFIC_WORKLOAD_VOXELS
+        acc[1] += 1
+    rec = {"source_sha256_16": smooth_source_hash(),
+           "what": "DRAM bytes (read + write) per output voxel of one launch, mean over the captured launches of each "
+                   "kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on the medium 512^3 workload (537 MB "
+                   "cube, larger than L2; the autotuner's candidates and the timed step); traffic is proportional to "
+                   "voxels, so the bench scales it to the launch's voxels",
+           "command": command,
+           "kernels": {k: round(v[0] / v[1], 3) for k, v in sorted(sums.items())},
+           "launches": {k: v[1] for k, v in sorted(sums.items())}}
+    with open(os.path.join(ROOT, "profiles", "smooth_traffic.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec["kernels"]))
+    return 0
+
+
+def smoothing_kernel_name(sc, pair, code):
+    """Name of the smoothing kernel a pair ran on, from the SC_KERNEL_* code
+    the library reports for it and the pair's cascade widths."""
+    fwhm, _ = pair
+    w = tuple(sc.sc_cascade_widths(fwhm)) if fwhm > 0 else (1, 1, 1)
+    names = {sc.SC_KERNEL_NONE: "none", sc.SC_KERNEL_IDENTITY: "k_identity", sc.SC_KERNEL_Z: "k_smooth_z",
+             sc.SC_KERNEL_WS32: "k_smooth_ws<%d,%d,%d>" % w, sc.SC_KERNEL_WS16: "k_smooth_ws<%d,%d,%d>/16" % w,
+             sc.SC_KERNEL_TILE: "k_smooth_tile<%d,%d,%d>" % w, sc.SC_KERNEL_GENERIC: "k_smooth_generic"}
+    return names.get(code, "unknown")
 
 
 class ClockSampler:
@@ -250,7 +309,7 @@ def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
         n_l = st["smooth_launches_pair"][k]
         if n_l == 0:
             continue
-        g = groups.setdefault(smoothing_kernel_name(sc, pair), [0.0, 0])
+        g = groups.setdefault(smoothing_kernel_name(sc, pair, st["smooth_kernel_pair"][k]), [0.0, 0])
         g[0] += st["ms_smooth_pair"][k]
         g[1] += n_l
     dom = max(groups, key=lambda name: groups[name][0])
@@ -650,7 +709,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="write profiles/smooth_traffic.json from an ncu --csv DRAM capture of the medium workload "
+                         "and exit (no GPU)")
+    ap.add_argument("--traffic-command", default="", help="the command that made NCU_CSV (stored in the record)")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args.traffic_command)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

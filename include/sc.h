@@ -74,6 +74,15 @@ typedef struct {
 /* Largest number of kernel pairs in one run. */
 #define SC_MAX_KERNELS 64
 
+/* Smoothing kernel a kernel pair ran on (sc_stats.smooth_kernel_pair). */
+#define SC_KERNEL_NONE 0     /* no smoothing launch: the pair is the unsmoothed cube */
+#define SC_KERNEL_IDENTITY 1 /* copy of the cube (a later (0, 1) pair) */
+#define SC_KERNEL_Z 2        /* spectral boxcar only */
+#define SC_KERNEL_WS32 3     /* warp-specialised spatial cascade + boxcar, 64 x 32 tiles */
+#define SC_KERNEL_WS16 4     /* the same with 64 x 16 tiles */
+#define SC_KERNEL_TILE 5     /* one tile per block, spatial cascade + boxcar */
+#define SC_KERNEL_GENERIC 6  /* any kernel pair */
+
 /* Counters and timings of the context (cumulative unless reset). */
 typedef struct {
   uint64_t launches;      /* CUDA kernels this library launched */
@@ -87,6 +96,7 @@ typedef struct {
   uint64_t smooth_voxels;   /* output voxels those launches produced */
   double ms_smooth_pair[SC_MAX_KERNELS];          /* ms_smooth split by kernel-pair index of the run */
   uint64_t smooth_launches_pair[SC_MAX_KERNELS];  /* smooth_launches split the same way */
+  int32_t smooth_kernel_pair[SC_MAX_KERNELS];     /* SC_KERNEL_* of each pair's latest smoothing (not reset) */
 } sc_stats;
 
 /* Create a context on CUDA device `device` with workspace for cubes of up to

@@ -317,6 +317,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   CK(launch_sigma0_done(c->st, replacement, W, nk, s));
   c->stats.launches += 1;
 
+  if (first_identity) c->stats.smooth_kernel_pair[0] = SC_KERNEL_NONE;
   for (int k = first_identity ? 1 : 0; k < nk; ++k) {
     CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
     SmoothArgs a = base_args(c, cube, dims);
@@ -332,10 +333,12 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       if (a.pd.h == 0 && a.pd.wz == 1) {
         CK(launch_identity(a, c->sms, s));
         c->stats.launches += 1;
+        c->stats.smooth_kernel_pair[k] = SC_KERNEL_IDENTITY;
       } else {
-        int l = 0;
-        CK(launch_smooth(a, c->sms, s, &l));
+        int l = 0, code = SC_KERNEL_NONE;
+        CK(launch_smooth(a, c->sms, s, &l, &code));
         c->stats.launches += l;
+        c->stats.smooth_kernel_pair[k] = code;
       }
     }
     rc = measure(c, c->S, n, 1, t, 1, std_mode, k, force, s);
@@ -618,9 +621,10 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
       CK(cudaEventRecord(c->lane_done[l], c->lane_streams[l]));
       CK(cudaStreamWaitEvent(q, c->lane_done[l], 0));
       sc_ctx* lc = c->lanes[l];
-      if (lc != c) {  // the lanes' launch counts and timing events belong to the context
+      if (lc != c) {  // the lanes' launch counts, kernels and timing events belong to the context
         c->stats.launches += lc->stats.launches;
         lc->stats.launches = 0;
+        memcpy(c->stats.smooth_kernel_pair, lc->stats.smooth_kernel_pair, sizeof(c->stats.smooth_kernel_pair));
         c->events.insert(c->events.end(), lc->events.begin(), lc->events.end());
         lc->events.clear();
       }
@@ -784,6 +788,7 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
   }
   c->stats.launches += lc->stats.launches + (storage != SC_STORE_F32 ? 1 : 0);
   lc->stats.launches = 0;
+  memcpy(c->stats.smooth_kernel_pair, lc->stats.smooth_kernel_pair, sizeof(c->stats.smooth_kernel_pair));
   if (rc) {
     c->job_events.push_back(done);
     c->job_slots.push_back(slot);
@@ -1003,10 +1008,12 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
     if (pd.h == 0 && pd.wz == 1) {
       CK(launch_identity(a, c->sms, s));
       c->stats.launches += 1;
+      c->stats.smooth_kernel_pair[0] = SC_KERNEL_IDENTITY;
     } else {
-      int l = 0;
-      CK(launch_smooth(a, c->sms, s, &l));
+      int l = 0, code = SC_KERNEL_NONE;
+      CK(launch_smooth(a, c->sms, s, &l, &code));
       c->stats.launches += l;
+      c->stats.smooth_kernel_pair[0] = code;
     }
   }
   return SC_OK;
@@ -1048,8 +1055,11 @@ int sc_get_stats(sc_ctx* c, sc_stats* out, int reset) {
   *out = c->stats;
   if (reset) {
     const uint32_t w = c->stats.warnings;
+    int32_t kern[SC_MAX_KERNELS];
+    memcpy(kern, c->stats.smooth_kernel_pair, sizeof(kern));
     memset(&c->stats, 0, sizeof(c->stats));
     c->stats.warnings = w;
+    memcpy(c->stats.smooth_kernel_pair, kern, sizeof(kern));
   }
   return SC_OK;
 }

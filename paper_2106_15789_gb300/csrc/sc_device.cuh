@@ -92,6 +92,22 @@ __device__ __forceinline__ long long quantize(float x, float scale) {
   return x < 0.0f ? -r : r;
 }
 
+// quantize() with the replacement of a masked voxel folded in: the magnitude
+// is the replacement's when `masked`, then one sign step for x < 0 (so -0 and
+// positive values take +, as sgn(0) = +1 requires). x + (x - x) makes NaN and
+// Inf quantise to 0; masked voxels are finite.
+__device__ __forceinline__ long long quantize_repl(float x, float scale, bool masked, long long qrepl) {
+  const float xf = x + (x - x);
+  const float y = __fmul_rn(fabsf(xf), scale);
+  const float th = floorf(__fmul_rn(y, 2.3283064365386963e-10f));  // 2^-32
+  const float lo_f = __fmaf_rn(-th, 4294967296.0f, y);
+  const unsigned int hi = __float2uint_rz(th);
+  const unsigned int lo = __float2uint_rn(lo_f);
+  const long long r = (long long)(((unsigned long long)hi << 32) | lo);
+  const long long m = masked ? qrepl : r;
+  return x < 0.0f ? -m : m;
+}
+
 // Correctly rounded (to nearest, ties to even) float of an unsigned 64-bit
 // integer, from integer operations (the 64-bit cvt runs on the FP64 pipe).
 // Branch-free.

@@ -211,9 +211,13 @@ cudaError_t launch_decode_half(const uint16_t* x, const float* scale, long long 
                                float* out, int sms, cudaStream_t s);
 // x[i] = uniform pseudo-random value in [-1, 1) from (i, seed) (autotuning input)
 cudaError_t launch_fill_noise(float* x, long long n, unsigned int seed, int sms, cudaStream_t s);
-cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);
+// Launch the smoothing kernel of a pair; adds the launches to *launches and
+// stores the SC_KERNEL_* code of the kernel that ran in *kernel (either may
+// be null).
+cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches, int* kernel = nullptr);
 cudaError_t launch_identity(const SmoothArgs& a, int sms, cudaStream_t s);
-cudaError_t launch_smooth(const SmoothArgs& a, int sms, cudaStream_t s, int* launches);
+// Tile height (32 or 16) of the warp-specialised kernel for a pair, 0 if none.
+int ws_tile_rows(const SmoothArgs& a);
 
 // Host helpers.
 int cascade_widths(double fwhm, int w[3]);

@@ -288,9 +288,14 @@ cudaError_t launch_fill_noise(float* x, long long n, unsigned int seed, int sms,
   return cudaGetLastError();
 }
 
-cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* launches) {
+cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* launches, int* kernel) {
   bool done = false;
   cudaError_t et = cudaSuccess;
+  auto ran = [&](int code) {
+    if (launches) ++*launches;
+    if (kernel) *kernel = code;
+    return cudaSuccess;
+  };
   // a kernel fixed by the autotuner, if it serves this pair (else the default order)
   if (a0.tune_kind == TUNE_TILE) {
     et = launch_smooth_tile(a0, sms, s, &done);
@@ -298,31 +303,19 @@ cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* la
     SmoothArgs g = a0;
     g.generic = 1;
     g.tune_kind = TUNE_AUTO;
-    return launch_smooth(g, sms, s, launches);
+    return launch_smooth(g, sms, s, launches, kernel);
   }
   if (et != cudaSuccess) return et;
-  if (done) {
-    if (launches) ++*launches;
-    return cudaSuccess;
-  }
+  if (done) return ran(SC_KERNEL_TILE);
   et = launch_smooth_z(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
-  if (done) {
-    if (launches) ++*launches;
-    return cudaSuccess;
-  }
+  if (done) return ran(SC_KERNEL_Z);
   et = launch_smooth_ws(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
-  if (done) {
-    if (launches) ++*launches;
-    return cudaSuccess;
-  }
+  if (done) return ran(ws_tile_rows(a0) == 16 ? SC_KERNEL_WS16 : SC_KERNEL_WS32);
   et = launch_smooth_tile(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
-  if (done) {
-    if (launches) ++*launches;
-    return cudaSuccess;
-  }
+  if (done) return ran(SC_KERNEL_TILE);
   SmoothArgs a = a0;
   if (a.tx == 0) choose_tiles(&a);
   const size_t smem = smooth_smem_bytes(a);
@@ -341,8 +334,9 @@ cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* la
   const long long items = tiles * a.zchunks;
   const int grid = (int)std::min<long long>(items, (long long)sms * occ);
   k_smooth_generic<<<grid, kSmoothThreads, smem, s>>>(a);
-  if (launches) ++*launches;
-  return cudaGetLastError();
+  et = cudaGetLastError();
+  if (et != cudaSuccess) return et;
+  return ran(SC_KERNEL_GENERIC);
 }
 
 void init_noise_attrs();

@@ -180,14 +180,8 @@ __device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const
       const int k = k0 + i, e = pt + k * kPT;
       if (k < G::NCONV && (k + 1 < G::NCONV || e < G::BY * G::PX)) {
         const int row = e / G::PX, col = e - row * G::PX;
-        // v + (v - v) is NaN for NaN and Inf, whose quantised value is 0;
-        // the working mask holds finite voxels only
-        long long q = quantize(v[i] + (v[i] - v[i]), fscale);
-        if (REPL && do_repl) {
-          const long long qr = v[i] >= 0.0f ? qrepl : -qrepl;
-          q = ((word[i] >> (col & 31)) & 1u) ? qr : q;
-        }
-        X[row * G::XP + col] = q;
+        const bool masked = REPL && do_repl && ((word[i] >> (col & 31)) & 1u);
+        X[row * G::XP + col] = quantize_repl(v[i], fscale, masked, qrepl);
       }
     }
   }
@@ -527,8 +521,9 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
 // it) 16 rows.
 template <int W1, int W2, int W3>
 cudaError_t launch_ws_for_wz(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
-  if (a.pd.wz <= ws::Tile<32>::kMaxWz && a.tune_kind != TUNE_WS16) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
-  if (a.pd.wz <= ws::Tile<16>::kMaxWz) return launch_ws<W1, W2, W3, 16>(a, sms, s, done);
+  const int rows = ws_tile_rows(a);
+  if (rows == 32) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
+  if (rows == 16) return launch_ws<W1, W2, W3, 16>(a, sms, s, done);
   return cudaSuccess;
 }
 
@@ -553,6 +548,14 @@ void init_ws_attrs() {
   set_ws_attr<3, 5, 5>();
   set_ws_attr<5, 5, 5>();
   set_ws_attr<7, 9, 9>();
+}
+
+// Tile height of the warp-specialised kernel for a pair: 32 rows for spectral
+// widths up to 15 (unless the autotuner chose 16), 16 rows up to 31, else 0.
+int ws_tile_rows(const SmoothArgs& a) {
+  if (a.pd.wz <= ws::Tile<32>::kMaxWz && a.tune_kind != TUNE_WS16) return 32;
+  if (a.pd.wz <= ws::Tile<16>::kMaxWz) return 16;
+  return 0;
 }
 
 // The warp-specialised kernel for the cascades of FWHM 3, 5, 6 and 10 px with

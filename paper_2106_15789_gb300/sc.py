@@ -43,6 +43,10 @@ SC_WARN_RANGE = 0x8
 
 SC_MAX_KERNELS = 64
 
+# smoothing kernel a pair ran on (stats()["smooth_kernel_pair"])
+SC_KERNEL_NONE, SC_KERNEL_IDENTITY, SC_KERNEL_Z, SC_KERNEL_WS32, SC_KERNEL_WS16, SC_KERNEL_TILE, SC_KERNEL_GENERIC = \
+    range(7)
+
 
 class sc_kernel(C.Structure):
     _fields_ = [("fwhm_spatial_px", C.c_float), ("boxcar_chan", C.c_int32)]
@@ -52,7 +56,8 @@ class sc_stats(C.Structure):
     _fields_ = [("launches", C.c_uint64), ("runs", C.c_uint64), ("warnings", C.c_uint32), ("reserved", C.c_uint32),
                 ("ms_smooth", C.c_double), ("ms_select", C.c_double), ("ms_clip", C.c_double),
                 ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64),
-                ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS)]
+                ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS),
+                ("smooth_kernel_pair", C.c_int32 * SC_MAX_KERNELS)]
 
 
 class ScError(RuntimeError):
