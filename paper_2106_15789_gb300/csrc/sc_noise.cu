@@ -477,13 +477,16 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict
 #pragma unroll
     for (int u = 0; u < kP2Unroll; ++u) {
       const long long ch = ch0 + u;
-      unsigned int k[4], sure_w[4];
+      unsigned int k[4], sure_w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
       for (int c = 0; c < 4; ++c) k[c] = cls[__float_as_uint(a[u][c]) >> 16];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) sure_w[c] = __ballot_sync(0xffffffffu, (k[c] & CLS_SURE) != 0u);
+      bool any_sure = false;  // warp-uniform
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
+        // most groups of 32 values hold no listed, sure or ambiguous value:
+        // one vote settles them
+        if (!__any_sync(0xffffffffu, k[c] != 0u)) continue;
+        sure_w[c] = __ballot_sync(0xffffffffu, (k[c] & CLS_SURE) != 0u);
         if (__any_sync(0xffffffffu, (k[c] & ~CLS_SURE) != 0u)) {
           const float s = a[u][c];
           const float as = fabsf(s);
@@ -499,8 +502,9 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict
           stage_push(bmed, pm, lanes_below, s, smed, nmed);
           stage_push(bamb, pamb, lanes_below, (unsigned long long)(ch * 128 + 32 * c + lane), samb, namb);
         }
+        any_sure |= sure_w[c] != 0u;
       }
-      {
+      if (any_sure) {
         // lane c owns mask word 4 * ch + c of this chunk (no SURE cells, so
         // no words, without a clip)
         unsigned int w = sure_w[0];

@@ -370,6 +370,13 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         if (G::XBUF == 1) named_bar_sync(kBarProducers, kPT);  // the only quantised tile is free again
       }
     }
+    // after a timed-out wait: let the loads still in flight land (bounded)
+    // before the block's shared memory is given up
+    if (TMA && pt == 0)
+      for (long long q = g; q < issued; ++q) {
+        bool late = false;
+        mbar_wait_bounded(raw_full + 8 * (int)(q % kStages), (unsigned)((q / kStages) & 1), &late);
+      }
   } else {
     // ======================= consumers =======================
     const int ct = tid - kPT;
@@ -466,6 +473,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         if (wz > 1) tmem_wait_st();
       }
     }
+    if (!TMA) cp_async_wait_all();
   }
   tmem_fence_before();
   __syncthreads();
