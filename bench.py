@@ -33,7 +33,8 @@ METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM ro
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
-             "stream512")
+             "stream512", "wallaby-noisescale")
+NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
 
 
 def dist_env():
@@ -699,6 +700,106 @@ def run_stream_bench(args, rank, world, local):
     return 0
 
 
+def run_noise_scale_bench(args, rank, world, local):
+    """Local noise normalisation of the WALLABY-shaped cube: 31 x 31 x 31
+    windows (the paper's speed test) on 16 x 16 x 16 cells, MAD noise; one step
+    is one sc_noise_scale call (per-cell window noise, then the division)."""
+    import numpy as np
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    window, grid = (31, 31, 31), (16, 16, 16)
+    spec, cube = make_workload("wallaby", rank, str(dev))
+    nvox = cube.numel()
+    out = torch.empty_like(cube)
+    ctx = Context(local, 1)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        ctx.noise_scale(cube, window, grid, "mad", out=out)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ctx.stats(reset=True)
+    ctx.set_profiling(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.noise_scale(cube, window, grid, "mad", out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    ctx.set_profiling(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    st = ctx.stats(reset=True)
+    value = nvox * args.steps * world / (ms * 1e-3)
+    win_ms, app_ms = st["ms_noise_window"] / args.steps, st["ms_noise_apply"] / args.steps
+    # roofline of the division pass (read the cube, write the result: 8 B per
+    # voxel); the window pass is bound by its shared-memory selections
+    peak, peak_kind = measured_hbm_peak()
+    achieved = 8.0 * nvox / (app_ms * 1e-3) / 1e9
+    ncells = -(-spec.nx // grid[0]) * -(-spec.ny // grid[1]) * -(-spec.nz // grid[2])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_noise_apply", "launch_ms": app_ms, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_voxel": 8.0,
+                "k_noise_window": {"launch_ms": win_ms, "cells": ncells,
+                                   "window_voxels_per_s": ncells * float(np.prod(window)) / (win_ms * 1e-3)}}
+    # end to end: pinned host cube in, normalised cube out, every step
+    cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+    cube_h.copy_(cube)
+    out_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = max(1, min(args.steps, 3))
+    for _ in range(n_e2e):
+        cube.copy_(cube_h, non_blocking=True)
+        ctx.noise_scale(cube, window, grid, "mad", out=out)
+        out_h.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": nvox * n_e2e * world / e2e_s, "unit": "voxels/s", "h2d_bytes_per_step": 4 * nvox,
+           "d2h_bytes_per_step": 4 * nvox, "steps": n_e2e, "api": "sc_noise_scale on a device copy of a pinned host "
+           "cube, result copied back to pinned host memory"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle.noise_scale as NS
+
+        sub = cube[:128, :1024, :1024].cpu().numpy()
+        t0 = time.perf_counter()
+        NS.noise_scale(sub, window, grid, "mad")
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+               "sample": f"1024x1024x128 corner of the same cube, same windows and cells, numpy float64, one thread, "
+                         f"{dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": NOISE_SCALE_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "noise-scale-wallaby-1200x1200x1024", "window": list(window),
+                           "cells": list(grid), "noise": "mad", "l2": "inputs (cube 5.9 GB) larger than L2"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
+                "clocks": sampler.summary(),
+                "breakdown_ms_per_step": {"noise_window": win_ms, "noise_apply": app_ms}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -725,6 +826,8 @@ def main():
         return run_half_bench(args, rank, world, local)
     if args.workload == "stream512":
         return run_stream_bench(args, rank, world, local)
+    if args.workload == "wallaby-noisescale":
+        return run_noise_scale_bench(args, rank, world, local)
 
     import torch
 

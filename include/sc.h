@@ -97,6 +97,8 @@ typedef struct {
   double ms_smooth_pair[SC_MAX_KERNELS];          /* ms_smooth split by kernel-pair index of the run */
   uint64_t smooth_launches_pair[SC_MAX_KERNELS];  /* smooth_launches split the same way */
   int32_t smooth_kernel_pair[SC_MAX_KERNELS];     /* SC_KERNEL_* of each pair's latest smoothing (not reset) */
+  double ms_noise_window;  /* sc_noise_scale: device time of the per-cell window noise (while profiling) */
+  double ms_noise_apply;   /* sc_noise_scale: device time of the division pass (while profiling) */
 } sc_stats;
 
 /* Create a context on CUDA device `device` with workspace for cubes of up to
@@ -262,6 +264,35 @@ int sc_smooth(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, sc_kernel
  * SC_ERR_UNSUPPORTED. */
 int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, double *sigma_host, uint32_t flags,
              void *cuda_stream);
+
+/* Local noise normalisation (SoFiA 2 Sect. 4.1: when the noise varies across
+ * the cube, measure it in a running window and divide the data by it; the
+ * speed test of Sect. 5 uses windows of 31 pixels / channels). The cube is
+ * cut into cells of grid[0] x grid[1] x grid[2] voxels (x, y, z; the last cell
+ * along an axis may be shorter; grid {1, 1, 1} is the literal running window,
+ * one cell per voxel). A cell's noise is sc_noise's statistic (noise_mode) of
+ * the finite voxels in the window of window[0] x window[1] x window[2] voxels
+ * (odd sizes) centred on the cell's centre voxel, start + (extent - 1) / 2 per
+ * axis, clipped to the cube. Then, for every voxel,
+ *   out[v] = cube[v] * fl32(1 / sigma(cell(v)))   (within 2^-23 relative of
+ *            cube[v] / sigma), or NaN where cube[v] is not finite or the
+ *            window's noise is 0 or undefined (no finite voxel).
+ *   cube_dev, out_dev  float32 [nz][ny][nx] device buffers (caller-owned);
+ *                out_dev may equal cube_dev (in place).
+ *   dims         {nx, ny, nz}, each in 1 .. 2^31 - 1.
+ *   sigma_host   NULL or double[ncz * ncy * ncx] (ncx = ceil(nx / grid[0]),
+ *                ...; x fastest): the noise of every cell, NaN for a window
+ *                without finite voxels. With it the call synchronises.
+ *   flags        reserved, pass 0.
+ * The window's voxels (clipped to the cube) must fit in shared memory:
+ * min(wx, nx) * min(wy, ny) * min(wz, nz) <= 49152. The library keeps a
+ * per-cell buffer of 12 bytes per cell in the context (grown on demand).
+ * Errors: SC_ERR_ARG (NULL pointer, dims, even or non-positive window, grid
+ * < 1, unknown mode), SC_ERR_UNSUPPORTED (SC_NOISE_GAUSS, window too large),
+ * SC_ERR_NOMEM, SC_ERR_CUDA. Asynchronous unless sigma_host is given. */
+int sc_noise_scale(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const int32_t *window,
+                   const int32_t *grid, int noise_mode, float *out_dev, double *sigma_host, uint32_t flags,
+                   void *cuda_stream);
 
 /* Noise level of a device float32 array, like sc_noise, for callers that
  * cannot allocate device memory when they need it: processes whose device

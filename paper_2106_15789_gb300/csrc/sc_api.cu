@@ -40,6 +40,9 @@ struct sc_ctx {
   DevState* st = nullptr;
   DevState* st_host = nullptr;   // pinned mirror for read-back
   float* stage_cube = nullptr;   // sc_run_host staging (lazy)
+  double* ns_sig = nullptr;      // sc_noise_scale: noise of every cell (lazy, grown)
+  float* ns_rinv = nullptr;      // and its float reciprocal
+  size_t ns_cap = 0;             // cells both hold
   uint8_t* stage_mask = nullptr;
   int profiling = 0;
   sc_stats stats{};
@@ -122,7 +125,7 @@ cudaEvent_t take_event(sc_ctx* c) {
   return e;
 }
 
-enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2 };
+enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2, EV_NOISE_WINDOW = 3, EV_NOISE_APPLY = 4 };
 
 struct Phase {
   sc_ctx* c;
@@ -162,6 +165,10 @@ void flush_events(sc_ctx* c) {
       }
     } else if (e.kind == EV_SELECT) {
       c->stats.ms_select += ms;
+    } else if (e.kind == EV_NOISE_WINDOW) {
+      c->stats.ms_noise_window += ms;
+    } else if (e.kind == EV_NOISE_APPLY) {
+      c->stats.ms_noise_apply += ms;
     } else {
       c->stats.ms_clip += ms;
     }
@@ -454,6 +461,8 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->st);
   cudaFree(c->stage_cube);
   cudaFree(c->stage_mask);
+  cudaFree(c->ns_sig);
+  cudaFree(c->ns_rinv);
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaFree(c->batch_res);
   if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
@@ -1040,6 +1049,60 @@ int sc_noise(sc_ctx* c, const float* data_dev, int64_t n, int noise_mode, double
   rc = status_to_code(*c->st_host);
   *sigma_host = rc == SC_OK ? (double)c->st_host->sigma_cur : 0.0;
   return rc;
+}
+
+int sc_noise_scale(sc_ctx* c, const float* cube_dev, const int64_t* dims, const int32_t* window, const int32_t* grid,
+                   int noise_mode, float* out_dev, double* sigma_host, uint32_t flags, void* cuda_stream) {
+  (void)flags;
+  if (!c || !cube_dev || !dims || !window || !grid || !out_dev) return SC_ERR_ARG;
+  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  long long d[3];
+  int w[3], g[3];
+  long long cells = 1, wvox = 1;
+  for (int i = 0; i < 3; ++i) {
+    d[i] = dims[i];
+    w[i] = window[i];
+    g[i] = grid[i];
+    if (d[i] <= 0 || d[i] > (1LL << 31) - 1 || w[i] <= 0 || w[i] % 2 == 0 || g[i] <= 0) return SC_ERR_ARG;
+    cells *= (d[i] + g[i] - 1) / g[i];
+    wvox *= std::min((long long)w[i], d[i]);
+  }
+  if (wvox > kNoiseScaleMaxWindow) return SC_ERR_UNSUPPORTED;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  if ((size_t)cells > c->ns_cap) {
+    cudaFree(c->ns_sig);
+    cudaFree(c->ns_rinv);
+    c->ns_sig = nullptr;
+    c->ns_rinv = nullptr;
+    c->ns_cap = 0;
+    if (cudaMalloc(&c->ns_sig, sizeof(double) * cells) != cudaSuccess ||
+        cudaMalloc(&c->ns_rinv, sizeof(float) * cells) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->ns_sig);
+      cudaFree(c->ns_rinv);
+      c->ns_sig = nullptr;
+      c->ns_rinv = nullptr;
+      return SC_ERR_NOMEM;
+    }
+    c->ns_cap = (size_t)cells;
+  }
+  {
+    Phase ph(c, s, EV_NOISE_WINDOW);
+    CK(launch_noise_window(cube_dev, d, w, g, noise_mode == SC_NOISE_STD ? 1 : 0, c->ns_sig, c->ns_rinv, c->sms, s));
+  }
+  {
+    Phase ph(c, s, EV_NOISE_APPLY);
+    CK(launch_noise_apply(cube_dev, d, w, g, out_dev, c->ns_rinv, c->sms, s));
+  }
+  c->stats.launches += 2;
+  if (sigma_host) {
+    CK(cudaMemcpyAsync(sigma_host, c->ns_sig, sizeof(double) * cells, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return SC_OK;
 }
 
 int sc_set_profiling(sc_ctx* c, int on) {

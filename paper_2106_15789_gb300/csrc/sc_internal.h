@@ -219,6 +219,15 @@ cudaError_t launch_identity(const SmoothArgs& a, int sms, cudaStream_t s);
 // Tile height (32 or 16) of the warp-specialised kernel for a pair, 0 if none.
 int ws_tile_rows(const SmoothArgs& a);
 
+// Local noise normalisation: the noise of every cell's window (sig_dev,
+// rinv_dev = float 1 / sigma or NaN, one per cell), then out = cube * rinv.
+constexpr long long kNoiseScaleMaxWindow = 49152;  // window voxels held in shared memory
+cudaError_t launch_noise_window(const float* cube, const long long dims[3], const int window[3], const int grid[3],
+                                int std_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s);
+cudaError_t launch_noise_apply(const float* cube, const long long dims[3], const int window[3], const int grid[3],
+                               float* out, const float* rinv_dev, int sms, cudaStream_t s);
+void init_noise_scale_attrs();
+
 // Host helpers.
 int cascade_widths(double fwhm, int w[3]);
 int make_pair(const sc_kernel& k, PairDesc* pd);

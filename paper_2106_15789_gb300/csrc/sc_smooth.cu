@@ -340,6 +340,7 @@ cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* la
 }
 
 void init_noise_attrs();
+void init_noise_scale_attrs();
 
 // Raise the dynamic shared-memory limits once per device (called by sc_create).
 void init_kernel_attrs() {
@@ -348,6 +349,7 @@ void init_kernel_attrs() {
   init_ws_attrs();
   init_z_attrs();
   init_noise_attrs();
+  init_noise_scale_attrs();
 }
 
 // ---------------------------------------------------------------------------

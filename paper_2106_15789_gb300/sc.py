@@ -57,7 +57,8 @@ class sc_stats(C.Structure):
                 ("ms_smooth", C.c_double), ("ms_select", C.c_double), ("ms_clip", C.c_double),
                 ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64),
                 ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS),
-                ("smooth_kernel_pair", C.c_int32 * SC_MAX_KERNELS)]
+                ("smooth_kernel_pair", C.c_int32 * SC_MAX_KERNELS), ("ms_noise_window", C.c_double),
+                ("ms_noise_apply", C.c_double)]
 
 
 class ScError(RuntimeError):
@@ -100,6 +101,8 @@ _SIGS = {
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
+    "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
+                                 _P, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_set_profiling": (C.c_int, [_P, C.c_int]),
     "sc_get_stats": (C.c_int, [_P, C.POINTER(sc_stats), C.c_int]),
 }
@@ -365,6 +368,34 @@ def sc_noise_static(data: torch.Tensor, noise_mode="mad", stream=None) -> float:
     return out.value
 
 
+def sc_noise_scale(ctx, cube: torch.Tensor, window=(31, 31, 31), grid=(16, 16, 16), noise_mode="mad",
+                   out: torch.Tensor | None = None, want_sigma: bool = False, stream=None):
+    """Local noise normalisation of a CUDA cube (nz, ny, nx); window and grid
+    are (x, y, z). Returns (normalised cube, per-cell noise as a numpy array
+    of shape (cells z, y, x), or None)."""
+    import numpy as np
+
+    _dev(cube, torch.float32, "cube")
+    if out is None:
+        out = torch.empty_like(cube)
+    _dev(out, torch.float32, "out")
+    if out.shape != cube.shape:
+        raise ValueError("out must have the cube's shape")
+    nz, ny, nx = cube.shape
+    gx, gy, gz = (int(v) for v in grid)
+    sig = None
+    if want_sigma and min(gx, gy, gz) > 0:
+        sig = np.empty((-(-nz // gz), -(-ny // gy), -(-nx // gx)), dtype=np.float64)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    code = lib().sc_noise_scale(ctx, C.c_void_p(cube.data_ptr()), _dims(cube.shape),
+                                (C.c_int32 * 3)(*(int(v) for v in window)), (C.c_int32 * 3)(gx, gy, gz), int(mode),
+                                C.c_void_p(out.data_ptr()),
+                                sig.ctypes.data_as(C.POINTER(C.c_double)) if sig is not None else None, 0,
+                                _stream(cube, stream))
+    _check(code, "sc_noise_scale")
+    return out, sig
+
+
 def sc_set_profiling(ctx, on: bool) -> None:
     _check(lib().sc_set_profiling(ctx, 1 if on else 0), "sc_set_profiling")
 
@@ -444,6 +475,10 @@ class Context:
 
     def noise(self, data, noise_mode="mad", flags=0, stream=None):
         return sc_noise(self.handle, data, noise_mode, flags, stream)
+
+    def noise_scale(self, cube, window=(31, 31, 31), grid=(16, 16, 16), noise_mode="mad", out=None,
+                    want_sigma=False, stream=None):
+        return sc_noise_scale(self.handle, cube, window, grid, noise_mode, out, want_sigma, stream)
 
     def set_profiling(self, on=True):
         sc_set_profiling(self.handle, on)
