@@ -285,7 +285,7 @@ int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, doub
  *                without finite voxels. With it the call synchronises.
  *   flags        reserved, pass 0.
  * The window's voxels (clipped to the cube) must fit in shared memory:
- * min(wx, nx) * min(wy, ny) * min(wz, nz) <= 49152. The library keeps a
+ * min(wx, nx) * min(wy, ny) * min(wz, nz) <= 47104. The library keeps a
  * per-cell buffer of 12 bytes per cell in the context (grown on demand).
  * Errors: SC_ERR_ARG (NULL pointer, dims, even or non-positive window, grid
  * < 1, unknown mode), SC_ERR_UNSUPPORTED (SC_NOISE_GAUSS, window too large),

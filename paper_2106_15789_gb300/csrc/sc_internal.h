@@ -221,7 +221,7 @@ int ws_tile_rows(const SmoothArgs& a);
 
 // Local noise normalisation: the noise of every cell's window (sig_dev,
 // rinv_dev = float 1 / sigma or NaN, one per cell), then out = cube * rinv.
-constexpr long long kNoiseScaleMaxWindow = 49152;  // window voxels held in shared memory
+constexpr long long kNoiseScaleMaxWindow = 47104;  // window voxels held in shared memory
 cudaError_t launch_noise_window(const float* cube, const long long dims[3], const int window[3], const int grid[3],
                                 int std_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s);
 cudaError_t launch_noise_apply(const float* cube, const long long dims[3], const int window[3], const int grid[3],

@@ -7,9 +7,11 @@
 //                   shared memory as order-preserving keys; the noise of the
 //                   chosen mode comes from them: MAD by two exact radix
 //                   selections in shared memory (the median, then the median
-//                   of |x - m| with the same key rounding as the S+C noise),
-//                   STD by two double-precision passes. Writes the cell's
-//                   noise (double) and the float32 reciprocal used below.
+//                   of the float32 keys |x - m|, rounded correctly for an odd
+//                   count and faithfully for an even one), STD by two passes
+//                   of compensated float32 sums combined in double. Writes
+//                   the cell's noise (double) and the float32 reciprocal used
+//                   below.
 //   k_noise_apply   out = in * (1 / sigma) per voxel (NaN where the input is
 //                   not finite or the cell has no positive noise).
 //
@@ -28,6 +30,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kBins = 2048;              // radix digits: 11, 11 and 10 bits
 constexpr unsigned kNone = 0xffffffffu;  // key of a non-finite voxel: above every finite key
 constexpr double kMadToSigma = 1.4826;
+constexpr int kCandCap = 6144;  // keys of one round-0 bin copied aside for the later rounds
 
 struct Geo {
   long long nx, ny, nz;
@@ -76,48 +79,76 @@ __device__ __forceinline__ unsigned block_scan_incl(unsigned v, unsigned* part, 
 struct SelScratch {
   unsigned hist[kBins];
   unsigned part[kWarps + 1];
-  unsigned digit, rank, next;
+  unsigned digit, rank, next, count, below;
 };
 
-// Key of order statistic `rank` (0-based) of keys[0 .. n) in shared memory,
-// by three rounds of radix digits (11, 11, 10 bits) counted in a shared
-// histogram over the keys that share the digits found so far. With want_next,
-// *next receives the key of order statistic rank + 1 (the caller guarantees
-// it exists). All threads of the block call it and get the same results.
-__device__ unsigned block_select(const unsigned* keys, int n, unsigned rank, SelScratch* S, bool want_next,
-                                 unsigned* next) {
+// Adds this lane's digit to a histogram; lanes of the warp with the same digit
+// add once. bin == kBins: nothing to add. All 32 lanes must call it.
+__device__ __forceinline__ void hist_add_warp(unsigned* hist, unsigned bin) {
+  const unsigned peers = __match_any_sync(0xffffffffu, bin);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1 && bin < (unsigned)kBins) atomicAdd(&hist[bin], __popc(peers));
+}
+
+// Appends k to out[] (at most cap entries) where `take`; the counter ends as
+// the number of takers, which may exceed cap. All 32 lanes must call it.
+__device__ __forceinline__ void append_warp(bool take, unsigned k, unsigned* out, unsigned cap, unsigned* counter) {
+  const unsigned ball = __ballot_sync(0xffffffffu, take);
+  if (ball) {
+    const int lane = threadIdx.x & 31;
+    unsigned off = 0u;
+    if (lane == 0) off = atomicAdd(counter, (unsigned)__popc(ball));
+    off = __shfl_sync(0xffffffffu, off, 0);
+    const unsigned pos = off + (unsigned)__popc(ball & ((1u << lane) - 1u));
+    if (take && pos < cap) out[pos] = k;
+  }
+}
+
+// The digit whose cumulative range in S->hist holds `rank`, and the rank
+// within it (S->digit, S->rank; the histogram is left intact).
+__device__ __forceinline__ void find_digit(SelScratch* S, unsigned rank) {
   const int tid = threadIdx.x;
+  const unsigned a = S->hist[2 * tid], b = S->hist[2 * tid + 1];
+  unsigned total;
+  const unsigned incl = block_scan_incl(a + b, S->part, &total);
+  const unsigned excl = incl - a - b;
+  if (rank >= excl && rank < excl + a) {
+    S->digit = 2u * tid;
+    S->rank = rank - excl;
+  } else if (rank >= excl + a && rank < incl) {
+    S->digit = 2u * tid + 1u;
+    S->rank = rank - excl - a;
+  }
+  __syncthreads();
+}
+
+// Exact radix selection (digits of 11, 11 and 10 bits, counted in a shared
+// histogram with warp-aggregated additions) of order statistic `rank` among
+// the m keys of src (all below kNone). With want_next, *next is the key of
+// order statistic rank + 1 of src, or kNone when rank is its last. All
+// threads of the block call it.
+__device__ unsigned select_keys(const unsigned* src, int m, unsigned rank, SelScratch* S, bool want_next,
+                                unsigned* next) {
+  const int tid = threadIdx.x, lane = tid & 31;
   unsigned prefix = 0u, pmask = 0u;
   for (int round = 0; round < 3; ++round) {
     const int shift = round == 0 ? 21 : (round == 1 ? 10 : 0);
     const unsigned dmask = round == 2 ? 0x3ffu : 0x7ffu;
     for (int i = tid; i < kBins; i += kThreads) S->hist[i] = 0u;
     __syncthreads();
-    for (int e = tid; e < n; e += kThreads) {
-      const unsigned k = keys[e];
-      if ((k & pmask) == prefix) atomicAdd(&S->hist[(k >> shift) & dmask], 1u);
+    for (int base = tid - lane; base < m; base += kThreads) {
+      const int e = base + lane;
+      const unsigned k = e < m ? src[e] : kNone;
+      hist_add_warp(S->hist, (e < m && (k & pmask) == prefix) ? (k >> shift) & dmask : (unsigned)kBins);
     }
     __syncthreads();
-    // two bins per thread: find the one whose cumulative range holds rank
-    const unsigned a = S->hist[2 * tid], b = S->hist[2 * tid + 1];
-    unsigned total;
-    const unsigned incl = block_scan_incl(a + b, S->part, &total);
-    const unsigned excl = incl - a - b;
-    if (rank >= excl && rank < excl + a) {
-      S->digit = 2u * tid;
-      S->rank = rank - excl;
-    } else if (rank >= excl + a && rank < incl) {
-      S->digit = 2u * tid + 1u;
-      S->rank = rank - excl - a;
-    }
-    __syncthreads();
+    find_digit(S, rank);
     const unsigned d = S->digit;
     rank = S->rank;
     prefix |= d << shift;
     pmask |= dmask << shift;
     if (round == 2 && want_next) {
       // the successor: the same key if it occurs again, else the next
-      // non-empty bin of this round, else the smallest larger key
+      // non-empty bin of this round, else the smallest larger key of src
       if (tid == 0) S->next = (rank + 1u < S->hist[d]) ? prefix : kNone;
       __syncthreads();
       if (S->next == kNone) {
@@ -125,8 +156,8 @@ __device__ unsigned block_select(const unsigned* keys, int n, unsigned rank, Sel
           if (S->hist[i] != 0u) atomicMin(&S->next, (prefix & ~dmask) | (unsigned)i);
         __syncthreads();
         if (S->next == kNone) {
-          for (int e = tid; e < n; e += kThreads) {
-            const unsigned k = keys[e];
+          for (int e = tid; e < m; e += kThreads) {
+            const unsigned k = src[e];
             if (k > prefix) atomicMin(&S->next, k);
           }
           __syncthreads();
@@ -139,7 +170,151 @@ __device__ unsigned block_select(const unsigned* keys, int n, unsigned rank, Sel
   return prefix;
 }
 
+constexpr int kSampleStride = 8;  // every 8th voxel of the window is sampled for the bracket
+
+// Order statistics r and (with want_next) r + 1 of key_of(k) over the finite
+// keys k of keys[0 .. n) (nf of them). A sample of the window brackets the
+// rank: the keys inside the bracket are copied into cand in one counting
+// pass and selected there; when the bracket misses (or overflows cand), or
+// the window is small, the selection runs over all keys. When `rewrite`, the
+// keys are replaced by key_of(k) if the full selection is needed (the caller
+// needs them no more).
+template <class KeyOf>
+__device__ void select_order(unsigned* keys, int n, unsigned nf, unsigned r, bool want_next, KeyOf key_of,
+                             bool rewrite, unsigned* cand, SelScratch* S, unsigned* k1, unsigned* k2) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned nx = kNone;
+  if (nf <= (unsigned)kCandCap) {  // small window: select over a copy of all finite keys
+    if (tid == 0) S->count = 0u;
+    __syncthreads();
+    for (int base = tid - lane; base < n; base += kThreads) {
+      const int e = base + lane;
+      const unsigned k = e < n ? keys[e] : kNone;
+      append_warp(k != kNone, k != kNone ? key_of(k) : kNone, cand, kCandCap, &S->count);
+    }
+    __syncthreads();
+    *k1 = select_keys(cand, (int)nf, r, S, want_next, &nx);
+    *k2 = nx;
+    __syncthreads();
+    return;
+  }
+  // sample every kSampleStride-th voxel
+  if (tid == 0) S->count = 0u;
+  __syncthreads();
+  for (int j0 = tid - lane; j0 * kSampleStride < n; j0 += kThreads) {
+    const int e = (j0 + lane) * kSampleStride;
+    const unsigned k = e < n ? keys[e] : kNone;
+    append_warp(k != kNone, k != kNone ? key_of(k) : kNone, cand, kCandCap, &S->count);
+  }
+  __syncthreads();
+  const unsigned s = min(S->count, (unsigned)kCandCap);
+  bool done = false;
+  if (s >= 64u) {
+    // sample ranks around the expected one, 4 binomial standard deviations
+    // wide, widened to whole top-11-bit bins of one histogram of the sample
+    const unsigned p = (unsigned)(((unsigned long long)r * s) / nf);
+    const unsigned delta = 2u * (unsigned)sqrtf((float)s) + 4u;
+    const unsigned rlo = p > delta ? p - delta : 0u, rhi = min(p + delta, s - 1u);
+    for (int i = tid; i < kBins; i += kThreads) S->hist[i] = 0u;
+    __syncthreads();
+    for (int base = tid - lane; base < (int)s; base += kThreads) {
+      const int e = base + lane;
+      hist_add_warp(S->hist, e < (int)s ? cand[e] >> 21 : (unsigned)kBins);
+    }
+    __syncthreads();
+    find_digit(S, rlo);
+    const unsigned lo = S->digit << 21;
+    find_digit(S, rhi);
+    const unsigned hi = (S->digit << 21) | 0x1fffffu;
+    // one counting pass: keys below the bracket, keys inside it into cand
+    if (tid == 0) {
+      S->count = 0u;
+      S->below = 0u;
+    }
+    __syncthreads();
+    unsigned below = 0u;
+    for (int base = tid - lane; base < n; base += kThreads) {
+      const int e = base + lane;
+      const unsigned k = e < n ? keys[e] : kNone;
+      const unsigned a = k != kNone ? key_of(k) : kNone;
+      below += (a < lo) ? 1u : 0u;
+      append_warp(a != kNone && a >= lo && a <= hi, a, cand, kCandCap, &S->count);
+    }
+    below = __reduce_add_sync(0xffffffffu, below);
+    if (lane == 0) atomicAdd(&S->below, below);
+    __syncthreads();
+    const unsigned c_lo = S->below, cnt = S->count;
+    if (cnt <= (unsigned)kCandCap && r >= c_lo && r < c_lo + cnt) {
+      *k1 = select_keys(cand, (int)cnt, r - c_lo, S, want_next, &nx);
+      if (want_next && nx == kNone) {
+        // order statistic r + 1 lies above the bracket: the smallest key above it
+        if (tid == 0) S->next = kNone;
+        __syncthreads();
+        for (int e = tid; e < n; e += kThreads) {
+          const unsigned k = keys[e];
+          if (k != kNone) {
+            const unsigned a = key_of(k);
+            if (a > hi) atomicMin(&S->next, a);
+          }
+        }
+        __syncthreads();
+        nx = S->next;
+      }
+      *k2 = nx;
+      done = true;
+    }
+    __syncthreads();
+  }
+  if (!done) {  // the whole window (rare for noise-like data)
+    if (rewrite) {
+      for (int e = tid; e < n; e += kThreads)
+        if (keys[e] != kNone) keys[e] = key_of(keys[e]);
+      __syncthreads();
+    }
+    // select_keys needs keys below kNone only: count the kNone slots out by
+    // giving the selection all n slots (they sort last) and the same rank
+    *k1 = select_keys(keys, n, r, S, want_next, &nx);
+    *k2 = nx;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ double key_value(unsigned k) { return (double)fkey_inv(k); }
+
+// *s + *c += x with Neumaier's compensation (the running error of the float
+// sum is kept in *c).
+__device__ __forceinline__ void neumaier_add(float* s, float* c, float x) {
+  const float t = __fadd_rn(*s, x);
+  const float e = fabsf(*s) >= fabsf(x) ? __fadd_rn(__fsub_rn(*s, t), x) : __fadd_rn(__fsub_rn(x, t), *s);
+  *c = __fadd_rn(*c, e);
+  *s = t;
+}
+
+// x - b exactly as s + err (Knuth's TwoSum, round-to-nearest float ops).
+__device__ __forceinline__ float two_diff(float x, float b, float* err) {
+  const float s = __fsub_rn(x, b);
+  const float bb = __fsub_rn(s, x);
+  *err = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-b, bb));
+  return s;
+}
+
+// The MAD key of x: the float of |x - m| with m = (a + b) / 2 (a == b for an
+// odd count: one correctly rounded subtraction). For an even count, x - a/2
+// and then - b/2 are taken exactly as sums of two floats and added back, which
+// rounds the exact difference faithfully (within one unit in the last place)
+// in single precision, without the slow FP64 pipe.
+__device__ __forceinline__ unsigned mad_key(float x, float a, float b, bool even) {
+  float d;
+  if (!even) {
+    d = __fsub_rn(x, a);
+  } else {
+    float e1, e2;
+    const float t = two_diff(x, 0.5f * a, &e1);
+    const float u = two_diff(t, 0.5f * b, &e2);
+    d = __fadd_rn(u, __fadd_rn(e1, e2));
+  }
+  return __float_as_uint(fabsf(d)) | 0x80000000u;  // fkey of a non-negative float
+}
 
 __device__ __forceinline__ double block_sum_d(double v, double* part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -167,7 +342,8 @@ __global__ void __launch_bounds__(nscale::kThreads, 1)
                    float* __restrict__ rinv_out) {
   using namespace nscale;
   extern __shared__ __align__(16) unsigned char ns_smem[];
-  unsigned* const keys = reinterpret_cast<unsigned*>(ns_smem);
+  unsigned* const cand = reinterpret_cast<unsigned*>(ns_smem);  // [kCandCap]
+  unsigned* const keys = cand + kCandCap;                          // [window voxels]
   __shared__ SelScratch S;
   __shared__ double dpart[kWarps + 1];
   __shared__ unsigned s_count;
@@ -185,54 +361,135 @@ __global__ void __launch_bounds__(nscale::kThreads, 1)
     const int lx = (int)(x1 - x0), ly = (int)(y1 - y0), lz = (int)(z1 - z0);
     const int n = lx * ly * lz;
     if (tid == 0) s_count = 0u;
+    // Median bracket (MAD mode, windows larger than the copy-aside buffer): a
+    // sample of every kSampleStride-th voxel, read straight from the cube,
+    // and its top-11-bit histogram give key bounds [lo, hi] around the middle
+    // rank, so that the load pass below can count the keys under lo and copy
+    // those inside into cand.
+    bool med_bracket = !std_mode && n > kCandCap;
+    unsigned lo = 0u, hi = kNone - 1u;
+    if (med_bracket) {
+      if (tid == 0) S.count = 0u;
+      __syncthreads();
+      const int lxy = lx * ly;
+      for (int j0 = tid - lane; j0 * kSampleStride < n; j0 += kThreads) {
+        const int e = (j0 + lane) * kSampleStride;
+        unsigned k = kNone;
+        if (e < n) {
+          const int dz = e / lxy, rem = e - dz * lxy, dy = rem / lx, dx = rem - dy * lx;
+          const float v = __ldg(cube + (z0 + dz) * plane + (y0 + dy) * g.nx + x0 + dx);
+          if (isfinite(v)) k = fkey(v);
+        }
+        append_warp(k != kNone, k, cand, kCandCap, &S.count);
+      }
+      __syncthreads();
+      const unsigned ns = min(S.count, (unsigned)kCandCap);
+      med_bracket = ns >= 64u;
+      if (med_bracket) {
+        const unsigned p = (ns - 1u) / 2u;
+        const unsigned delta = 2u * (unsigned)sqrtf((float)ns) + 4u;
+        for (int i = tid; i < kBins; i += kThreads) S.hist[i] = 0u;
+        __syncthreads();
+        for (int base = tid - lane; base < (int)ns; base += kThreads) {
+          const int e = base + lane;
+          hist_add_warp(S.hist, e < (int)ns ? cand[e] >> 21 : (unsigned)kBins);
+        }
+        __syncthreads();
+        find_digit(&S, p > delta ? p - delta : 0u);
+        lo = S.digit << 21;
+        find_digit(&S, min(p + delta, ns - 1u));
+        hi = (S.digit << 21) | 0x1fffffu;
+      }
+      if (tid == 0) {
+        S.count = 0u;
+        S.below = 0u;
+      }
+    }
     __syncthreads();
-    // the window's keys, one warp per row
-    unsigned finite = 0u;
-    for (int row = warp; row < ly * lz; row += kWarps) {
-      const int dz = row / ly, dy = row - dz * ly;
-      const float* src = cube + (z0 + dz) * plane + (y0 + dy) * g.nx + x0;
-      for (int dx = lane; dx < lx; dx += 32) {
-        const float v = __ldg(src + dx);
-        const bool ok = isfinite(v);
-        keys[row * lx + dx] = ok ? fkey(v) : kNone;
-        finite += ok ? 1u : 0u;
+    // the window's keys: warps over rows, four planes' loads issued together;
+    // with a bracket, also the keys under it counted and those in it copied
+    unsigned finite = 0u, below = 0u;
+    constexpr int kPlanesAtOnce = 4;
+    for (int dz0 = 0; dz0 < lz; dz0 += kPlanesAtOnce) {
+      for (int dy = warp; dy < ly; dy += kWarps) {
+        for (int dx0 = 0; dx0 < lx; dx0 += 32) {
+          const int dx = dx0 + lane;
+          float v[kPlanesAtOnce];
+#pragma unroll
+          for (int u = 0; u < kPlanesAtOnce; ++u)
+            v[u] = (dz0 + u < lz && dx < lx) ? __ldg(cube + (z0 + dz0 + u) * plane + (y0 + dy) * g.nx + x0 + dx)
+                                             : __int_as_float(0x7fc00000);
+#pragma unroll
+          for (int u = 0; u < kPlanesAtOnce; ++u) {
+            const bool ok = isfinite(v[u]);
+            const unsigned k = ok ? fkey(v[u]) : kNone;
+            if (dz0 + u < lz && dx < lx) keys[((dz0 + u) * ly + dy) * lx + dx] = k;
+            finite += ok ? 1u : 0u;
+            if (med_bracket) {
+              below += (ok && k < lo) ? 1u : 0u;
+              append_warp(ok && k >= lo && k <= hi, k, cand, kCandCap, &S.count);
+            }
+          }
+        }
       }
     }
     finite = __reduce_add_sync(0xffffffffu, finite);
-    if (lane == 0) atomicAdd(&s_count, finite);
+    below = __reduce_add_sync(0xffffffffu, below);
+    if (lane == 0) {
+      atomicAdd(&s_count, finite);
+      if (med_bracket) atomicAdd(&S.below, below);
+    }
     __syncthreads();
     const unsigned nf = s_count;
     double sigma;
     if (nf == 0u) {
       sigma = __longlong_as_double(0x7ff8000000000000LL);  // NaN: no finite voxel
     } else if (std_mode) {
-      double s = 0.0;
+      // float32 sums with Neumaier compensation per thread (the FP64 pipe is
+      // slow on this part), combined in double across the block
+      float s = 0.0f, sc = 0.0f;
       for (int e = tid; e < n; e += kThreads)
-        if (keys[e] != kNone) s += key_value(keys[e]);
-      const double mean = block_sum_d(s, dpart) / (double)nf;
-      double q = 0.0;
+        if (keys[e] != kNone) neumaier_add(&s, &sc, fkey_inv(keys[e]));
+      const double mean = block_sum_d((double)s + (double)sc, dpart) / (double)nf;
+      const float mh = __double2float_rn(mean), ml = __double2float_rn(mean - (double)mh);
+      float q = 0.0f, qc = 0.0f;
       for (int e = tid; e < n; e += kThreads)
         if (keys[e] != kNone) {
-          const double d = key_value(keys[e]) - mean;
-          q += d * d;
+          const float d = __fsub_rn(__fsub_rn(fkey_inv(keys[e]), mh), ml);
+          neumaier_add(&q, &qc, __fmul_rn(d, d));
         }
-      q = block_sum_d(q, dpart);
-      sigma = nf > 1u ? sqrt(q / (double)(nf - 1u)) : 0.0;
+      const double qq = block_sum_d((double)q + (double)qc, dpart);
+      sigma = nf > 1u ? sqrt(qq / (double)(nf - 1u)) : 0.0;
     } else {
       // median: order statistics (nf - 1) / 2 and nf / 2
       const unsigned r1 = (nf - 1u) / 2u;
       const bool even = (nf & 1u) == 0u;
-      unsigned k2 = 0u;
-      const unsigned k1 = block_select(keys, n, r1, &S, even, &k2);
-      const double m = even ? 0.5 * (key_value(k1) + key_value(k2)) : key_value(k1);
-      // MAD keys: the float of |x - m| (as the S+C noise measures it)
-      for (int e = tid; e < n; e += kThreads) {
-        const unsigned k = keys[e];
-        keys[e] = k == kNone ? kNone : fkey(__double2float_rn(fabs(key_value(k) - m)));
+      unsigned k1 = 0u, k2 = 0u;
+      const unsigned c_lo = S.below, cnt = S.count;
+      if (med_bracket && cnt <= (unsigned)kCandCap && r1 >= c_lo && r1 < c_lo + cnt) {
+        unsigned nx = kNone;
+        k1 = select_keys(cand, (int)cnt, r1 - c_lo, &S, even, &nx);
+        if (even && nx == kNone) {  // the next order statistic lies above the bracket
+          if (tid == 0) S.next = kNone;
+          __syncthreads();
+          for (int e = tid; e < n; e += kThreads) {
+            const unsigned k = keys[e];
+            if (k != kNone && k > hi) atomicMin(&S.next, k);
+          }
+          __syncthreads();
+          nx = S.next;
+        }
+        k2 = nx;
+        __syncthreads();
+      } else {
+        select_order(keys, n, nf, r1, even, [](unsigned k) { return k; }, false, cand, &S, &k1, &k2);
       }
-      __syncthreads();
-      unsigned a2 = 0u;
-      const unsigned a1 = block_select(keys, n, r1, &S, even, &a2);
+      // MAD: the same order statistics of |x - m|, m = (k1 + k2) / 2, as
+      // float32 keys computed on the fly
+      const float ma = fkey_inv(k1), mb = even ? fkey_inv(k2) : ma;
+      unsigned a1 = 0u, a2 = 0u;
+      select_order(keys, n, nf, r1, even, [=](unsigned k) { return mad_key(fkey_inv(k), ma, mb, even); }, true, cand,
+                   &S, &a1, &a2);
       const double mad = even ? 0.5 * (key_value(a1) + key_value(a2)) : key_value(a1);
       sigma = kMadToSigma * mad;
     }
@@ -244,22 +501,49 @@ __global__ void __launch_bounds__(nscale::kThreads, 1)
   }
 }
 
-__global__ void k_noise_apply(const float* in, float* out, nscale::Geo g, const float* __restrict__ rinv) {
+// One warp per (y, z) row; four voxels per lane step when the rows allow
+// 16-byte accesses.
+__global__ void __launch_bounds__(256) k_noise_apply(const float* in, float* out, nscale::Geo g,
+                                                     const float* __restrict__ rinv, int vec) {
+  const int lane = threadIdx.x & 31;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
   const long long rows = g.ny * g.nz;
-  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+  const float qnan = __int_as_float(0x7fc00000);
+  for (long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
     const long long z = row / g.ny, y = row - z * g.ny;
     const float* rr = rinv + ((z / g.gz) * g.ncy + y / g.gy) * (long long)g.ncx;
     const float* src = in + row * g.nx;
     float* dst = out + row * g.nx;
-    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
-      const float v = src[x];
-      const float r = __ldg(rr + x / g.gx);
-      dst[x] = isfinite(v) ? __fmul_rn(v, r) : __int_as_float(0x7fc00000);
+    if (vec) {
+      const int nq = (int)(g.nx >> 2);
+      for (int q = lane; q < nq; q += 32) {
+        const int x = 4 * q;
+        int c = x / g.gx, r = x - c * g.gx;  // cell and position in it of voxel x
+        const float4 v = reinterpret_cast<const float4*>(src)[q];
+        float o[4];
+        const float vin[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          o[k] = isfinite(vin[k]) ? __fmul_rn(vin[k], __ldg(rr + c)) : qnan;
+          if (++r == g.gx) {
+            ++c;
+            r = 0;
+          }
+        }
+        reinterpret_cast<float4*>(dst)[q] = make_float4(o[0], o[1], o[2], o[3]);
+      }
+    } else {
+      for (int x = lane; x < g.nx; x += 32) {
+        const float v = src[x];
+        dst[x] = isfinite(v) ? __fmul_rn(v, __ldg(rr + x / g.gx)) : qnan;
+      }
     }
   }
 }
 
-size_t noise_window_smem(long long window_voxels) { return sizeof(unsigned) * (size_t)window_voxels; }
+size_t noise_window_smem(long long window_voxels) {
+  return sizeof(unsigned) * ((size_t)nscale::kCandCap + (size_t)window_voxels);
+}
 
 namespace {
 nscale::Geo make_geo(const long long dims[3], const int window[3], const int grid[3]) {
@@ -294,8 +578,11 @@ cudaError_t launch_noise_apply(const float* cube, const long long dims[3], const
                                float* out, const float* rinv_dev, int sms, cudaStream_t s) {
   const nscale::Geo g = make_geo(dims, window, grid);
   const long long rows = g.ny * g.nz;
-  const int blocks = (int)(rows < 8LL * sms ? rows : 8LL * sms);
-  k_noise_apply<<<blocks, 256, 0, s>>>(cube, out, g, rinv_dev);
+  const long long want = (rows + 7) / 8;  // eight warps (rows) per block
+  const int blocks = (int)(want < 16LL * sms ? want : 16LL * sms);
+  const int vec = (g.nx % 4 == 0) && (reinterpret_cast<uintptr_t>(cube) & 15u) == 0 &&
+                  (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+  k_noise_apply<<<blocks, 256, 0, s>>>(cube, out, g, rinv_dev, vec);
   return cudaGetLastError();
 }
 

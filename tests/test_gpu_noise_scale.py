@@ -81,6 +81,16 @@ def test_duplicates_and_in_place(ctx):
     check(ctx, c, (9, 9, 9), (6, 6, 6), "mad", in_place=True)
 
 
+def test_crowded_bins(ctx):
+    """Values from {-1, 0, 1}: a third of every window shares one key, more
+    than the candidate buffer holds, so the selections run over all keys;
+    median 0 and MAD 1 in every window."""
+    rng = np.random.default_rng(21)
+    c = rng.integers(-1, 2, size=(40, 40, 40)).astype(np.float32)
+    g, sig = check(ctx, c, (31, 31, 31), (16, 16, 16), "mad")
+    np.testing.assert_allclose(sig, 1.4826, rtol=1e-15)
+
+
 def test_degenerate(ctx):
     c = np.full((8, 9, 10), 2.5, dtype=np.float32)
     g, sig = check(ctx, c, (3, 3, 3), (4, 4, 4), "mad")
