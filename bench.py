@@ -33,7 +33,7 @@ METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM ro
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
-             "stream512", "wallaby-noisescale")
+             "stream512", "wallaby-noisescale", "medium-noisescale")
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
 
 
@@ -719,7 +719,14 @@ def run_noise_scale_bench(args, rank, world, local):
         pg = dist
     sc.lib()
     window, grid = (31, 31, 31), (16, 16, 16)
-    spec, cube = make_workload("wallaby", rank, str(dev))
+    if args.workload == "medium-noisescale":  # a 256^3 cube for profiling
+        from synth.cubes import CubeSpec, make_cube
+
+        spec = CubeSpec(nx=256, ny=256, nz=256, seed=12, n_gal=40, ripple=0.3, nan_border=4, name="noise-256")
+        with torch.no_grad():
+            cube = make_cube(spec, device=str(dev))
+    else:
+        spec, cube = make_workload("wallaby", rank, str(dev))
     nvox = cube.numel()
     out = torch.empty_like(cube)
     ctx = Context(local, 1)
@@ -777,7 +784,7 @@ def run_noise_scale_bench(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle.noise_scale as NS
 
-        sub = cube[:128, :1024, :1024].cpu().numpy()
+        sub = cube[:128, :1024, :1024].cpu().numpy()  # (the whole cube when it is smaller)
         t0 = time.perf_counter()
         NS.noise_scale(sub, window, grid, "mad")
         dt = time.perf_counter() - t0
@@ -788,8 +795,9 @@ def run_noise_scale_bench(args, rank, world, local):
         line = {"metric": NOISE_SCALE_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "noise-scale-wallaby-1200x1200x1024", "window": list(window),
-                           "cells": list(grid), "noise": "mad", "l2": "inputs (cube 5.9 GB) larger than L2"},
+                "config": {"workload": f"noise-scale-{spec.nx}x{spec.ny}x{spec.nz}", "window": list(window),
+                           "cells": list(grid), "noise": "mad",
+                           "l2": "inputs larger than L2" if nvox * 4 > 129e6 else "no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
                 "clocks": sampler.summary(),
                 "breakdown_ms_per_step": {"noise_window": win_ms, "noise_apply": app_ms}}
@@ -826,7 +834,7 @@ def main():
         return run_half_bench(args, rank, world, local)
     if args.workload == "stream512":
         return run_stream_bench(args, rank, world, local)
-    if args.workload == "wallaby-noisescale":
+    if args.workload.endswith("-noisescale"):
         return run_noise_scale_bench(args, rank, world, local)
 
     import torch

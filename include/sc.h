@@ -294,6 +294,35 @@ int sc_noise_scale(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, cons
                    const int32_t *grid, int noise_mode, float *out_dev, double *sigma_host, uint32_t flags,
                    void *cuda_stream);
 
+/* Linker (SoFiA 2 Sect. 4.3; radius 2 and minimum sizes 8 pixels / 5
+ * channels in Sect. 6): turns a detection mask into numbered detections by
+ * friends-of-friends linking and removes those outside the size limits.
+ * Two mask voxels are friends when dx^2 + dy^2 <= r_xy^2 and |dz| <= r_z;
+ * a detection is a connected component of the mask under that relation.
+ * A detection's size along an axis is its extent (max - min + 1); it is
+ * removed when its x or y extent is below min_xy or its z extent below
+ * min_z, or, for a limit above 0, when its x or y extent exceeds max_xy or
+ * its z extent max_z. The kept detections are numbered 1 .. n in raster order
+ * (z, then y, then x) of their first voxel.
+ *   mask_dev     uint8 [nz][ny][nx] device buffer, nonzero = detected.
+ *   dims         {nx, ny, nz}; nx * ny * nz < 2^31 - 1 (int32 voxel indices).
+ *   r_xy, r_z    merging radii in voxels, 0 .. 32.
+ *   labels_dev   int32 [nz][ny][nx] device buffer (caller-owned, output): the
+ *                detection id of every voxel, 0 for none. Also the
+ *                union-find workspace, so it may not alias mask_dev.
+ *   *n_out       number of kept detections.
+ *   extents_host NULL or int32[extents_cap][7]: for detections 1 .. n (the
+ *                first extents_cap of them) x_min, x_max, y_min, y_max,
+ *                z_min, z_max and the voxel count.
+ *   flags        reserved, pass 0.
+ * The library keeps per-chunk and per-detection buffers in the context (grown
+ * on demand). Synchronises the stream (the number of detections sizes the
+ * second half). Errors: SC_ERR_ARG (NULL pointer, dims, radii, negative
+ * limits), SC_ERR_NOMEM, SC_ERR_CUDA. */
+int sc_link(sc_ctx *ctx, const uint8_t *mask_dev, const int64_t *dims, int r_xy, int r_z, int min_xy, int min_z,
+            int max_xy, int max_z, int32_t *labels_dev, int64_t *n_out, int32_t *extents_host, int64_t extents_cap,
+            uint32_t flags, void *cuda_stream);
+
 /* Noise level of a device float32 array, like sc_noise, for callers that
  * cannot allocate device memory when they need it: processes whose device
  * memory belongs to another allocator or a fixed pool, real-time pipelines

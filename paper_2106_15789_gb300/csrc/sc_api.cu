@@ -43,6 +43,11 @@ struct sc_ctx {
   double* ns_sig = nullptr;      // sc_noise_scale: noise of every cell (lazy, grown)
   float* ns_rinv = nullptr;      // and its float reciprocal
   size_t ns_cap = 0;             // cells both hold
+  int* lk_chunk = nullptr;       // sc_link: per-chunk root counts / offsets (lazy, grown)
+  size_t lk_chunk_cap = 0;
+  int* lk_tot = nullptr;         // sc_link: one device int (a total)
+  int* lk_comp = nullptr;        // sc_link: [4 arrays of cap][7 or 1 ints] per detection
+  size_t lk_comp_cap = 0;
   uint8_t* stage_mask = nullptr;
   int profiling = 0;
   sc_stats stats{};
@@ -463,6 +468,9 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->stage_mask);
   cudaFree(c->ns_sig);
   cudaFree(c->ns_rinv);
+  cudaFree(c->lk_chunk);
+  cudaFree(c->lk_tot);
+  cudaFree(c->lk_comp);
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaFree(c->batch_res);
   if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
@@ -1102,6 +1110,77 @@ int sc_noise_scale(sc_ctx* c, const float* cube_dev, const int64_t* dims, const 
     CK(cudaMemcpyAsync(sigma_host, c->ns_sig, sizeof(double) * cells, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
+  return SC_OK;
+}
+
+int sc_link(sc_ctx* c, const uint8_t* mask_dev, const int64_t* dims, int r_xy, int r_z, int min_xy, int min_z,
+            int max_xy, int max_z, int32_t* labels_dev, int64_t* n_out, int32_t* extents_host, int64_t extents_cap,
+            uint32_t flags, void* cuda_stream) {
+  (void)flags;
+  if (!c || !mask_dev || !dims || !labels_dev || !n_out) return SC_ERR_ARG;
+  if (r_xy < 0 || r_z < 0 || r_xy > kLinkMaxRadius || r_z > kLinkMaxRadius || min_xy < 0 || min_z < 0 || max_xy < 0 ||
+      max_z < 0 || extents_cap < 0 || (extents_cap > 0 && !extents_host))
+    return SC_ERR_ARG;
+  long long d[3];
+  long long n = 1;
+  for (int i = 0; i < 3; ++i) {
+    d[i] = dims[i];
+    if (d[i] <= 0 || d[i] > INT32_MAX) return SC_ERR_ARG;
+    n *= d[i];
+    if (n >= (long long)INT32_MAX) return SC_ERR_ARG;  // voxel indices are int32
+  }
+  DeviceGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  const long long chunks = link_chunks(n);
+  if (!c->lk_tot && cudaMalloc(&c->lk_tot, sizeof(int) * 2) != cudaSuccess) {
+    cudaGetLastError();
+    c->lk_tot = nullptr;
+    return SC_ERR_NOMEM;
+  }
+  if ((size_t)chunks > c->lk_chunk_cap) {
+    cudaFree(c->lk_chunk);
+    c->lk_chunk_cap = 0;
+    if (cudaMalloc(&c->lk_chunk, sizeof(int) * chunks) != cudaSuccess) {
+      cudaGetLastError();
+      c->lk_chunk = nullptr;
+      return SC_ERR_NOMEM;
+    }
+    c->lk_chunk_cap = (size_t)chunks;
+  }
+  CK(launch_link_components(mask_dev, d, r_xy, r_z, labels_dev, c->lk_chunk, c->lk_tot, c->sms, s));
+  c->stats.launches += 7;
+  int ncomp = 0;
+  CK(cudaMemcpyAsync(&ncomp, c->lk_tot, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int kept = 0;
+  if (ncomp > 0) {
+    if ((size_t)ncomp > c->lk_comp_cap) {
+      cudaFree(c->lk_comp);
+      c->lk_comp_cap = 0;
+      if (cudaMalloc(&c->lk_comp, sizeof(int) * 16 * (size_t)ncomp) != cudaSuccess) {
+        cudaGetLastError();
+        c->lk_comp = nullptr;
+        return SC_ERR_NOMEM;
+      }
+      c->lk_comp_cap = (size_t)ncomp;
+    }
+    int* ext = c->lk_comp;
+    int* ext_out = ext + 7 * (size_t)ncomp;
+    int* keep = ext_out + 7 * (size_t)ncomp;
+    int* new_id = keep + (size_t)ncomp;
+    CK(launch_link_filter(d, labels_dev, ncomp, min_xy, min_z, max_xy, max_z, ext, keep, ext_out, new_id, c->lk_tot,
+                          c->sms, s));
+    c->stats.launches += 6;
+    CK(cudaMemcpyAsync(&kept, c->lk_tot, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const long long rows = std::min<long long>(kept, extents_cap);
+    if (rows > 0) {
+      CK(cudaMemcpyAsync(extents_host, ext_out, sizeof(int) * 7 * (size_t)rows, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+  }
+  *n_out = kept;
   return SC_OK;
 }
 

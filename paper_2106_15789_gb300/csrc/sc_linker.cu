@@ -1,0 +1,338 @@
+// Linker (SoFiA 2 Sect. 4.3; merging radius and size limits of Sect. 6): the
+// detected voxels of a mask become numbered detections by friends-of-friends
+// linking, then size filters remove the too small and too large ones.
+//
+// Friends: dx^2 + dy^2 <= r_xy^2 and |dz| <= r_z. Detections are the
+// connected components, numbered 1, 2, ... in raster order of their first
+// voxel; sizes are the extents along x, y and z.
+//
+//   k_cc_init      lab[v] = v in the mask, kBackground elsewhere
+//   k_cc_union     every mask voxel links to its friends after it in raster
+//                  order: lock-free union-find on lab, the larger root hung
+//                  under the smaller, so that a component's root is its
+//                  first voxel
+//   k_cc_compress  lab[v] = root of v (read-only walks)
+//   k_cc_count     roots per chunk of kChunk voxels
+//   k_scan_block   exclusive scan of the chunk counts (one block)
+//   k_cc_number    lab[root] = -(id), ids consecutive in raster order
+//   k_cc_final     lab[v] = id of v's root (0 outside the mask)
+//   k_cc_extent    bounding box and voxel count per detection (atomics)
+//   k_cc_keep      size filters -> keep flags; k_scan_block -> new ids
+//   k_cc_relabel   lab[v] = new id (0 for removed detections)
+#include <climits>
+#include <cstdint>
+
+#include "sc_internal.h"
+
+namespace sc {
+namespace link {
+
+constexpr int kChunk = 4096;        // voxels per numbering chunk (1024 threads x 4)
+constexpr int kChunkThreads = 1024;
+constexpr int kBackground = INT_MIN;
+
+struct Geo {
+  int nx, ny, nz;
+  long long n;
+  int rxy, rz;
+};
+
+__device__ __forceinline__ int find_root(int* lab, int x) {
+  int p = lab[x];
+  while (p != x) {
+    const int gp = lab[p];
+    if (gp != p) lab[x] = gp;  // path halving (a benign race: any ancestor will do)
+    x = p;
+    p = gp;
+  }
+  return x;
+}
+
+// Links the trees of a and b, the larger root under the smaller.
+__device__ __forceinline__ void unite(int* lab, int a, int b) {
+  while (true) {
+    a = find_root(lab, a);
+    b = find_root(lab, b);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicCAS(&lab[b], b, a);
+    if (old == b) return;  // b was still a root and now hangs under a
+    b = old;               // b got a parent meanwhile: retry from there
+  }
+}
+
+}  // namespace link
+
+using link::Geo;
+
+__global__ void k_cc_init(const uint8_t* __restrict__ mask, int* __restrict__ lab, long long n) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    lab[v] = mask[v] ? (int)v : link::kBackground;
+}
+
+__global__ void k_cc_union(const uint8_t* __restrict__ mask, int* lab, Geo g) {
+  const long long plane = (long long)g.nx * g.ny;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n; v += (long long)gridDim.x * blockDim.x) {
+    if (!mask[v]) continue;
+    const int z = (int)(v / plane), rem = (int)(v - (long long)z * plane), y = rem / g.nx, x = rem - y * g.nx;
+    // friends after v in raster order: dz > 0, or dz == 0 and (dy, dx) > (0, 0)
+    for (int dz = 0; dz <= g.rz; ++dz) {
+      const int zz = z + dz;
+      if (zz >= g.nz) break;
+      for (int dy = -g.rxy; dy <= g.rxy; ++dy) {
+        if (dz == 0 && dy < 0) continue;
+        const int yy = y + dy;
+        if (yy < 0 || yy >= g.ny) continue;
+        const int ddx = (int)sqrtf((float)(g.rxy * g.rxy - dy * dy));
+        int lo = -ddx, hi = ddx;
+        while ((lo - 1) * (lo - 1) + dy * dy <= g.rxy * g.rxy) --lo;  // guard the float square root
+        while (lo * lo + dy * dy > g.rxy * g.rxy) ++lo;
+        while ((hi + 1) * (hi + 1) + dy * dy <= g.rxy * g.rxy) ++hi;
+        while (hi * hi + dy * dy > g.rxy * g.rxy) --hi;
+        if (dz == 0 && dy == 0) lo = 1;
+        const long long row = (long long)zz * plane + (long long)yy * g.nx;
+        for (int dx = lo; dx <= hi; ++dx) {
+          const int xx = x + dx;
+          if (xx < 0 || xx >= g.nx) continue;
+          const long long u = row + xx;
+          if (mask[u]) link::unite(lab, (int)v, (int)u);
+        }
+      }
+    }
+  }
+}
+
+// Every mask voxel points at its root afterwards. The walk only reads:
+// halving paths here could overwrite a voxel's final root with an older
+// ancestor read before it.
+__global__ void k_cc_compress(const uint8_t* __restrict__ mask, int* lab, long long n) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
+    if (mask[v]) {
+      int x = (int)v, p = lab[x];
+      while (p != x) {
+        x = p;
+        p = lab[x];
+      }
+      lab[v] = x;
+    }
+}
+
+// Roots (lab[v] == v) per chunk.
+__global__ void __launch_bounds__(link::kChunkThreads) k_cc_count(const int* __restrict__ lab, long long n,
+                                                                  int* __restrict__ counts) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * link::kChunk;
+  int c = 0;
+  for (int i = threadIdx.x; i < link::kChunk; i += blockDim.x) {
+    const long long v = base + i;
+    if (v < n && lab[v] == (int)v) ++c;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) counts[blockIdx.x] = s;
+}
+
+// Exclusive scan of a[0 .. len) in place by one block of 1024 threads, tile
+// by tile; *total receives the sum.
+__global__ void __launch_bounds__(1024) k_scan_block(int* a, long long len, int* total) {
+  __shared__ int part[33];
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (long long t0 = 0; t0 < len; t0 += 1024) {
+    const long long i = t0 + tid;
+    const int v = i < len ? a[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const int w = part[lane];
+      int wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += y;
+      }
+      part[lane] = wi - w;
+      if (lane == 31) part[32] = wi;
+    }
+    __syncthreads();
+    if (i < len) a[i] = carry + part[warp] + x - v;
+    __syncthreads();
+    if (tid == 0) carry += part[32];
+    __syncthreads();
+  }
+  if (tid == 0) *total = carry;
+}
+
+// lab[root] = -(id) with ids 1, 2, ... in raster order of the roots.
+__global__ void __launch_bounds__(link::kChunkThreads) k_cc_number(int* lab, long long n, const int* __restrict__ off) {
+  __shared__ int part[33];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long base = (long long)blockIdx.x * link::kChunk + 4LL * tid;  // four consecutive voxels per thread
+  bool root[4];
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long long v = base + k;
+    root[k] = v < n && lab[v] == (int)v;
+    c += root[k] ? 1 : 0;
+  }
+  int x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) part[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const int w = part[lane];
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    part[lane] = wi - w;
+  }
+  __syncthreads();
+  int id = off[blockIdx.x] + part[warp] + x - c;  // roots before this thread's first voxel
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (root[k]) lab[base + k] = -(++id);
+}
+
+// Every mask voxel takes its root's id; roots hold -(id) (or +id once their
+// own thread has passed), non-roots the root's index.
+__global__ void k_cc_final(int* lab, long long n) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int l = lab[v];
+    if (l == link::kBackground) {
+      lab[v] = 0;
+    } else if (l < 0) {
+      lab[v] = -l;
+    } else {
+      const int r = lab[l];
+      lab[v] = r < 0 ? -r : r;
+    }
+  }
+}
+
+// ext[7 * (id - 1) ...] = x_min, x_max, y_min, y_max, z_min, z_max, count
+__global__ void k_cc_extent(const int* __restrict__ lab, Geo g, int* ext) {
+  const long long plane = (long long)g.nx * g.ny;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n; v += (long long)gridDim.x * blockDim.x) {
+    const int id = lab[v];
+    if (id <= 0) continue;
+    const int z = (int)(v / plane), rem = (int)(v - (long long)z * plane), y = rem / g.nx, x = rem - y * g.nx;
+    int* e = ext + 7LL * (id - 1);
+    atomicMin(e + 0, x);
+    atomicMax(e + 1, x);
+    atomicMin(e + 2, y);
+    atomicMax(e + 3, y);
+    atomicMin(e + 4, z);
+    atomicMax(e + 5, z);
+    atomicAdd(e + 6, 1);
+  }
+}
+
+__global__ void k_cc_ext_init(int* ext, int ncomp) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncomp; i += gridDim.x * blockDim.x) {
+    int* e = ext + 7LL * i;
+    e[0] = e[2] = e[4] = INT_MAX;
+    e[1] = e[3] = e[5] = -1;
+    e[6] = 0;
+  }
+}
+
+__global__ void k_cc_keep(const int* __restrict__ ext, int ncomp, int min_xy, int min_z, int max_xy, int max_z,
+                          int* keep) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncomp; i += gridDim.x * blockDim.x) {
+    const int* e = ext + 7LL * i;
+    const int sx = e[1] - e[0] + 1, sy = e[3] - e[2] + 1, sz = e[5] - e[4] + 1;
+    bool k = sx >= min_xy && sy >= min_xy && sz >= min_z;
+    if (max_xy > 0) k = k && sx <= max_xy && sy <= max_xy;
+    if (max_z > 0) k = k && sz <= max_z;
+    keep[i] = k ? 1 : 0;
+  }
+}
+
+// After the exclusive scan of the keep flags: the kept rows moved to the
+// front of out (ids 1 .. kept), and new_id[i] = id of detection i + 1 or 0.
+__global__ void k_cc_compact(const int* __restrict__ ext, const int* keep_flag, const int* __restrict__ keep_off,
+                             int ncomp, int* out, int* new_id) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ncomp; i += gridDim.x * blockDim.x) {
+    if (keep_flag[i]) {
+      const int j = keep_off[i];
+      for (int c = 0; c < 7; ++c) out[7LL * j + c] = ext[7LL * i + c];
+      new_id[i] = j + 1;
+    } else {
+      new_id[i] = 0;
+    }
+  }
+}
+
+__global__ void k_cc_relabel(int* lab, long long n, const int* __restrict__ new_id) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
+    const int id = lab[v];
+    if (id > 0) lab[v] = new_id[id - 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+inline int grid_for(long long n, int sms, int threads) {
+  const long long want = (n + threads - 1) / threads;
+  const long long cap = 16LL * sms;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+}  // namespace
+
+long long link_chunks(long long n) { return (n + link::kChunk - 1) / link::kChunk; }
+
+cudaError_t launch_link_components(const uint8_t* mask, const long long dims[3], int r_xy, int r_z, int* lab,
+                                   int* chunk_off, int* d_total, int sms, cudaStream_t s) {
+  Geo g{(int)dims[0], (int)dims[1], (int)dims[2], dims[0] * dims[1] * dims[2], r_xy, r_z};
+  const long long chunks = link_chunks(g.n);
+  k_cc_init<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g.n);
+  k_cc_union<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g);
+  k_cc_compress<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g.n);
+  k_cc_count<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
+  k_scan_block<<<1, 1024, 0, s>>>(chunk_off, chunks, d_total);
+  k_cc_number<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
+  k_cc_final<<<grid_for(g.n, sms, 256), 256, 0, s>>>(lab, g.n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_link_filter(const long long dims[3], int* lab, int ncomp, int min_xy, int min_z, int max_xy,
+                               int max_z, int* ext, int* keep, int* ext_out, int* new_id, int* d_total, int sms,
+                               cudaStream_t s) {
+  Geo g{(int)dims[0], (int)dims[1], (int)dims[2], dims[0] * dims[1] * dims[2], 0, 0};
+  if (ncomp <= 0) return cudaSuccess;
+  k_cc_ext_init<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, ncomp);
+  k_cc_extent<<<grid_for(g.n, sms, 256), 256, 0, s>>>(lab, g, ext);
+  k_cc_keep<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, ncomp, min_xy, min_z, max_xy, max_z, keep);
+  // keep flags are kept in new_id while keep becomes their exclusive scan
+  cudaError_t e = cudaMemcpyAsync(new_id, keep, sizeof(int) * (size_t)ncomp, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  k_scan_block<<<1, 1024, 0, s>>>(keep, ncomp, d_total);
+  k_cc_compact<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, new_id, keep, ncomp, ext_out, new_id);
+  k_cc_relabel<<<grid_for(g.n, sms, 256), 256, 0, s>>>(lab, g.n, new_id);
+  return cudaGetLastError();
+}
+
+}  // namespace sc

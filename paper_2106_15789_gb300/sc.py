@@ -103,6 +103,8 @@ _SIGS = {
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
                                  _P, C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_link": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P,
+                          C.POINTER(C.c_int64), _P, C.c_int64, C.c_uint32, _P]),
     "sc_set_profiling": (C.c_int, [_P, C.c_int]),
     "sc_get_stats": (C.c_int, [_P, C.POINTER(sc_stats), C.c_int]),
 }
@@ -396,6 +398,29 @@ def sc_noise_scale(ctx, cube: torch.Tensor, window=(31, 31, 31), grid=(16, 16, 1
     return out, sig
 
 
+def sc_link(ctx, mask: torch.Tensor, r_xy: int = 2, r_z: int = 2, min_xy: int = 1, min_z: int = 1, max_xy: int = 0,
+            max_z: int = 0, labels: torch.Tensor | None = None, extents_cap: int | None = None, stream=None):
+    """Friends-of-friends detections of a CUDA uint8 mask (nz, ny, nx) with
+    size filters. Returns (int32 labels, n, extents as a numpy int32 array
+    [min(n, extents_cap)][7]: x_min, x_max, y_min, y_max, z_min, z_max, count)."""
+    import numpy as np
+
+    _dev(mask, torch.uint8, "mask")
+    if labels is None:
+        labels = torch.empty(mask.shape, dtype=torch.int32, device=mask.device)
+    _dev(labels, torch.int32, "labels")
+    if labels.shape != mask.shape:
+        raise ValueError("labels must have the mask's shape")
+    cap = (1 << 20) if extents_cap is None else max(0, int(extents_cap))
+    ext = np.zeros((cap, 7), dtype=np.int32)
+    n = C.c_int64()
+    code = lib().sc_link(ctx, C.c_void_p(mask.data_ptr()), _dims(mask.shape), int(r_xy), int(r_z), int(min_xy),
+                         int(min_z), int(max_xy), int(max_z), C.c_void_p(labels.data_ptr()), C.byref(n),
+                         ext.ctypes.data_as(C.c_void_p) if cap > 0 else None, cap, 0, _stream(mask, stream))
+    _check(code, "sc_link")
+    return labels, int(n.value), ext[:min(int(n.value), cap)]
+
+
 def sc_set_profiling(ctx, on: bool) -> None:
     _check(lib().sc_set_profiling(ctx, 1 if on else 0), "sc_set_profiling")
 
@@ -479,6 +504,10 @@ class Context:
     def noise_scale(self, cube, window=(31, 31, 31), grid=(16, 16, 16), noise_mode="mad", out=None,
                     want_sigma=False, stream=None):
         return sc_noise_scale(self.handle, cube, window, grid, noise_mode, out, want_sigma, stream)
+
+    def link(self, mask, r_xy=2, r_z=2, min_xy=1, min_z=1, max_xy=0, max_z=0, labels=None, extents_cap=None,
+             stream=None):
+        return sc_link(self.handle, mask, r_xy, r_z, min_xy, min_z, max_xy, max_z, labels, extents_cap, stream)
 
     def set_profiling(self, on=True):
         sc_set_profiling(self.handle, on)
