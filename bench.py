@@ -33,7 +33,8 @@ METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM ro
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
-             "stream512", "wallaby-noisescale", "medium-noisescale")
+             "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link")
+LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
 
 
@@ -69,7 +70,7 @@ def measured_hbm_peak():
 
 
 SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_tile.cu", "sc_smooth_z.cu", "sc_tile_common.cuh",
-                  "sc_device.cuh", "sc_internal.h")
+                  "sc_device.cuh")  # the smoothing kernels' code (declarations elsewhere do not change their traffic)
 
 
 def smooth_source_hash():
@@ -808,6 +809,101 @@ def run_noise_scale_bench(args, rank, world, local):
     return 0
 
 
+def run_link_bench(args, rank, world, local):
+    """The linker on the S+C mask of the WALLABY-shaped cube with the paper's
+    settings (merging radius 2 pixels / channels, minimum size 8 pixels and 5
+    channels); one step is one sc_link call."""
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    spec, cube = make_workload("wallaby", rank, str(dev))
+    nvox = cube.numel()
+    ctx = Context(local, nvox)
+    mask, _, _ = ctx.run(cube, KERNELS_12, SC_THRESHOLD, "mad", SC_REPLACEMENT)
+    del cube
+    labels = torch.empty(mask.shape, dtype=torch.int32, device=dev)
+    params = dict(r_xy=2, r_z=2, min_xy=8, min_z=5)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        _, n_det, _ = ctx.link(mask, labels=labels, extents_cap=0, **params)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.stats(reset=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, n_det, _ = ctx.link(mask, labels=labels, extents_cap=0, **params)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    st = ctx.stats(reset=True)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    value = nvox * args.steps * world / (ms * 1e-3)
+    peak, peak_kind = measured_hbm_peak()
+    # algorithmic bytes: read the mask (1 B) and write the labels (4 B) per voxel
+    achieved = 5.0 * nvox / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sc_link (all 13 kernels of a call)", "launch_ms": ms / args.steps,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": 5.0}
+    # end to end: the mask from pinned host memory, the labels back to it
+    mask_h = torch.empty(mask.shape, dtype=torch.uint8, pin_memory=True)
+    mask_h.copy_(mask)
+    lab_h = torch.empty(mask.shape, dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    n_e2e = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        mask.copy_(mask_h, non_blocking=True)
+        ctx.link(mask, labels=labels, extents_cap=0, **params)
+        lab_h.copy_(labels, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": nvox * n_e2e * world / e2e_s, "unit": "voxels/s", "h2d_bytes_per_step": nvox,
+           "d2h_bytes_per_step": 4 * nvox, "steps": n_e2e,
+           "api": "sc_link on a device copy of a pinned host mask, labels copied back to pinned host memory"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle.linker as LK
+
+        sub = mask[:256, :512, :512].cpu().numpy()
+        t0 = time.perf_counter()
+        LK.link(sub, **params)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+               "sample": f"512x512x256 corner of the same mask, same settings, numpy / scipy connected components, "
+                         f"one thread, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": LINK_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+                "config": {"workload": "link-wallaby-1200x1200x1024-sc-mask", **params,
+                           "mask_fraction": float(mask.float().mean().item()), "detections": n_det,
+                           "l2": "inputs (mask 1.5 GB, labels 5.9 GB) larger than L2"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
+                "clocks": sampler.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -836,6 +932,8 @@ def main():
         return run_stream_bench(args, rank, world, local)
     if args.workload.endswith("-noisescale"):
         return run_noise_scale_bench(args, rank, world, local)
+    if args.workload == "wallaby-link":
+        return run_link_bench(args, rank, world, local)
 
     import torch
 

@@ -232,21 +232,38 @@ __global__ void k_cc_final(int* lab, long long n) {
   }
 }
 
-// ext[7 * (id - 1) ...] = x_min, x_max, y_min, y_max, z_min, z_max, count
+// ext[7 * (id - 1) ...] = x_min, x_max, y_min, y_max, z_min, z_max, count.
+// Lanes of a warp with the same id (neighbours along x, mostly) combine their
+// coordinates first, so a detection's seven words see one atomic per group.
 __global__ void k_cc_extent(const int* __restrict__ lab, Geo g, int* ext) {
   const long long plane = (long long)g.nx * g.ny;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n; v += (long long)gridDim.x * blockDim.x) {
-    const int id = lab[v];
-    if (id <= 0) continue;
-    const int z = (int)(v / plane), rem = (int)(v - (long long)z * plane), y = rem / g.nx, x = rem - y * g.nx;
-    int* e = ext + 7LL * (id - 1);
-    atomicMin(e + 0, x);
-    atomicMax(e + 1, x);
-    atomicMin(e + 2, y);
-    atomicMax(e + 3, y);
-    atomicMin(e + 4, z);
-    atomicMax(e + 5, z);
-    atomicAdd(e + 6, 1);
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; v0 < g.n; v0 += stride) {
+    const long long v = v0 + lane;
+    const int id = v < g.n ? lab[v] : 0;
+    if (__ballot_sync(0xffffffffu, id > 0) == 0u) continue;
+    int x = 0, y = 0, z = 0;
+    if (id > 0) {
+      z = (int)(v / plane);
+      const int rem = (int)(v - (long long)z * plane);
+      y = rem / g.nx;
+      x = rem - y * g.nx;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, id);  // lanes of the same detection (or background)
+    const int xmin = __reduce_min_sync(peers, x), xmax = __reduce_max_sync(peers, x);
+    const int ymin = __reduce_min_sync(peers, y), ymax = __reduce_max_sync(peers, y);
+    const int zmin = __reduce_min_sync(peers, z), zmax = __reduce_max_sync(peers, z);
+    if (id > 0 && lane == __ffs(peers) - 1) {
+      int* e = ext + 7LL * (id - 1);
+      atomicMin(e + 0, xmin);
+      atomicMax(e + 1, xmax);
+      atomicMin(e + 2, ymin);
+      atomicMax(e + 3, ymax);
+      atomicMin(e + 4, zmin);
+      atomicMax(e + 5, zmax);
+      atomicAdd(e + 6, __popc(peers));
+    }
   }
 }
 

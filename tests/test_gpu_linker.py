@@ -48,7 +48,8 @@ def test_ragged_and_thin(ctx, shape):
 
 def test_empty_and_full(ctx):
     assert check(ctx, np.zeros((10, 11, 12), bool), 2, 2) == 0
-    assert check(ctx, np.ones((10, 11, 12), bool), 1, 0) == 1
+    assert check(ctx, np.ones((10, 11, 12), bool), 1, 1) == 1
+    assert check(ctx, np.ones((10, 11, 12), bool), 1, 0) == 10  # r_z = 0: the planes do not link
     assert check(ctx, np.ones((10, 11, 12), bool), 0, 0) == 10 * 11 * 12
 
 
