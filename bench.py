@@ -33,7 +33,8 @@ METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM ro
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
-             "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link")
+             "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag")
+FLAG_METRIC = "auto-flagger voxels/s on 1 GB300 (channel and pixel MAD noise, k = 4)"
 LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
 
@@ -809,6 +810,96 @@ def run_noise_scale_bench(args, rank, world, local):
     return 0
 
 
+def run_autoflag_bench(args, rank, world, local):
+    """The auto-flagger on the WALLABY-shaped cube: channel and pixel noises
+    (MAD), their median and MAD-based RMS, flags beyond 4 RMS, blanking; one
+    step is one sc_autoflag call."""
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    spec, cube = make_workload("wallaby", rank, str(dev))
+    nvox = cube.numel()
+    out = torch.empty_like(cube)
+    ctx = Context(local, 1)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, out=out)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.stats(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    sampler.stop()
+    st = ctx.stats(reset=True)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    value = nvox * args.steps * world / (ms * 1e-3)
+    peak, peak_kind = measured_hbm_peak()
+    # algorithmic bytes: the cube read once for the channel noises, once for
+    # the pixel noises and once for the blanking, the result written: 16 B
+    achieved = 16.0 * nvox / (ms / args.steps * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "sc_autoflag (all kernels of a call)", "launch_ms": ms / args.steps,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": 16.0}
+    cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+    cube_h.copy_(cube)
+    out_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
+    torch.cuda.synchronize()
+    n_e2e = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        cube.copy_(cube_h, non_blocking=True)
+        ctx.autoflag(cube, 4.0, out=out)
+        out_h.copy_(out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": nvox * n_e2e * world / e2e_s, "unit": "voxels/s", "h2d_bytes_per_step": 4 * nvox,
+           "d2h_bytes_per_step": 4 * nvox, "steps": n_e2e,
+           "api": "sc_autoflag on a device copy of a pinned host cube, blanked cube copied back"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle.flagger as FL
+
+        sub = cube[:, :48, :48].cpu().numpy()
+        t0 = time.perf_counter()
+        FL.autoflag(sub, 4.0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+               "sample": f"48x48x{sub.shape[0]} corner of the same cube, k = 4, numpy float64, one thread, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": FLAG_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "autoflag-wallaby-1200x1200x1024", "k": 4.0, "noise": "mad",
+                           "flagged_channels": int(fc.sum()), "flagged_pixels": int(fp.sum()),
+                           "l2": "inputs (cube 5.9 GB) larger than L2"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
+                "clocks": sampler.summary()}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
 def run_link_bench(args, rank, world, local):
     """The linker on the S+C mask of the WALLABY-shaped cube with the paper's
     settings (merging radius 2 pixels / channels, minimum size 8 pixels and 5
@@ -934,6 +1025,8 @@ def main():
         return run_noise_scale_bench(args, rank, world, local)
     if args.workload == "wallaby-link":
         return run_link_bench(args, rank, world, local)
+    if args.workload == "wallaby-autoflag":
+        return run_autoflag_bench(args, rank, world, local)
 
     import torch
 

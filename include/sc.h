@@ -323,6 +323,32 @@ int sc_link(sc_ctx *ctx, const uint8_t *mask_dev, const int64_t *dims, int r_xy,
             int max_xy, int max_z, int32_t *labels_dev, int64_t *n_out, int32_t *extents_host, int64_t extents_cap,
             uint32_t flags, void *cuda_stream);
 
+/* Auto-flagger (SoFiA 2 Sect. 4.1): blanks spectral channels and / or
+ * spatial pixels whose noise deviates from the median noise across all
+ * channels (pixels) by more than k times the RMS estimated from the MAD.
+ * The noise of a channel is sc_noise's statistic (noise_mode) of its plane's
+ * finite voxels, that of a pixel of its spectrum's finite voxels; both are
+ * kept as float32. Across the channels (pixels) with a noise: M = median,
+ * R = 1.4826 * median(|noise - M|); a channel (pixel) is flagged when
+ * |noise - M| > k * R (in double). With both kinds requested, both are
+ * measured on the input and blanked together.
+ *   cube_dev, out_dev  float32 [nz][ny][nx]; out_dev may equal cube_dev.
+ *   what         SC_AUTOFLAG_CHANNELS and / or SC_AUTOFLAG_PIXELS.
+ *   chan_flags_host / chan_noise_host  NULL or [nz];
+ *   pix_flags_host / pix_noise_host    NULL or [ny * nx] (x fastest);
+ *   n_flagged    NULL or int64[2]: flagged channels, flagged pixels.
+ *   flags        reserved, pass 0.
+ * Pixels mode needs nz <= 1536 (a tile of spectra in shared memory). The
+ * library keeps 5 bytes per channel and per pixel in the context. Synchronises
+ * when any host output is given. Errors: SC_ERR_ARG (NULL pointer, dims,
+ * k < 0, what), SC_ERR_UNSUPPORTED (SC_NOISE_GAUSS, pixels with nz > 1536),
+ * SC_ERR_NOMEM, SC_ERR_CUDA. */
+#define SC_AUTOFLAG_CHANNELS 0x1u
+#define SC_AUTOFLAG_PIXELS 0x2u
+int sc_autoflag(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, double k, uint32_t what, int noise_mode,
+                float *out_dev, uint8_t *chan_flags_host, uint8_t *pix_flags_host, float *chan_noise_host,
+                float *pix_noise_host, int64_t *n_flagged, uint32_t flags, void *cuda_stream);
+
 /* Noise level of a device float32 array, like sc_noise, for callers that
  * cannot allocate device memory when they need it: processes whose device
  * memory belongs to another allocator or a fixed pool, real-time pipelines

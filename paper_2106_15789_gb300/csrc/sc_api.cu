@@ -48,6 +48,8 @@ struct sc_ctx {
   int* lk_tot = nullptr;         // sc_link: one device int (a total)
   int* lk_comp = nullptr;        // sc_link: [4 arrays of cap][7 or 1 ints] per detection
   size_t lk_comp_cap = 0;
+  unsigned char* af_buf = nullptr;  // sc_autoflag: noises, flags and statistics (lazy, grown)
+  size_t af_cap = 0;
   uint8_t* stage_mask = nullptr;
   int profiling = 0;
   sc_stats stats{};
@@ -471,6 +473,7 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->lk_chunk);
   cudaFree(c->lk_tot);
   cudaFree(c->lk_comp);
+  cudaFree(c->af_buf);
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaFree(c->batch_res);
   if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
@@ -1157,6 +1160,7 @@ int sc_link(sc_ctx* c, const uint8_t* mask_dev, const int64_t* dims, int r_xy, i
   if (ncomp > 0) {
     if ((size_t)ncomp > c->lk_comp_cap) {
       cudaFree(c->lk_comp);
+  cudaFree(c->af_buf);
       c->lk_comp_cap = 0;
       if (cudaMalloc(&c->lk_comp, sizeof(int) * 16 * (size_t)ncomp) != cudaSuccess) {
         cudaGetLastError();
@@ -1181,6 +1185,77 @@ int sc_link(sc_ctx* c, const uint8_t* mask_dev, const int64_t* dims, int r_xy, i
     }
   }
   *n_out = kept;
+  return SC_OK;
+}
+
+int sc_autoflag(sc_ctx* c, const float* cube_dev, const int64_t* dims, double k, uint32_t what, int noise_mode,
+                float* out_dev, uint8_t* chan_flags_host, uint8_t* pix_flags_host, float* chan_noise_host,
+                float* pix_noise_host, int64_t* n_flagged, uint32_t flags, void* cuda_stream) {
+  (void)flags;
+  if (!c || !cube_dev || !dims || !out_dev || !(k >= 0.0) || what == 0u ||
+      (what & ~(SC_AUTOFLAG_CHANNELS | SC_AUTOFLAG_PIXELS)))
+    return SC_ERR_ARG;
+  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  long long d[3];
+  for (int i = 0; i < 3; ++i) {
+    d[i] = dims[i];
+    if (d[i] <= 0 || d[i] > INT32_MAX) return SC_ERR_ARG;
+  }
+  const bool ch = (what & SC_AUTOFLAG_CHANNELS) != 0u, px = (what & SC_AUTOFLAG_PIXELS) != 0u;
+  if (px && d[2] > kFlagMaxChannelsForPixels) return SC_ERR_UNSUPPORTED;
+  const long long plane = d[0] * d[1];
+  // layout: stats[4] doubles | chan noise [nz] | pix noise [plane] | chan flags [nz] | pix flags [plane]
+  const size_t need = 64 + sizeof(float) * (size_t)(d[2] + plane) + (size_t)(d[2] + plane) + 16;
+  DeviceGuard guard(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  if (need > c->af_cap) {
+    cudaFree(c->af_buf);
+    c->af_cap = 0;
+    if (cudaMalloc(&c->af_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->af_buf = nullptr;
+      return SC_ERR_NOMEM;
+    }
+    c->af_cap = need;
+  }
+  double* stats = reinterpret_cast<double*>(c->af_buf);
+  float* cn = reinterpret_cast<float*>(c->af_buf + 64);
+  float* pn = cn + d[2];
+  uint8_t* cf = reinterpret_cast<uint8_t*>(pn + plane);
+  uint8_t* pf = cf + d[2];
+  CK(launch_autoflag(cube_dev, d, k, ch ? 1 : 0, px ? 1 : 0, noise_mode == SC_NOISE_STD ? 1 : 0, out_dev, cn, pn, cf,
+                     pf, stats, c->sms, s));
+  c->stats.launches += (ch ? 3 : 0) + (px ? 3 : 0) + 1;
+  const bool want_counts = n_flagged != nullptr;
+  std::vector<uint8_t> cf_h, pf_h;
+  if (ch && (chan_flags_host || want_counts)) {
+    cf_h.resize((size_t)d[2]);
+    CK(cudaMemcpyAsync(cf_h.data(), cf, (size_t)d[2], cudaMemcpyDeviceToHost, s));
+  }
+  if (px && (pix_flags_host || want_counts)) {
+    pf_h.resize((size_t)plane);
+    CK(cudaMemcpyAsync(pf_h.data(), pf, (size_t)plane, cudaMemcpyDeviceToHost, s));
+  }
+  if (ch && chan_noise_host) CK(cudaMemcpyAsync(chan_noise_host, cn, sizeof(float) * d[2], cudaMemcpyDeviceToHost, s));
+  if (px && pix_noise_host) CK(cudaMemcpyAsync(pix_noise_host, pn, sizeof(float) * plane, cudaMemcpyDeviceToHost, s));
+  if (!cf_h.empty() || !pf_h.empty() || chan_noise_host || pix_noise_host) CK(cudaStreamSynchronize(s));
+  if (chan_flags_host) {
+    if (ch) memcpy(chan_flags_host, cf_h.data(), (size_t)d[2]);
+    else memset(chan_flags_host, 0, (size_t)d[2]);
+  }
+  if (pix_flags_host) {
+    if (px) memcpy(pix_flags_host, pf_h.data(), (size_t)plane);
+    else memset(pix_flags_host, 0, (size_t)plane);
+  }
+  if (want_counts) {
+    long long nc = 0, np = 0;
+    for (uint8_t f : cf_h) nc += f;
+    for (uint8_t f : pf_h) np += f;
+    n_flagged[0] = nc;
+    n_flagged[1] = np;
+  }
   return SC_OK;
 }
 

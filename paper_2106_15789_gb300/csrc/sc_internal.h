@@ -231,6 +231,13 @@ void init_noise_scale_attrs();
 // Linker: components (lab = id in raster order of first voxels, 0 outside the
 // mask; *d_total = their number), then size filters (lab renumbered,
 // ext_out = kept rows, *d_total = kept).
+// Auto-flagger: channel and pixel noises, their median / RMS (stats[0..1]
+// channels, [2..3] pixels), flags and the blanked cube.
+constexpr int kFlagMaxChannelsForPixels = 1536;  // spectra staged in shared memory
+cudaError_t launch_autoflag(const float* cube, const long long dims[3], double k, int channels, int pixels,
+                            int std_mode, float* out, float* chan_noise, float* pix_noise, uint8_t* chan_flags,
+                            uint8_t* pix_flags, double* stats, int sms, cudaStream_t s);
+
 constexpr int kLinkMaxRadius = 32;  // merging radii in voxels
 long long link_chunks(long long n);
 cudaError_t launch_link_components(const uint8_t* mask, const long long dims[3], int r_xy, int r_z, int* lab,

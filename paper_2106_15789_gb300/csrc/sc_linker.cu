@@ -6,11 +6,12 @@
 // connected components, numbered 1, 2, ... in raster order of their first
 // voxel; sizes are the extents along x, y and z.
 //
-//   k_cc_init      lab[v] = v in the mask, kBackground elsewhere
-//   k_cc_union     every mask voxel links to its friends after it in raster
-//                  order: lock-free union-find on lab, the larger root hung
-//                  under the smaller, so that a component's root is its
-//                  first voxel
+//   k_cc_init      lab[v] = start of v's row run in the mask, kBackground
+//                  elsewhere
+//   k_cc_union     every run links to the runs within reach after it in
+//                  raster order (a warp per run, lanes along the rows):
+//                  lock-free union-find on lab, the larger root hung under the
+//                  smaller, so that a component's root is its first voxel
 //   k_cc_compress  lab[v] = root of v (read-only walks)
 //   k_cc_count     roots per chunk of kChunk voxels
 //   k_scan_block   exclusive scan of the chunk counts (one block)
@@ -69,37 +70,90 @@ __device__ __forceinline__ void unite(int* lab, int a, int b) {
 
 using link::Geo;
 
-__global__ void k_cc_init(const uint8_t* __restrict__ mask, int* __restrict__ lab, long long n) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-    lab[v] = mask[v] ? (int)v : link::kBackground;
+// lab[v] = start of v's run (the maximal row segment of mask voxels holding
+// v; consecutive voxels of a row are friends when r_xy >= 1) in the mask,
+// kBackground elsewhere. Run starts are the smallest index of their run, so
+// they are consistent with roots hung under smaller indices.
+__global__ void k_cc_init(const uint8_t* __restrict__ mask, int* __restrict__ lab, Geo g) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n; v += (long long)gridDim.x * blockDim.x) {
+    if (!mask[v]) {
+      lab[v] = link::kBackground;
+      continue;
+    }
+    long long s = v;
+    if (g.rxy >= 1) {
+      const long long row0 = (v / g.nx) * g.nx;
+      while (s > row0 && mask[s - 1]) --s;
+    }
+    lab[v] = (int)s;
+  }
 }
 
+// Friends-of-friends between runs: every run links once to the next run of
+// its row within reach and to the first voxel of every run that meets its
+// reach in each friend row after it in raster order (dz > 0, or dz == 0 and
+// dy > 0); the other half of the relation is the mirror of these. A warp
+// takes 32 consecutive voxels, finds the runs that start among them, and
+// works through each run with all 32 lanes (row positions side by side).
 __global__ void k_cc_union(const uint8_t* __restrict__ mask, int* lab, Geo g) {
   const long long plane = (long long)g.nx * g.ny;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < g.n; v += (long long)gridDim.x * blockDim.x) {
-    if (!mask[v]) continue;
-    const int z = (int)(v / plane), rem = (int)(v - (long long)z * plane), y = rem / g.nx, x = rem - y * g.nx;
-    // friends after v in raster order: dz > 0, or dz == 0 and (dy, dx) > (0, 0)
-    for (int dz = 0; dz <= g.rz; ++dz) {
-      const int zz = z + dz;
-      if (zz >= g.nz) break;
-      for (int dy = -g.rxy; dy <= g.rxy; ++dy) {
-        if (dz == 0 && dy < 0) continue;
-        const int yy = y + dy;
-        if (yy < 0 || yy >= g.ny) continue;
-        const int ddx = (int)sqrtf((float)(g.rxy * g.rxy - dy * dy));
-        int lo = -ddx, hi = ddx;
-        while ((lo - 1) * (lo - 1) + dy * dy <= g.rxy * g.rxy) --lo;  // guard the float square root
-        while (lo * lo + dy * dy > g.rxy * g.rxy) ++lo;
-        while ((hi + 1) * (hi + 1) + dy * dy <= g.rxy * g.rxy) ++hi;
-        while (hi * hi + dy * dy > g.rxy * g.rxy) --hi;
-        if (dz == 0 && dy == 0) lo = 1;
-        const long long row = (long long)zz * plane + (long long)yy * g.nx;
-        for (int dx = lo; dx <= hi; ++dx) {
-          const int xx = x + dx;
-          if (xx < 0 || xx >= g.nx) continue;
-          const long long u = row + xx;
-          if (mask[u]) link::unite(lab, (int)v, (int)u);
+  const int lane = threadIdx.x & 31;
+  const long long nseg = (g.n + 31) / 32;
+  const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+  const int r2 = g.rxy * g.rxy;
+  for (long long seg = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); seg < nseg; seg += warps) {
+    const long long b = seg * 32;
+    const long long v = b + lane;
+    // x of every lane (a segment may cross a row boundary)
+    int x = (int)(b % g.nx) + lane;
+    while (x >= g.nx) x -= g.nx;
+    const bool in = v < g.n && mask[v];
+    const bool starts = in && (g.rxy == 0 || x == 0 || !mask[v - 1]);
+    unsigned todo = __ballot_sync(0xffffffffu, starts);
+    while (todo) {
+      const int ls = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const long long vs = b + ls;  // the run's first voxel
+      const int z = (int)(vs / plane), rem = (int)(vs - (long long)z * plane), y = rem / g.nx, xs = rem - y * g.nx;
+      const long long rowv = vs - xs;
+      // end of the run
+      int e = xs;
+      if (g.rxy >= 1) {
+        for (int off = 0;; off += 32) {
+          const int xx = xs + off + lane;
+          const bool m = xx < g.nx && mask[rowv + xx];
+          const unsigned gap = __ballot_sync(0xffffffffu, !m);
+          if (gap) {
+            e = xs + off + __ffs(gap) - 2;
+            break;
+          }
+        }
+      }
+      // the same row: the next run within reach (further runs in reach chain to it)
+      if (g.rxy >= 2) {
+        const int xx = e + 2 + lane;
+        const bool m = lane <= g.rxy - 2 && xx < g.nx && mask[rowv + xx];
+        const unsigned bal = __ballot_sync(0xffffffffu, m);
+        if (bal && lane == __ffs(bal) - 1) link::unite(lab, (int)vs, (int)(rowv + xx));
+      }
+      for (int dz = 0; dz <= g.rz; ++dz) {
+        const int zz = z + dz;
+        if (zz >= g.nz) break;
+        for (int dy = (dz == 0 ? 1 : -g.rxy); dy <= g.rxy; ++dy) {
+          const int yy = y + dy;
+          if (yy < 0 || yy >= g.ny) continue;
+          int ddx = (int)sqrtf((float)(r2 - dy * dy));  // largest |dx| with dx^2 + dy^2 <= r_xy^2
+          while ((ddx + 1) * (ddx + 1) + dy * dy <= r2) ++ddx;
+          while (ddx > 0 && ddx * ddx + dy * dy > r2) --ddx;
+          const int lo = max(0, xs - ddx), hi = min(g.nx - 1, e + ddx);
+          const long long row = (long long)zz * plane + (long long)yy * g.nx;
+          for (int off = 0; lo + off <= hi; off += 32) {
+            const int xx = lo + off + lane;
+            const bool ok = xx <= hi;
+            const bool m = ok && mask[row + xx];
+            const bool before = ok && xx > lo && mask[row + xx - 1];
+            if (m && !before) link::unite(lab, (int)vs, (int)(row + xx));
+          }
         }
       }
     }
@@ -325,8 +379,8 @@ cudaError_t launch_link_components(const uint8_t* mask, const long long dims[3],
                                    int* chunk_off, int* d_total, int sms, cudaStream_t s) {
   Geo g{(int)dims[0], (int)dims[1], (int)dims[2], dims[0] * dims[1] * dims[2], r_xy, r_z};
   const long long chunks = link_chunks(g.n);
-  k_cc_init<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g.n);
-  k_cc_union<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g);
+  k_cc_init<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g);
+  k_cc_union<<<grid_for((g.n + 31) / 32 * 32, sms, 256), 256, 0, s>>>(mask, lab, g);
   k_cc_compress<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g.n);
   k_cc_count<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
   k_scan_block<<<1, 1024, 0, s>>>(chunk_off, chunks, d_total);

@@ -34,6 +34,7 @@ SC_FLAG_ACCUMULATE = 0x1
 SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
+SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
 SC_STORE_F32, SC_STORE_BF16, SC_STORE_FP16 = 0, 1, 2
 
 SC_WARN_ZERO_SIGMA = 0x1
@@ -103,6 +104,8 @@ _SIGS = {
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
                                  _P, C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_autoflag": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.c_double, C.c_uint32, C.c_int, _P, _P, _P, _P, _P,
+                              C.POINTER(C.c_int64), C.c_uint32, _P]),
     "sc_link": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P,
                           C.POINTER(C.c_int64), _P, C.c_int64, C.c_uint32, _P]),
     "sc_set_profiling": (C.c_int, [_P, C.c_int]),
@@ -421,6 +424,30 @@ def sc_link(ctx, mask: torch.Tensor, r_xy: int = 2, r_z: int = 2, min_xy: int = 
     return labels, int(n.value), ext[:min(int(n.value), cap)]
 
 
+def sc_autoflag(ctx, cube: torch.Tensor, k: float, channels: bool = True, pixels: bool = True, noise_mode="mad",
+                out: torch.Tensor | None = None, stream=None):
+    """Auto-flagging of a CUDA cube (nz, ny, nx). Returns (blanked cube,
+    channel flags [nz] bool, pixel flags [ny, nx] bool, channel noises [nz]
+    float32, pixel noises [ny, nx] float32) as numpy arrays besides the cube."""
+    import numpy as np
+
+    _dev(cube, torch.float32, "cube")
+    if out is None:
+        out = torch.empty_like(cube)
+    _dev(out, torch.float32, "out")
+    nz, ny, nx = cube.shape
+    fc, fp = np.zeros(nz, dtype=np.uint8), np.zeros((ny, nx), dtype=np.uint8)
+    cn, pn = np.full(nz, np.nan, dtype=np.float32), np.full((ny, nx), np.nan, dtype=np.float32)
+    what = (SC_AUTOFLAG_CHANNELS if channels else 0) | (SC_AUTOFLAG_PIXELS if pixels else 0)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)
+    code = lib().sc_autoflag(ctx, C.c_void_p(cube.data_ptr()), _dims(cube.shape), float(k), int(what), int(mode),
+                             C.c_void_p(out.data_ptr()), ptr(fc), ptr(fp), ptr(cn) if channels else None,
+                             ptr(pn) if pixels else None, None, 0, _stream(cube, stream))
+    _check(code, "sc_autoflag")
+    return out, fc.astype(bool), fp.astype(bool), cn, pn
+
+
 def sc_set_profiling(ctx, on: bool) -> None:
     _check(lib().sc_set_profiling(ctx, 1 if on else 0), "sc_set_profiling")
 
@@ -504,6 +531,9 @@ class Context:
     def noise_scale(self, cube, window=(31, 31, 31), grid=(16, 16, 16), noise_mode="mad", out=None,
                     want_sigma=False, stream=None):
         return sc_noise_scale(self.handle, cube, window, grid, noise_mode, out, want_sigma, stream)
+
+    def autoflag(self, cube, k, channels=True, pixels=True, noise_mode="mad", out=None, stream=None):
+        return sc_autoflag(self.handle, cube, k, channels, pixels, noise_mode, out, stream)
 
     def link(self, mask, r_xy=2, r_z=2, min_xy=1, min_z=1, max_xy=0, max_z=0, labels=None, extents_cap=None,
              stream=None):
