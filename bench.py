@@ -878,12 +878,13 @@ def run_autoflag_bench(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle.flagger as FL
 
-        sub = cube[:, :48, :48].cpu().numpy()
+        sub = cube[:, :256, :256].cpu().numpy()
         t0 = time.perf_counter()
         FL.autoflag(sub, 4.0)
         dt = time.perf_counter() - t0
         cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
-               "sample": f"48x48x{sub.shape[0]} corner of the same cube, k = 4, numpy float64, one thread, {dt:.1f} s"}
+               "sample": f"256x256x{sub.shape[0]} corner of the same cube, k = 4, numpy float64, one thread, "
+                         f"{dt:.1f} s"}
     if rank == 0:
         line = {"metric": FLAG_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
