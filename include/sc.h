@@ -74,6 +74,18 @@ typedef struct {
 /* Largest number of kernel pairs in one run. */
 #define SC_MAX_KERNELS 64
 
+/* sc_smooth only: run a given kernel variant where it serves the pair (the
+ * dispatcher's choice otherwise), flags |= SC_SMOOTH_VARIANT(v). Every variant
+ * gives the same floats; this exists for tests and tuning experiments. */
+#define SC_VARIANT_WS 1        /* warp-specialised, 64 x 32 tiles */
+#define SC_VARIANT_TILE 2      /* one tile per block */
+#define SC_VARIANT_GENERIC 3   /* generic kernel */
+#define SC_VARIANT_Z8 4        /* spectral-only, 8 voxels per thread */
+#define SC_VARIANT_Z4 5        /* spectral-only, 4 voxels per thread */
+#define SC_VARIANT_WS16 6      /* warp-specialised, 64 x 16 tiles */
+#define SC_VARIANT_Z4_512 7    /* spectral-only, 4 voxels per thread, 512-thread blocks */
+#define SC_SMOOTH_VARIANT(v) (((uint32_t)(v) & 0xffu) << 16)
+
 /* Smoothing kernel a kernel pair ran on (sc_stats.smooth_kernel_pair). */
 #define SC_KERNEL_NONE 0     /* no smoothing launch: the pair is the unsmoothed cube */
 #define SC_KERNEL_IDENTITY 1 /* copy of the cube (a later (0, 1) pair) */

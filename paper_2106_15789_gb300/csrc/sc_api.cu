@@ -894,6 +894,7 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
       } else {
         cands.push_back({TUNE_Z8, zf});
         cands.push_back({TUNE_Z4, zf});
+        if (pd.wz <= 15) cands.push_back({TUNE_Z4W, zf});
       }
     }
     // fixed-point scales of this pair on the synthetic cube, replacement value 1
@@ -992,6 +993,7 @@ int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc
 int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel kernel, const uint8_t* mask_dev,
               float replacement_value, float* out_dev, uint32_t flags, void* cuda_stream) {
   if (!c || !cube_dev || !out_dev || (const void*)cube_dev == (const void*)out_dev) return SC_ERR_ARG;
+  if (((flags >> 16) & 0xffu) > (unsigned)SC_VARIANT_Z4_512) return SC_ERR_ARG;
   if (!std::isfinite(replacement_value)) return SC_ERR_ARG;
   DeviceGuard g(c->device);
   long long n = 0;
@@ -1023,6 +1025,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   a.hist = nullptr;
   a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
   a.repl_possible = repl > 0.0f ? 1 : 0;
+  a.tune_kind = (int)((flags >> 16) & 0xffu);  // a variant chosen by the caller (SC_SMOOTH_VARIANT)
   {
     Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, 0);
     if (pd.h == 0 && pd.wz == 1) {

@@ -85,19 +85,19 @@ __device__ __forceinline__ void cp_wait() {
 
 }  // namespace zonly
 
-template <int VPT, bool VEC, bool REPL>
-__global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
+template <int VPT, bool VEC, bool REPL, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
   using namespace zonly;
   extern __shared__ __align__(16) unsigned char zsmem[];
-  float* const zring = reinterpret_cast<float*>(zsmem);  // [kDepth][kThreads * VPT]
+  float* const zring = reinterpret_cast<float*>(zsmem);  // [kDepth][THREADS * VPT]
   unsigned long long* const zmask =
-      reinterpret_cast<unsigned long long*>(zsmem + sizeof(float) * kDepth * kThreads * VPT);  // [kDepth][kThreads]
+      reinterpret_cast<unsigned long long*>(zsmem + sizeof(float) * kDepth * THREADS * VPT);  // [kDepth][THREADS]
   unsigned int* const zhist =
-      reinterpret_cast<unsigned int*>(zsmem + sizeof(float) * kDepth * kThreads * VPT + 8 * kDepth * kThreads);
+      reinterpret_cast<unsigned int*>(zsmem + sizeof(float) * kDepth * THREADS * VPT + 8 * kDepth * THREADS);
   __shared__ unsigned tmem_holder;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (a.hist)
-    for (int i = tid; i < kNumBins; i += kThreads) zhist[i] = 0u;
+    for (int i = tid; i < kNumBins; i += THREADS) zhist[i] = 0u;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
                  "r"(kTmemCols)
@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tbase = tmem_holder;
-  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(256 * (warp >> 2));
+  // THREADS / 128 warp groups share the 512 columns of the four lane quarters
+  constexpr int kGroupCols = kTmemCols / (THREADS / 128);
+  const unsigned tmine = tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(kGroupCols * (warp >> 2));
 
   const BinCfg cfg = a.win ? a.st->win : kFullRange;
   const float fscale = a.st->fx_scale[a.pair];
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
   const bool do_repl = REPL && qrepl > 0;
   const int wz = a.pd.wz, r = (wz - 1) / 2;
   const long long nz = a.nz, P = (long long)a.nx * a.ny, N = P * nz;
-  const long long per_block = (long long)kThreads * VPT;
+  const long long per_block = (long long)THREADS * VPT;
   const long long groups = (P + per_block - 1) / per_block;
   const long long n_items = groups * a.zchunks;
   constexpr int W = 2 * VPT;  // TMEM columns per ring slot
@@ -145,24 +147,26 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
     // Per-thread ring of kDepth planes in shared memory, filled by cp.async:
     // the thread's VPT values and the mask word(s) holding its bits. Each
     // thread reads back only what it copied itself, so no barrier is needed.
-    float* my_vals = zring + (size_t)tid * VPT;                       // stage stride kThreads*VPT floats
-    unsigned long long* my_mask = zmask + tid;                        // stage stride kThreads
+    float* my_vals = zring + (size_t)tid * VPT;                       // stage stride THREADS*VPT floats
+    unsigned long long* my_mask = zmask + tid;                        // stage stride THREADS
     auto issue = [&](int zp, int stage) {
       const bool zok = zp >= 0 && zp < nz;
       const long long base = (long long)zp * P + p0;
-      float* dv = my_vals + (size_t)stage * kThreads * VPT;
+      float* dv = my_vals + (size_t)stage * THREADS * VPT;
       if (VEC) {
+        // nv is a multiple of 4 here (the plane and p0 are), so whole quads
 #pragma unroll
-        for (int q = 0; q < VPT / 4; ++q)
-          cp16(smem_u32(dv + 4 * q), zok && nv == VPT ? (const void*)(a.C + base + 4 * q) : (const void*)a.C,
-               zok && nv == VPT);
+        for (int q = 0; q < VPT / 4; ++q) {
+          const bool ok = zok && 4 * q < nv;
+          cp16(smem_u32(dv + 4 * q), ok ? (const void*)(a.C + base + 4 * q) : (const void*)a.C, ok);
+        }
       } else {
 #pragma unroll
         for (int i = 0; i < VPT; ++i)
           cp4(smem_u32(dv + i), zok && i < nv ? (const void*)(a.C + base + i) : (const void*)a.C, zok && i < nv);
       }
       if (do_repl) {
-        unsigned* dm = reinterpret_cast<unsigned*>(my_mask + (size_t)stage * kThreads);
+        unsigned* dm = reinterpret_cast<unsigned*>(my_mask + (size_t)stage * THREADS);
         const long long w = base >> 5;
         const bool ok = zok && nv > 0;
         cp4(smem_u32(dm), ok ? (const void*)(a.mbits + w) : (const void*)a.mbits, ok);
@@ -178,12 +182,12 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
       cp_wait<kDepth - 1>();
       const int st = j % kDepth;
       float cur[VPT];
-      const float* sv = my_vals + (size_t)st * kThreads * VPT;
+      const float* sv = my_vals + (size_t)st * THREADS * VPT;
 #pragma unroll
       for (int i = 0; i < VPT; ++i) cur[i] = sv[i];
       unsigned mcur = 0u;
       if (do_repl && zp >= 0 && zp < nz && nv > 0) {
-        const unsigned* mm = reinterpret_cast<const unsigned*>(my_mask + (size_t)st * kThreads);
+        const unsigned* mm = reinterpret_cast<const unsigned*>(my_mask + (size_t)st * THREADS);
         const unsigned long long two = (unsigned long long)mm[0] | ((unsigned long long)mm[1] << 32);
         const long long base = (long long)zp * P + p0;
         mcur = (unsigned)(two >> (base & 31)) & ((1u << VPT) - 1u);
@@ -228,10 +232,11 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
           if (a.hist && !isn && i < nv) atomicAdd(&zhist[bin_of(s[i], cfg)], 1u);
         }
         float* out = a.S + (long long)zo * P + p0;
-        if (VEC && nv == VPT) {
+        if (VEC) {
 #pragma unroll
           for (int q = 0; q < VPT / 4; ++q)
-            reinterpret_cast<float4*>(out)[q] = make_float4(s[4 * q], s[4 * q + 1], s[4 * q + 2], s[4 * q + 3]);
+            if (4 * q < nv)
+              reinterpret_cast<float4*>(out)[q] = make_float4(s[4 * q], s[4 * q + 1], s[4 * q + 2], s[4 * q + 3]);
         } else {
 #pragma unroll
           for (int i = 0; i < VPT; ++i)
@@ -247,37 +252,37 @@ __global__ void __launch_bounds__(zonly::kThreads, 1) k_smooth_z(SmoothArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kTmemCols) : "memory");
   if (a.hist)
-    for (int i = tid; i < kNumBins; i += kThreads)
+    for (int i = tid; i < kNumBins; i += THREADS)
       if (zhist[i]) atomicAdd(a.hist + i, (unsigned long long)zhist[i]);
 }
 
 namespace {
 
 
-template <int VPT, bool VEC, bool REPL>
+template <int VPT, bool VEC, bool REPL, int THREADS>
 void set_z_attr() {
   cudaFuncAttributes fa{};
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (cudaFuncGetAttributes(&fa, k_smooth_z<VPT, VEC, REPL>) != cudaSuccess) return;
-  cudaFuncSetAttribute(k_smooth_z<VPT, VEC, REPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncGetAttributes(&fa, k_smooth_z<VPT, VEC, REPL, THREADS>) != cudaSuccess) return;
+  cudaFuncSetAttribute(k_smooth_z<VPT, VEC, REPL, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        optin - (int)fa.sharedSizeBytes);
 }
 
-template <int VPT>
+template <int VPT, int THREADS = zonly::kThreads>
 void set_z_attrs() {
-  set_z_attr<VPT, false, false>();
-  set_z_attr<VPT, false, true>();
-  set_z_attr<VPT, true, false>();
-  set_z_attr<VPT, true, true>();
+  set_z_attr<VPT, false, false, THREADS>();
+  set_z_attr<VPT, false, true, THREADS>();
+  set_z_attr<VPT, true, false, THREADS>();
+  set_z_attr<VPT, true, true, THREADS>();
 }
 
-template <int VPT, bool VEC, bool REPL>
+template <int VPT, bool VEC, bool REPL, int THREADS>
 cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   SmoothArgs a = a0;
   const long long P = (long long)a.nx * a.ny;
-  const long long per_block = (long long)zonly::kThreads * VPT;
+  const long long per_block = (long long)THREADS * VPT;
   const long long groups = (P + per_block - 1) / per_block;
   long long zch = (tune_items_per_sm(a) * sms + groups - 1) / groups;
   const long long max_ch = (a.nz + 15) / 16;
@@ -288,25 +293,26 @@ cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   const int grid = (int)(items < sms ? items : sms);
   // one block per SM (it holds all of the SM's TMEM): request more than half
   // of the shared memory
-  const size_t need = sizeof(float) * zonly::kDepth * zonly::kThreads * VPT + 8 * zonly::kDepth * zonly::kThreads +
+  const size_t need = sizeof(float) * zonly::kDepth * THREADS * VPT + 8 * zonly::kDepth * THREADS +
                       (a.hist ? sizeof(unsigned) * kNumBins : 0);
   const size_t smem = tc::one_block_per_sm_smem(need);
-  k_smooth_z<VPT, VEC, REPL><<<grid, zonly::kThreads, smem, s>>>(a);
+  k_smooth_z<VPT, VEC, REPL, THREADS><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int VPT>
+template <int VPT, int THREADS = zonly::kThreads>
 cudaError_t launch_z_vpt(const SmoothArgs& a, int sms, cudaStream_t s) {
   const bool vec = VPT >= 4 && ((long long)a.nx * a.ny) % 4 == 0 && (reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 &&
                    (reinterpret_cast<uintptr_t>(a.S) & 15u) == 0;
   const bool repl = a.mbits != nullptr && a.repl_possible;
-  if (vec) return repl ? launch_z<VPT, true, true>(a, sms, s) : launch_z<VPT, true, false>(a, sms, s);
-  return repl ? launch_z<VPT, false, true>(a, sms, s) : launch_z<VPT, false, false>(a, sms, s);
+  if (vec) return repl ? launch_z<VPT, true, true, THREADS>(a, sms, s) : launch_z<VPT, true, false, THREADS>(a, sms, s);
+  return repl ? launch_z<VPT, false, true, THREADS>(a, sms, s) : launch_z<VPT, false, false, THREADS>(a, sms, s);
 }
 
 }  // namespace
 
 void init_z_attrs() {
+  set_z_attrs<4, 512>();
   set_z_attrs<8>();
   set_z_attrs<4>();
   set_z_attrs<1>();
@@ -318,6 +324,8 @@ cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* 
   if (a.generic || a.pd.h != 0 || a.pd.wz <= 1) return cudaSuccess;
   *done = true;
   if (a.tune_kind == TUNE_Z4 && a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
+  // 512 threads of 4 voxels: twice the warps per scheduler, a 16-slot ring
+  if (a.tune_kind == TUNE_Z4W && a.pd.wz <= 15) return launch_z_vpt<4, 512>(a, sms, s);
   if (a.pd.wz <= 15) return launch_z_vpt<8>(a, sms, s);
   if (a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   return launch_z_vpt<1>(a, sms, s);

@@ -35,6 +35,13 @@ SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
 SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
+# sc_smooth kernel variants (flags |= variant << 16)
+SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512 = \
+    range(1, 8)
+
+
+def SC_SMOOTH_VARIANT(v: int) -> int:
+    return (int(v) & 0xFF) << 16
 SC_STORE_F32, SC_STORE_BF16, SC_STORE_FP16 = 0, 1, 2
 
 SC_WARN_ZERO_SIGMA = 0x1

@@ -255,6 +255,29 @@ def test_kernel_of_each_pair(ctx):
     assert all(c == sc.SC_KERNEL_GENERIC for c in codes[1:]), codes
 
 
+@pytest.mark.parametrize("shape", [(96, 64, 64), (37, 70, 131), (40, 33, 68)])
+def test_every_variant_gives_the_same_floats(ctx, shape):
+    """Each kernel variant the autotuner may choose, forced through sc_smooth,
+    equals the generic kernel bit for bit (with and without replacement)."""
+    from paper_2106_15789_gb300 import sc
+
+    rng = np.random.default_rng(sum(shape))
+    c = rng.standard_normal(shape).astype(np.float32)
+    c[rng.random(shape) < 0.03] = np.nan
+    cube = torch.from_numpy(c).cuda()
+    mask = torch.from_numpy((rng.random(shape) < 0.05).astype(np.uint8)).cuda()
+    spatial = [sc.SC_VARIANT_WS, sc.SC_VARIANT_WS16, sc.SC_VARIANT_TILE]
+    spectral = [sc.SC_VARIANT_Z8, sc.SC_VARIANT_Z4, sc.SC_VARIANT_Z4_512]
+    for kernel, variants in (((0.0, 3), spectral), ((0.0, 15), spectral), ((3.0, 7), spatial), ((6.0, 15), spatial),
+                             ((5.0, 1), spatial)):
+        for m, v in ((None, 0.0), (mask, 2.5)):
+            ref = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_FLAG_GENERIC).clone()
+            for var in variants:
+                got = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_SMOOTH_VARIANT(var))
+                assert torch.equal(torch.isnan(got), torch.isnan(ref)), (kernel, var)
+                assert torch.equal(torch.nan_to_num(got), torch.nan_to_num(ref)), (kernel, var)
+
+
 @pytest.mark.parametrize("shape", [(128, 64, 64), (37, 70, 131), (9, 33, 65), (3, 1, 200)])
 def test_specialised_kernels_equal_generic(ctx, shape):
     """Exact fixed-point arithmetic: every smoothing kernel variant gives the
