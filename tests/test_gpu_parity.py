@@ -233,6 +233,20 @@ def test_stats_and_profiling(ctx):
     assert st["ms_smooth"] > 0 and st["smooth_launches"] == 11
 
 
+def test_unaligned_cube_gives_the_same_result(ctx):
+    """A cube starting 4 bytes past a 16-byte boundary takes the paths
+    without 16-byte loads and TMA; the result must not change."""
+    cube = small_cube().cuda()
+    buf = torch.empty(cube.numel() + 1, device="cuda")
+    buf[1:].copy_(cube.flatten())
+    view = buf[1:].view(cube.shape)
+    assert view.data_ptr() % 16 == 4
+    m0, s0, z0 = ctx.run(cube, KERNELS_12, T)
+    m0 = m0.clone()
+    m1, s1, z1 = ctx.run(view, KERNELS_12, T)
+    assert torch.equal(m0, m1) and s0 == s1 and z0 == z1
+
+
 def test_kernel_of_each_pair(ctx):
     """The library reports which smoothing kernel each pair ran on: none for
     the unsmoothed cube, the spectral kernel for spatially unsmoothed pairs,
