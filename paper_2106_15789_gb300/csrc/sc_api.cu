@@ -1155,15 +1155,15 @@ int sc_link(sc_ctx* c, const uint8_t* mask_dev, const int64_t* dims, int r_xy, i
     c->lk_chunk_cap = (size_t)chunks;
   }
   CK(launch_link_components(mask_dev, d, r_xy, r_z, labels_dev, c->lk_chunk, c->lk_tot, c->sms, s));
-  c->stats.launches += 7;
+  c->stats.launches += 4;
   int ncomp = 0;
   CK(cudaMemcpyAsync(&ncomp, c->lk_tot, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   int kept = 0;
+  int *ext = nullptr, *ext_out = nullptr, *keep = nullptr, *new_id = nullptr;
   if (ncomp > 0) {
     if ((size_t)ncomp > c->lk_comp_cap) {
       cudaFree(c->lk_comp);
-  cudaFree(c->af_buf);
       c->lk_comp_cap = 0;
       if (cudaMalloc(&c->lk_comp, sizeof(int) * 16 * (size_t)ncomp) != cudaSuccess) {
         cudaGetLastError();
@@ -1172,13 +1172,16 @@ int sc_link(sc_ctx* c, const uint8_t* mask_dev, const int64_t* dims, int r_xy, i
       }
       c->lk_comp_cap = (size_t)ncomp;
     }
-    int* ext = c->lk_comp;
-    int* ext_out = ext + 7 * (size_t)ncomp;
-    int* keep = ext_out + 7 * (size_t)ncomp;
-    int* new_id = keep + (size_t)ncomp;
-    CK(launch_link_filter(d, labels_dev, ncomp, min_xy, min_z, max_xy, max_z, ext, keep, ext_out, new_id, c->lk_tot,
-                          c->sms, s));
-    c->stats.launches += 6;
+    ext = c->lk_comp;
+    ext_out = ext + 7 * (size_t)ncomp;
+    keep = ext_out + 7 * (size_t)ncomp;
+    new_id = keep + (size_t)ncomp;
+  }
+  // numbering, final labels and extents, then the size filters
+  CK(launch_link_filter(d, labels_dev, c->lk_chunk, ncomp, min_xy, min_z, max_xy, max_z, ext, keep, ext_out, new_id,
+                        c->lk_tot, c->sms, s));
+  c->stats.launches += ncomp > 0 ? 7 : 2;
+  if (ncomp > 0) {
     CK(cudaMemcpyAsync(&kept, c->lk_tot, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const long long rows = std::min<long long>(kept, extents_cap);

@@ -233,9 +233,10 @@ cudaError_t launch_noise_apply(const float* cube, const long long dims[3], const
                                float* out, const float* rinv_dev, int sms, cudaStream_t s);
 void init_noise_scale_attrs();
 
-// Linker: components (lab = id in raster order of first voxels, 0 outside the
-// mask; *d_total = their number), then size filters (lab renumbered,
-// ext_out = kept rows, *d_total = kept).
+// Linker: components (lab = roots; chunk_off = exclusive scan of the roots
+// per chunk; *d_total = their number), then ids in raster order of the first
+// voxels with extents, and the size filters (lab renumbered, ext_out = kept
+// rows, *d_total = kept). ext etc. may be null when there is no component.
 // Auto-flagger: channel and pixel noises, their median / RMS (stats[0..1]
 // channels, [2..3] pixels), flags and the blanked cube.
 constexpr int kFlagMaxChannelsForPixels = 1536;  // spectra staged in shared memory
@@ -247,9 +248,9 @@ constexpr int kLinkMaxRadius = 32;  // merging radii in voxels
 long long link_chunks(long long n);
 cudaError_t launch_link_components(const uint8_t* mask, const long long dims[3], int r_xy, int r_z, int* lab,
                                    int* chunk_off, int* d_total, int sms, cudaStream_t s);
-cudaError_t launch_link_filter(const long long dims[3], int* lab, int ncomp, int min_xy, int min_z, int max_xy,
-                               int max_z, int* ext, int* keep, int* ext_out, int* new_id, int* d_total, int sms,
-                               cudaStream_t s);
+cudaError_t launch_link_filter(const long long dims[3], int* lab, int* chunk_off, int ncomp, int min_xy, int min_z,
+                               int max_xy, int max_z, int* ext, int* keep, int* ext_out, int* new_id, int* d_total,
+                               int sms, cudaStream_t s);
 
 // Host helpers.
 int cascade_widths(double fwhm, int w[3]);

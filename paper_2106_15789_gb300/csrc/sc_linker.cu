@@ -12,12 +12,13 @@
 //                  raster order (a warp per run, lanes along the rows):
 //                  lock-free union-find on lab, the larger root hung under the
 //                  smaller, so that a component's root is its first voxel
-//   k_cc_compress  lab[v] = root of v (read-only walks)
-//   k_cc_count     roots per chunk of kChunk voxels
-//   k_scan_block   exclusive scan of the chunk counts (one block)
+//   k_cc_compress  lab[v] = root of v (read-only walks); roots per chunk of
+//                  kChunk voxels
+//   k_scan_block   exclusive scan of the chunk counts (one block); the host
+//                  reads the number of components and sizes the rest
 //   k_cc_number    lab[root] = -(id), ids consecutive in raster order
-//   k_cc_final     lab[v] = id of v's root (0 outside the mask)
-//   k_cc_extent    bounding box and voxel count per detection (atomics)
+//   k_cc_final     lab[v] = id of v's root (0 outside the mask), and the
+//                  bounding box and voxel count per detection (atomics)
 //   k_cc_keep      size filters -> keep flags; k_scan_block -> new ids
 //   k_cc_relabel   lab[v] = new id (0 for removed detections)
 #include <climits>
@@ -160,37 +161,35 @@ __global__ void k_cc_union(const uint8_t* __restrict__ mask, int* lab, Geo g) {
   }
 }
 
-// Every mask voxel points at its root afterwards. The walk only reads:
-// halving paths here could overwrite a voxel's final root with an older
-// ancestor read before it.
-__global__ void k_cc_compress(const uint8_t* __restrict__ mask, int* lab, long long n) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x)
-    if (mask[v]) {
+// Every mask voxel points at its root afterwards, and counts[chunk] holds the
+// roots of each chunk of kChunk voxels (a block per chunk, four consecutive
+// voxels per thread). The walks only read: halving paths here could overwrite
+// a voxel's final root with an older ancestor read before it. A voxel is a
+// root exactly when its walk ends at itself, whatever other threads write.
+__global__ void __launch_bounds__(link::kChunkThreads) k_cc_compress(const uint8_t* __restrict__ mask, int* lab,
+                                                                     long long n, int* __restrict__ counts) {
+  __shared__ int s_roots;
+  if (threadIdx.x == 0) s_roots = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * link::kChunk + 4LL * threadIdx.x;
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const long long v = base + k;
+    if (v < n && mask[v]) {
       int x = (int)v, p = lab[x];
       while (p != x) {
         x = p;
         p = lab[x];
       }
-      lab[v] = x;
+      if (x == (int)v) ++c;
+      else lab[v] = x;
     }
-}
-
-// Roots (lab[v] == v) per chunk.
-__global__ void __launch_bounds__(link::kChunkThreads) k_cc_count(const int* __restrict__ lab, long long n,
-                                                                  int* __restrict__ counts) {
-  __shared__ int s;
-  if (threadIdx.x == 0) s = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * link::kChunk;
-  int c = 0;
-  for (int i = threadIdx.x; i < link::kChunk; i += blockDim.x) {
-    const long long v = base + i;
-    if (v < n && lab[v] == (int)v) ++c;
   }
   c = __reduce_add_sync(0xffffffffu, c);
-  if ((threadIdx.x & 31) == 0) atomicAdd(&s, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_roots, c);
   __syncthreads();
-  if (threadIdx.x == 0) counts[blockIdx.x] = s;
+  if (threadIdx.x == 0) counts[blockIdx.x] = s_roots;
 }
 
 // Exclusive scan of a[0 .. len) in place by one block of 1024 threads, tile
@@ -271,31 +270,30 @@ __global__ void __launch_bounds__(link::kChunkThreads) k_cc_number(int* lab, lon
 }
 
 // Every mask voxel takes its root's id; roots hold -(id) (or +id once their
-// own thread has passed), non-roots the root's index.
-__global__ void k_cc_final(int* lab, long long n) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const int l = lab[v];
-    if (l == link::kBackground) {
-      lab[v] = 0;
-    } else if (l < 0) {
-      lab[v] = -l;
-    } else {
-      const int r = lab[l];
-      lab[v] = r < 0 ? -r : r;
-    }
-  }
-}
-
-// ext[7 * (id - 1) ...] = x_min, x_max, y_min, y_max, z_min, z_max, count.
-// Lanes of a warp with the same id (neighbours along x, mostly) combine their
-// coordinates first, so a detection's seven words see one atomic per group.
-__global__ void k_cc_extent(const int* __restrict__ lab, Geo g, int* ext) {
+// own thread has passed), non-roots the root's index. Then the bounding box
+// and voxel count of each detection, ext[7 * (id - 1) ...] = x_min, x_max,
+// y_min, y_max, z_min, z_max, count: lanes of a warp with the same id
+// (neighbours along x, mostly) combine their coordinates first, so a
+// detection's seven words see one atomic per group.
+__global__ void k_cc_final(int* lab, Geo g, int* ext) {
   const long long plane = (long long)g.nx * g.ny;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long v0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - lane; v0 < g.n; v0 += stride) {
     const long long v = v0 + lane;
-    const int id = v < g.n ? lab[v] : 0;
+    int id = 0;
+    if (v < g.n) {
+      const int l = lab[v];
+      if (l == link::kBackground) {
+        id = 0;
+      } else if (l < 0) {
+        id = -l;
+      } else {
+        const int r = lab[l];
+        id = r < 0 ? -r : r;
+      }
+      lab[v] = id;
+    }
     if (__ballot_sync(0xffffffffu, id > 0) == 0u) continue;
     int x = 0, y = 0, z = 0;
     if (id > 0) {
@@ -381,21 +379,20 @@ cudaError_t launch_link_components(const uint8_t* mask, const long long dims[3],
   const long long chunks = link_chunks(g.n);
   k_cc_init<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g);
   k_cc_union<<<grid_for((g.n + 31) / 32 * 32, sms, 256), 256, 0, s>>>(mask, lab, g);
-  k_cc_compress<<<grid_for(g.n, sms, 256), 256, 0, s>>>(mask, lab, g.n);
-  k_cc_count<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
+  k_cc_compress<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(mask, lab, g.n, chunk_off);
   k_scan_block<<<1, 1024, 0, s>>>(chunk_off, chunks, d_total);
-  k_cc_number<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
-  k_cc_final<<<grid_for(g.n, sms, 256), 256, 0, s>>>(lab, g.n);
   return cudaGetLastError();
 }
 
-cudaError_t launch_link_filter(const long long dims[3], int* lab, int ncomp, int min_xy, int min_z, int max_xy,
-                               int max_z, int* ext, int* keep, int* ext_out, int* new_id, int* d_total, int sms,
-                               cudaStream_t s) {
+cudaError_t launch_link_filter(const long long dims[3], int* lab, int* chunk_off, int ncomp, int min_xy, int min_z,
+                               int max_xy, int max_z, int* ext, int* keep, int* ext_out, int* new_id, int* d_total,
+                               int sms, cudaStream_t s) {
   Geo g{(int)dims[0], (int)dims[1], (int)dims[2], dims[0] * dims[1] * dims[2], 0, 0};
-  if (ncomp <= 0) return cudaSuccess;
-  k_cc_ext_init<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, ncomp);
-  k_cc_extent<<<grid_for(g.n, sms, 256), 256, 0, s>>>(lab, g, ext);
+  const long long chunks = link_chunks(g.n);
+  if (ncomp > 0) k_cc_ext_init<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, ncomp);
+  k_cc_number<<<(unsigned)chunks, link::kChunkThreads, 0, s>>>(lab, g.n, chunk_off);
+  k_cc_final<<<grid_for((g.n + 31) / 32 * 32, sms, 256), 256, 0, s>>>(lab, g, ext);
+  if (ncomp <= 0) return cudaGetLastError();
   k_cc_keep<<<grid_for(ncomp, sms, 256), 256, 0, s>>>(ext, ncomp, min_xy, min_z, max_xy, max_z, keep);
   // keep flags are kept in new_id while keep becomes their exclusive scan
   cudaError_t e = cudaMemcpyAsync(new_id, keep, sizeof(int) * (size_t)ncomp, cudaMemcpyDeviceToDevice, s);
