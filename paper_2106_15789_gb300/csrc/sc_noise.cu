@@ -403,7 +403,7 @@ cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, c
 // shared-memory region and flushes them with one atomic per batch.
 constexpr int kP2Threads = 512;
 constexpr int kP2Warps = kP2Threads / 32;
-constexpr int kP2Unroll = 4;                 // chunks in flight per warp
+constexpr int kP2Unroll = 2;                 // chunks a warp classifies per iteration (the next ones load meanwhile)
 constexpr int kP2FlushAt = 64;               // flush a list holding more than this after a chunk
 constexpr int kP2Stage = kP2FlushAt + 128;   // one chunk adds at most 128 entries per list
 constexpr size_t kP2Smem =
@@ -434,6 +434,27 @@ __device__ __forceinline__ void stage_push(unsigned int b, bool pred, unsigned i
   cnt += __popc(b);
 }
 
+// Loads the kP2Unroll chunks of 128 values from chunk ch0 on; values past n
+// read as NaN (class 0, never sure, never listed).
+__device__ __forceinline__ void p2_load(const float* __restrict__ src, long long n, long long ch0, int lane,
+                                        float (&a)[kP2Unroll][4]) {
+  const float* base = src + ch0 * 128 + lane;
+  if ((ch0 + kP2Unroll) * 128 <= n) {
+#pragma unroll
+    for (int u = 0; u < kP2Unroll; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[u][c] = __ldg(base + 128 * u + 32 * c);
+  } else {
+#pragma unroll
+    for (int u = 0; u < kP2Unroll; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const long long v = (ch0 + u) * 128 + 32 * c + lane;
+        a[u][c] = v < n ? __ldg(src + v) : __int_as_float(0x7fc00000);
+      }
+  }
+}
+
 __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict__ src, long long n,
                                                          uint32_t* mbits, DevState* st, Lists L) {
   extern __shared__ __align__(16) unsigned char p2_smem[];
@@ -456,24 +477,11 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict
   int nmed = 0, nmad = 0, namb = 0;
   const long long nchunks = (n + 127) >> 7;
   const long long wstride = (long long)gridDim.x * kP2Warps * kP2Unroll;
-  for (long long ch0 = ((long long)blockIdx.x * kP2Warps + warp) * kP2Unroll; ch0 < nchunks; ch0 += wstride) {
-    // values past n read as NaN: class 0, never sure, never listed
-    float a[kP2Unroll][4];
-    const float* base = src + ch0 * 128 + lane;
-    if ((ch0 + kP2Unroll) * 128 <= n) {
-#pragma unroll
-      for (int u = 0; u < kP2Unroll; ++u)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) a[u][c] = __ldg(base + 128 * u + 32 * c);
-    } else {
-#pragma unroll
-      for (int u = 0; u < kP2Unroll; ++u)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const long long v = (ch0 + u) * 128 + 32 * c + lane;
-          a[u][c] = v < n ? __ldg(src + v) : __int_as_float(0x7fc00000);
-        }
-    }
+  float a[kP2Unroll][4], nxt[kP2Unroll][4];
+  long long ch0 = ((long long)blockIdx.x * kP2Warps + warp) * kP2Unroll;
+  if (ch0 < nchunks) p2_load(src, n, ch0, lane, a);
+  for (; ch0 < nchunks; ch0 += wstride) {
+    if (ch0 + wstride < nchunks) p2_load(src, n, ch0 + wstride, lane, nxt);
 #pragma unroll
     for (int u = 0; u < kP2Unroll; ++u) {
       const long long ch = ch0 + u;
@@ -524,6 +532,10 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict
         if (namb > kP2FlushAt) stage_flush(samb, namb, L.amb, &st->n_amb, L.cap.amb, &st->status);
       }
     }
+#pragma unroll
+    for (int u = 0; u < kP2Unroll; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[u][c] = nxt[u][c];
   }
   stage_flush(smed, nmed, L.med, &st->n_cand_med, L.cap.med, &st->status);
   stage_flush(smad, nmad, L.mad, &st->n_cand_mad, L.cap.mad, &st->status);
