@@ -33,7 +33,8 @@ METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM ro
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
-             "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag")
+             "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag",
+             "wallaby-gauss", "medium-gauss")
 FLAG_METRIC = "auto-flagger voxels/s on 1 GB300 (channel and pixel MAD noise, k = 4)"
 LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
@@ -241,7 +242,7 @@ def make_workload(name: str, rank: int, device: str):
     return spec, cube
 
 
-def cpu_baseline(cube_dev, kernels, t, n_repl):
+def cpu_baseline(cube_dev, kernels, t, n_repl, mode="mad"):
     """FP64 oracle (as it stands) on an interior 192 x 192 x 256 sub-cube."""
     from oracle.sc_oracle import sc_filter
 
@@ -250,7 +251,7 @@ def cpu_baseline(cube_dev, kernels, t, n_repl):
     z0, y0, x0 = (nz - sz) // 2, (ny - sy) // 2, (nx - sx) // 2
     sub = cube_dev[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx].float().cpu().numpy()
     t0 = time.perf_counter()
-    sc_filter(sub, kernels, t, "mad", n_repl)
+    sc_filter(sub, kernels, t, mode, n_repl)
     dt = time.perf_counter() - t0
     return {"value": sub.size * len(kernels) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"interior {sx}x{sy}x{sz} sub-cube of the same cube, {len(kernels)} pairs, numpy float64, "
@@ -288,7 +289,7 @@ def run_reference(args, rank, world):
     return 0
 
 
-def config_dict(workload, kernels):
+def config_dict(workload, kernels, mode="mad"):
     from synth.cubes import SC_REPLACEMENT, SC_THRESHOLD
 
     names = {"wallaby": "wallaby-1200x1200x1024", "medium": "medium-512x512x512", "small": "small-64x64x128",
@@ -297,11 +298,23 @@ def config_dict(workload, kernels):
              "wallaby-bf16": "wallaby-1200x1200x1024 stored as BF16 + per-channel float32 scales",
              "wallaby-fp16": "wallaby-1200x1200x1024 stored as FP16 + per-channel float32 scales",
              "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
+    workload = workload.removesuffix("-gauss")
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
-            "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": "mad", "replacement": SC_REPLACEMENT,
+            "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": mode, "replacement": SC_REPLACEMENT,
             "precision": "float32 cube, exact fixed-point smoothing", "l2": "inputs (cube 5.9 GB) larger than L2"
             if workload == "wallaby" else ("inputs (10.9 GB of sub-cubes) larger than L2" if workload == "batch64"
                                            else "no flush")}
+
+
+def gauss_hist_roofline(st, peak, peak_kind):
+    """Roofline of the Gaussian-fit histogram pass: 4 algorithmic bytes per
+    value read (the float32 array; the 2 KiB of counts are negligible), over
+    its live CUDA-event time."""
+    if not st["ms_gauss_hist"] > 0:
+        return None
+    gbs = st["gauss_hist_values"] * 4.0 / (st["ms_gauss_hist"] * 1e-3) / 1e9
+    return {"kernel": "k_gauss_hist", "bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "peak_kind": peak_kind, "bytes_per_value": 4, "traffic": None}
 
 
 def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
@@ -328,7 +341,7 @@ def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
             "smoothing_ms_by_kernel": {name: round(v[0] / steps, 3) for name, v in groups.items()}}
 
 
-def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world):
+def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world, mode="mad"):
     """End to end through sc_run from pinned host memory: every step copies its
     cube host -> device and its mask device -> host; with two device buffers
     the next cube's copy and the previous mask's copy run on a copy stream
@@ -361,7 +374,7 @@ def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world):
             compute.wait_event(loaded[b])
             if i >= 2:
                 compute.wait_event(sent[b])  # its mask of step i - 2 has left the device
-            ctx.run(bufs[b], kernels, t, "mad", n_repl, mask=masks[b])  # sigmas: synchronous
+            ctx.run(bufs[b], kernels, t, mode, n_repl, mask=masks[b])  # sigmas: synchronous
             computed[b].record(compute)
             with torch.cuda.stream(copy):
                 copy.wait_event(computed[b])
@@ -1045,7 +1058,8 @@ def main():
     sc.lib()  # fails loudly when the CUDA library is missing
     kernels = KERNELS_12
     t, n_repl = SC_THRESHOLD, SC_REPLACEMENT
-    spec, cube = make_workload(args.workload, rank, str(dev))
+    mode = "gauss" if args.workload.endswith("-gauss") else "mad"
+    spec, cube = make_workload(args.workload.removesuffix("-gauss"), rank, str(dev))
     nvox = cube.numel()
     mask = torch.empty(cube.shape, dtype=torch.uint8, device=dev)
     ctx = Context(local, nvox)
@@ -1055,7 +1069,7 @@ def main():
     tune_s = time.perf_counter() - t_tune
 
     def step():
-        return ctx.run(cube, kernels, t, "mad", n_repl, mask=mask)
+        return ctx.run(cube, kernels, t, mode, n_repl, mask=mask)
 
     for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
         step()
@@ -1091,22 +1105,26 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world)
+        e2e = pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world, mode)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cube, kernels, t, n_repl)
+        cpu = cpu_baseline(cube, kernels, t, n_repl, mode)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**config_dict(args.workload, kernels), "autotune_s": round(tune_s, 2)},
+                "config": {**config_dict(args.workload, kernels, mode), "autotune_s": round(tune_s, 2)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(st["launches"]), "clocks": sampler.summary(),
                 "breakdown_ms_per_step": {"smooth": st["ms_smooth"] / args.steps,
                                           "select": st["ms_select"] / args.steps,
-                                          "clip": st["ms_clip"] / args.steps},
+                                          "clip": st["ms_clip"] / args.steps,
+                                          **({"gauss_hist": st["ms_gauss_hist"] / args.steps,
+                                              "gauss_fit": st["ms_gauss_fit"] / args.steps} if mode == "gauss"
+                                             else {})},
+                **({"roofline_gauss_hist": gauss_hist_roofline(st, peak, peak_kind)} if mode == "gauss" else {}),
                 "sigma0": sig0, "sigmas": sig, "mask_fraction": float(mask.float().mean().item()),
                 "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
         print(json.dumps(line), flush=True)

@@ -41,14 +41,25 @@ extern "C" {
 #define SC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define SC_ERR_ALLNAN (-4)      /* the cube has no finite voxel: no noise level exists */
 #define SC_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
-#define SC_ERR_UNSUPPORTED (-6) /* option not implemented (noise mode SC_NOISE_GAUSS) */
+#define SC_ERR_UNSUPPORTED (-6) /* option not implemented (SC_NOISE_GAUSS in sc_noise_scale / sc_autoflag) */
 #define SC_ERR_BUDGET (-7)      /* request exceeds the context's sizes / memory budget */
 #define SC_ERR_INTERNAL (-8)    /* a device-side consistency check failed */
 
 /* ---- noise estimators (Sect. 4.1: robust RMS from the MAD) ------------ */
 #define SC_NOISE_MAD 0   /* 1.4826 * median(|S - median(S)|), exact medians */
 #define SC_NOISE_STD 1   /* sqrt(sum((S - mean)^2) / (n - 1)) */
-#define SC_NOISE_GAUSS 2 /* Gaussian fit: not defined by the paper -> SC_ERR_UNSUPPORTED */
+#define SC_NOISE_GAUSS 2 /* width of the least-squares Gaussian through a histogram of S (below) */
+
+/* SC_NOISE_GAUSS is the library's own definition (the paper names no such
+ * estimator). With sigma_M the MAD noise and k = fl32(128 / (5 sigma_M)),
+ * every finite value s goes to bin floor(fl32(s * k)) + 128 when that lies in
+ * [0, 256). A Gaussian A exp(-xi^2 / (2 tau^2)) centred at 0 is fitted by
+ * least squares to the counts at the bin centres xi_i = (i + 0.5) / 128 - 1
+ * (A profiled out; tau the root of the stationarity condition in
+ * [0.05, 0.8], bisected to the last bit); the noise is tau * 128 / k. Without
+ * a root in that bracket the MAD noise stands (SC_WARN_GAUSS_FALLBACK); a zero
+ * MAD noise stays zero. It costs one more pass over S per measurement, and
+ * the clip then takes a pass of its own. */
 
 /* ---- flags for sc_run ------------------------------------------------- */
 #define SC_FLAG_ACCUMULATE 0x1u /* start from the caller's mask (nonzero = detected) instead of an empty one */
@@ -61,6 +72,7 @@ extern "C" {
 #define SC_WARN_FULL_SELECT 0x2u    /* a selection needed full passes (candidate set above capacity) */
 #define SC_WARN_FULL_CLIP 0x4u      /* a clip needed a separate pass (ambiguous set above capacity) */
 #define SC_WARN_RANGE 0x8u          /* max|X| / sigma_0 exceeds 2^20: smoothed values may lose exactness */
+#define SC_WARN_GAUSS_FALLBACK 0x10u /* SC_NOISE_GAUSS: a histogram without a Gaussian-fit root; the MAD noise stood */
 
 typedef struct sc_ctx sc_ctx;
 
@@ -111,6 +123,9 @@ typedef struct {
   int32_t smooth_kernel_pair[SC_MAX_KERNELS];     /* SC_KERNEL_* of each pair's latest smoothing (not reset) */
   double ms_noise_window;  /* sc_noise_scale: device time of the per-cell window noise (while profiling) */
   double ms_noise_apply;   /* sc_noise_scale: device time of the division pass (while profiling) */
+  double ms_gauss_hist;    /* SC_NOISE_GAUSS: device time of the 256-bin histogram passes (while profiling) */
+  double ms_gauss_fit;     /* SC_NOISE_GAUSS: device time of the least-squares fits (while profiling) */
+  uint64_t gauss_hist_values; /* values those histogram passes read */
 } sc_stats;
 
 /* Create a context on CUDA device `device` with workspace for cubes of up to
@@ -142,7 +157,7 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  *   kernels      n_kernels pairs, run in the order given (Sect. 5 uses
  *                spatial {0,5,10} x spectral {0,3,7,15}).
  *   threshold    t > 0: a voxel is detected when |S| > t*sigma_k.
- *   noise_mode   SC_NOISE_MAD or SC_NOISE_STD.
+ *   noise_mode   SC_NOISE_MAD, SC_NOISE_STD or SC_NOISE_GAUSS.
  *   replacement  n: masked voxels become sign(C)*n*sigma_0 before smoothing
  *                (Sect. 6.2); n <= 0 switches replacement off.
  *   mask_dev     uint8 [nz][ny][nx] output, 1 = detected, 0 = not. Zeroed
@@ -155,9 +170,8 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  * and device-side errors surface at the next synchronising call.
  * Errors: SC_ERR_ARG (dims <= 0, more voxels than max_voxels -> SC_ERR_BUDGET,
  * even boxcar, negative or non-finite FWHM, t <= 0 or not finite, n_kernels
- * outside 1..SC_MAX_KERNELS, NULL pointers), SC_ERR_UNSUPPORTED
- * (SC_NOISE_GAUSS), SC_ERR_ALLNAN (no finite voxel; mask left zero),
- * SC_ERR_CUDA. */
+ * outside 1..SC_MAX_KERNELS, NULL pointers, unknown noise mode),
+ * SC_ERR_ALLNAN (no finite voxel; mask left zero), SC_ERR_CUDA. */
 int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_kernel *kernels, int n_kernels,
            float threshold, int noise_mode, float replacement, uint8_t *mask_dev, double *sigma_host,
            double *sigma0_host, uint32_t flags, void *cuda_stream);
@@ -272,8 +286,8 @@ int sc_smooth(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, sc_kernel
 
 /* Noise level (Sect. 4.1 estimator) of the finite values of a device float32
  * array of n elements (NaN skipped). *sigma_host receives it (synchronises).
- * Errors: SC_ERR_ARG, SC_ERR_BUDGET (n > max_voxels), SC_ERR_ALLNAN,
- * SC_ERR_UNSUPPORTED. */
+ * Errors: SC_ERR_ARG (NULL pointer, n <= 0, unknown mode), SC_ERR_BUDGET
+ * (n > max_voxels), SC_ERR_ALLNAN, SC_ERR_CUDA. */
 int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, double *sigma_host, uint32_t flags,
              void *cuda_stream);
 
@@ -366,7 +380,7 @@ int sc_autoflag(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, double 
  * memory belongs to another allocator or a fixed pool, real-time pipelines
  * that forbid allocation (and the device synchronisation it implies) once
  * running, plug-ins that are handed only a stream and buffers. It needs no
- * context and allocates nothing: its scratch (2,590,976 bytes) is one static
+ * context and allocates nothing: its scratch (2,593,024 bytes) is one static
  * device array that every GPU loading this library holds until the process
  * exits. The paper has no counterpart; this is a library-level addition.
  *   - n <= 4194304 (4 Mi values), else SC_ERR_BUDGET.

@@ -36,6 +36,7 @@ struct sc_ctx {
   float* S = nullptr;
   uint32_t* mbits = nullptr;
   unsigned long long* hist = nullptr;
+  unsigned long long* ghist = nullptr;  // SC_NOISE_GAUSS: 256 bin counts
   Lists L{};
   DevState* st = nullptr;
   DevState* st_host = nullptr;   // pinned mirror for read-back
@@ -132,7 +133,8 @@ cudaEvent_t take_event(sc_ctx* c) {
   return e;
 }
 
-enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2, EV_NOISE_WINDOW = 3, EV_NOISE_APPLY = 4 };
+enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2, EV_NOISE_WINDOW = 3, EV_NOISE_APPLY = 4, EV_GAUSS_HIST = 5,
+       EV_GAUSS_FIT = 6 };
 
 struct Phase {
   sc_ctx* c;
@@ -176,6 +178,11 @@ void flush_events(sc_ctx* c) {
       c->stats.ms_noise_window += ms;
     } else if (e.kind == EV_NOISE_APPLY) {
       c->stats.ms_noise_apply += ms;
+    } else if (e.kind == EV_GAUSS_HIST) {
+      c->stats.ms_gauss_hist += ms;
+      c->stats.gauss_hist_values += e.voxels;
+    } else if (e.kind == EV_GAUSS_FIT) {
+      c->stats.ms_gauss_fit += ms;
     } else {
       c->stats.ms_clip += ms;
     }
@@ -218,11 +225,14 @@ int status_to_code(const DevState& h) {
 
 // One noise measurement (and optional clip) over src, whose histogram is in
 // c->hist. pair: index for sigma[] (-1: none).
-int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip, int std_mode, int pair,
+int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip, int noise_mode, int pair,
             unsigned int force, cudaStream_t s) {
+  const int std_mode = noise_mode == SC_NOISE_STD;
+  const bool gauss = noise_mode == SC_NOISE_GAUSS;
   {
     Phase ph(c, s, EV_SELECT);
-    CK(launch_plan(c->st, c->hist, win, src, n, c->L, t, clip, std_mode, force, s));
+    // the Gaussian fit moves sigma after the MAD: its clip waits for the fit
+    CK(launch_plan(c->st, c->hist, win, src, n, c->L, t, gauss ? 0 : clip, std_mode, force, s));
     c->stats.launches += 1;
     if (std_mode) {
       CK(launch_std(src, n, c->st, c->sms, s));
@@ -235,9 +245,18 @@ int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip
       c->stats.launches += 11;
     }
   }
+  if (gauss) {
+    {
+      Phase ph(c, s, EV_GAUSS_HIST, (unsigned long long)n);
+      CK(launch_gauss_hist(src, n, c->st, c->ghist, c->sms, s));
+    }
+    Phase ph(c, s, EV_GAUSS_FIT);
+    CK(launch_gauss_fit(c->st, c->ghist, pair, clip, s));
+    c->stats.launches += 2;
+  }
   if (clip) {
     Phase ph(c, s, EV_CLIP);
-    if (!std_mode) {
+    if (!std_mode && !gauss) {
       CK(launch_resolve(src, c->mbits, c->st, c->L, c->sms, s));
       c->stats.launches += 1;
     }
@@ -254,8 +273,7 @@ int validate_common(sc_ctx* c, const float* cube, const int64_t* dims, const sc_
   if (rc) return rc;
   if (nk < 1 || nk > SC_MAX_KERNELS) return SC_ERR_ARG;
   if (!(t > 0.0f) || !std::isfinite(t)) return SC_ERR_ARG;
-  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
-  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   pds->resize(nk);
   for (int k = 0; k < nk; ++k) {
     rc = make_pair(kernels[k], &(*pds)[k]);
@@ -326,7 +344,8 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       c->stats.launches += 2;
     }
   }
-  rc = measure(c, cube, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, std_mode, first_identity ? 0 : -1, force, s);
+  rc = measure(c, cube, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, noise_mode, first_identity ? 0 : -1, force,
+               s);
   if (rc) return rc;
   CK(launch_sigma0_done(c->st, replacement, W, nk, s));
   c->stats.launches += 1;
@@ -355,7 +374,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
         c->stats.smooth_kernel_pair[k] = code;
       }
     }
-    rc = measure(c, c->S, n, 1, t, 1, std_mode, k, force, s);
+    rc = measure(c, c->S, n, 1, t, 1, noise_mode, k, force, s);
     if (rc) return rc;
   }
   {
@@ -428,6 +447,7 @@ int sc_create(sc_ctx** out, int device, size_t max_voxels) {
   bool ok = cudaMalloc(&c->S, sizeof(float) * max_voxels) == cudaSuccess &&
             cudaMalloc(&c->mbits, sizeof(uint32_t) * nwords) == cudaSuccess &&
             cudaMalloc(&c->hist, sizeof(unsigned long long) * kNumBins) == cudaSuccess &&
+            cudaMalloc(&c->ghist, sizeof(unsigned long long) * kGaussBins) == cudaSuccess &&
             cudaMalloc(&c->L.med, sizeof(float) * c->L.cap.med) == cudaSuccess &&
             cudaMalloc(&c->L.mad, sizeof(float) * c->L.cap.mad) == cudaSuccess &&
             cudaMalloc(&c->L.amb, sizeof(unsigned long long) * c->L.cap.amb) == cudaSuccess &&
@@ -461,6 +481,7 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->S);
   cudaFree(c->mbits);
   cudaFree(c->hist);
+  cudaFree(c->ghist);
   cudaFree(c->L.med);
   cudaFree(c->L.mad);
   cudaFree(c->L.amb);
@@ -1046,8 +1067,7 @@ int sc_noise(sc_ctx* c, const float* data_dev, int64_t n, int noise_mode, double
              void* cuda_stream) {
   if (!c || !data_dev || !sigma_host || n <= 0) return SC_ERR_ARG;
   if ((unsigned long long)n > c->max_voxels) return SC_ERR_BUDGET;
-  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
-  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   c->last = s;
@@ -1056,7 +1076,7 @@ int sc_noise(sc_ctx* c, const float* data_dev, int64_t n, int noise_mode, double
   CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
   CK(launch_hist(data_dev, n, c->st, c->hist, 0, 0, c->sms, s));
   c->stats.launches += 1;
-  int rc = measure(c, data_dev, n, 0, 1.0f, 0, noise_mode == SC_NOISE_STD, SC_MAX_KERNELS, force, s);
+  int rc = measure(c, data_dev, n, 0, 1.0f, 0, noise_mode, SC_MAX_KERNELS, force, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(c->st_host, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

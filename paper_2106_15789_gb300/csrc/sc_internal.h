@@ -203,6 +203,14 @@ cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, Dev
                              cudaStream_t s);
 cudaError_t launch_std(const float* src, long long n, DevState* st, int sms, cudaStream_t s);
 cudaError_t launch_std_final(DevState* st, int pair, cudaStream_t s);
+// Gaussian-fit noise (after the MAD measurement of the same array): the
+// 256-bin histogram over +-5 MAD noises into ghist[256], then the fit, which
+// replaces sigma_cur (and sigma[pair] for pair >= 0) and, with clip, marks the
+// plan for a full clip pass.
+constexpr int kGaussBins = 256;
+cudaError_t launch_gauss_hist(const float* src, long long n, const DevState* st, unsigned long long* ghist, int sms,
+                              cudaStream_t s);
+cudaError_t launch_gauss_fit(DevState* st, const unsigned long long* ghist, int pair, int clip, cudaStream_t s);
 // DevState::win from the full-range histogram of a raw cube (median of |x|)
 cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s);
 cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,

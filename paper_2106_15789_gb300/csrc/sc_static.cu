@@ -37,7 +37,8 @@ constexpr size_t kOffHist = align_up(kOffState + sizeof(DevState));
 constexpr size_t kOffMed = align_up(kOffHist + sizeof(unsigned long long) * kNumBins);
 constexpr size_t kOffMad = align_up(kOffMed + sizeof(float) * kStaticCapMed);
 constexpr size_t kOffCls = align_up(kOffMad + sizeof(float) * kStaticCapMad);
-constexpr size_t kStaticBytes = align_up(kOffCls + kClassTableBytes);
+constexpr size_t kOffGHist = align_up(kOffCls + kClassTableBytes);
+constexpr size_t kStaticBytes = align_up(kOffGHist + sizeof(unsigned long long) * kGaussBins);
 
 // The scratch itself. In host code this name is a host-side stand-in, not a
 // device address: only the pointer from cudaGetSymbolAddress goes to kernels.
@@ -77,8 +78,7 @@ extern "C" int sc_noise_static(const float* data_dev, int64_t n, int noise_mode,
                                void* cuda_stream) {
   if (!data_dev || !sigma_host || n <= 0) return SC_ERR_ARG;
   if (n > kStaticMaxValues) return SC_ERR_BUDGET;
-  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
-  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   unsigned char* base = nullptr;
   int sms = 0;
   int rc = scratch_for_current_device(&base, &sms);
@@ -105,6 +105,11 @@ extern "C" int sc_noise_static(const float* data_dev, int64_t n, int noise_mode,
     CKS(launch_pass2(data_dev, n, nullptr, st, L, sms, s));
     CKS(launch_select(st, 0, -1, sms, s));
     CKS(launch_select(st, 1, SC_MAX_KERNELS, sms, s));
+  }
+  if (noise_mode == SC_NOISE_GAUSS) {
+    unsigned long long* ghist = reinterpret_cast<unsigned long long*>(base + kOffGHist);
+    CKS(launch_gauss_hist(data_dev, n, st, ghist, sms, s));
+    CKS(launch_gauss_fit(st, ghist, SC_MAX_KERNELS, 0, s));
   }
   unsigned int status = 0u;
   float sigma = 0.0f;

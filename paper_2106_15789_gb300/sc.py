@@ -48,6 +48,7 @@ SC_WARN_ZERO_SIGMA = 0x1
 SC_WARN_FULL_SELECT = 0x2
 SC_WARN_FULL_CLIP = 0x4
 SC_WARN_RANGE = 0x8
+SC_WARN_GAUSS_FALLBACK = 0x10
 
 SC_MAX_KERNELS = 64
 
@@ -66,7 +67,8 @@ class sc_stats(C.Structure):
                 ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64),
                 ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS),
                 ("smooth_kernel_pair", C.c_int32 * SC_MAX_KERNELS), ("ms_noise_window", C.c_double),
-                ("ms_noise_apply", C.c_double)]
+                ("ms_noise_apply", C.c_double), ("ms_gauss_hist", C.c_double), ("ms_gauss_fit", C.c_double),
+                ("gauss_hist_values", C.c_uint64)]
 
 
 class ScError(RuntimeError):

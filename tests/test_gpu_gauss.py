@@ -1,0 +1,185 @@
+"""Parity of the Gaussian-fit noise mode (SC_NOISE_GAUSS) with the FP64 oracle,
+through the C ABI: sc_noise, sc_noise_static and the S+C runs.
+
+Tolerance. The kernel's MAD noise sigma_M comes from float32 keys of
+|s - median| (exact order statistics, rounded once), the oracle's from exact
+float64 ones: the two differ by at most 2^-23 relative. The histogram's scale
+k = fl32(128 / (5 sigma_M)) can then differ by an ulp, and values within that
+ulp of a bin edge fall into the neighbouring bin. So a kernel result is
+accepted when it is within SIG_RTOL of the oracle's Gaussian-fit noise taken
+with sigma_M scaled by (1 + j 2^-24), j = -2..2 (the oracle evaluated at the
+sigma_M values that rounding allows; no kernel value enters it).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.sc_oracle as O
+from synth.cubes import KERNELS_12, SMALL, CubeSpec, make_cube
+
+pytestmark = pytest.mark.gpu
+
+T = 3.5
+N_REPL = 2.0
+SIG_RTOL = 1e-6
+BAND = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2106_15789_gb300 import Context
+
+    c = Context(0, 1 << 25)
+    yield c
+    c.close()
+
+
+def gauss_refs(v: np.ndarray) -> list[float]:
+    """The oracle's Gaussian-fit noise of the finite float32 values v, at the
+    exact sigma_M and at sigma_M moved by up to two float32 ulps."""
+    s_mad = O.noise(v, "mad")
+    if not s_mad > 0.0:
+        return [0.0]
+    out = []
+    for j in (-2, -1, 0, 1, 2):
+        sm = s_mad * (1.0 + j * 2.0 ** -24)
+        tau = O.gauss_fit(O.gauss_histogram(v, sm))
+        out.append(sm if tau is None else tau * 128.0 / float(O.gauss_scale(sm)))
+    return out
+
+
+def close_to_any(got: float, refs: list[float]) -> bool:
+    return any((got == 0.0) if r == 0.0 else abs(got - r) <= SIG_RTOL * r for r in refs)
+
+
+def noise_cases():
+    rng = np.random.default_rng(321)
+    cases = {f"normal{n}": rng.standard_normal(n) for n in (1, 2, 3, 10, 101, 1000, 100_001, 2_000_000)}
+    x = rng.standard_normal(300_000)
+    x[rng.random(x.size) < 0.1] = np.nan
+    x[:7] = np.inf
+    x[7:9] = -np.inf
+    cases["nan_inf"] = x
+    cases["rounded"] = np.round(rng.standard_normal(200_000), 1)
+    cases["integers"] = rng.integers(-3, 4, 100_000).astype(float)
+    cases["offset"] = 1000.0 + rng.standard_normal(100_000)  # empty histogram around 0: MAD noise stands
+    cases["tiny"] = 1e-20 * rng.standard_normal(50_000)
+    cases["huge"] = 1e20 * rng.standard_normal(50_000)
+    cases["cauchy"] = rng.standard_cauchy(300_000)
+    cases["skewed"] = rng.exponential(1.0, 100_000)
+    cases["constant"] = np.full(1000, 2.5)
+    e = rng.standard_normal(1_000_003) * 0.7
+    src = rng.random(e.size) < 0.03
+    e[src] = np.abs(e[src]) * 6.0 + 3.0  # bright positive emission on 3 % of the values
+    cases["emission"] = e
+    return cases
+
+
+@pytest.mark.parametrize("name", list(noise_cases().keys()))
+def test_noise_matches_oracle(ctx, name):
+    from paper_2106_15789_gb300 import sc
+
+    v = noise_cases()[name].astype(np.float32)
+    d = torch.from_numpy(v).cuda()
+    fin = v[np.isfinite(v)].astype(np.float64)
+    got = ctx.noise(d, "gauss")
+    refs = gauss_refs(fin)
+    assert close_to_any(got, refs), (got, refs)
+    # the candidate lists and the full passes give the same MAD, so the same fit
+    assert ctx.noise(d, "gauss", flags=sc.SC_FLAG_NO_FAST_SELECT) == got
+    # the no-allocation entry point runs the same kernels
+    assert sc.sc_noise_static(d, "gauss") == got
+
+
+def test_noise_large(ctx):
+    """2^25 values with an emission tail: the fit stays near the true sigma
+    while the MAD noise is pulled up."""
+    rng = np.random.default_rng(9)
+    v = (rng.standard_normal(1 << 25) * 1.3).astype(np.float32)
+    src = rng.random(v.size) < 0.02
+    v[src] = np.abs(v[src]) * 5.0 + 4.0
+    d = torch.from_numpy(v).cuda()
+    got = ctx.noise(d, "gauss")
+    assert close_to_any(got, gauss_refs(v.astype(np.float64)))
+    assert abs(got - 1.3) < 0.005 * 1.3 < abs(ctx.noise(d, "mad") - 1.3)
+
+
+def test_fallback_and_zero(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    rng = np.random.default_rng(4)
+    d = torch.from_numpy((500.0 + rng.standard_normal(20_000)).astype(np.float32)).cuda()
+    assert ctx.noise(d, "gauss") == ctx.noise(d, "mad")
+    assert ctx.noise(torch.full((999,), -4.0, device="cuda"), "gauss") == 0.0
+    # a run on a cube far from 0 keeps the MAD noise and says so
+    cube = (300.0 + torch.randn(24, 20, 22)).cuda()
+    ctx.stats(reset=True)
+    _, sig, s0 = ctx.run(cube, [(0.0, 1), (0.0, 3)], T, "gauss", N_REPL)
+    assert ctx.stats()["warnings"] & sc.SC_WARN_GAUSS_FALLBACK
+    assert s0 == pytest.approx(O.noise(cube.cpu().numpy().ravel().astype(np.float64), "mad"), rel=2 ** -22)
+
+
+def band_disagreements(mask_gpu, m_ref, ss, sigmas, t):
+    diff = np.argwhere(mask_gpu != m_ref)
+    bad = []
+    for p in diff:
+        p = tuple(p)
+        if not any(sk > 0 and abs(abs(s[p]) / sk - t) < BAND for s, sk in zip(ss, sigmas)):
+            bad.append(p)
+    return len(diff), bad
+
+
+def check_run(ctx, cube, kernels, t=T, n=N_REPL, flags=0, mask0=None):
+    c_np = cube.numpy()
+    mask = None if mask0 is None else torch.from_numpy(mask0.astype(np.uint8)).cuda()
+    m, sig, s0 = ctx.run(cube.cuda(), kernels, t, "gauss", n, mask=mask, flags=flags)
+    m_ref, s_ref, s0_ref, ss = O.sc_filter(c_np, kernels, t, "gauss", n, mask=mask0, return_smoothed=True)
+    # sigma_0 from the raw cube; sigma_k from S_k, which depends on the earlier
+    # pairs' masks and so can differ where a voxel sat on a threshold
+    assert close_to_any(s0, gauss_refs(c_np[np.isfinite(c_np)].astype(np.float64))), (s0, s0_ref)
+    for k, (a, b) in enumerate(zip(sig, s_ref)):
+        assert abs(a - b) <= 4 * SIG_RTOL * b, (k, kernels[k], a, b)
+    ndiff, bad = band_disagreements(m.cpu().numpy(), m_ref, ss, s_ref, t)
+    assert not bad, f"{len(bad)} mask disagreements outside the threshold band, e.g. {bad[:5]}"
+    return m, sig, s0
+
+
+def test_small_cube(ctx):
+    m, sig, s0 = check_run(ctx, make_cube(SMALL), KERNELS_12)
+    assert m.sum().item() > 0
+
+
+def test_replacement_off_and_low_threshold(ctx):
+    check_run(ctx, make_cube(SMALL), KERNELS_12, n=0.0)
+    check_run(ctx, make_cube(SMALL), [(0.0, 1), (5.0, 3), (10.0, 7)], t=2.5, n=1.5)
+
+
+def test_accumulate(ctx):
+    from paper_2106_15789_gb300 import sc
+
+    cube = make_cube(SMALL)
+    rng = np.random.default_rng(2)
+    m0 = rng.random(cube.shape) < 0.002
+    check_run(ctx, cube, KERNELS_12[4:], flags=sc.SC_FLAG_ACCUMULATE, mask0=m0)
+
+
+@pytest.mark.parametrize("shape", [(19, 23, 37), (1, 50, 40), (30, 1, 1), (5, 3, 200), (33, 65, 31), (2, 1, 1)])
+def test_ragged_shapes(ctx, shape):
+    rng = np.random.default_rng(sum(shape) + 1)
+    c = rng.standard_normal(shape)
+    for _ in range(4):
+        p = tuple(int(rng.integers(0, n)) for n in shape)
+        c[p] += rng.choice([-1, 1]) * 8.0
+    c[rng.random(shape) < 0.05] = np.nan
+    c = c.astype(np.float32)
+    if not np.isfinite(c).any():
+        c.flat[0] = 1.0
+    check_run(ctx, torch.from_numpy(c), [(0.0, 0), (3.0, 3), (10.0, 15), (6.0, 1), (0.0, 31)], t=2.5)
+
+
+def test_batch_matches_single_runs(ctx):
+    cubes = [make_cube(CubeSpec(**{**SMALL.__dict__, "seed": SMALL.seed + i})).cuda() for i in range(3)]
+    masks, sigs, s0s = ctx.run_batch(cubes, KERNELS_12, T, "gauss", N_REPL)
+    for cube, m, sig, s0 in zip(cubes, masks, sigs, s0s):
+        m1, sig1, s01 = ctx.run(cube, KERNELS_12, T, "gauss", N_REPL)
+        assert torch.equal(m, m1) and sig == sig1 and s0 == s01

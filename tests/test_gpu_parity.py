@@ -212,7 +212,7 @@ def test_errors(ctx):
     good = torch.randn(8, 8, 8, device="cuda")
     for kernels, t, mode, code in (([(3.0, 4)], T, "mad", sc.SC_ERR_ARG), ([(-1.0, 3)], T, "mad", sc.SC_ERR_ARG),
                                    ([(float("nan"), 3)], T, "mad", sc.SC_ERR_ARG), ([(3.0, 3)], 0.0, "mad", sc.SC_ERR_ARG),
-                                   ([(3.0, 3)], T, "gauss", sc.SC_ERR_UNSUPPORTED), ([(3.0, 3)] * 65, T, "mad", sc.SC_ERR_ARG),
+                                   ([(3.0, 3)], T, 7, sc.SC_ERR_ARG), ([(3.0, 3)] * 65, T, "mad", sc.SC_ERR_ARG),
                                    ([(3.0, 129)], T, "mad", sc.SC_ERR_UNSUPPORTED)):
         with pytest.raises(sc.ScError) as e:
             ctx.run(good, kernels, t, mode)
