@@ -14,11 +14,13 @@
 //   D(tau) = sum(g^2) sum(h xi^2 g) - sum(h g) sum(xi^2 g^2) = 0.
 // D > 0 for Gaussians much narrower than the counts and D < 0 for much wider
 // ones, so bisection over tau in [0.05, 0.8], keeping D(lo) > 0 >= D(hi),
-// finds the root to the last bit. Without a sign change at the bracket's ends
+// finds the root to the last bit (the kernel takes Newton steps inside that
+// bracket to the same root). Without a sign change at the bracket's ends
 // the MAD noise stands (SC_WARN_GAUSS_FALLBACK); a zero MAD noise stays zero.
 //
 // k_gauss_hist is a streaming pass over the array (4 bytes a value, HBM
-// bound); k_gauss_fit is one block of 256 threads, one per bin, in float64.
+// bound); k_gauss_fit is one block of 128 threads, one per mirror pair of
+// bins, in float64.
 #include "sc_internal.h"
 
 namespace sc {
@@ -79,37 +81,51 @@ __global__ void __launch_bounds__(kGHThreads) k_gauss_hist(const float* __restri
   }
 }
 
-// Sum of v over the block's 256 threads in a fixed order (xor tree in each
-// warp, then warps 0..7 in turn); every thread gets the total.
-__device__ __forceinline__ void block_sum4(double v[4], double (*red)[4]) {
+// Sum of v over the fit block's 128 threads in a fixed order (xor tree in
+// each warp, then warps 0..3 in turn); every thread gets the same totals.
+constexpr int kGFitThreads = kGHalf;
+__device__ __forceinline__ void block_sum6(double v[6], double (*red)[6]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < 6; ++j)
     for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
   const int warp = threadIdx.x >> 5;
   __syncthreads();  // the previous call's readers are done with red
   if ((threadIdx.x & 31) == 0)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) red[warp][j] = v[j];
+    for (int j = 0; j < 6; ++j) red[warp][j] = v[j];
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < 6; ++j) {
     double t = 0.0;
-    for (int w = 0; w < kGBins / 32; ++w) t += red[w][j];
+    for (int w = 0; w < kGFitThreads / 32; ++w) t += red[w][j];
     v[j] = t;
   }
 }
 
-// D(tau) of the bin this thread holds, summed over the block.
-__device__ __forceinline__ double gauss_d(double tau, double h, double x2, double (*red)[4]) {
-  const double g = exp(-x2 / (2.0 * tau * tau));
-  double v[4] = {g * g, h * x2 * g, h * g, x2 * g * g};
-  block_sum4(v, red);
+// D(tau) and dD/dtau over the folded bins. Thread t holds the mirror pair of
+// bins 128 + t and 127 - t, which share xi^2 = ((t + 0.5) / 128)^2, with
+// H = their summed counts. Over half the bins,
+//   A = sum g^2, B = sum H xi^2 g, C = sum H g, E = sum xi^2 g^2,
+// and the full-histogram D is 2 (A B - C E): same sign, same root. With
+// dg/dtau = g xi^2 / tau^3 (F = sum H xi^4 g, G = sum xi^4 g^2):
+//   d(A B - C E)/dtau = (E B + A F - 2 C G) / tau^3.
+__device__ __forceinline__ double gauss_d(double tau, double hh, double x2, double (*red)[6], double* slope) {
+  const double c = 0.5 / (tau * tau);
+  const double g = exp(-x2 * c);
+  const double gg = g * g, hg = hh * g;
+  double v[6] = {gg, hg * x2, hg, gg * x2, hg * x2 * x2, gg * x2 * x2};
+  block_sum6(v, red);
+  *slope = (__dmul_rn(v[3], v[1]) + __dmul_rn(v[0], v[4]) - 2.0 * __dmul_rn(v[2], v[5])) / (tau * tau * tau);
   return __dsub_rn(__dmul_rn(v[0], v[1]), __dmul_rn(v[2], v[3]));
 }
 
-__global__ void __launch_bounds__(kGBins) k_gauss_fit(DevState* st, const unsigned long long* ghist, int pair,
-                                                      int clip) {
-  __shared__ double red[kGBins / 32][4];
+// The root of D in [0.05, 0.8] by Newton steps kept inside the bracket
+// (a step that would leave it bisects instead); D(lo) > 0 >= D(hi) holds
+// throughout, so this converges to the root the bisection of the definition
+// converges to, within the rounding of the sums.
+__global__ void __launch_bounds__(kGFitThreads) k_gauss_fit(DevState* st, const unsigned long long* ghist, int pair,
+                                                            int clip) {
+  __shared__ double red[kGFitThreads / 32][6];
   const int flags = st->plan.flags;
   const double sm = st->sigma_cur_d;
   __syncthreads();  // every thread has read the plan before thread 0 rewrites it
@@ -118,30 +134,37 @@ __global__ void __launch_bounds__(kGBins) k_gauss_fit(DevState* st, const unsign
   if (clip && threadIdx.x == 0) st->plan.flags = flags | PLAN_CLIP | PLAN_CLIP_FULL;
   if (!(sm > 0.0)) return;  // sigma stays 0: the clip adds nothing
   const float k = __double2float_rn((double)kGHalf / (kGRange * sm));
-  const int i = threadIdx.x;
-  const double xi = ((double)i + 0.5) / (double)kGHalf - 1.0;
+  const int t = threadIdx.x;
+  const double xi = ((double)(kGHalf + t) + 0.5) / (double)kGHalf - 1.0;
   const double x2 = xi * xi;
-  const double h = (double)ghist[i];
-  double lo = kGTauLo, hi = kGTauHi;
-  const bool bracket = gauss_d(lo, h, x2, red) > 0.0 && gauss_d(hi, h, x2, red) < 0.0;
-  double tau = 0.0;
+  const double hh = (double)ghist[kGHalf + t] + (double)ghist[kGHalf - 1 - t];
+  double lo = kGTauLo, hi = kGTauHi, slope = 0.0;
+  const bool bracket = gauss_d(lo, hh, x2, red, &slope) > 0.0 && gauss_d(hi, hh, x2, red, &slope) < 0.0;
+  double tau = 0.5 * (lo + hi);
   if (bracket) {
-    // every thread holds the same sums, so the loop is block-uniform
+    // every thread holds the same totals, so the loop is block-uniform
     for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) {
-        tau = mid;
+      const double d = gauss_d(tau, hh, x2, red, &slope);
+      if (d == 0.0) break;
+      if (d > 0.0) {
+        lo = tau;
+      } else {
+        hi = tau;
+      }
+      double next = tau - d / slope;
+      if (fabs(next - tau) <= 0x1p-50 * tau) {  // converged: keep the step, inside the bracket
+        tau = fmin(fmax(next, lo), hi);
         break;
       }
-      if (gauss_d(mid, h, x2, red) > 0.0) {
-        lo = mid;
-      } else {
-        hi = mid;
+      if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
+      if (hi - lo <= 0x1p-50 * tau) {
+        tau = 0.5 * (lo + hi);
+        break;
       }
-      tau = 0.5 * (lo + hi);
+      tau = next;
     }
   }
-  if (i != 0) return;
+  if (t != 0) return;
   if (!bracket) {
     st->warn |= SC_WARN_GAUSS_FALLBACK;
     return;  // the MAD noise stands
@@ -166,7 +189,7 @@ cudaError_t launch_gauss_hist(const float* src, long long n, const DevState* st,
 }
 
 cudaError_t launch_gauss_fit(DevState* st, const unsigned long long* ghist, int pair, int clip, cudaStream_t s) {
-  k_gauss_fit<<<1, kGBins, 0, s>>>(st, ghist, pair, clip);
+  k_gauss_fit<<<1, kGFitThreads, 0, s>>>(st, ghist, pair, clip);
   return cudaGetLastError();
 }
 

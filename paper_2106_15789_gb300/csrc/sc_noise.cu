@@ -838,6 +838,33 @@ cudaError_t launch_resolve(const float* src, uint32_t* mbits, DevState* st, List
   return cudaGetLastError();
 }
 
+// Lane l holds values l, l + 32, l + 64 and l + 96 of chunk ch (each load
+// instruction reads 128 contiguous bytes), so ballot c is mask word 4 ch + c
+// as it stands; 0 past n.
+__device__ __forceinline__ void clip_load(const float* __restrict__ src, long long n, long long ch, int lane,
+                                          float (&a)[4]) {
+  const long long v0 = ch * 128 + lane;
+  if (ch * 128 + 128 <= n) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[c] = __ldg(src + v0 + 32 * c);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[c] = (v0 + 32 * c < n) ? __ldg(src + v0 + 32 * c) : 0.0f;
+  }
+}
+
+// Sets chunk ch's detected bits: lane c < 4 owns word 4 ch + c.
+__device__ __forceinline__ void clip_store(uint32_t* mbits, long long ch, int lane, float thr, const float (&a)[4]) {
+  unsigned int w = 0u;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float m = fabsf(a[c]);  // NaN fails the first compare, Inf the second
+    const unsigned int b = __ballot_sync(0xffffffffu, m > thr && m <= FLT_MAX);
+    w = lane == c ? b : w;
+  }
+  if (lane < 4 && w) atomicOr(mbits + ch * 4 + lane, w);  // no return value: no wait for the word
+}
+
 __global__ void __launch_bounds__(256) k_clip_full(const float* __restrict__ src, long long n, uint32_t* mbits,
                                                    DevState* st) {
   const NoisePlan& p = st->plan;
@@ -847,27 +874,15 @@ __global__ void __launch_bounds__(256) k_clip_full(const float* __restrict__ src
   const float thr = __fmul_rn(p.threshold, sg);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long nchunks = (n + 127) / 128;
-  const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0);
-  for (long long ch = (long long)blockIdx.x * 8 + warp; ch < nchunks; ch += (long long)gridDim.x * 8) {
-    const long long v0 = ch * 128 + lane * 4;
-    float a[4];
-    if (vec && v0 + 3 < n) {
-      float4 t4 = __ldg(reinterpret_cast<const float4*>(src + v0));
-      a[0] = t4.x; a[1] = t4.y; a[2] = t4.z; a[3] = t4.w;
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) a[c] = (v0 + c < n) ? __ldg(src + v0 + c) : 0.0f;
-    }
-    unsigned int bits[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) bits[c] = __ballot_sync(0xffffffffu, isfinite(a[c]) && fabsf(a[c]) > thr);
-    if (lane < 4) {
-      unsigned int w = 0u;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) w |= spread4(bits[c] >> (8 * lane)) << c;
-      const long long wi = ch * 4 + lane;
-      if (w && wi * 32 < n) mbits[wi] |= w;
-    }
+  const long long stride = (long long)gridDim.x * 8;
+  // two chunks a warp per iteration, all eight loads issued before a ballot
+  for (long long ch = (long long)blockIdx.x * 8 + warp; ch < nchunks; ch += 2 * stride) {
+    const long long ch2 = ch + stride;
+    float a[4], b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    clip_load(src, n, ch, lane, a);
+    if (ch2 < nchunks) clip_load(src, n, ch2, lane, b);
+    clip_store(mbits, ch, lane, thr, a);
+    if (ch2 < nchunks) clip_store(mbits, ch2, lane, thr, b);
   }
 }
 

@@ -91,6 +91,26 @@ def test_noise_matches_oracle(ctx, name):
     assert sc.sc_noise_static(d, "gauss") == got
 
 
+@pytest.mark.parametrize("seed", range(16))
+def test_random_samples(ctx, seed):
+    """Random sizes, widths and shapes: Gaussian, Gaussian with bright
+    emission, Cauchy, values rounded to a coarse grid."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(10, 300_000))
+    v = rng.standard_normal(n) * rng.uniform(0.1, 10.0)
+    if seed % 4 == 1:
+        src = rng.random(n) < 0.05
+        v[src] = np.abs(v[src]) * 4.0 + 6.0 * v.std()
+    elif seed % 4 == 2:
+        v = rng.standard_cauchy(n)
+    elif seed % 4 == 3:
+        v = np.round(v, 1)
+    v = v.astype(np.float32)
+    got = ctx.noise(torch.from_numpy(v).cuda(), "gauss")
+    refs = gauss_refs(v.astype(np.float64))
+    assert close_to_any(got, refs), (got, refs)
+
+
 def test_noise_large(ctx):
     """2^25 values with an emission tail: the fit stays near the true sigma
     while the MAD noise is pulled up."""
