@@ -838,6 +838,8 @@ cudaError_t launch_resolve(const float* src, uint32_t* mbits, DevState* st, List
   return cudaGetLastError();
 }
 
+static int g_clip_blocks_per_sm = 0;  // resident k_clip_full blocks per SM (init_noise_attrs)
+
 // Lane l holds values l, l + 32, l + 64 and l + 96 of chunk ch (each load
 // instruction reads 128 contiguous bytes), so ballot c is mask word 4 ch + c
 // as it stands; 0 past n.
@@ -888,11 +890,15 @@ __global__ void __launch_bounds__(256) k_clip_full(const float* __restrict__ src
 
 cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, DevState* st, int sms,
                              cudaStream_t s) {
+  // one wave: as many blocks as are resident at once (a second, partial wave
+  // would run on a fraction of the SMs)
+  const long long cap = (long long)(g_clip_blocks_per_sm > 0 ? g_clip_blocks_per_sm : 4) * sms;
   long long want = (n + 1023) / 1024;
-  int grid = (int)(want < 1 ? 1 : (want > 8LL * sms ? 8LL * sms : want));
+  int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
   k_clip_full<<<grid, 256, 0, s>>>(src, n, mbits, st);
   return cudaGetLastError();
 }
+
 
 // ---------------------------------------------------------------------------
 // After sigma_0: replacement value, bin window, fixed-point scales.
@@ -1039,6 +1045,12 @@ void init_noise_attrs() {
   cudaFuncSetAttribute(k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)((kNumBins + 1) * sizeof(unsigned long long)));
   cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP2Smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_clip_full, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    b = 0;
+  }
+  if (b > 0) g_clip_blocks_per_sm = b;
 }
 
 }  // namespace sc
