@@ -34,7 +34,7 @@ UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
              "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag",
-             "wallaby-gauss", "medium-gauss")
+             "wallaby-gauss", "medium-gauss", "wallaby-noisescale-gauss", "wallaby-autoflag-gauss")
 FLAG_METRIC = "auto-flagger voxels/s on 1 GB300 (channel and pixel MAD noise, k = 4)"
 LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
@@ -734,6 +734,7 @@ def run_noise_scale_bench(args, rank, world, local):
         pg = dist
     sc.lib()
     window, grid = (31, 31, 31), (16, 16, 16)
+    mode = "gauss" if args.workload.endswith("-gauss") else "mad"
     if args.workload == "medium-noisescale":  # a 256^3 cube for profiling
         from synth.cubes import CubeSpec, make_cube
 
@@ -747,7 +748,7 @@ def run_noise_scale_bench(args, rank, world, local):
     ctx = Context(local, 1)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 3)):
-        ctx.noise_scale(cube, window, grid, "mad", out=out)
+        ctx.noise_scale(cube, window, grid, mode, out=out)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -758,7 +759,7 @@ def run_noise_scale_bench(args, rank, world, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        ctx.noise_scale(cube, window, grid, "mad", out=out)
+        ctx.noise_scale(cube, window, grid, mode, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
     if pg:
@@ -788,7 +789,7 @@ def run_noise_scale_bench(args, rank, world, local):
     n_e2e = max(1, min(args.steps, 3))
     for _ in range(n_e2e):
         cube.copy_(cube_h, non_blocking=True)
-        ctx.noise_scale(cube, window, grid, "mad", out=out)
+        ctx.noise_scale(cube, window, grid, mode, out=out)
         out_h.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -801,7 +802,7 @@ def run_noise_scale_bench(args, rank, world, local):
 
         sub = cube[:128, :1024, :1024].cpu().numpy()  # (the whole cube when it is smaller)
         t0 = time.perf_counter()
-        NS.noise_scale(sub, window, grid, "mad")
+        NS.noise_scale(sub, window, grid, mode)
         dt = time.perf_counter() - t0
         cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
                "sample": f"1024x1024x128 corner of the same cube, same windows and cells, numpy float64, one thread, "
@@ -811,7 +812,7 @@ def run_noise_scale_bench(args, rank, world, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"noise-scale-{spec.nx}x{spec.ny}x{spec.nz}", "window": list(window),
-                           "cells": list(grid), "noise": "mad",
+                           "cells": list(grid), "noise": mode,
                            "l2": "inputs larger than L2" if nvox * 4 > 129e6 else "no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
                 "clocks": sampler.summary(),
@@ -841,12 +842,13 @@ def run_autoflag_bench(args, rank, world, local):
         pg = dist
     sc.lib()
     spec, cube = make_workload("wallaby", rank, str(dev))
+    mode = "gauss" if args.workload.endswith("-gauss") else "mad"
     nvox = cube.numel()
     out = torch.empty_like(cube)
     ctx = Context(local, 1)
     stream = torch.cuda.current_stream(dev)
     for _ in range(max(args.warmup, 3)):
-        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, out=out)
+        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, noise_mode=mode, out=out)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -856,7 +858,7 @@ def run_autoflag_bench(args, rank, world, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, out=out)
+        _, fc, fp, _, _ = ctx.autoflag(cube, 4.0, noise_mode=mode, out=out)
     e1.record(stream)
     torch.cuda.synchronize()
     if pg:
@@ -880,7 +882,7 @@ def run_autoflag_bench(args, rank, world, local):
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         cube.copy_(cube_h, non_blocking=True)
-        ctx.autoflag(cube, 4.0, out=out)
+        ctx.autoflag(cube, 4.0, noise_mode=mode, out=out)
         out_h.copy_(out, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -891,18 +893,19 @@ def run_autoflag_bench(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle.flagger as FL
 
-        sub = cube[:, :256, :256].cpu().numpy()
+        side = 256 if mode == "mad" else 96  # about 10-30 s of oracle work either way
+        sub = cube[:, :side, :side].cpu().numpy()
         t0 = time.perf_counter()
-        FL.autoflag(sub, 4.0)
+        FL.autoflag(sub, 4.0, mode=mode)
         dt = time.perf_counter() - t0
         cpu = {"value": sub.size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
-               "sample": f"256x256x{sub.shape[0]} corner of the same cube, k = 4, numpy float64, one thread, "
+               "sample": f"{side}x{side}x{sub.shape[0]} corner of the same cube, k = 4, numpy float64, one thread, "
                          f"{dt:.1f} s"}
     if rank == 0:
         line = {"metric": FLAG_METRIC, "value": value, "unit": "voxels/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "autoflag-wallaby-1200x1200x1024", "k": 4.0, "noise": "mad",
+                "config": {"workload": "autoflag-wallaby-1200x1200x1024", "k": 4.0, "noise": mode,
                            "flagged_channels": int(fc.sum()), "flagged_pixels": int(fp.sum()),
                            "l2": "inputs (cube 5.9 GB) larger than L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(st["launches"]),
@@ -1035,11 +1038,11 @@ def main():
         return run_half_bench(args, rank, world, local)
     if args.workload == "stream512":
         return run_stream_bench(args, rank, world, local)
-    if args.workload.endswith("-noisescale"):
+    if args.workload.endswith(("-noisescale", "-noisescale-gauss")):
         return run_noise_scale_bench(args, rank, world, local)
     if args.workload == "wallaby-link":
         return run_link_bench(args, rank, world, local)
-    if args.workload == "wallaby-autoflag":
+    if args.workload in ("wallaby-autoflag", "wallaby-autoflag-gauss"):
         return run_autoflag_bench(args, rank, world, local)
 
     import torch

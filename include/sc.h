@@ -41,7 +41,7 @@ extern "C" {
 #define SC_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define SC_ERR_ALLNAN (-4)      /* the cube has no finite voxel: no noise level exists */
 #define SC_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
-#define SC_ERR_UNSUPPORTED (-6) /* option not implemented (SC_NOISE_GAUSS in sc_noise_scale / sc_autoflag) */
+#define SC_ERR_UNSUPPORTED (-6) /* option outside what the kernels serve (window, spectrum or boxcar too large) */
 #define SC_ERR_BUDGET (-7)      /* request exceeds the context's sizes / memory budget */
 #define SC_ERR_INTERNAL (-8)    /* a device-side consistency check failed */
 
@@ -314,7 +314,7 @@ int sc_noise(sc_ctx *ctx, const float *data_dev, int64_t n, int noise_mode, doub
  * min(wx, nx) * min(wy, ny) * min(wz, nz) <= 47104. The library keeps a
  * per-cell buffer of 12 bytes per cell in the context (grown on demand).
  * Errors: SC_ERR_ARG (NULL pointer, dims, even or non-positive window, grid
- * < 1, unknown mode), SC_ERR_UNSUPPORTED (SC_NOISE_GAUSS, window too large),
+ * < 1, unknown mode), SC_ERR_UNSUPPORTED (window too large),
  * SC_ERR_NOMEM, SC_ERR_CUDA. Asynchronous unless sigma_host is given. */
 int sc_noise_scale(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const int32_t *window,
                    const int32_t *grid, int noise_mode, float *out_dev, double *sigma_host, uint32_t flags,
@@ -367,7 +367,7 @@ int sc_link(sc_ctx *ctx, const uint8_t *mask_dev, const int64_t *dims, int r_xy,
  * Pixels mode needs nz <= 1536 (a tile of spectra in shared memory). The
  * library keeps 5 bytes per channel and per pixel in the context. Synchronises
  * when any host output is given. Errors: SC_ERR_ARG (NULL pointer, dims,
- * k < 0, what), SC_ERR_UNSUPPORTED (SC_NOISE_GAUSS, pixels with nz > 1536),
+ * k < 0, what, unknown mode), SC_ERR_UNSUPPORTED (pixels with nz > 1536),
  * SC_ERR_NOMEM, SC_ERR_CUDA. */
 #define SC_AUTOFLAG_CHANNELS 0x1u
 #define SC_AUTOFLAG_PIXELS 0x2u

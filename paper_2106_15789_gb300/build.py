@@ -30,8 +30,10 @@ def nvcc() -> str:
 
 
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-I", CSRC, *extra]
+    # every compiler warning is an error (a value-less return in a bool
+    # function, for one, is undefined behaviour the optimiser may exploit)
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Werror", "all-warnings", "-Xcompiler", "-fPIC", "-I",
+                   os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
 
 def _compile(src: str, verbose: bool, extra) -> str:

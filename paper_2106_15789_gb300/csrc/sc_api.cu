@@ -1089,8 +1089,7 @@ int sc_noise_scale(sc_ctx* c, const float* cube_dev, const int64_t* dims, const 
                    int noise_mode, float* out_dev, double* sigma_host, uint32_t flags, void* cuda_stream) {
   (void)flags;
   if (!c || !cube_dev || !dims || !window || !grid || !out_dev) return SC_ERR_ARG;
-  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
-  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   long long d[3];
   int w[3], g[3];
   long long cells = 1, wvox = 1;
@@ -1125,7 +1124,7 @@ int sc_noise_scale(sc_ctx* c, const float* cube_dev, const int64_t* dims, const 
   }
   {
     Phase ph(c, s, EV_NOISE_WINDOW);
-    CK(launch_noise_window(cube_dev, d, w, g, noise_mode == SC_NOISE_STD ? 1 : 0, c->ns_sig, c->ns_rinv, c->sms, s));
+    CK(launch_noise_window(cube_dev, d, w, g, noise_mode, c->ns_sig, c->ns_rinv, c->sms, s));
   }
   {
     Phase ph(c, s, EV_NOISE_APPLY);
@@ -1221,8 +1220,7 @@ int sc_autoflag(sc_ctx* c, const float* cube_dev, const int64_t* dims, double k,
   if (!c || !cube_dev || !dims || !out_dev || !(k >= 0.0) || what == 0u ||
       (what & ~(SC_AUTOFLAG_CHANNELS | SC_AUTOFLAG_PIXELS)))
     return SC_ERR_ARG;
-  if (noise_mode == SC_NOISE_GAUSS) return SC_ERR_UNSUPPORTED;
-  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD) return SC_ERR_ARG;
+  if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   long long d[3];
   for (int i = 0; i < 3; ++i) {
     d[i] = dims[i];
@@ -1251,7 +1249,7 @@ int sc_autoflag(sc_ctx* c, const float* cube_dev, const int64_t* dims, double k,
   float* pn = cn + d[2];
   uint8_t* cf = reinterpret_cast<uint8_t*>(pn + plane);
   uint8_t* pf = cf + d[2];
-  CK(launch_autoflag(cube_dev, d, k, ch ? 1 : 0, px ? 1 : 0, noise_mode == SC_NOISE_STD ? 1 : 0, out_dev, cn, pn, cf,
+  CK(launch_autoflag(cube_dev, d, k, ch ? 1 : 0, px ? 1 : 0, noise_mode, out_dev, cn, pn, cf,
                      pf, stats, c->sms, s));
   c->stats.launches += (ch ? 3 : 0) + (px ? 3 : 0) + 1;
   const bool want_counts = n_flagged != nullptr;

@@ -138,15 +138,6 @@ __device__ __forceinline__ bool mask_bit(const uint32_t* mbits, long long v) {
   return mbits != nullptr && ((__ldg(mbits + (v >> 5)) >> (v & 31)) & 1u);
 }
 
-// Spread the 8 bits of b to bit positions 0, 4, 8, ..., 28.
-__device__ __forceinline__ unsigned int spread4(unsigned int b) {
-  b &= 0xffu;
-  b = (b | (b << 12)) & 0x000f000fu;
-  b = (b | (b << 6)) & 0x03030303u;
-  b = (b | (b << 3)) & 0x11111111u;
-  return b;
-}
-
 __device__ __forceinline__ float warp_sum_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

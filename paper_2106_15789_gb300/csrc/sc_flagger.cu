@@ -17,6 +17,7 @@
 #include <cstdint>
 
 #include "sc_device.cuh"
+#include "sc_gaussfit.cuh"
 #include "sc_internal.h"
 
 namespace sc {
@@ -171,11 +172,12 @@ __device__ unsigned stream_select(const float* __restrict__ src, long long n, un
   return prefix;
 }
 
-// Noise of the finite values of src[0 .. n) (NaN if none) in the S+C sense;
-// for MAD mode also the median m (the stats kernel needs it). All threads
-// call it and get the same values.
-__device__ void block_noise(const float* __restrict__ src, long long n, int std_mode, Scratch* S, double* sigma,
+// Noise of the finite values of src[0 .. n) (NaN if none) in the S+C sense
+// (mode SC_NOISE_MAD, _STD or _GAUSS); for MAD mode also the median m (the
+// stats kernel needs it). All threads call it and get the same values.
+__device__ void block_noise(const float* __restrict__ src, long long n, int mode, Scratch* S, double* sigma,
                             double* median) {
+  const bool std_mode = mode == SC_NOISE_STD;
   const int tid = threadIdx.x, lane = tid & 31;
   // finite count
   unsigned c = 0u;
@@ -224,6 +226,37 @@ __device__ void block_noise(const float* __restrict__ src, long long n, int std_
   const double mad = even ? 0.5 * ((double)fkey_inv(a1) + (double)fkey_inv(a2)) : (double)fkey_inv(a1);
   *sigma = kMadToSigma * mad;
   *median = even ? 0.5 * ((double)ma + (double)mb) : (double)ma;
+  if (mode == SC_NOISE_GAUSS && *sigma > 0.0) {
+    // the 256-bin histogram of the finite values, then the fit (the MAD noise
+    // stands without a root)
+    const float k = gfit::scale_of(*sigma);
+    __syncthreads();  // the selection is done with S->hist
+    for (int i = tid; i < gfit::kBins; i += kThreads) S->hist[i] = 0u;
+    __syncthreads();
+    for (long long i = tid; i < n; i += kThreads) {
+      const int b = gfit::bin_of(__ldg(src + i), k);
+      if (b >= 0) atomicAdd(&S->hist[b], 1u);
+    }
+    __syncthreads();
+    // one warp fits (four folded bins a lane, no block barriers); the others wait
+    if (tid < 32) {
+      double hh[4], x2[4];
+      bool use[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int t = lane + 32 * j;
+        hh[j] = (double)S->hist[gfit::kHalf + t] + (double)S->hist[gfit::kHalf - 1 - t];
+        x2[j] = gfit::xi2_of(t);
+        use[j] = true;
+      }
+      const double tau = gfit::fit_tau(hh, x2, use, gfit::WarpSum6{});
+      if (lane == 0) S->dpart[0] = tau;
+    }
+    __syncthreads();
+    const double tau = S->dpart[0];
+    if (tau > 0.0) *sigma = gfit::noise_of(tau, k);
+    __syncthreads();
+  }
 }
 
 // ---- per-pixel noise: a warp per pixel, the spectrum in registers ----------
@@ -249,11 +282,11 @@ __device__ __forceinline__ unsigned warp_select(const unsigned (&k)[VPL], unsign
 }  // namespace flag
 
 __global__ void __launch_bounds__(flag::kThreads, 1)
-    k_chan_noise(const float* __restrict__ cube, long long plane, int nz, int std_mode, float* __restrict__ noise) {
+    k_chan_noise(const float* __restrict__ cube, long long plane, int nz, int mode, float* __restrict__ noise) {
   __shared__ flag::Scratch S;
   for (int z = blockIdx.x; z < nz; z += gridDim.x) {
     double sigma, m;
-    flag::block_noise(cube + (long long)z * plane, plane, std_mode, &S, &sigma, &m);
+    flag::block_noise(cube + (long long)z * plane, plane, mode, &S, &sigma, &m);
     if (threadIdx.x == 0) noise[z] = __double2float_rn(sigma);
     __syncthreads();
   }
@@ -265,7 +298,7 @@ __global__ void __launch_bounds__(flag::kThreads, 1) k_noise_stats(const float* 
                                                                    double* stats) {
   __shared__ flag::Scratch S;
   double sigma, m;
-  flag::block_noise(noise, n, 0, &S, &sigma, &m);
+  flag::block_noise(noise, n, SC_NOISE_MAD, &S, &sigma, &m);
   if (threadIdx.x == 0) {
     stats[0] = m;
     stats[1] = sigma;
@@ -274,9 +307,12 @@ __global__ void __launch_bounds__(flag::kThreads, 1) k_noise_stats(const float* 
 
 template <int VPL>
 __global__ void __launch_bounds__(flag::kPixThreads) k_pix_noise(const float* __restrict__ cube, int nx, int ny,
-                                                                 int nz, int std_mode, float* __restrict__ noise) {
+                                                                 int nz, int mode, float* __restrict__ noise) {
   using namespace flag;
   extern __shared__ float tile[];  // [nz][33]: 32 pixels of a row (one padding column)
+  // Gaussian-fit mode: then 256 counts per warp
+  unsigned* const whist = reinterpret_cast<unsigned*>(tile + 33 * nz) + (threadIdx.x >> 5) * gfit::kBins;
+  const bool std_mode = mode == SC_NOISE_STD;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long plane = (long long)nx * ny;
   const int xtiles = (nx + 31) / 32;
@@ -339,7 +375,33 @@ __global__ void __launch_bounds__(flag::kPixThreads) k_pix_noise(const float* __
         const unsigned a1 = warp_select<VPL>(k, r1);
         const unsigned a2 = even ? warp_select<VPL>(k, r1 + 1u) : a1;
         const double mad = 0.5 * ((double)fkey_inv(a1) + (double)fkey_inv(a2));
-        out = __double2float_rn(kMadToSigma * mad);
+        double sigma = kMadToSigma * mad;
+        if (mode == SC_NOISE_GAUSS && sigma > 0.0) {
+          // the spectrum's 256-bin histogram in this warp's counts, then a
+          // warp-wide fit over the 128 folded bins (4 a lane)
+          for (int i = lane; i < gfit::kBins; i += 32) whist[i] = 0u;
+          __syncwarp();
+          const float ks = gfit::scale_of(sigma);
+#pragma unroll
+          for (int i = 0; i < VPL; ++i) {
+            const int b = gfit::bin_of(v[i], ks);  // NaN (and padding) give -1
+            if (b >= 0) atomicAdd(whist + b, 1u);
+          }
+          __syncwarp();
+          double hh[4], x2[4];
+          bool use[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int t = lane + 32 * j;
+            hh[j] = (double)whist[gfit::kHalf + t] + (double)whist[gfit::kHalf - 1 - t];
+            x2[j] = gfit::xi2_of(t);
+            use[j] = true;
+          }
+          const double tau = gfit::fit_tau(hh, x2, use, gfit::WarpSum6{});
+          if (tau > 0.0) sigma = gfit::noise_of(tau, ks);
+          __syncwarp();  // the counts are reset by the next pixel
+        }
+        out = __double2float_rn(sigma);
       }
       if (lane == 0) noise[(long long)y * nx + x0 + p] = out;
     }
@@ -368,34 +430,35 @@ __global__ void k_blank(const float* in, float* out, int nx, int ny, int nz, con
 // ---------------------------------------------------------------------------
 namespace {
 template <int VPL>
-cudaError_t launch_pix(const float* cube, int nx, int ny, int nz, int std_mode, float* noise, int sms,
+cudaError_t launch_pix(const float* cube, int nx, int ny, int nz, int mode, float* noise, int sms,
                        cudaStream_t s) {
-  const size_t smem = sizeof(float) * 33 * (size_t)nz;
+  const size_t smem = sizeof(float) * 33 * (size_t)nz +
+                      (mode == SC_NOISE_GAUSS ? sizeof(unsigned) * gfit::kBins * flag::kPixWarps : 0);
   cudaFuncSetAttribute(k_pix_noise<VPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long long tiles = (long long)((nx + 31) / 32) * ny;
   const int grid = (int)(tiles < 4LL * sms ? tiles : 4LL * sms);
-  k_pix_noise<VPL><<<grid, flag::kPixThreads, smem, s>>>(cube, nx, ny, nz, std_mode, noise);
+  k_pix_noise<VPL><<<grid, flag::kPixThreads, smem, s>>>(cube, nx, ny, nz, mode, noise);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_autoflag(const float* cube, const long long dims[3], double k, int channels, int pixels,
-                            int std_mode, float* out, float* chan_noise, float* pix_noise, uint8_t* chan_flags,
+                            int mode, float* out, float* chan_noise, float* pix_noise, uint8_t* chan_flags,
                             uint8_t* pix_flags, double* stats, int sms, cudaStream_t s) {
   const int nx = (int)dims[0], ny = (int)dims[1], nz = (int)dims[2];
   const long long plane = (long long)nx * ny, n = plane * nz;
   cudaError_t e = cudaSuccess;
   if (channels) {
-    k_chan_noise<<<nz < 2 * sms ? nz : 2 * sms, flag::kThreads, 0, s>>>(cube, plane, nz, std_mode, chan_noise);
+    k_chan_noise<<<nz < 2 * sms ? nz : 2 * sms, flag::kThreads, 0, s>>>(cube, plane, nz, mode, chan_noise);
     k_noise_stats<<<1, flag::kThreads, 0, s>>>(chan_noise, nz, stats);
     k_flag<<<(nz + 255) / 256, 256, 0, s>>>(chan_noise, nz, stats, k, chan_flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (pixels) {
-    if (nz <= 256) e = launch_pix<8>(cube, nx, ny, nz, std_mode, pix_noise, sms, s);
-    else if (nz <= 512) e = launch_pix<16>(cube, nx, ny, nz, std_mode, pix_noise, sms, s);
-    else if (nz <= 1024) e = launch_pix<32>(cube, nx, ny, nz, std_mode, pix_noise, sms, s);
-    else e = launch_pix<48>(cube, nx, ny, nz, std_mode, pix_noise, sms, s);
+    if (nz <= 256) e = launch_pix<8>(cube, nx, ny, nz, mode, pix_noise, sms, s);
+    else if (nz <= 512) e = launch_pix<16>(cube, nx, ny, nz, mode, pix_noise, sms, s);
+    else if (nz <= 1024) e = launch_pix<32>(cube, nx, ny, nz, mode, pix_noise, sms, s);
+    else e = launch_pix<48>(cube, nx, ny, nz, mode, pix_noise, sms, s);
     if (e != cudaSuccess) return e;
     k_noise_stats<<<1, flag::kThreads, 0, s>>>(pix_noise, plane, stats + 2);
     const long long g = (plane + 255) / 256;

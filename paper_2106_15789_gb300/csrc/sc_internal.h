@@ -236,7 +236,7 @@ int ws_tile_rows(const SmoothArgs& a);
 // rinv_dev = float 1 / sigma or NaN, one per cell), then out = cube * rinv.
 constexpr long long kNoiseScaleMaxWindow = 47104;  // window voxels held in shared memory
 cudaError_t launch_noise_window(const float* cube, const long long dims[3], const int window[3], const int grid[3],
-                                int std_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s);
+                                int noise_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s);
 cudaError_t launch_noise_apply(const float* cube, const long long dims[3], const int window[3], const int grid[3],
                                float* out, const float* rinv_dev, int sms, cudaStream_t s);
 void init_noise_scale_attrs();
@@ -249,7 +249,7 @@ void init_noise_scale_attrs();
 // channels, [2..3] pixels), flags and the blanked cube.
 constexpr int kFlagMaxChannelsForPixels = 1536;  // spectra staged in shared memory
 cudaError_t launch_autoflag(const float* cube, const long long dims[3], double k, int channels, int pixels,
-                            int std_mode, float* out, float* chan_noise, float* pix_noise, uint8_t* chan_flags,
+                            int noise_mode, float* out, float* chan_noise, float* pix_noise, uint8_t* chan_flags,
                             uint8_t* pix_flags, double* stats, int sms, cudaStream_t s);
 
 constexpr int kLinkMaxRadius = 32;  // merging radii in voxels

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "sc_device.cuh"
+#include "sc_gaussfit.cuh"
 #include "sc_internal.h"
 
 namespace sc {
@@ -180,7 +181,7 @@ constexpr int kSampleStride = 8;  // every 8th voxel of the window is sampled fo
 // keys are replaced by key_of(k) if the full selection is needed (the caller
 // needs them no more).
 template <class KeyOf>
-__device__ void select_order(unsigned* keys, int n, unsigned nf, unsigned r, bool want_next, KeyOf key_of,
+__device__ bool select_order(unsigned* keys, int n, unsigned nf, unsigned r, bool want_next, KeyOf key_of,
                              bool rewrite, unsigned* cand, SelScratch* S, unsigned* k1, unsigned* k2) {
   const int tid = threadIdx.x, lane = tid & 31;
   unsigned nx = kNone;
@@ -196,7 +197,7 @@ __device__ void select_order(unsigned* keys, int n, unsigned nf, unsigned r, boo
     *k1 = select_keys(cand, (int)nf, r, S, want_next, &nx);
     *k2 = nx;
     __syncthreads();
-    return;
+    return false;  // the keys are as they were
   }
   // sample every kSampleStride-th voxel
   if (tid == 0) S->count = 0u;
@@ -277,6 +278,7 @@ __device__ void select_order(unsigned* keys, int n, unsigned nf, unsigned r, boo
     *k2 = nx;
   }
   __syncthreads();
+  return !done && rewrite;  // keys[] now holds key_of of the original keys
 }
 
 __device__ __forceinline__ double key_value(unsigned k) { return (double)fkey_inv(k); }
@@ -338,9 +340,10 @@ __device__ __forceinline__ double block_sum_d(double v, double* part) {
 }  // namespace nscale
 
 __global__ void __launch_bounds__(nscale::kThreads, 1)
-    k_noise_window(const float* __restrict__ cube, nscale::Geo g, int std_mode, double* __restrict__ sig_out,
+    k_noise_window(const float* __restrict__ cube, nscale::Geo g, int mode, double* __restrict__ sig_out,
                    float* __restrict__ rinv_out) {
   using namespace nscale;
+  const bool std_mode = mode == SC_NOISE_STD;
   extern __shared__ __align__(16) unsigned char ns_smem[];
   unsigned* const cand = reinterpret_cast<unsigned*>(ns_smem);  // [kCandCap]
   unsigned* const keys = cand + kCandCap;                          // [window voxels]
@@ -488,10 +491,51 @@ __global__ void __launch_bounds__(nscale::kThreads, 1)
       // float32 keys computed on the fly
       const float ma = fkey_inv(k1), mb = even ? fkey_inv(k2) : ma;
       unsigned a1 = 0u, a2 = 0u;
-      select_order(keys, n, nf, r1, even, [=](unsigned k) { return mad_key(fkey_inv(k), ma, mb, even); }, true, cand,
-                   &S, &a1, &a2);
+      const bool rewrote =
+          select_order(keys, n, nf, r1, even, [=](unsigned k) { return mad_key(fkey_inv(k), ma, mb, even); }, true,
+                       cand, &S, &a1, &a2);
       const double mad = even ? 0.5 * (key_value(a1) + key_value(a2)) : key_value(a1);
       sigma = kMadToSigma * mad;
+      if (mode == SC_NOISE_GAUSS && sigma > 0.0) {
+        // the window's 256-bin histogram (from the keys in shared memory, or
+        // read again from the cube where the selection rewrote them), then a
+        // one-warp fit; the MAD noise stands without a root
+        const float k = gfit::scale_of(sigma);
+        __syncthreads();  // the selection is done with S.hist
+        for (int i = tid; i < gfit::kBins; i += kThreads) S.hist[i] = 0u;
+        __syncthreads();
+        if (!rewrote) {
+          for (int e = tid; e < n; e += kThreads) {
+            const unsigned key = keys[e];
+            const int b = key != kNone ? gfit::bin_of(fkey_inv(key), k) : -1;
+            if (b >= 0) atomicAdd(&S.hist[b], 1u);
+          }
+        } else {
+          for (int dz = 0; dz < lz; ++dz)
+            for (int dy = warp; dy < ly; dy += kWarps)
+              for (int dx = lane; dx < lx; dx += 32) {
+                const int b = gfit::bin_of(__ldg(cube + (z0 + dz) * plane + (y0 + dy) * g.nx + x0 + dx), k);
+                if (b >= 0) atomicAdd(&S.hist[b], 1u);
+              }
+        }
+        __syncthreads();
+        if (warp == 0) {
+          double hh[4], x2[4];
+          bool use[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int t = lane + 32 * j;
+            hh[j] = (double)S.hist[gfit::kHalf + t] + (double)S.hist[gfit::kHalf - 1 - t];
+            x2[j] = gfit::xi2_of(t);
+            use[j] = true;
+          }
+          const double tau = gfit::fit_tau(hh, x2, use, gfit::WarpSum6{});
+          if (lane == 0) dpart[0] = tau;
+        }
+        __syncthreads();
+        const double tau = dpart[0];
+        if (tau > 0.0) sigma = gfit::noise_of(tau, k);
+      }
     }
     if (tid == 0) {
       sig_out[cell] = sigma;
@@ -565,12 +609,12 @@ nscale::Geo make_geo(const long long dims[3], const int window[3], const int gri
 }  // namespace
 
 cudaError_t launch_noise_window(const float* cube, const long long dims[3], const int window[3], const int grid[3],
-                                int std_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s) {
+                                int noise_mode, double* sig_dev, float* rinv_dev, int sms, cudaStream_t s) {
   const nscale::Geo g = make_geo(dims, window, grid);
   const long long cells = (long long)g.ncx * g.ncy * g.ncz;
   const long long wvox = (long long)min((long long)g.wx, g.nx) * min((long long)g.wy, g.ny) * min((long long)g.wz, g.nz);
   const int blocks = (int)(cells < sms ? cells : sms);
-  k_noise_window<<<blocks, nscale::kThreads, noise_window_smem(wvox), s>>>(cube, g, std_mode, sig_dev, rinv_dev);
+  k_noise_window<<<blocks, nscale::kThreads, noise_window_smem(wvox), s>>>(cube, g, noise_mode, sig_dev, rinv_dev);
   return cudaGetLastError();
 }
 

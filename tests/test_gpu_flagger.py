@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import oracle.flagger as FL
+from gauss_common import close_to_any, gauss_refs
 from synth.cubes import SMALL, CubeSpec, make_cube
 
 pytestmark = pytest.mark.gpu
@@ -89,6 +90,37 @@ def test_rfi_cubes(ctx, mode, shape):
         assert fc.sum() >= 3 and fp.sum() >= 1
 
 
+@pytest.mark.parametrize("shape", [(64, 40, 48), (300, 20, 21), (1030, 5, 6)])
+def test_gauss_mode(ctx, shape):
+    """Gaussian-fit channel and pixel noises against the oracle at the MAD
+    noises that rounding allows (tests/gauss_common.py); flags equal to the
+    oracle's except within 1e-4 of k R (a noise may move by ~1e-6 with the MAD
+    noise's rounding); the blanking follows the library's flags exactly."""
+    c = rfi_cube(shape, sum(shape) + 1)
+    cube = torch.from_numpy(c).cuda()
+    out, fc, fp, cn, pn = ctx.autoflag(cube, 4.0, True, True, "gauss")
+    _, rc, rp = FL.autoflag(c, 4.0, True, True, "gauss")
+    nz, ny, nx = shape
+    for z in range(nz):
+        refs = gauss_refs(c[z].ravel())
+        assert close_to_any(float(cn[z]), refs, 2.0 ** -22), (z, cn[z], refs)
+    for y in range(ny):
+        for x in range(nx):
+            refs = gauss_refs(c[:, y, x])
+            assert close_to_any(float(pn[y, x]), refs, 2.0 ** -22), ((y, x), pn[y, x], refs)
+    for got, ref, noise in ((fc, rc, FL.channel_noise(c, "gauss")), (fp, rp, FL.pixel_noise(c, "gauss"))):
+        _, m, r = FL.flags(noise, 4.0)
+        v = np.asarray(noise, dtype=np.float64).ravel()
+        for i in np.flatnonzero(got.ravel() != ref.ravel()):
+            assert abs(abs(v[i] - m) - 4.0 * r) <= 1e-4 * 4.0 * r, (i, v[i], m, r)
+    assert fc.sum() >= 3
+    o = out.cpu().numpy()
+    exp = c.copy()
+    exp[fc] = np.nan
+    exp[:, fp] = np.nan
+    assert np.array_equal(np.isnan(o), np.isnan(exp))
+
+
 def test_small_cube_each_kind_and_in_place(ctx):
     c = make_cube(SMALL).numpy()
     check(ctx, c, 3.0, channels=True, pixels=False)
@@ -114,8 +146,8 @@ def test_arguments(ctx):
         ctx.autoflag(c, -1.0)
     assert e.value.code == sc.SC_ERR_ARG
     with pytest.raises(sc.ScError) as e:
-        ctx.autoflag(c, 3.0, noise_mode="gauss")
-    assert e.value.code == sc.SC_ERR_UNSUPPORTED
+        ctx.autoflag(c, 3.0, noise_mode=7)
+    assert e.value.code == sc.SC_ERR_ARG
     big = torch.zeros((1600, 2, 2), device="cuda")
     with pytest.raises(sc.ScError) as e:
         ctx.autoflag(big, 3.0, channels=False, pixels=True)

@@ -1,27 +1,20 @@
 """Parity of the Gaussian-fit noise mode (SC_NOISE_GAUSS) with the FP64 oracle,
-through the C ABI: sc_noise, sc_noise_static and the S+C runs.
-
-Tolerance. The kernel's MAD noise sigma_M comes from float32 keys of
-|s - median| (exact order statistics, rounded once), the oracle's from exact
-float64 ones: the two differ by at most 2^-23 relative. The histogram's scale
-k = fl32(128 / (5 sigma_M)) can then differ by an ulp, and values within that
-ulp of a bin edge fall into the neighbouring bin. So a kernel result is
-accepted when it is within SIG_RTOL of the oracle's Gaussian-fit noise taken
-with sigma_M scaled by (1 + j 2^-24), j = -2..2 (the oracle evaluated at the
-sigma_M values that rounding allows; no kernel value enters it).
+through the C ABI: sc_noise, sc_noise_static and the S+C runs. The tolerance
+(the oracle at the MAD noises that float rounding allows) is explained in
+tests/gauss_common.py.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle.sc_oracle as O
+from gauss_common import SIG_RTOL, close_to_any, gauss_refs
 from synth.cubes import KERNELS_12, SMALL, CubeSpec, make_cube
 
 pytestmark = pytest.mark.gpu
 
 T = 3.5
 N_REPL = 2.0
-SIG_RTOL = 1e-6
 BAND = 1e-4
 
 
@@ -32,24 +25,6 @@ def ctx():
     c = Context(0, 1 << 25)
     yield c
     c.close()
-
-
-def gauss_refs(v: np.ndarray) -> list[float]:
-    """The oracle's Gaussian-fit noise of the finite float32 values v, at the
-    exact sigma_M and at sigma_M moved by up to two float32 ulps."""
-    s_mad = O.noise(v, "mad")
-    if not s_mad > 0.0:
-        return [0.0]
-    out = []
-    for j in (-2, -1, 0, 1, 2):
-        sm = s_mad * (1.0 + j * 2.0 ** -24)
-        tau = O.gauss_fit(O.gauss_histogram(v, sm))
-        out.append(sm if tau is None else tau * 128.0 / float(O.gauss_scale(sm)))
-    return out
-
-
-def close_to_any(got: float, refs: list[float]) -> bool:
-    return any((got == 0.0) if r == 0.0 else abs(got - r) <= SIG_RTOL * r for r in refs)
 
 
 def noise_cases():

@@ -14,6 +14,7 @@ import torch
 
 import oracle.noise_scale as NS
 import oracle.sc_oracle as O
+from gauss_common import close_to_any, gauss_refs
 from synth.cubes import SMALL, CubeSpec, make_cube
 
 pytestmark = pytest.mark.gpu
@@ -100,13 +101,61 @@ def test_degenerate(ctx):
     check(ctx, c, (5, 1, 5), (10, 20, 10), "mad")
 
 
+def check_gauss(ctx, c, window, grid):
+    """Gaussian-fit mode: every cell's noise against the oracle at the MAD
+    noises that rounding allows (tests/gauss_common.py), window by window;
+    the output is the cube times the float reciprocal of the library's own
+    cell noise."""
+    cube = torch.from_numpy(c).cuda()
+    got, sig = ctx.noise_scale(cube, window, grid, "gauss", want_sigma=True)
+    nz, ny, nx = c.shape
+    (wx, wy, wz), (gx, gy, gz) = window, grid
+    for k, (_, _, zc) in enumerate(NS.cells(nz, gz)):
+        for j, (_, _, yc) in enumerate(NS.cells(ny, gy)):
+            for i, (_, _, xc) in enumerate(NS.cells(nx, gx)):
+                v = c[NS.window_slice(zc, wz, nz), NS.window_slice(yc, wy, ny), NS.window_slice(xc, wx, nx)]
+                refs = gauss_refs(v.ravel())
+                assert close_to_any(sig[k, j, i], refs), ((k, j, i), sig[k, j, i], refs)
+    per = sig[np.arange(nz)[:, None, None] // gz, np.arange(ny)[None, :, None] // gy,
+              np.arange(nx)[None, None, :] // gx]
+    good = np.isfinite(per) & (per > 0) & np.isfinite(c)
+    g = got.cpu().numpy().astype(np.float64)
+    assert np.array_equal(np.isnan(g), ~good)
+    np.testing.assert_allclose(g[good], c[good].astype(np.float64) / per[good], rtol=OUT_RTOL, atol=0)
+    return sig
+
+
+def test_gauss_small_cube_window31(ctx):
+    check_gauss(ctx, make_cube(SMALL).numpy(), (31, 31, 31), (16, 16, 16))
+
+
+@pytest.mark.parametrize("shape,window,grid", [((33, 45, 67), (7, 5, 9), (4, 3, 5)),
+                                               ((40, 20, 20), (3, 41, 61), (7, 40, 25))])
+def test_gauss_ragged(ctx, shape, window, grid):
+    rng = np.random.default_rng(sum(shape) + 5)
+    c = (rng.standard_normal(shape) * (1.0 + np.arange(shape[0])[:, None, None] / 10.0)).astype(np.float32)
+    c[rng.random(shape) < 0.05] = np.nan
+    check_gauss(ctx, c, window, grid)
+
+
+def test_gauss_emission_and_offset(ctx):
+    """Bright positive emission in one corner of the windows, and a cell far
+    from 0 (the fit falls back to the MAD noise there)."""
+    rng = np.random.default_rng(17)
+    c = rng.standard_normal((24, 32, 32)).astype(np.float32)
+    src = rng.random(c.shape) < 0.04
+    c[src] = np.abs(c[src]) * 5.0 + 5.0
+    c[:8, :16, :16] += 400.0
+    check_gauss(ctx, c, (15, 15, 9), (16, 16, 8))
+
+
 def test_arguments(ctx):
     from paper_2106_15789_gb300 import sc
 
     c = torch.zeros((8, 8, 8), device="cuda")
     for window, grid, mode, code in (((4, 3, 3), (2, 2, 2), "mad", sc.SC_ERR_ARG),
                                      ((3, 3, 3), (0, 2, 2), "mad", sc.SC_ERR_ARG),
-                                     ((3, 3, 3), (2, 2, 2), "gauss", sc.SC_ERR_UNSUPPORTED)):
+                                     ((3, 3, 3), (2, 2, 2), 7, sc.SC_ERR_ARG)):
         with pytest.raises(sc.ScError) as e:
             ctx.noise_scale(c, window, grid, mode)
         assert e.value.code == code
