@@ -85,3 +85,33 @@ def test_create_without_gpu_fails_cleanly(lib):
     h = ctypes.c_void_p()
     assert lib.sc_create(ctypes.byref(h), 0, 1000) == sc.SC_ERR_CUDA
     assert not h.value
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of sc_stats and sc_kernel have the C header's size and
+    field offsets (a C program built against include/sc.h prints them)."""
+    import shutil
+    import subprocess
+
+    from paper_2106_15789_gb300 import sc
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sc_stats": sc.sc_stats, "sc_kernel": sc.sc_kernel}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sc.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
