@@ -166,8 +166,11 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  *                pair's sigma is 0; that pair then adds nothing).
  *   sigma0_host  NULL or double[1]: noise of the raw cube.
  * Returns after the stream has finished when sigma_host or sigma0_host is
- * given (needed to copy them); otherwise returns once all work is enqueued
- * and device-side errors surface at the next synchronising call.
+ * given (needed to copy them), with the run's device-side status
+ * (SC_ERR_ALLNAN, SC_ERR_TIMEOUT, SC_ERR_INTERNAL). Otherwise it returns once
+ * all work is enqueued: launch errors are still returned, but that device-side
+ * status is not read (the next run clears it), so a caller that needs it
+ * passes sigma0_host.
  * Errors: SC_ERR_ARG (dims <= 0, more voxels than max_voxels -> SC_ERR_BUDGET,
  * even boxcar, negative or non-finite FWHM, t <= 0 or not finite, n_kernels
  * outside 1..SC_MAX_KERNELS, NULL pointers, unknown noise mode),
