@@ -179,6 +179,19 @@ int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_ker
            float threshold, int noise_mode, float replacement, uint8_t *mask_dev, double *sigma_host,
            double *sigma0_host, uint32_t flags, void *cuda_stream);
 
+/* Stream-ordered copy of the sigmas of the latest sc_run on this context:
+ * sigma_k of its first n_kernels pairs into sigma_dst[n_kernels] and sigma_0
+ * into sigma0_dst[1], as float32 (the precision the device keeps them in;
+ * sc_run's sigma_host holds the same values widened to double). The copies
+ * are enqueued on cuda_stream behind the work already there and nothing
+ * synchronises, so a pipeline of sc_run calls made without sigma pointers
+ * can collect every run's sigmas without stopping. Each destination may be
+ * NULL, device memory or pinned host memory; it holds the values once the
+ * stream has reached the copy. A run whose device-side status was an error
+ * leaves zeros. Errors: SC_ERR_ARG (NULL ctx, n_kernels outside
+ * 1..SC_MAX_KERNELS), SC_ERR_CUDA. */
+int sc_copy_sigmas(sc_ctx *ctx, float *sigma_dst, float *sigma0_dst, int n_kernels, void *cuda_stream);
+
 /* S+C over many independent cubes (the sub-regions SoFiA-X splits a survey
  * into, Sect. 3): each cube gets its own sigma_0 and sigma_k, all with the
  * same kernel list and parameters as sc_run.

@@ -1063,6 +1063,18 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   return SC_OK;
 }
 
+int sc_copy_sigmas(sc_ctx* c, float* sigma_dst, float* sigma0_dst, int n_kernels, void* cuda_stream) {
+  if (!c || n_kernels < 1 || n_kernels > SC_MAX_KERNELS) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const unsigned char* st = reinterpret_cast<const unsigned char*>(c->st);
+  if (sigma_dst)
+    CK(cudaMemcpyAsync(sigma_dst, st + offsetof(DevState, sigma), sizeof(float) * n_kernels, cudaMemcpyDefault, s));
+  if (sigma0_dst)
+    CK(cudaMemcpyAsync(sigma0_dst, st + offsetof(DevState, sigma0), sizeof(float), cudaMemcpyDefault, s));
+  return SC_OK;
+}
+
 int sc_noise(sc_ctx* c, const float* data_dev, int64_t n, int noise_mode, double* sigma_host, uint32_t flags,
              void* cuda_stream) {
   if (!c || !data_dev || !sigma_host || n <= 0) return SC_ERR_ARG;

@@ -110,6 +110,7 @@ _SIGS = {
                               C.c_int, C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_copy_sigmas": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
                                  _P, C.POINTER(C.c_double), C.c_uint32, _P]),
@@ -358,6 +359,25 @@ def sc_smooth(ctx, cube: torch.Tensor, kernel, mask: torch.Tensor | None = None,
     return out
 
 
+def sc_copy_sigmas(ctx, sigma: torch.Tensor | None, sigma0: torch.Tensor | None, n_kernels: int, stream=None) -> None:
+    """Enqueue copies of the latest run's float32 sigmas into sigma
+    [n_kernels] and sigma0 [1] (CUDA or pinned host float32 tensors, or None);
+    nothing synchronises."""
+    ref = None
+    for t, n, name in ((sigma, n_kernels, "sigma"), (sigma0, 1, "sigma0")):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() < n \
+                or not (t.is_cuda or t.is_pinned()):
+            raise ValueError(f"{name} must be a contiguous CUDA or pinned float32 tensor of at least {n} values")
+        ref = t if t.is_cuda else ref
+    if stream is None:
+        stream = torch.cuda.current_stream(ref.device if ref is not None else None)
+    s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    _check(lib().sc_copy_sigmas(ctx, ptr(sigma), ptr(sigma0), int(n_kernels), s), "sc_copy_sigmas")
+
+
 def sc_noise(ctx, data: torch.Tensor, noise_mode="mad", flags: int = 0, stream=None) -> float:
     """Noise level of the finite values of a CUDA float32 tensor."""
     _dev(data, torch.float32, "data")
@@ -547,6 +567,9 @@ class Context:
     def link(self, mask, r_xy=2, r_z=2, min_xy=1, min_z=1, max_xy=0, max_z=0, labels=None, extents_cap=None,
              stream=None):
         return sc_link(self.handle, mask, r_xy, r_z, min_xy, min_z, max_xy, max_z, labels, extents_cap, stream)
+
+    def copy_sigmas(self, sigma, sigma0, n_kernels, stream=None):
+        sc_copy_sigmas(self.handle, sigma, sigma0, n_kernels, stream)
 
     def set_profiling(self, on=True):
         sc_set_profiling(self.handle, on)
