@@ -115,6 +115,8 @@ def _mut_mean_centre(orig):
     def f(noise, k):
         v = np.asarray(noise, dtype=np.float64)
         ok = np.isfinite(v)
+        if not ok.any():
+            return orig(noise, k)
         m = float(v[ok].mean())
         r = 1.4826 * float(np.median(np.abs(v[ok] - m)))
         out = np.zeros(v.shape, dtype=bool)
