@@ -23,6 +23,7 @@
 // When a candidate set would exceed its buffer, the plan switches that part
 // to full passes over S (k_sel_* on the whole array, k_clip_full); results are
 // identical, only slower.
+#include <atomic>
 #include <cfloat>
 #include <cstdio>
 
@@ -838,7 +839,9 @@ cudaError_t launch_resolve(const float* src, uint32_t* mbits, DevState* st, List
   return cudaGetLastError();
 }
 
-static int g_clip_blocks_per_sm = 0;  // resident k_clip_full blocks per SM (init_noise_attrs)
+// resident k_clip_full blocks per SM (init_noise_attrs, which every context
+// creation runs, possibly from several host threads at once)
+static std::atomic<int> g_clip_blocks_per_sm{0};
 
 // Lane l holds values l, l + 32, l + 64 and l + 96 of chunk ch (each load
 // instruction reads 128 contiguous bytes), so ballot c is mask word 4 ch + c
@@ -892,7 +895,8 @@ cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, Dev
                              cudaStream_t s) {
   // one wave: as many blocks as are resident at once (a second, partial wave
   // would run on a fraction of the SMs)
-  const long long cap = (long long)(g_clip_blocks_per_sm > 0 ? g_clip_blocks_per_sm : 4) * sms;
+  const int per_sm = g_clip_blocks_per_sm.load(std::memory_order_relaxed);
+  const long long cap = (long long)(per_sm > 0 ? per_sm : 4) * sms;
   long long want = (n + 1023) / 1024;
   int grid = (int)(want < 1 ? 1 : (want > cap ? cap : want));
   k_clip_full<<<grid, 256, 0, s>>>(src, n, mbits, st);
@@ -1050,7 +1054,7 @@ void init_noise_attrs() {
     cudaGetLastError();
     b = 0;
   }
-  if (b > 0) g_clip_blocks_per_sm = b;
+  if (b > 0) g_clip_blocks_per_sm.store(b, std::memory_order_relaxed);
 }
 
 }  // namespace sc
