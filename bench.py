@@ -110,6 +110,9 @@ def ncu_kernel_key(name):
     m = re.search(r"k_smooth_tile<(\d+), (\d+), (\d+),", name)
     if m:
         return "k_smooth_tile<%s,%s,%s>" % m.group(1, 2, 3)
+    m = re.search(r"k_smooth_p<(\d+), (\d+)>", name)
+    if m:
+        return "k_smooth_p<R=%s>" % m.group(2) + ("/16" if m.group(1) == "16" else "")
     for k in ("k_smooth_z", "k_smooth_generic", "k_identity"):
         if k + "<" in name or k + "(" in name:
             return k
@@ -163,7 +166,8 @@ def smoothing_kernel_name(sc, pair, code):
     w = tuple(sc.sc_cascade_widths(fwhm)) if fwhm > 0 else (1, 1, 1)
     names = {sc.SC_KERNEL_NONE: "none", sc.SC_KERNEL_IDENTITY: "k_identity", sc.SC_KERNEL_Z: "k_smooth_z",
              sc.SC_KERNEL_WS32: "k_smooth_ws<%d,%d,%d>" % w, sc.SC_KERNEL_WS16: "k_smooth_ws<%d,%d,%d>/16" % w,
-             sc.SC_KERNEL_TILE: "k_smooth_tile<%d,%d,%d>" % w, sc.SC_KERNEL_GENERIC: "k_smooth_generic"}
+             sc.SC_KERNEL_TILE: "k_smooth_tile<%d,%d,%d>" % w, sc.SC_KERNEL_GENERIC: "k_smooth_generic",
+             sc.SC_KERNEL_SHARED: "k_smooth_p<%d,%d,%d>" % w}
     return names.get(code, "unknown")
 
 

@@ -66,6 +66,7 @@ extern "C" {
 #define SC_FLAG_GENERIC 0x2u    /* use the generic (any-width) smoothing kernels even where a specialised one exists */
 #define SC_FLAG_NO_FAST_SELECT 0x4u /* skip the one-pass candidate selection; select by full passes (slow, for tests) */
 #define SC_FLAG_GRAPH 0x8u          /* sc_run_batch: capture the batch once into a CUDA graph and replay it */
+#define SC_FLAG_NO_SHARE 0x10u      /* smooth every pair in full (no shared spatial passes; same results, slower) */
 
 /* ---- warning bits (sc_stats.warnings, set per run) -------------------- */
 #define SC_WARN_ZERO_SIGMA 0x1u     /* some pair had sigma == 0 and added nothing to the mask */
@@ -106,6 +107,7 @@ typedef struct {
 #define SC_KERNEL_WS16 4     /* the same with 64 x 16 tiles */
 #define SC_KERNEL_TILE 5     /* one tile per block, spatial cascade + boxcar */
 #define SC_KERNEL_GENERIC 6  /* any kernel pair */
+#define SC_KERNEL_SHARED 7   /* spectral pass over the spatial sums of an earlier pair with the same spatial kernel */
 
 /* Counters and timings of the context (cumulative unless reset). */
 typedef struct {
@@ -171,6 +173,16 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  * all work is enqueued: launch errors are still returned, but that device-side
  * status is not read (the next run clears it), so a caller that needs it
  * passes sigma0_host.
+ * Shared spatial passes: when consecutive pairs have the same spatial kernel
+ * (FWHM 3, 5, 6 or 10 px, boxcars up to 31 channels), the first of them also
+ * stores its spatial sums (int64 per voxel) and each later one adds only the
+ * corrections for voxels masked since then (Sect. 6.2 replacement is the only
+ * difference between their inputs, and the smoothing is linear and exact).
+ * The results are bit for bit those of smoothing every pair in full
+ * (SC_FLAG_NO_SHARE). The context allocates for this, on first use, 8 bytes
+ * per voxel of the cube plus a correction list of max(2^20, max_voxels/16)
+ * entries of 8 bytes and a copy of the working mask; a failed allocation
+ * only switches the sharing off.
  * Errors: SC_ERR_ARG (dims <= 0, more voxels than max_voxels -> SC_ERR_BUDGET,
  * even boxcar, negative or non-finite FWHM, t <= 0 or not finite, n_kernels
  * outside 1..SC_MAX_KERNELS, NULL pointers, unknown noise mode),
@@ -191,6 +203,25 @@ int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_ker
  * leaves zeros. Errors: SC_ERR_ARG (NULL ctx, n_kernels outside
  * 1..SC_MAX_KERNELS), SC_ERR_CUDA. */
 int sc_copy_sigmas(sc_ctx *ctx, float *sigma_dst, float *sigma0_dst, int n_kernels, void *cuda_stream);
+
+/* Copy of the smoothed cube S of the last kernel pair of the context's latest
+ * sc_run / sc_run_host / sc_run_half (float32 [nz][ny][nx] of that cube, NaN
+ * at non-finite input voxels) into dst (device or pinned host memory), the
+ * first n values, stream-ordered after that run on cuda_stream. When the run's
+ * only pair is (0, 0) its S is the cube itself and the buffer holds no value
+ * of that run. Library addition (the paper's S+C keeps this second cube copy
+ * internally, Sect. 5); used to check smoothed values. Errors: SC_ERR_ARG
+ * (NULL, n < 0), SC_ERR_BUDGET (n > max_voxels), SC_ERR_CUDA. */
+int sc_copy_smoothed(sc_ctx *ctx, float *dst, int64_t n, void *cuda_stream);
+
+/* Cap on the correction list of the shared spatial passes (see sc_run), in
+ * entries; 0 restores the default (the list's full capacity). A pair whose
+ * corrections exceed the cap is smoothed in full instead, with the same
+ * results: the decision is taken on the device, so no synchronisation is
+ * needed. Library addition with no counterpart in the paper; it lets tests
+ * reach the fallback and lets callers trade speed for a smaller list.
+ * Errors: SC_ERR_ARG (NULL ctx). */
+int sc_set_share_limit(sc_ctx *ctx, uint64_t max_entries);
 
 /* S+C over many independent cubes (the sub-regions SoFiA-X splits a survey
  * into, Sect. 3): each cube gets its own sigma_0 and sigma_k, all with the

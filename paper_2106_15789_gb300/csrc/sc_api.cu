@@ -101,6 +101,18 @@ struct sc_ctx {
   std::vector<unsigned char*> job_slots;
   cudaEvent_t clock_ev = nullptr;
   double clock_host = 0.0;
+  // shared spatial passes (allocated on first use, grown for larger cubes)
+  long long* sh_P = nullptr;          // P' of the first pair of a spatial kernel
+  size_t sh_P_cap = 0;                // elements
+  uint32_t* sh_snap = nullptr;        // working mask when P' was made (max_voxels bits + padding)
+  unsigned* sh_cnt = nullptr;         // per-bucket counts (kept zero between pairs)
+  unsigned* sh_offs = nullptr;        // their exclusive scan
+  unsigned long long* sh_bsum = nullptr;
+  size_t sh_bk_cap = 0;               // buckets + 1 the three arrays hold
+  unsigned long long* sh_ent = nullptr;  // correction entries
+  unsigned long long sh_ent_cap = 0;
+  unsigned long long sh_limit = 0;    // sc_set_share_limit (0: the buffer's capacity)
+  ShareState* sh_ss = nullptr;
 };
 
 namespace {
@@ -295,6 +307,69 @@ void apply_tuning(sc_ctx* c, const int64_t* dims, SmoothArgs* a) {
   a->tune_zfactor = it->second[1];
 }
 
+// Buffers of the shared spatial passes for a cube of these dimensions
+// (allocated or grown here; never inside a stream capture).
+int ensure_share(sc_ctx* c, const int64_t* dims) {
+  const long long nx = dims[0], ny = dims[1], nz = dims[2];
+  const long long pitch = (nx + 1) & ~1LL;  // an even pitch: 16-byte aligned rows for TMA
+  const size_t need_p = (size_t)pitch * ny * nz;
+  // buckets of the smaller tile height (16 rows) bound those of both heights
+  const size_t need_bk = (size_t)((nx + 63) / 64) * ((ny + 15) / 16) * nz + 1;
+  const bool fits = c->sh_P_cap >= need_p && c->sh_bk_cap >= need_bk && c->sh_ent && c->sh_snap && c->sh_ss;
+  if (fits) return SC_OK;
+  if (c->capturing) return SC_ERR_BUDGET;
+  if (!c->sh_snap) {
+    const size_t nwords = (c->max_voxels + 31) / 32 + 8;
+    const unsigned long long cap = std::max<unsigned long long>(1ull << 20, (unsigned long long)c->max_voxels / 16);
+    if (cudaMalloc(&c->sh_snap, sizeof(uint32_t) * nwords) != cudaSuccess ||
+        cudaMalloc(&c->sh_ent, sizeof(unsigned long long) * (cap + 2)) != cudaSuccess ||
+        cudaMalloc(&c->sh_ss, sizeof(ShareState)) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    c->sh_ent_cap = cap;
+    if (cudaMemset(c->sh_snap, 0, sizeof(uint32_t) * nwords) != cudaSuccess ||
+        cudaMemset(c->sh_ent, 0, sizeof(unsigned long long) * (cap + 2)) != cudaSuccess ||
+        cudaMemset(c->sh_ss, 0, sizeof(ShareState)) != cudaSuccess)
+      return SC_ERR_CUDA;
+  }
+  if (c->sh_P_cap < need_p) {
+    cudaStreamSynchronize(c->last);
+    cudaFree(c->sh_P);
+    c->sh_P = nullptr;
+    c->sh_P_cap = 0;
+    if (cudaMalloc(&c->sh_P, sizeof(long long) * need_p) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    c->sh_P_cap = need_p;
+  }
+  if (c->sh_bk_cap < need_bk) {
+    cudaStreamSynchronize(c->last);
+    cudaFree(c->sh_cnt);
+    cudaFree(c->sh_offs);
+    cudaFree(c->sh_bsum);
+    c->sh_cnt = nullptr;
+    c->sh_offs = nullptr;
+    c->sh_bsum = nullptr;
+    c->sh_bk_cap = 0;
+    const size_t nb = need_bk + 4096;
+    if (cudaMalloc(&c->sh_cnt, sizeof(unsigned) * nb) != cudaSuccess ||
+        cudaMalloc(&c->sh_offs, sizeof(unsigned) * nb) != cudaSuccess ||
+        cudaMalloc(&c->sh_bsum, sizeof(unsigned long long) * (nb / 4096 + 2)) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    if (cudaMemset(c->sh_cnt, 0, sizeof(unsigned) * nb) != cudaSuccess) return SC_ERR_CUDA;
+    c->sh_bk_cap = need_bk;
+  }
+  return SC_OK;
+}
+
+bool same_spatial(const PairDesc& a, const PairDesc& b) {
+  return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2];
+}
+
 SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims) {
   SmoothArgs a;
   memset(&a, 0, sizeof(a));
@@ -319,7 +394,10 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   const int std_mode = (noise_mode == SC_NOISE_STD);
   const unsigned int force = (flags & SC_FLAG_NO_FAST_SELECT) ? (PLAN_MED_FULL | PLAN_MAD_FULL | PLAN_CLIP_FULL) : 0u;
   PairWeights W{};
-  for (int k = 0; k < nk; ++k) W.w[k] = pds[k].W;
+  for (int k = 0; k < nk; ++k) {
+    W.w[k] = pds[k].W;
+    W.wf[k] = pds[k].Wf;
+  }
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   const long long nwords = (n + 31) / 32;
   if (flags & SC_FLAG_ACCUMULATE) {
@@ -351,6 +429,11 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   c->stats.launches += 1;
 
   if (first_identity) c->stats.smooth_kernel_pair[0] = SC_KERNEL_NONE;
+  // Shared spatial passes: the first of consecutive pairs with one spatial
+  // kernel stores its spatial sums, the later ones reuse them.
+  const bool share_on = !(flags & (SC_FLAG_NO_SHARE | SC_FLAG_GENERIC));
+  bool share_cnt_clear = false;
+  int p_owner = -1;  // pair whose spatial sums sh_P holds
   for (int k = first_identity ? 1 : 0; k < nk; ++k) {
     CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
     SmoothArgs a = base_args(c, cube, dims);
@@ -361,8 +444,62 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     a.win = 1;
     a.generic = (flags & SC_FLAG_GENERIC) ? 1 : 0;
     a.repl_possible = replacement > 0.0f ? 1 : 0;
-    {
+    int share_mode = 0;  // 0: plain, 1: store the spatial sums, 2: reuse them
+    if (share_on && share_supported(a.pd)) {
+      if (p_owner >= 0 && same_spatial(pds[p_owner], a.pd)) {
+        share_mode = 2;
+      } else if (k + 1 < nk && share_supported(pds[k + 1]) && same_spatial(a.pd, pds[k + 1]) &&
+                 ensure_share(c, dims) == SC_OK) {
+        share_mode = 1;
+      }
+    }
+    if (share_mode != 2) p_owner = -1;
+    if (share_mode == 2) {
       Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
+      ShareArgs sh{};
+      sh.P = c->sh_P;
+      sh.pitch = (dims[0] + 1) & ~1LL;
+      sh.msnap = c->sh_snap;
+      sh.cnt = c->sh_cnt;
+      sh.bsum = c->sh_bsum;
+      sh.ent = c->sh_ent;
+      sh.cap = c->sh_limit > 0 ? std::min(c->sh_limit, c->sh_ent_cap) : c->sh_ent_cap;
+      sh.ss = c->sh_ss;
+      sh.ty = share_tile_rows(a.pd.wz);
+      sh.tiles_x = (int)((dims[0] + 63) / 64);
+      sh.tiles_y = (int)((dims[1] + sh.ty - 1) / sh.ty);
+      sh.n_buckets = (long long)sh.tiles_x * sh.tiles_y * dims[2];
+      CK(cudaMemsetAsync(c->sh_ss, 0, sizeof(ShareState), s));
+      if (a.repl_possible) {
+        // voxels masked since the spatial sums were made, listed per bucket
+        if (!share_cnt_clear) {
+          CK(cudaMemsetAsync(c->sh_cnt, 0, sizeof(unsigned) * (size_t)(sh.n_buckets + 1), s));
+          share_cnt_clear = true;
+        }
+        sh.offs = c->sh_offs;
+        CK(launch_share_prep(a, sh, c->sms, s));
+        c->stats.launches += 4;
+      }
+      // the full kernel, run only if the list overflowed
+      SmoothArgs full = a;
+      full.gate = &c->sh_ss->overflow;
+      full.tune_kind = TUNE_AUTO;
+      int l = 0, code = SC_KERNEL_NONE;
+      CK(launch_smooth(full, c->sms, s, &l, &code));
+      c->stats.launches += l;
+      bool done = false;
+      CK(launch_smooth_p(a, sh, c->sms, s, &done));
+      if (!done) return SC_ERR_INTERNAL;
+      c->stats.launches += 1;
+      c->stats.smooth_kernel_pair[k] = SC_KERNEL_SHARED;
+    } else {
+      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
+      if (share_mode == 1) {
+        CK(cudaMemcpyAsync(c->sh_snap, c->mbits, sizeof(uint32_t) * nwords, cudaMemcpyDeviceToDevice, s));
+        a.pout = c->sh_P;
+        a.ppitch = (dims[0] + 1) & ~1LL;
+        a.tune_kind = TUNE_AUTO;
+      }
       if (a.pd.h == 0 && a.pd.wz == 1) {
         CK(launch_identity(a, c->sms, s));
         c->stats.launches += 1;
@@ -372,6 +509,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
         CK(launch_smooth(a, c->sms, s, &l, &code));
         c->stats.launches += l;
         c->stats.smooth_kernel_pair[k] = code;
+        if (share_mode == 1 && (code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16)) p_owner = k;
       }
     }
     rc = measure(c, c->S, n, 1, t, 1, noise_mode, k, force, s);
@@ -495,6 +633,13 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->lk_tot);
   cudaFree(c->lk_comp);
   cudaFree(c->af_buf);
+  cudaFree(c->sh_P);
+  cudaFree(c->sh_snap);
+  cudaFree(c->sh_cnt);
+  cudaFree(c->sh_offs);
+  cudaFree(c->sh_bsum);
+  cudaFree(c->sh_ent);
+  cudaFree(c->sh_ss);
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaFree(c->batch_res);
   if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
@@ -921,6 +1066,7 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
     // fixed-point scales of this pair on the synthetic cube, replacement value 1
     PairWeights W{};
     W.w[0] = pd.W;
+    W.wf[0] = pd.Wf;
     if (cudaMemsetAsync(c->st, 0, sizeof(DevState), s) != cudaSuccess ||
         launch_maxabs(c->stage_cube, n, c->st, c->sms, s) != cudaSuccess ||
         launch_fx_setup(c->st, 1.0f, W, 1, s) != cudaSuccess) {
@@ -1033,6 +1179,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   const float repl = replacement_value > 0.0f ? replacement_value : 0.0f;  // quantised exactly per pair
   PairWeights W{};
   W.w[0] = pd.W;
+  W.wf[0] = pd.Wf;
   CK(launch_maxabs(cube_dev, n, c->st, c->sms, s));
   CK(launch_fx_setup(c->st, repl, W, 1, s));
   c->stats.launches += 2;
@@ -1060,6 +1207,20 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
       c->stats.smooth_kernel_pair[0] = code;
     }
   }
+  return SC_OK;
+}
+
+int sc_copy_smoothed(sc_ctx* c, float* dst, int64_t n, void* cuda_stream) {
+  if (!c || !dst || n < 0) return SC_ERR_ARG;
+  if ((unsigned long long)n > c->max_voxels) return SC_ERR_BUDGET;
+  DeviceGuard g(c->device);
+  CK(cudaMemcpyAsync(dst, c->S, sizeof(float) * (size_t)n, cudaMemcpyDefault, (cudaStream_t)cuda_stream));
+  return SC_OK;
+}
+
+int sc_set_share_limit(sc_ctx* c, uint64_t max_entries) {
+  if (!c) return SC_ERR_ARG;
+  c->sh_limit = max_entries;
   return SC_OK;
 }
 

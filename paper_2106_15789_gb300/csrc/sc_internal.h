@@ -139,16 +139,22 @@ struct Lists {
 constexpr int kMaxHalf = 40;    // largest spatial half-width (sum of (w-1)/2)
 constexpr int kMaxBoxcar = 127; // largest spectral boxcar
 
+// Spectral widths up to this share one fixed-point scale per spatial kernel
+// (so that the pairs of one spatial kernel can share its spatial passes).
+constexpr int kShareMaxWz = 31;
+
 struct PairDesc {
   int w[3];       // spatial cascade widths (1 = identity)
   int h;          // spatial half-width
   int wz;         // spectral width (1 = identity)
   long long W;    // integer weight total (w0 w1 w2)^2 * wz
+  long long Wf;   // weight bound fixing the scale: (w0 w1 w2)^2 * max(wz, kShareMaxWz)
   int taps[2 * kMaxHalf + 1];  // composed integer kernel, 2h+1 taps, sum = w0 w1 w2
 };
 
 struct PairWeights {
-  long long w[SC_MAX_KERNELS];  // integer weight total of every pair (passed by value to kernels)
+  long long w[SC_MAX_KERNELS];   // integer weight total of every pair (passed by value to kernels)
+  long long wf[SC_MAX_KERNELS];  // the bound that fixes each pair's fixed-point scale
 };
 
 struct SmoothArgs {
@@ -169,7 +175,48 @@ struct SmoothArgs {
   int generic;               // force the generic FIR path
   int tune_kind;             // TUNE_* kernel choice (TUNE_AUTO: the dispatcher decides)
   int tune_zfactor;          // work items per SM targeted by the z chunking (0: 2)
+  // Shared spatial passes (warp-specialised kernel only): when pout is set,
+  // the kernel also stores P' = 32 * (spatial sum of X_q) + nonfinite(C) of
+  // every voxel, row pitch ppitch elements.
+  long long* pout;
+  long long ppitch;
+  const unsigned* gate;      // non-null: the kernel runs only if *gate != 0
 };
+
+// ---------------------------------------------------------------------------
+// Shared spatial passes (sc_smooth_p.cu). For the later pairs of a run of
+// pairs with one spatial kernel, S comes from the stored P' of the run's
+// first pair plus the corrections of voxels masked since then.
+struct ShareState {
+  unsigned long long total;  // correction entries of the current pair
+  unsigned overflow;         // 1: more entries than the list holds (the full kernel runs)
+  unsigned pad;
+};
+
+struct ShareArgs {
+  long long* P;              // P' of the run's first pair, [nz][ny][pitch]
+  long long pitch;
+  const uint32_t* msnap;     // working mask when P' was made
+  unsigned* cnt;             // [n_buckets + 1] per-bucket counts (all zero between pairs)
+  unsigned* offs;            // [n_buckets + 1] exclusive scan of cnt (offs[n_buckets] = total); null: no corrections
+  unsigned long long* bsum;  // block sums of the scan
+  unsigned long long* ent;   // entries: low word (hy << 8 | hx) in the halo'd tile, high word the cube value's bits
+  unsigned long long cap;    // entry capacity (the buffer holds cap + 2)
+  ShareState* ss;
+  int ty;                    // tile height of the buckets and of k_smooth_p (32 or 16)
+  int tiles_x, tiles_y;
+  long long n_buckets;       // tiles_x * tiles_y * nz
+};
+
+// Tile height (32 or 16) of the shared-pass kernel for a spectral width, 0 if none.
+int share_tile_rows(int wz);
+// True if a pair's spatial passes can be stored for / taken from another pair.
+bool share_supported(const PairDesc& pd);
+// Per-pair correction lists: counts, scan and fill (with R = the pair's spatial half-width).
+cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s);
+// The spectral pass over P' with the corrections; *done = false if it does not serve the pair.
+cudaError_t launch_smooth_p(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s, bool* done);
+void init_share_attrs();
 
 // Kernel choices the autotuner may fix for a (dims, kernel pair).
 enum TuneKind : int {

@@ -348,6 +348,7 @@ void init_kernel_attrs() {
   init_tile_attrs();
   init_ws_attrs();
   init_z_attrs();
+  init_share_attrs();
   init_noise_attrs();
   init_noise_scale_attrs();
 }
@@ -400,6 +401,7 @@ int make_pair(const sc_kernel& k, PairDesc* pd) {
   for (int i = 0; i < 2 * kMaxHalf + 1; ++i) pd->taps[i] = (i < len) ? (int)t[i] : 0;
   const long long wxy = (long long)pd->w[0] * pd->w[1] * pd->w[2];
   pd->W = wxy * wxy * pd->wz;
+  pd->Wf = wxy * wxy * (pd->wz > kShareMaxWz ? pd->wz : kShareMaxWz);
   return SC_OK;
 }
 

@@ -1,0 +1,612 @@
+// Shared spatial passes of the smoothing (SoFiA 2 Sect. 4.2 and 5: one
+// spatial Gaussian combined with several spectral boxcars; Sect. 6.2: the
+// replacement of already-detected voxels at the start of every pair).
+//
+// For the pairs (K_xy, w_1), (K_xy, w_2), ... of one spatial kernel, the
+// replaced input of pair j differs from that of the first pair only at the
+// voxels masked since then (the mask only grows):
+//
+//   X_j = X_1 + D_j,   D_j(v) = sgn(C(v)) n sigma_0 - C(v)  on M_j \ M_1, else 0.
+//
+// The smoothing is linear and exact in the fixed-point arithmetic of this
+// library (every pair of one spatial kernel quantises with the same scale), so
+//
+//   K_xy * X_j,q = P + K_xy * D_j,q  exactly,   P = K_xy * X_1,q.
+//
+// The first pair's warp-specialised kernel stores P' = 32 P + nonfinite(C)
+// (int64 per voxel). Every later pair then:
+//
+//   prep        lists the voxels of M_j \ M_1 once per bucket (a 64 x ty tile
+//               of this kernel and a plane) whose halo'd region holds them,
+//               with their cube values: a count pass, an exclusive scan and
+//               a fill pass over the two masks;
+//   k_smooth_p  streams the P' tiles by TMA and the bucket's list by a bulk
+//               copy, adds d K(a) K(b) of every listed voxel into a shared
+//               tile of corrections, runs the spectral boxcar over the
+//               corrected planes (ring in Tensor Memory) and writes S and its
+//               histogram.
+//
+// The result is bit for bit the full kernel's on X_j: the two differ only in
+// the order of exact integer additions. Reading 8 bytes of P' replaces the
+// cube read, quantisation and both spatial cascades of the pair. When a
+// pair's list does not fit its buffer, k_smooth_p does nothing and a gated
+// launch of the full kernel computes the pair instead.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "sc_device.cuh"
+#include "sc_internal.h"
+#include "sc_tile_common.cuh"
+
+namespace sc {
+namespace share {
+
+using namespace tc;
+
+constexpr int TX = 64;            // tile width
+constexpr int VPT = 4;            // rows of one column per compute thread
+constexpr int kStages = 8;        // P' tiles in flight (a power of two)
+constexpr int kEnt = 256;         // list entries staged per plane (the rest are read from global memory)
+constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
+
+__device__ __forceinline__ int floor_div64(int a) { return a >= 0 ? a / TX : -((-a + TX - 1) / TX); }
+__device__ __forceinline__ int floor_divt(int a, int t) { return a >= 0 ? a / t : -((-a + t - 1) / t); }
+
+// Calls f(bucket, pos) for every bucket whose halo'd region holds voxel v:
+// tiles t with t*T - R <= c < t*T + T + R along each axis; pos = (hy << 8) | hx
+// is the voxel's place in that region.
+template <class F>
+__device__ __forceinline__ void for_buckets(long long v, long long nx, long long ny, const ShareArgs& sh, int R, F f) {
+  const long long plane = nx * ny;
+  const long long z = v / plane;
+  const long long rem = v - z * plane;
+  const int y = (int)(rem / nx), x = (int)(rem - (long long)y * nx);
+  const int tx_lo = max(0, floor_div64(x - R)), tx_hi = min(sh.tiles_x - 1, (x + R) / TX);
+  const int ty_lo = max(0, floor_divt(y - R, sh.ty)), ty_hi = min(sh.tiles_y - 1, (y + R) / sh.ty);
+  for (int ty = ty_lo; ty <= ty_hi; ++ty)
+    for (int tx = tx_lo; tx <= tx_hi; ++tx) {
+      const long long b = (z * sh.tiles_y + ty) * sh.tiles_x + tx;
+      const unsigned pos = ((unsigned)(y - (ty * sh.ty - R)) << 8) | (unsigned)(x - (tx * TX - R));
+      f(b, pos);
+    }
+}
+
+// Delta words M_j & ~M_1, four at a time (both masks carry padding words).
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__ mbits, const float* __restrict__ C,
+                                                    long long n, long long nx, long long ny, ShareArgs sh, int R) {
+  const long long nq = ((n + 31) / 32 + 3) / 4;
+  const uint4* m4 = reinterpret_cast<const uint4*>(mbits);
+  const uint4* s4 = reinterpret_cast<const uint4*>(sh.msnap);
+  const bool write = FILL && sh.ss->overflow == 0u;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+       q += (long long)gridDim.x * blockDim.x) {
+    const uint4 a = __ldg(m4 + q), b = __ldg(s4 + q);
+    const unsigned d[4] = {a.x & ~b.x, a.y & ~b.y, a.z & ~b.z, a.w & ~b.w};
+    if ((d[0] | d[1] | d[2] | d[3]) == 0u) continue;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      unsigned w = d[k];
+      while (w) {
+        const int bit = __ffs(w) - 1;
+        w &= w - 1u;
+        const long long v = (4 * q + k) * 32 + bit;
+        if (v >= n) break;
+        if (FILL) {
+          const unsigned long long cb = (unsigned long long)__float_as_uint(__ldg(C + v)) << 32;
+          for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned pos) {
+            const unsigned slot = atomicSub(sh.cnt + bk, 1u) - 1u;
+            const unsigned long long idx = (unsigned long long)__ldg(sh.offs + bk) + slot;
+            if (write && idx < sh.cap) sh.ent[idx] = cb | pos;
+          });
+        } else {
+          for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned) { atomicAdd(sh.cnt + bk, 1u); });
+        }
+      }
+    }
+  }
+}
+
+// Exclusive scan of m counts, in chunks of kScanChunk: the chunk's own scan
+// and its total.
+__global__ void __launch_bounds__(1024) k_share_scan1(const unsigned* __restrict__ cnt, unsigned* __restrict__ offs,
+                                                      unsigned long long* __restrict__ bsum, long long m) {
+  __shared__ unsigned wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const long long base = (long long)blockIdx.x * kScanChunk + 4 * t;
+  unsigned v[4], tot = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = base + k < m ? cnt[base + k] : 0u;
+    tot += v[k];
+  }
+  unsigned inc = tot;  // inclusive scan over the warp
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned x = wsum[lane], xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    wsum[lane] = xi - x;  // exclusive over warps
+    if (lane == 31) bsum[blockIdx.x] = xi;
+  }
+  __syncthreads();
+  unsigned run = wsum[warp] + inc - tot;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (base + k < m) offs[base + k] = run;
+    run += v[k];
+  }
+}
+
+// Adds the totals of the chunks before each chunk; the last chunk's block
+// records the grand total and whether it exceeds the list's capacity.
+__global__ void __launch_bounds__(1024) k_share_scan2(unsigned* __restrict__ offs,
+                                                      const unsigned long long* __restrict__ bsum, long long m,
+                                                      ShareState* ss, unsigned long long cap) {
+  __shared__ unsigned long long red[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  unsigned long long p = 0;
+  for (long long i = t; i < blockIdx.x; i += 1024) p += bsum[i];
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+  if (lane == 0) red[warp] = p;
+  __syncthreads();
+  unsigned long long pre = 0;
+  for (int w = 0; w < 32; ++w) pre += red[w];
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  for (int k = t; k < kScanChunk; k += 1024)
+    if (base + k < m) offs[base + k] += (unsigned)pre;
+  if (blockIdx.x == gridDim.x - 1 && t == 0) {
+    const unsigned long long total = pre + bsum[blockIdx.x];
+    ss->total = total;
+    ss->overflow = total > cap ? 1u : 0u;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+template <int VPT>
+struct TmRing;
+template <>
+struct TmRing<8> {
+  static __device__ __forceinline__ void ld(unsigned t, unsigned (&v)[16]) { tmem_ld16(t, v); }
+  static __device__ __forceinline__ void st(unsigned t, const unsigned (&v)[16]) { tmem_st16(t, v); }
+};
+template <>
+struct TmRing<4> {
+  static __device__ __forceinline__ void ld(unsigned t, unsigned (&v)[8]) { tmem_ld8(t, v); }
+  static __device__ __forceinline__ void st(unsigned t, const unsigned (&v)[8]) { tmem_st8(t, v); }
+};
+
+struct Meta {
+  unsigned cnt, off0, shift, pad;
+};
+
+// A compute thread owns VPT rows of one column of the 64 x TY tile, so TY / 2
+// compute warps; the warps of one TMEM lane quarter split its 512 columns,
+// which bounds the spectral ring to kMaxWz planes (15 for TY 32, 31 for 16).
+template <int TY, int R>
+struct PGeo {
+  static constexpr int kCW = TY / 2;           // compute warps
+  static constexpr int kCT = 32 * kCW;
+  static constexpr int kThreads = kCT + 32;    // + the issuing warp
+  static constexpr int NT = 2 * R + 1;         // taps per axis
+  static constexpr int kSlotCols = 2 * VPT;    // TMEM columns per ring slot
+  static constexpr int kColsPerWarp = kTmemCols / (kCW / 4);
+  static constexpr int kMaxWz = (kColsPerWarp / kSlotCols - 1) | 1;
+  static constexpr size_t kPBytes = sizeof(long long) * TY * TX;
+  static_assert(kCT == TX * (TY / VPT), "one compute thread per column segment");
+  static_assert(kCW % 4 == 0, "compute warps cover the TMEM lane quarters evenly");
+  static_assert(TY + 2 * R <= 256 && TX + 2 * R <= 256, "positions fit 8 bits per axis");
+};
+
+struct PSmem {
+  size_t p, e, q, kk, meta, hist, mbar, total;
+};
+constexpr int kBars = 2 * kStages + 4;  // full[kStages], empty[kStages], stamped[2], qfree[2]
+
+template <int TY, int R>
+__host__ __device__ constexpr PSmem p_layout() {
+  using G = PGeo<TY, R>;
+  PSmem s{};
+  size_t o = 0;
+  s.p = o;  // [kStages][TY][64] P' tiles
+  o = al128(o + kStages * G::kPBytes);
+  s.e = o;  // [kStages][kEnt] list entries
+  o = al128(o + sizeof(unsigned long long) * kStages * kEnt);
+  s.q = o;  // [2][TY][64] corrections (planes with corrections alternate)
+  o = al128(o + 2 * G::kPBytes);
+  s.kk = o;  // [NT * NT] products of the 1-D taps
+  o = al128(o + sizeof(int) * G::NT * G::NT);
+  s.meta = o;
+  o = al128(o + sizeof(Meta) * kStages);
+  s.hist = o;
+  o = al128(o + sizeof(unsigned) * kNumBins);
+  s.mbar = o;
+  o = al128(o + kBars * sizeof(unsigned long long));
+  s.total = o + 128;
+  return s;
+}
+
+}  // namespace share
+
+template <int TY, int R>
+__global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
+    k_smooth_p(const __grid_constant__ CUtensorMap pmap, SmoothArgs a, ShareArgs sh) {
+  using namespace share;
+  using G = PGeo<TY, R>;
+  constexpr int NT = G::NT, kCW = G::kCW, kThreads = G::kThreads;
+  if (sh.ss->overflow) return;  // the gated full kernel computes this pair (block-uniform)
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
+  constexpr PSmem L = p_layout<TY, R>();
+  long long* const Ps = reinterpret_cast<long long*>(smem + L.p);
+  unsigned long long* const Es = reinterpret_cast<unsigned long long*>(smem + L.e);
+  long long* const Qt = reinterpret_cast<long long*>(smem + L.q);
+  int* const kk = reinterpret_cast<int*>(smem + L.kk);
+  Meta* const meta = reinterpret_cast<Meta*>(smem + L.meta);
+  unsigned* const hist = reinterpret_cast<unsigned*>(smem + L.hist);
+  const unsigned mbar = smem_u32(smem + L.mbar);
+  const unsigned full = mbar, empty = mbar + 8 * kStages, stamped = mbar + 16 * kStages,
+                 qfree = mbar + 16 * kStages + 16;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wz = a.pd.wz, r = (wz - 1) / 2;
+  const long long nx = a.nx, ny = a.ny, nz = a.nz, plane = nx * ny;
+  const long long n_tiles = (long long)sh.tiles_x * sh.tiles_y;
+  const long long n_items = n_tiles * a.zchunks;
+
+  if (a.hist)
+    for (int i = tid; i < kNumBins; i += kThreads) hist[i] = 0u;
+  for (int i = tid; i < 2 * TY * TX; i += kThreads) Qt[i] = 0ll;
+  for (int i = tid; i < NT * NT; i += kThreads) kk[i] = a.pd.taps[i / NT] * a.pd.taps[i % NT];
+  __shared__ unsigned tmem_holder;
+  if (warp == 0) tmem_alloc(&tmem_holder);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full + 8 * s, 1u);
+      mbar_init(empty + 8 * s, (unsigned)kCW);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(stamped + 8 * b, (unsigned)kCW);
+      mbar_init(qfree + 8 * b, (unsigned)kCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  const unsigned tbase = tmem_holder;
+  bool timed_out = false;
+
+  auto item_geo = [&](long long it, int* x0, int* y0, int* z0, int* ns) {
+    const long long t = it % n_tiles;
+    const int zc = (int)(it / n_tiles);
+    *x0 = (int)(t % sh.tiles_x) * TX;
+    *y0 = (int)(t / sh.tiles_x) * TY;
+    *z0 = zc * a.lz;
+    *ns = (int)(min((long long)*z0 + a.lz, nz) - *z0) + 2 * r;
+  };
+
+  if (warp == kCW) {
+    // ===================== issuing warp =====================
+    // List bounds of up to 32 planes of one item per batch; lane l holds those
+    // of plane j0 + l. The next batch is fetched while this one is issued.
+    auto load_batch = [&](long long it, int j0, unsigned* o0, unsigned* o1) {
+      *o0 = 0u;
+      *o1 = 0u;
+      if (!sh.offs || it >= n_items) return;
+      int x0, y0, z0, ns;
+      item_geo(it, &x0, &y0, &z0, &ns);
+      const int jl = j0 + lane;
+      const long long zl = (long long)z0 - r + jl;
+      if (jl < ns && zl >= 0 && zl < nz) {
+        const long long b = (zl * sh.tiles_y + y0 / TY) * sh.tiles_x + x0 / TX;
+        *o0 = __ldg(sh.offs + b);
+        *o1 = __ldg(sh.offs + b + 1);
+      }
+    };
+    unsigned g = 0;  // planes issued
+    long long it = blockIdx.x;
+    int j0 = 0;
+    unsigned c0, c1;
+    load_batch(it, 0, &c0, &c1);
+    while (it < n_items) {
+      int x0, y0, z0, ns;
+      item_geo(it, &x0, &y0, &z0, &ns);
+      const long long nit = j0 + 32 < ns ? it : it + gridDim.x;
+      const int nj0 = j0 + 32 < ns ? j0 + 32 : 0;
+      unsigned n0, n1;
+      load_batch(nit, nj0, &n0, &n1);
+      const int nj = min(32, ns - j0);
+      for (int jj = 0; jj < nj; ++jj, ++g) {
+        const unsigned b0 = __shfl_sync(0xffffffffu, c0, jj), b1 = __shfl_sync(0xffffffffu, c1, jj);
+        if (lane == 0) {
+          const int s = (int)(g & (kStages - 1));
+          mbar_wait_bounded(empty + 8 * s, ((g / kStages) & 1u) ^ 1u, &timed_out);
+          const unsigned cnt = b1 - b0, shift = b0 & 1u;
+          unsigned ncp = cnt ? min(cnt + shift, (unsigned)kEnt) : 0u;
+          ncp = (ncp + 1u) & ~1u;  // whole 16-byte units (the list has two spare entries)
+          meta[s] = Meta{cnt, b0, shift, 0u};
+          mbar_expect_tx(full + 8 * s, (unsigned)(G::kPBytes + 8u * ncp));
+          tma_load_3d(smem_u32(Ps + (size_t)s * TY * TX), &pmap, x0, y0, z0 - r + j0 + jj, full + 8 * s);
+          if (ncp) bulk_load(smem_u32(Es + (size_t)s * kEnt), sh.ent + (b0 - shift), 8u * ncp, full + 8 * s);
+        }
+        __syncwarp();
+      }
+      c0 = n0;
+      c1 = n1;
+      it = nit;
+      j0 = nj0;
+    }
+    // let every load still in flight land before the block gives up its shared memory
+    if (lane == 0)
+      for (unsigned q = g > (unsigned)kStages ? g - kStages : 0u; q < g; ++q) {
+        bool late = false;
+        mbar_wait_bounded(full + 8 * (int)(q & (kStages - 1)), (q / kStages) & 1u, &late);
+      }
+  } else {
+    // ===================== compute warps =====================
+    const int xc = tid & (TX - 1), grp = tid >> 6;
+    const unsigned tmine =
+        tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(G::kColsPerWarp * (warp >> 2));
+    const BinCfg cfg = a.win ? a.st->win : kFullRange;
+    const float inv = a.st->fx_inv[a.pair];
+    const float fscale = a.st->fx_scale[a.pair];
+    const long long qrepl = a.st->fx_qrepl[a.pair];
+    const bool want_hist = a.hist != nullptr;
+    unsigned g = 0;   // planes consumed
+    unsigned nq = 0;  // planes with corrections so far
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+      int x0, y0, z0, ns;
+      item_geo(item, &x0, &y0, &z0, &ns);
+      long long zsum[VPT];
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) zsum[i] = 0;
+      if (wz > 1) {
+        unsigned zero[2 * VPT];
+#pragma unroll
+        for (int i = 0; i < 2 * VPT; ++i) zero[i] = 0u;
+        for (int s = 0; s < wz; ++s) TmRing<VPT>::st(tmine + (unsigned)(G::kSlotCols * s), zero);
+        tmem_wait_st();
+      }
+      unsigned long long nfh = 0ull;  // nonfinite flags of the recent planes, newest lowest
+      const long long gx = (long long)x0 + xc;
+      const long long gy0 = (long long)y0 + grp * VPT;
+      unsigned rows_in = 0u;
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) rows_in |= (gx < nx && gy0 + i < ny ? 1u : 0u) << i;
+      float* out = a.S + (long long)z0 * plane + gy0 * nx + gx;  // output plane z0 + (j - 2r) once j >= 2r
+      int slot = 0;
+      for (int j = 0; j < ns; ++j, ++g) {
+        const int s = (int)(g & (kStages - 1));
+        unsigned old[2 * VPT];
+        const unsigned ta = tmine + (unsigned)(G::kSlotCols * slot);
+        if (wz > 1) TmRing<VPT>::ld(ta, old);
+        mbar_wait_bounded(full + 8 * s, (g / kStages) & 1u, &timed_out);
+        const Meta md = meta[s];
+        long long p[VPT];
+        const long long* pt = Ps + (size_t)s * TY * TX + (grp * VPT) * TX + xc;
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) p[i] = pt[i * TX];
+        if (md.cnt > 0u && qrepl > 0) {
+          // corrections: the k-th such plane of the block uses tile k % 2;
+          // its previous use must be consumed by every compute warp first
+          const int b = (int)(nq & 1u);
+          const unsigned use = nq >> 1;
+          long long* const Q = Qt + b * TY * TX;
+          if (use > 0) mbar_wait_bounded(qfree + 8 * b, (use - 1u) & 1u, &timed_out);
+          const unsigned long long* es = Es + (size_t)s * kEnt;
+          for (unsigned e_i = warp; e_i < md.cnt && !timed_out; e_i += kCW) {
+            const unsigned long long e =
+                (e_i + md.shift < (unsigned)kEnt) ? es[e_i + md.shift] : __ldg(sh.ent + md.off0 + e_i);
+            const unsigned pos = (unsigned)e;
+            const float c = __uint_as_float((unsigned)(e >> 32));
+            const int ly = (int)(pos >> 8) - R, lx = (int)(pos & 0xffu) - R;
+            // X_j,q - X_1,q at this voxel: sgn(C) (qrepl - rint(|C| 2^f)), sgn(0) = +1
+            long long d = qrepl - quantize(fabsf(c), fscale);
+            if (c < 0.0f) d = -d;
+            d *= 32;
+            for (int tp = lane; tp < NT * NT; tp += 32) {
+              const int ai = tp / NT, bi = tp - ai * NT;
+              const int oy = ly + ai - R, ox = lx + bi - R;
+              if ((unsigned)oy < (unsigned)TY && (unsigned)ox < (unsigned)TX)
+                atomicAdd(reinterpret_cast<unsigned long long*>(Q + oy * TX + ox), (unsigned long long)(d * kk[tp]));
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(stamped + 8 * b);
+          mbar_wait_bounded(stamped + 8 * b, use & 1u, &timed_out);
+#pragma unroll
+          for (int i = 0; i < VPT; ++i) {
+            long long* qp = Q + (grp * VPT + i) * TX + xc;
+            p[i] += *qp;
+            *qp = 0ll;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(qfree + 8 * b);
+          ++nq;
+        }
+        unsigned nb = 0u;
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) nb |= (unsigned)(p[i] & 1ll) << i;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + 8 * s);
+        if (wz > 1) {
+          unsigned nw[2 * VPT];
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < VPT; ++i) {
+            const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
+            zsum[i] += p[i] - o;
+            nw[2 * i] = (unsigned)((unsigned long long)p[i] & 0xffffffffull);
+            nw[2 * i + 1] = (unsigned)((unsigned long long)p[i] >> 32);
+          }
+          TmRing<VPT>::st(ta, nw);
+          if (++slot == wz) slot = 0;
+        } else {
+#pragma unroll
+          for (int i = 0; i < VPT; ++i) zsum[i] = p[i];
+        }
+        nfh = (nfh << VPT) | nb;
+        if (j >= 2 * r) {
+          const unsigned nbo = (unsigned)(nfh >> (VPT * r)) & ((1u << VPT) - 1u);
+#pragma unroll
+          for (int i = 0; i < VPT; ++i) {
+            const bool isn = (nbo >> i) & 1u;
+            // sum of P' = 32 sum(P) + (number of nonfinite flags < 32)
+            const float sv = dequantize(zsum[i] >> 5, inv);
+            const float sval = isn ? __int_as_float(0x7fc00000) : sv;
+            if ((rows_in >> i) & 1u) {
+              out[i * nx] = sval;
+              if (want_hist && !isn) atomicAdd(&hist[bin_of(sval, cfg)], 1u);
+            }
+          }
+          out += plane;
+        }
+        if (wz > 1) tmem_wait_st();
+      }
+    }
+  }
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tbase);
+  if (timed_out) atomicOr(&a.st->status, (unsigned)SC_ST_TIMEOUT);
+  if (a.hist)
+    for (int i = tid; i < kNumBins; i += kThreads)
+      if (hist[i]) atomicAdd(a.hist + i, (unsigned long long)hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+namespace {
+
+bool encode_p_map(CUtensorMap* map, const long long* base, long long nx, long long ny, long long nz, long long pitch,
+                  int ty) {
+  memset(map, 0, sizeof(*map));
+  if (pitch % 2 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tc::tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * 8, (cuuint64_t)pitch * ny * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)share::TX, (cuuint32_t)ty, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<long long*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS;
+}
+
+// Spatial half-width R of the cascades the warp-specialised kernel serves.
+int share_R(const PairDesc& pd) {
+  const int* w = pd.w;
+  if (w[0] == 1 && w[1] == 3 && w[2] == 3) return 2;
+  if (w[0] == 3 && w[1] == 5 && w[2] == 5) return 5;
+  if (w[0] == 5 && w[1] == 5 && w[2] == 5) return 6;
+  if (w[0] == 7 && w[1] == 9 && w[2] == 9) return 11;
+  return -1;
+}
+
+template <int TY, int R>
+cudaError_t launch_p(const SmoothArgs& a0, const ShareArgs& sh, int sms, cudaStream_t s) {
+  using namespace share;
+  constexpr PSmem L = p_layout<TY, R>();
+  SmoothArgs a = a0;
+  CUtensorMap map;
+  if (!encode_p_map(&map, sh.P, a.nx, a.ny, a.nz, sh.pitch, TY)) return cudaErrorInvalidValue;
+  // z chunks: fewest planes on the busiest block (each chunk re-reads 2r halo planes)
+  const long long tiles = (long long)sh.tiles_x * sh.tiles_y;
+  const int r = (a.pd.wz - 1) / 2;
+  long long best = -1, best_cost = 0;
+  const long long max_ch = std::max(1LL, (long long)a.nz / 16);
+  for (long long zch = 1; zch <= std::min(max_ch, 64LL); ++zch) {
+    const long long lz = (a.nz + zch - 1) / zch;
+    const long long chunks = (a.nz + lz - 1) / lz;
+    const long long per_block = (tiles * chunks + sms - 1) / sms;
+    const long long cost = per_block * (lz + 2 * r);
+    if (best < 0 || cost < best_cost) {
+      best = lz;
+      best_cost = cost;
+    }
+  }
+  a.lz = (int)best;
+  a.zchunks = (a.nz + a.lz - 1) / a.lz;
+  const long long items = tiles * a.zchunks;
+  const int grid = (int)std::min<long long>(items, (long long)sms);
+  k_smooth_p<TY, R><<<grid, PGeo<TY, R>::kThreads, tc::one_block_per_sm_smem(L.total), s>>>(map, a, sh);
+  return cudaGetLastError();
+}
+
+template <int TY>
+cudaError_t launch_p_ty(const SmoothArgs& a, const ShareArgs& sh, int R, int sms, cudaStream_t s) {
+  switch (R) {
+    case 2: return launch_p<TY, 2>(a, sh, sms, s);
+    case 5: return launch_p<TY, 5>(a, sh, sms, s);
+    case 6: return launch_p<TY, 6>(a, sh, sms, s);
+    default: return launch_p<TY, 11>(a, sh, sms, s);
+  }
+}
+
+template <int TY, int R>
+void set_p_attr() {
+  tc::set_dyn_smem_limit(k_smooth_p<TY, R>);
+}
+
+}  // namespace
+
+int share_tile_rows(int wz) {
+  if (wz <= share::PGeo<32, 2>::kMaxWz) return 32;
+  if (wz <= share::PGeo<16, 2>::kMaxWz) return 16;
+  return 0;
+}
+
+bool share_supported(const PairDesc& pd) {
+  return pd.h > 0 && share_R(pd) == pd.h && pd.wz <= kShareMaxWz && share_tile_rows(pd.wz) > 0;
+}
+
+cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s) {
+  using namespace share;
+  const long long n = (long long)a.nx * a.ny * a.nz;
+  const int R = a.pd.h;
+  const long long m = sh.n_buckets + 1;
+  const long long nblk = (m + kScanChunk - 1) / kScanChunk;
+  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  k_share_scan1<<<(unsigned)nblk, 1024, 0, s>>>(sh.cnt, sh.offs, sh.bsum, m);
+  k_share_scan2<<<(unsigned)nblk, 1024, 0, s>>>(sh.offs, sh.bsum, m, sh.ss, sh.cap);
+  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth_p(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s, bool* done) {
+  *done = false;
+  if (!share_supported(a.pd)) return cudaSuccess;
+  const int ty = share_tile_rows(a.pd.wz);
+  if (ty != sh.ty) return cudaSuccess;
+  const cudaError_t e = ty == 32 ? launch_p_ty<32>(a, sh, a.pd.h, sms, s) : launch_p_ty<16>(a, sh, a.pd.h, sms, s);
+  if (e == cudaSuccess) *done = true;
+  return e;
+}
+
+void init_share_attrs() {
+  set_p_attr<32, 2>();
+  set_p_attr<32, 5>();
+  set_p_attr<32, 6>();
+  set_p_attr<32, 11>();
+  set_p_attr<16, 2>();
+  set_p_attr<16, 5>();
+  set_p_attr<16, 6>();
+  set_p_attr<16, 11>();
+}
+
+}  // namespace sc

@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
   using T = Tile<TY>;
   constexpr int kCW = T::kCW, kCT = T::kCT, kThreads = T::kThreads;
   constexpr int R = G::R, RA = G::RA;
+  if (a.gate && *a.gate == 0u) return;  // a fallback launch that is not needed (block-uniform)
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   const Smem L = smem_layout<W1, W2, W3, TY>(a.hist != nullptr);
@@ -439,6 +440,14 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         if (!TMA) issue_async(ct);
         nan_hi = (nan_hi << SEGY) | (nan_lo >> (64 - SEGY));
         nan_lo = (nan_lo << SEGY) | nbyte;
+        if (a.pout && j >= r && j < n_steps - r) {
+          // the plane's spatial sums for the later pairs of this spatial
+          // kernel: P' = 32 P + nonfinite flag (planes of this chunk only)
+          long long* po = a.pout + ((long long)zp * ny + gy0) * a.ppitch + gx;
+#pragma unroll
+          for (int i = 0; i < SEGY; ++i)
+            if ((rows_in >> i) & 1u) po[i * a.ppitch] = P[i] * 32 + (long long)((nbyte >> i) & 1u);
+        }
         if (wz > 1) {
           unsigned nw[kSlotCols];
           tmem_wait_ld();

@@ -34,6 +34,7 @@ SC_FLAG_ACCUMULATE = 0x1
 SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
+SC_FLAG_NO_SHARE = 0x10
 SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
 # sc_smooth kernel variants (flags |= variant << 16)
 SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512 = \
@@ -53,8 +54,8 @@ SC_WARN_GAUSS_FALLBACK = 0x10
 SC_MAX_KERNELS = 64
 
 # smoothing kernel a pair ran on (stats()["smooth_kernel_pair"])
-SC_KERNEL_NONE, SC_KERNEL_IDENTITY, SC_KERNEL_Z, SC_KERNEL_WS32, SC_KERNEL_WS16, SC_KERNEL_TILE, SC_KERNEL_GENERIC = \
-    range(7)
+SC_KERNEL_NONE, SC_KERNEL_IDENTITY, SC_KERNEL_Z, SC_KERNEL_WS32, SC_KERNEL_WS16, SC_KERNEL_TILE, SC_KERNEL_GENERIC, \
+    SC_KERNEL_SHARED = range(8)
 
 
 class sc_kernel(C.Structure):
@@ -111,6 +112,8 @@ _SIGS = {
     "sc_smooth": (C.c_int, [_P, _P, C.POINTER(C.c_int64), sc_kernel, _P, C.c_float, _P, C.c_uint32, _P]),
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_copy_sigmas": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "sc_set_share_limit": (C.c_int, [_P, C.c_uint64]),
+    "sc_copy_smoothed": (C.c_int, [_P, _P, C.c_int64, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
                                  _P, C.POINTER(C.c_double), C.c_uint32, _P]),
@@ -477,6 +480,20 @@ def sc_autoflag(ctx, cube: torch.Tensor, k: float, channels: bool = True, pixels
     return out, fc.astype(bool), fp.astype(bool), cn, pn
 
 
+def sc_copy_smoothed(ctx, shape, device: int = 0, stream=None) -> torch.Tensor:
+    """The smoothed cube of the last pair of the latest run, as a new device tensor."""
+    n = 1
+    for d in shape:
+        n *= int(d)
+    out = torch.empty(tuple(shape), dtype=torch.float32, device=f"cuda:{device}")
+    _check(lib().sc_copy_smoothed(ctx, C.c_void_p(out.data_ptr()), n, _stream(out, stream)), "sc_copy_smoothed")
+    return out
+
+
+def sc_set_share_limit(ctx, max_entries: int) -> None:
+    _check(lib().sc_set_share_limit(ctx, int(max_entries)), "sc_set_share_limit")
+
+
 def sc_set_profiling(ctx, on: bool) -> None:
     _check(lib().sc_set_profiling(ctx, 1 if on else 0), "sc_set_profiling")
 
@@ -570,6 +587,12 @@ class Context:
 
     def copy_sigmas(self, sigma, sigma0, n_kernels, stream=None):
         sc_copy_sigmas(self.handle, sigma, sigma0, n_kernels, stream)
+
+    def copy_smoothed(self, shape, stream=None):
+        return sc_copy_smoothed(self.handle, shape, self.device, stream)
+
+    def set_share_limit(self, max_entries):
+        sc_set_share_limit(self.handle, max_entries)
 
     def set_profiling(self, on=True):
         sc_set_profiling(self.handle, on)

@@ -251,18 +251,22 @@ def test_kernel_of_each_pair(ctx):
     """The library reports which smoothing kernel each pair ran on: none for
     the unsmoothed cube, the spectral kernel for spatially unsmoothed pairs,
     the warp-specialised 64 x 32 one for FWHM 3 and 6 px with widths <= 15,
-    the 64 x 16 one for width 31, the generic one when forced."""
+    the 64 x 16 one for width 31, the shared spatial passes for the later
+    pairs of one spatial kernel, the generic one when forced."""
     from paper_2106_15789_gb300 import sc
 
     cube = small_cube().cuda()  # nx = 64: TMA-addressable
-    ctx.run(cube, KERNELS_20, T)
-    codes = ctx.stats()["smooth_kernel_pair"][:len(KERNELS_20)]
-    for (fwhm, wz), code in zip(KERNELS_20, codes):
-        if fwhm == 0:
-            want = sc.SC_KERNEL_NONE if wz == 0 else sc.SC_KERNEL_Z
-        else:
-            want = sc.SC_KERNEL_WS32 if wz <= 15 else sc.SC_KERNEL_WS16
-        assert code == want, ((fwhm, wz), code)
+    for flags in (0, sc.SC_FLAG_NO_SHARE):
+        ctx.run(cube, KERNELS_20, T, flags=flags)
+        codes = ctx.stats()["smooth_kernel_pair"][:len(KERNELS_20)]
+        for k, ((fwhm, wz), code) in enumerate(zip(KERNELS_20, codes)):
+            if fwhm == 0:
+                want = sc.SC_KERNEL_NONE if wz == 0 else sc.SC_KERNEL_Z
+            elif flags == 0 and KERNELS_20[k - 1][0] == fwhm:
+                want = sc.SC_KERNEL_SHARED
+            else:
+                want = sc.SC_KERNEL_WS32 if wz <= 15 else sc.SC_KERNEL_WS16
+            assert code == want, ((fwhm, wz), flags, code)
     ctx.run(cube, KERNELS_12, T, flags=sc.SC_FLAG_GENERIC)
     codes = ctx.stats(reset=True)["smooth_kernel_pair"][:len(KERNELS_12)]
     assert codes[0] == sc.SC_KERNEL_NONE
