@@ -200,7 +200,9 @@ int sc_run(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, const sc_ker
  * can collect every run's sigmas without stopping. Each destination may be
  * NULL, device memory or pinned host memory; it holds the values once the
  * stream has reached the copy. A run whose device-side status was an error
- * leaves zeros. Errors: SC_ERR_ARG (NULL ctx, n_kernels outside
+ * (no finite voxel, a timed-out wait, a failed consistency check) leaves
+ * zeros in both: a small kernel stages the values, or zeros, in stream order
+ * before the copies. Errors: SC_ERR_ARG (NULL ctx, n_kernels outside
  * 1..SC_MAX_KERNELS), SC_ERR_CUDA. */
 int sc_copy_sigmas(sc_ctx *ctx, float *sigma_dst, float *sigma0_dst, int n_kernels, void *cuda_stream);
 
@@ -215,11 +217,14 @@ int sc_copy_sigmas(sc_ctx *ctx, float *sigma_dst, float *sigma0_dst, int n_kerne
 int sc_copy_smoothed(sc_ctx *ctx, float *dst, int64_t n, void *cuda_stream);
 
 /* Cap on the correction list of the shared spatial passes (see sc_run), in
- * entries; 0 restores the default (the list's full capacity). A pair whose
- * corrections exceed the cap is smoothed in full instead, with the same
- * results: the decision is taken on the device, so no synchronisation is
- * needed. Library addition with no counterpart in the paper; it lets tests
- * reach the fallback and lets callers trade speed for a smaller list.
+ * entries (an entry is a voxel masked since the spatial sums were stored,
+ * once for each tile whose halo holds it). A pair whose corrections exceed
+ * the cap is smoothed in full instead, with the same results: the decision
+ * is taken on the device, so no synchronisation is needed. 0 restores the
+ * default, a cost bound of max(65536, voxels/128) entries beyond which the
+ * full smoothing is the faster one; any cap is limited by the list's
+ * capacity. Library addition with no counterpart in the paper; it lets tests
+ * reach both paths and lets callers tune the trade-off.
  * Errors: SC_ERR_ARG (NULL ctx). */
 int sc_set_share_limit(sc_ctx *ctx, uint64_t max_entries);
 

@@ -41,6 +41,7 @@ struct sc_ctx {
   DevState* st = nullptr;
   DevState* st_host = nullptr;   // pinned mirror for read-back
   float* stage_cube = nullptr;   // sc_run_host staging (lazy)
+  float* sig_out = nullptr;      // sc_copy_sigmas staging: SC_MAX_KERNELS + 1 floats
   double* ns_sig = nullptr;      // sc_noise_scale: noise of every cell (lazy, grown)
   float* ns_rinv = nullptr;      // and its float reciprocal
   size_t ns_cap = 0;             // cells both hold
@@ -463,7 +464,11 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       sh.cnt = c->sh_cnt;
       sh.bsum = c->sh_bsum;
       sh.ent = c->sh_ent;
-      sh.cap = c->sh_limit > 0 ? std::min(c->sh_limit, c->sh_ent_cap) : c->sh_ent_cap;
+      // the caller's cap, else a cost bound (beyond about one correction per
+      // 128 voxels the full kernel is the faster one), within the list's capacity
+      sh.cap = c->sh_limit > 0 ? c->sh_limit
+                               : std::max<unsigned long long>(1ull << 16, (unsigned long long)n / 128);
+      sh.cap = std::min(sh.cap, c->sh_ent_cap);
       sh.ss = c->sh_ss;
       sh.ty = share_tile_rows(a.pd.wz);
       sh.tiles_x = (int)((dims[0] + 63) / 64);
@@ -591,6 +596,7 @@ int sc_create(sc_ctx** out, int device, size_t max_voxels) {
             cudaMalloc(&c->L.amb, sizeof(unsigned long long) * c->L.cap.amb) == cudaSuccess &&
             cudaMalloc(&c->L.cls, kClassTableBytes) == cudaSuccess &&
             cudaMalloc(&c->st, sizeof(DevState)) == cudaSuccess &&
+            cudaMalloc(&c->sig_out, sizeof(float) * (SC_MAX_KERNELS + 1)) == cudaSuccess &&
             cudaHostAlloc(&c->st_host, sizeof(DevState), cudaHostAllocDefault) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -625,6 +631,7 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->L.amb);
   cudaFree(c->L.cls);
   cudaFree(c->st);
+  cudaFree(c->sig_out);
   cudaFree(c->stage_cube);
   cudaFree(c->stage_mask);
   cudaFree(c->ns_sig);
@@ -1228,11 +1235,12 @@ int sc_copy_sigmas(sc_ctx* c, float* sigma_dst, float* sigma0_dst, int n_kernels
   if (!c || n_kernels < 1 || n_kernels > SC_MAX_KERNELS) return SC_ERR_ARG;
   DeviceGuard g(c->device);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const unsigned char* st = reinterpret_cast<const unsigned char*>(c->st);
-  if (sigma_dst)
-    CK(cudaMemcpyAsync(sigma_dst, st + offsetof(DevState, sigma), sizeof(float) * n_kernels, cudaMemcpyDefault, s));
-  if (sigma0_dst)
-    CK(cudaMemcpyAsync(sigma0_dst, st + offsetof(DevState, sigma0), sizeof(float), cudaMemcpyDefault, s));
+  if (!sigma_dst && !sigma0_dst) return SC_OK;
+  // staged by a kernel that writes zeros when the run's status is an error
+  CK(launch_sigma_out(c->st, n_kernels, c->sig_out, s));
+  c->stats.launches += 1;
+  if (sigma_dst) CK(cudaMemcpyAsync(sigma_dst, c->sig_out, sizeof(float) * n_kernels, cudaMemcpyDefault, s));
+  if (sigma0_dst) CK(cudaMemcpyAsync(sigma0_dst, c->sig_out + n_kernels, sizeof(float), cudaMemcpyDefault, s));
   return SC_OK;
 }
 

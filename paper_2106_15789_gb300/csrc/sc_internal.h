@@ -188,9 +188,10 @@ struct SmoothArgs {
 // pairs with one spatial kernel, S comes from the stored P' of the run's
 // first pair plus the corrections of voxels masked since then.
 struct ShareState {
-  unsigned long long total;  // correction entries of the current pair
-  unsigned overflow;         // 1: more entries than the list holds (the full kernel runs)
+  unsigned long long total;      // correction entries of the current pair
+  unsigned overflow;             // 1: more entries than the list holds (the full kernel runs)
   unsigned pad;
+  unsigned long long next_item;  // work-item counter of the shared pass (zero before each pair)
 };
 
 struct ShareArgs {
@@ -200,7 +201,7 @@ struct ShareArgs {
   unsigned* cnt;             // [n_buckets + 1] per-bucket counts (all zero between pairs)
   unsigned* offs;            // [n_buckets + 1] exclusive scan of cnt (offs[n_buckets] = total); null: no corrections
   unsigned long long* bsum;  // block sums of the scan
-  unsigned long long* ent;   // entries: low word (hy << 8 | hx) in the halo'd tile, high word the cube value's bits
+  unsigned long long* ent;   // entries: d * 2^16 + (hy << 8 | hx), d the voxel's fixed-point correction
   unsigned long long cap;    // entry capacity (the buffer holds cap + 2)
   ShareState* ss;
   int ty;                    // tile height of the buckets and of k_smooth_p (32 or 16)
@@ -262,6 +263,8 @@ cudaError_t launch_gauss_fit(DevState* st, const unsigned long long* ghist, int 
 cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s);
 cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,
                                cudaStream_t s);
+// out[0..n-1] = sigma_k, out[n] = sigma_0, or zeros after a device-side error
+cudaError_t launch_sigma_out(const DevState* st, int n, float* out, cudaStream_t s);
 cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s);
 cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s);
 cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s);

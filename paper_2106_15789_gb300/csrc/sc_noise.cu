@@ -988,6 +988,19 @@ cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeight
   return cudaGetLastError();
 }
 
+// The latest run's sigmas for sc_copy_sigmas: out[k] = sigma_k (k < n),
+// out[n] = sigma_0, all zero when the run's device-side status is an error
+// (its sigmas are then meaningless).
+__global__ void k_sigma_out(const DevState* st, int n, float* out) {
+  const bool ok = st->status == 0u;
+  for (int k = threadIdx.x; k <= n; k += blockDim.x) out[k] = ok ? (k < n ? st->sigma[k] : st->sigma0) : 0.0f;
+}
+
+cudaError_t launch_sigma_out(const DevState* st, int n, float* out, cudaStream_t s) {
+  k_sigma_out<<<1, 64, 0, s>>>(st, n, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // uint8 mask <-> 1-bit working mask.
 // Working mask from a caller's uint8 mask: a bit for every set voxel whose

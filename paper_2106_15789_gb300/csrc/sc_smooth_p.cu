@@ -18,13 +18,13 @@
 //
 //   prep        lists the voxels of M_j \ M_1 once per bucket (a 64 x ty tile
 //               of this kernel and a plane) whose halo'd region holds them,
-//               with their cube values: a count pass, an exclusive scan and
-//               a fill pass over the two masks;
+//               with their fixed-point corrections d = X_j,q - X_1,q: a count
+//               pass, an exclusive scan and a fill pass over the two masks;
 //   k_smooth_p  streams the P' tiles by TMA and the bucket's list by a bulk
-//               copy, adds d K(a) K(b) of every listed voxel into a shared
-//               tile of corrections, runs the spectral boxcar over the
-//               corrected planes (ring in Tensor Memory) and writes S and its
-//               histogram.
+//               copy; every voxel gathers d K(a) K(b) from the listed voxels
+//               within reach; then the spectral boxcar runs over the
+//               corrected planes (ring in Tensor Memory) and S and its
+//               histogram are written.
 //
 // The result is bit for bit the full kernel's on X_j: the two differ only in
 // the order of exact integer additions. Reading 8 bytes of P' replaces the
@@ -47,7 +47,7 @@ using namespace tc;
 constexpr int TX = 64;            // tile width
 constexpr int VPT = 4;            // rows of one column per compute thread
 constexpr int kStages = 8;        // P' tiles in flight (a power of two)
-constexpr int kEnt = 256;         // list entries staged per plane (the rest are read from global memory)
+constexpr int kEnt = 768;         // list entries staged per plane (the rest are read from global memory)
 constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
 
 __device__ __forceinline__ int floor_div64(int a) { return a >= 0 ? a / TX : -((-a + TX - 1) / TX); }
@@ -73,13 +73,20 @@ __device__ __forceinline__ void for_buckets(long long v, long long nx, long long
 }
 
 // Delta words M_j & ~M_1, four at a time (both masks carry padding words).
+// An entry is the voxel's exact fixed-point correction
+// d = sgn(C) (qrepl - rint(|C| 2^f)) (sgn(0) = +1) times 2^16 plus its place
+// (hy << 8 | hx) in the bucket's halo'd tile; |d| < 2^46 for every cascade
+// served (f leaves bitlen((w1 w2 w3)^2 31 - 1) >= 12 bits of headroom).
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__ mbits, const float* __restrict__ C,
-                                                    long long n, long long nx, long long ny, ShareArgs sh, int R) {
+                                                    long long n, long long nx, long long ny, ShareArgs sh, int R,
+                                                    const DevState* st, int pair) {
   const long long nq = ((n + 31) / 32 + 3) / 4;
   const uint4* m4 = reinterpret_cast<const uint4*>(mbits);
   const uint4* s4 = reinterpret_cast<const uint4*>(sh.msnap);
   const bool write = FILL && sh.ss->overflow == 0u;
+  const float fscale = FILL ? st->fx_scale[pair] : 0.0f;
+  const long long qrepl = FILL ? st->fx_qrepl[pair] : 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
        q += (long long)gridDim.x * blockDim.x) {
     const uint4 a = __ldg(m4 + q), b = __ldg(s4 + q);
@@ -94,11 +101,14 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
         const long long v = (4 * q + k) * 32 + bit;
         if (v >= n) break;
         if (FILL) {
-          const unsigned long long cb = (unsigned long long)__float_as_uint(__ldg(C + v)) << 32;
+          const float c = __ldg(C + v);
+          long long d = qrepl - quantize(fabsf(c), fscale);
+          if (c < 0.0f) d = -d;
+          const unsigned long long dhi = (unsigned long long)(d * 65536);
           for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned pos) {
             const unsigned slot = atomicSub(sh.cnt + bk, 1u) - 1u;
             const unsigned long long idx = (unsigned long long)__ldg(sh.offs + bk) + slot;
-            if (write && idx < sh.cap) sh.ent[idx] = cb | pos;
+            if (write && idx < sh.cap) sh.ent[idx] = dhi | pos;
           });
         } else {
           for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned) { atomicAdd(sh.cnt + bk, 1u); });
@@ -190,17 +200,45 @@ struct TmRing<4> {
 };
 
 struct Meta {
+  int item;  // work item of the stage (-1: no more items)
+  int j;     // plane index within the item
   unsigned cnt, off0, shift, pad;
 };
 
-// A compute thread owns VPT rows of one column of the 64 x TY tile, so TY / 2
-// compute warps; the warps of one TMEM lane quarter split its 512 columns,
-// which bounds the spectral ring to kMaxWz planes (15 for TY 32, 31 for 16).
+// Composed integer taps of a three-box cascade (the spatial kernels this
+// pass serves, identified by their half-width R), known at compile time.
+struct TapArr {
+  int v[2 * 11 + 1];
+};
+__host__ __device__ constexpr TapArr box_taps(int w1, int w2, int w3) {
+  TapArr t{};
+  const int ws[3] = {w1, w2, w3};
+  int len = 1;
+  t.v[0] = 1;
+  for (int b = 0; b < 3; ++b) {
+    TapArr n{};
+    for (int i = 0; i < len; ++i)
+      for (int d = 0; d < ws[b]; ++d) n.v[i + d] += t.v[i];
+    len += ws[b] - 1;
+    t = n;
+  }
+  return t;
+}
+template <int R>
+__host__ __device__ constexpr TapArr taps_for() {
+  return R == 2 ? box_taps(1, 3, 3) : (R == 5 ? box_taps(3, 5, 5) : (R == 6 ? box_taps(5, 5, 5) : box_taps(7, 9, 9)));
+}
+
+// Roles of a block: kCW compute warps (a thread owns VPT rows of one column
+// of the 64 x TY tile, so a warp owns 32 columns x VPT rows; the warps of one
+// TMEM lane quarter split its 512 columns, which bounds the spectral ring to
+// kMaxWz planes: 15 for TY 32, 31 for TY 16) and one issuing warp.
 template <int TY, int R>
 struct PGeo {
   static constexpr int kCW = TY / 2;           // compute warps
   static constexpr int kCT = 32 * kCW;
-  static constexpr int kThreads = kCT + 32;    // + the issuing warp
+  static constexpr int kIssuer = kCW;          // warp index of the issuing warp
+  static constexpr int kThreads = kCT + 32;
   static constexpr int NT = 2 * R + 1;         // taps per axis
   static constexpr int kSlotCols = 2 * VPT;    // TMEM columns per ring slot
   static constexpr int kColsPerWarp = kTmemCols / (kCW / 4);
@@ -212,9 +250,9 @@ struct PGeo {
 };
 
 struct PSmem {
-  size_t p, e, q, kk, meta, hist, mbar, total;
+  size_t p, e, kk, meta, hist, mbar, total;
 };
-constexpr int kBars = 2 * kStages + 4;  // full[kStages], empty[kStages], stamped[2], qfree[2]
+constexpr int kBars = 2 * kStages;  // full[kStages] (TMA landed), empty[kStages] (consumed)
 
 template <int TY, int R>
 __host__ __device__ constexpr PSmem p_layout() {
@@ -225,10 +263,8 @@ __host__ __device__ constexpr PSmem p_layout() {
   o = al128(o + kStages * G::kPBytes);
   s.e = o;  // [kStages][kEnt] list entries
   o = al128(o + sizeof(unsigned long long) * kStages * kEnt);
-  s.q = o;  // [2][TY][64] corrections (planes with corrections alternate)
-  o = al128(o + 2 * G::kPBytes);
-  s.kk = o;  // [NT * NT] products of the 1-D taps
-  o = al128(o + sizeof(int) * G::NT * G::NT);
+  s.kk = o;  // [NT] 1-D taps
+  o = al128(o + sizeof(int) * G::NT);
   s.meta = o;
   o = al128(o + sizeof(Meta) * kStages);
   s.hist = o;
@@ -241,6 +277,14 @@ __host__ __device__ constexpr PSmem p_layout() {
 
 }  // namespace share
 
+// Work items (a 64 x TY tile and a chunk of lz planes, with r halo planes on
+// each side) are handed out by an atomic counter, so blocks whose tiles hold
+// many corrections do not hold the kernel up. Per plane: the issuing warp
+// takes a free stage and loads the P' tile (TMA) and the bucket's list (bulk
+// copy); each compute warp gathers the corrections of its 32 x VPT voxels
+// from the list (32 entries tested at once by a ballot; a lane adds only to
+// its own voxels, so no atomics), runs the spectral ring and writes S. Stages carry the item and plane index,
+// and a last stage with item -1 ends the block.
 template <int TY, int R>
 __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
     k_smooth_p(const __grid_constant__ CUtensorMap pmap, SmoothArgs a, ShareArgs sh) {
@@ -253,13 +297,12 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
   constexpr PSmem L = p_layout<TY, R>();
   long long* const Ps = reinterpret_cast<long long*>(smem + L.p);
   unsigned long long* const Es = reinterpret_cast<unsigned long long*>(smem + L.e);
-  long long* const Qt = reinterpret_cast<long long*>(smem + L.q);
-  int* const kk = reinterpret_cast<int*>(smem + L.kk);
+  int* const taps1 = reinterpret_cast<int*>(smem + L.kk);
+  constexpr TapArr K = taps_for<R>();
   Meta* const meta = reinterpret_cast<Meta*>(smem + L.meta);
   unsigned* const hist = reinterpret_cast<unsigned*>(smem + L.hist);
   const unsigned mbar = smem_u32(smem + L.mbar);
-  const unsigned full = mbar, empty = mbar + 8 * kStages, stamped = mbar + 16 * kStages,
-                 qfree = mbar + 16 * kStages + 16;
+  const unsigned full = mbar, empty = mbar + 8 * kStages;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wz = a.pd.wz, r = (wz - 1) / 2;
   const long long nx = a.nx, ny = a.ny, nz = a.nz, plane = nx * ny;
@@ -268,18 +311,15 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
 
   if (a.hist)
     for (int i = tid; i < kNumBins; i += kThreads) hist[i] = 0u;
-  for (int i = tid; i < 2 * TY * TX; i += kThreads) Qt[i] = 0ll;
-  for (int i = tid; i < NT * NT; i += kThreads) kk[i] = a.pd.taps[i / NT] * a.pd.taps[i % NT];
+#pragma unroll
+  for (int i = 0; i < NT; ++i)
+    if (tid == i) taps1[i] = K.v[i];  // compile-time indices keep K out of local memory
   __shared__ unsigned tmem_holder;
   if (warp == 0) tmem_alloc(&tmem_holder);
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full + 8 * s, 1u);
       mbar_init(empty + 8 * s, (unsigned)kCW);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(stamped + 8 * b, (unsigned)kCW);
-      mbar_init(qfree + 8 * b, (unsigned)kCW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -299,8 +339,13 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
     *ns = (int)(min((long long)*z0 + a.lz, nz) - *z0) + 2 * r;
   };
 
-  if (warp == kCW) {
+  if (warp == G::kIssuer) {
     // ===================== issuing warp =====================
+    auto grab = [&]() -> long long {
+      unsigned long long v = 0ull;
+      if (lane == 0) v = atomicAdd(&sh.ss->next_item, 1ull);
+      return (long long)__shfl_sync(0xffffffffu, v, 0);
+    };
     // List bounds of up to 32 planes of one item per batch; lane l holds those
     // of plane j0 + l. The next batch is fetched while this one is issued.
     auto load_batch = [&](long long it, int j0, unsigned* o0, unsigned* o1) {
@@ -317,18 +362,18 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
         *o1 = __ldg(sh.offs + b + 1);
       }
     };
-    unsigned g = 0;  // planes issued
-    long long it = blockIdx.x;
+    unsigned g = 0;  // stages published
+    long long cur = grab();
+    long long nxt = cur < n_items ? grab() : n_items;
     int j0 = 0;
     unsigned c0, c1;
-    load_batch(it, 0, &c0, &c1);
-    while (it < n_items) {
+    load_batch(cur, 0, &c0, &c1);
+    while (cur < n_items) {
       int x0, y0, z0, ns;
-      item_geo(it, &x0, &y0, &z0, &ns);
-      const long long nit = j0 + 32 < ns ? it : it + gridDim.x;
-      const int nj0 = j0 + 32 < ns ? j0 + 32 : 0;
+      item_geo(cur, &x0, &y0, &z0, &ns);
+      const bool last = j0 + 32 >= ns;
       unsigned n0, n1;
-      load_batch(nit, nj0, &n0, &n1);
+      load_batch(last ? nxt : cur, last ? 0 : j0 + 32, &n0, &n1);
       const int nj = min(32, ns - j0);
       for (int jj = 0; jj < nj; ++jj, ++g) {
         const unsigned b0 = __shfl_sync(0xffffffffu, c0, jj), b1 = __shfl_sync(0xffffffffu, c1, jj);
@@ -338,7 +383,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
           const unsigned cnt = b1 - b0, shift = b0 & 1u;
           unsigned ncp = cnt ? min(cnt + shift, (unsigned)kEnt) : 0u;
           ncp = (ncp + 1u) & ~1u;  // whole 16-byte units (the list has two spare entries)
-          meta[s] = Meta{cnt, b0, shift, 0u};
+          meta[s] = Meta{(int)cur, j0 + jj, cnt, b0, shift, 0u};
           mbar_expect_tx(full + 8 * s, (unsigned)(G::kPBytes + 8u * ncp));
           tma_load_3d(smem_u32(Ps + (size_t)s * TY * TX), &pmap, x0, y0, z0 - r + j0 + jj, full + 8 * s);
           if (ncp) bulk_load(smem_u32(Es + (size_t)s * kEnt), sh.ent + (b0 - shift), 8u * ncp, full + 8 * s);
@@ -347,15 +392,28 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
       }
       c0 = n0;
       c1 = n1;
-      it = nit;
-      j0 = nj0;
+      if (last) {
+        cur = nxt;
+        nxt = cur < n_items ? grab() : n_items;
+        j0 = 0;
+      } else {
+        j0 += 32;
+      }
     }
-    // let every load still in flight land before the block gives up its shared memory
-    if (lane == 0)
+    if (lane == 0) {
+      // the last stage: no item
+      const int s = (int)(g & (kStages - 1));
+      mbar_wait_bounded(empty + 8 * s, ((g / kStages) & 1u) ^ 1u, &timed_out);
+      meta[s] = Meta{-1, 0, 0u, 0u, 0u, 0u};
+      mbar_arrive(full + 8 * s);
+      ++g;
+      // let every load still in flight land before the block gives up its shared memory
       for (unsigned q = g > (unsigned)kStages ? g - kStages : 0u; q < g; ++q) {
         bool late = false;
         mbar_wait_bounded(full + 8 * (int)(q & (kStages - 1)), (q / kStages) & 1u, &late);
       }
+    }
+    __syncwarp();
   } else {
     // ===================== compute warps =====================
     const int xc = tid & (TX - 1), grp = tid >> 6;
@@ -363,120 +421,130 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
         tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(G::kColsPerWarp * (warp >> 2));
     const BinCfg cfg = a.win ? a.st->win : kFullRange;
     const float inv = a.st->fx_inv[a.pair];
-    const float fscale = a.st->fx_scale[a.pair];
     const long long qrepl = a.st->fx_qrepl[a.pair];
+    const int wx0 = xc & ~31, wy0 = grp * VPT;  // the warp's 32 x VPT voxels
     const bool want_hist = a.hist != nullptr;
-    unsigned g = 0;   // planes consumed
-    unsigned nq = 0;  // planes with corrections so far
-    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
-      int x0, y0, z0, ns;
-      item_geo(item, &x0, &y0, &z0, &ns);
-      long long zsum[VPT];
+    // histogram bin (as bin_of): magnitude bits shifted, windowed, clamped, mirrored for negatives
+    const int bin_shift = 23 - cfg.MB, bin_base = (cfg.e_base << cfg.MB) - 1, bin_top = (cfg.E << cfg.MB) + 1;
+    long long zsum[VPT];
+    unsigned long long nfh = 0ull;  // nonfinite flags of the recent planes, newest lowest
+    unsigned rows_in = 0u;
+    float* out = nullptr;
+    int slot = 0;
+    for (unsigned g = 0;; ++g) {
+      const int s = (int)(g & (kStages - 1));
+      mbar_wait_bounded(full + 8 * s, (g / kStages) & 1u, &timed_out);
+      if (timed_out) break;
+      const Meta md = meta[s];
+      if (md.item < 0) break;
+      if (md.j == 0) {
+        int x0, y0, z0, ns;
+        item_geo(md.item, &x0, &y0, &z0, &ns);
 #pragma unroll
-      for (int i = 0; i < VPT; ++i) zsum[i] = 0;
-      if (wz > 1) {
-        unsigned zero[2 * VPT];
-#pragma unroll
-        for (int i = 0; i < 2 * VPT; ++i) zero[i] = 0u;
-        for (int s = 0; s < wz; ++s) TmRing<VPT>::st(tmine + (unsigned)(G::kSlotCols * s), zero);
-        tmem_wait_st();
-      }
-      unsigned long long nfh = 0ull;  // nonfinite flags of the recent planes, newest lowest
-      const long long gx = (long long)x0 + xc;
-      const long long gy0 = (long long)y0 + grp * VPT;
-      unsigned rows_in = 0u;
-#pragma unroll
-      for (int i = 0; i < VPT; ++i) rows_in |= (gx < nx && gy0 + i < ny ? 1u : 0u) << i;
-      float* out = a.S + (long long)z0 * plane + gy0 * nx + gx;  // output plane z0 + (j - 2r) once j >= 2r
-      int slot = 0;
-      for (int j = 0; j < ns; ++j, ++g) {
-        const int s = (int)(g & (kStages - 1));
-        unsigned old[2 * VPT];
-        const unsigned ta = tmine + (unsigned)(G::kSlotCols * slot);
-        if (wz > 1) TmRing<VPT>::ld(ta, old);
-        mbar_wait_bounded(full + 8 * s, (g / kStages) & 1u, &timed_out);
-        const Meta md = meta[s];
-        long long p[VPT];
-        const long long* pt = Ps + (size_t)s * TY * TX + (grp * VPT) * TX + xc;
-#pragma unroll
-        for (int i = 0; i < VPT; ++i) p[i] = pt[i * TX];
-        if (md.cnt > 0u && qrepl > 0) {
-          // corrections: the k-th such plane of the block uses tile k % 2;
-          // its previous use must be consumed by every compute warp first
-          const int b = (int)(nq & 1u);
-          const unsigned use = nq >> 1;
-          long long* const Q = Qt + b * TY * TX;
-          if (use > 0) mbar_wait_bounded(qfree + 8 * b, (use - 1u) & 1u, &timed_out);
-          const unsigned long long* es = Es + (size_t)s * kEnt;
-          for (unsigned e_i = warp; e_i < md.cnt && !timed_out; e_i += kCW) {
-            const unsigned long long e =
-                (e_i + md.shift < (unsigned)kEnt) ? es[e_i + md.shift] : __ldg(sh.ent + md.off0 + e_i);
-            const unsigned pos = (unsigned)e;
-            const float c = __uint_as_float((unsigned)(e >> 32));
-            const int ly = (int)(pos >> 8) - R, lx = (int)(pos & 0xffu) - R;
-            // X_j,q - X_1,q at this voxel: sgn(C) (qrepl - rint(|C| 2^f)), sgn(0) = +1
-            long long d = qrepl - quantize(fabsf(c), fscale);
-            if (c < 0.0f) d = -d;
-            d *= 32;
-            for (int tp = lane; tp < NT * NT; tp += 32) {
-              const int ai = tp / NT, bi = tp - ai * NT;
-              const int oy = ly + ai - R, ox = lx + bi - R;
-              if ((unsigned)oy < (unsigned)TY && (unsigned)ox < (unsigned)TX)
-                atomicAdd(reinterpret_cast<unsigned long long*>(Q + oy * TX + ox), (unsigned long long)(d * kk[tp]));
-            }
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(stamped + 8 * b);
-          mbar_wait_bounded(stamped + 8 * b, use & 1u, &timed_out);
-#pragma unroll
-          for (int i = 0; i < VPT; ++i) {
-            long long* qp = Q + (grp * VPT + i) * TX + xc;
-            p[i] += *qp;
-            *qp = 0ll;
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(qfree + 8 * b);
-          ++nq;
-        }
-        unsigned nb = 0u;
-#pragma unroll
-        for (int i = 0; i < VPT; ++i) nb |= (unsigned)(p[i] & 1ll) << i;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty + 8 * s);
+        for (int i = 0; i < VPT; ++i) zsum[i] = 0;
         if (wz > 1) {
-          unsigned nw[2 * VPT];
-          tmem_wait_ld();
+          unsigned zero[2 * VPT];
 #pragma unroll
-          for (int i = 0; i < VPT; ++i) {
-            const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
-            zsum[i] += p[i] - o;
-            nw[2 * i] = (unsigned)((unsigned long long)p[i] & 0xffffffffull);
-            nw[2 * i + 1] = (unsigned)((unsigned long long)p[i] >> 32);
-          }
-          TmRing<VPT>::st(ta, nw);
-          if (++slot == wz) slot = 0;
-        } else {
-#pragma unroll
-          for (int i = 0; i < VPT; ++i) zsum[i] = p[i];
+          for (int i = 0; i < 2 * VPT; ++i) zero[i] = 0u;
+          for (int k = 0; k < wz; ++k) TmRing<VPT>::st(tmine + (unsigned)(G::kSlotCols * k), zero);
+          tmem_wait_st();
         }
-        nfh = (nfh << VPT) | nb;
-        if (j >= 2 * r) {
-          const unsigned nbo = (unsigned)(nfh >> (VPT * r)) & ((1u << VPT) - 1u);
+        nfh = 0ull;
+        slot = 0;
+        const long long gx = (long long)x0 + xc;
+        const long long gy0 = (long long)y0 + grp * VPT;
+        rows_in = 0u;
 #pragma unroll
-          for (int i = 0; i < VPT; ++i) {
-            const bool isn = (nbo >> i) & 1u;
-            // sum of P' = 32 sum(P) + (number of nonfinite flags < 32)
-            const float sv = dequantize(zsum[i] >> 5, inv);
-            const float sval = isn ? __int_as_float(0x7fc00000) : sv;
-            if ((rows_in >> i) & 1u) {
-              out[i * nx] = sval;
-              if (want_hist && !isn) atomicAdd(&hist[bin_of(sval, cfg)], 1u);
+        for (int i = 0; i < VPT; ++i) rows_in |= (gx < nx && gy0 + i < ny ? 1u : 0u) << i;
+        out = a.S + (long long)z0 * plane + gy0 * nx + gx;  // output plane z0 + (j - 2r) once j >= 2r
+      }
+      unsigned old[2 * VPT];
+      const unsigned ta = tmine + (unsigned)(G::kSlotCols * slot);
+      if (wz > 1) TmRing<VPT>::ld(ta, old);
+      long long p[VPT];
+      const long long* pt = Ps + (size_t)s * TY * TX + (grp * VPT) * TX + xc;
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) p[i] = pt[i * TX];
+      if (md.cnt > 0u && qrepl > 0) {
+        // corrections d K(a) K(b) of the listed voxels within reach: the lanes
+        // load 32 entries at once, a ballot marks those that can reach the
+        // warp's 32 x VPT voxels, and only those are broadcast and applied
+        const unsigned long long* es = Es + (size_t)s * kEnt;
+        for (unsigned i0 = 0; i0 < md.cnt; i0 += 32) {
+          const unsigned i = i0 + (unsigned)lane;
+          unsigned long long e = 0xffffull;  // beyond the list: a place no warp can reach
+          if (i < md.cnt) e = (i + md.shift < (unsigned)kEnt) ? es[i + md.shift] : __ldg(sh.ent + md.off0 + i);
+          const int ly = (int)(((unsigned)e >> 8) & 0xffu) - R, lx = (int)((unsigned)e & 0xffu) - R;
+          unsigned reach =
+              __ballot_sync(0xffffffffu, lx + R >= wx0 && lx - R < wx0 + 32 && ly + R >= wy0 && ly - R < wy0 + VPT);
+          while (reach) {
+            // two entries per round, so that their latencies overlap (a
+            // missing second one is the unreachable place)
+            const int s0 = __ffs(reach) - 1;
+            reach &= reach - 1u;
+            const int s1 = reach ? __ffs(reach) - 1 : 0;
+            const bool two = reach != 0u;
+            reach &= reach - 1u;
+            const unsigned long long ej0 = __shfl_sync(0xffffffffu, e, s0);
+            unsigned long long ej1 = __shfl_sync(0xffffffffu, e, s1);
+            if (!two) ej1 = 0xffffull;
+            const int jy0 = (int)(((unsigned)ej0 >> 8) & 0xffu) - R, jx0 = (int)((unsigned)ej0 & 0xffu) - R;
+            const int jy1 = (int)(((unsigned)ej1 >> 8) & 0xffu) - R, jx1 = (int)((unsigned)ej1 & 0xffu) - R;
+            const int b0 = xc - jx0 + R, b1 = xc - jx1 + R;
+            const bool in0 = (unsigned)b0 < (unsigned)NT, in1 = (unsigned)b1 < (unsigned)NT;
+            const long long dk0 = in0 ? ((long long)ej0 >> 16) * (32 * taps1[b0]) : 0ll;
+            const long long dk1 = in1 ? ((long long)ej1 >> 16) * (32 * taps1[b1]) : 0ll;
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+              const int a0 = wy0 + k - jy0 + R, a1 = wy0 + k - jy1 + R;
+              if ((unsigned)a0 < (unsigned)NT) p[k] += dk0 * taps1[a0];
+              if ((unsigned)a1 < (unsigned)NT) p[k] += dk1 * taps1[a1];
             }
           }
-          out += plane;
         }
-        if (wz > 1) tmem_wait_st();
       }
+      unsigned nb = 0u;
+#pragma unroll
+      for (int i = 0; i < VPT; ++i) nb |= (unsigned)(p[i] & 1ll) << i;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty + 8 * s);
+      if (wz > 1) {
+        unsigned nw[2 * VPT];
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+          const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
+          zsum[i] += p[i] - o;
+          nw[2 * i] = (unsigned)((unsigned long long)p[i] & 0xffffffffull);
+          nw[2 * i + 1] = (unsigned)((unsigned long long)p[i] >> 32);
+        }
+        TmRing<VPT>::st(ta, nw);
+        if (++slot == wz) slot = 0;
+      } else {
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) zsum[i] = p[i];
+      }
+      nfh = (nfh << VPT) | nb;
+      if (md.j >= 2 * r) {
+        const unsigned nbo = (unsigned)(nfh >> (VPT * r)) & ((1u << VPT) - 1u);
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) {
+          const bool isn = (nbo >> i) & 1u;
+          // sum of P' = 32 sum(P) + (number of nonfinite flags < 32)
+          const float sv = dequantize(zsum[i] >> 5, inv);
+          const float sval = isn ? __int_as_float(0x7fc00000) : sv;
+          if ((rows_in >> i) & 1u) {
+            out[i * nx] = sval;
+            if (want_hist && !isn) {
+              const unsigned u = __float_as_uint(sval);
+              const int bm = min(max((int)((u & 0x7fffffffu) >> bin_shift) - bin_base, 0), bin_top);
+              atomicAdd(&hist[kBinsPerSign + (bm ^ ((int)u >> 31))], 1u);
+            }
+          }
+        }
+        out += plane;
+      }
+      if (wz > 1) tmem_wait_st();
     }
   }
   tmem_fence_before();
@@ -522,19 +590,23 @@ template <int TY, int R>
 cudaError_t launch_p(const SmoothArgs& a0, const ShareArgs& sh, int sms, cudaStream_t s) {
   using namespace share;
   constexpr PSmem L = p_layout<TY, R>();
+  constexpr TapArr K = taps_for<R>();
+  for (int i = 0; i < 2 * R + 1; ++i)
+    if (a0.pd.taps[i] != K.v[i]) return cudaErrorInvalidValue;  // not the cascade this instance serves
   SmoothArgs a = a0;
   CUtensorMap map;
   if (!encode_p_map(&map, sh.P, a.nx, a.ny, a.nz, sh.pitch, TY)) return cudaErrorInvalidValue;
-  // z chunks: fewest planes on the busiest block (each chunk re-reads 2r halo planes)
+  // z chunks (items are handed out dynamically): the planes a block streams
+  // on average, halo planes included, plus one item's planes for the tail
   const long long tiles = (long long)sh.tiles_x * sh.tiles_y;
   const int r = (a.pd.wz - 1) / 2;
-  long long best = -1, best_cost = 0;
+  long long best = -1;
+  double best_cost = 0.0;
   const long long max_ch = std::max(1LL, (long long)a.nz / 16);
   for (long long zch = 1; zch <= std::min(max_ch, 64LL); ++zch) {
     const long long lz = (a.nz + zch - 1) / zch;
     const long long chunks = (a.nz + lz - 1) / lz;
-    const long long per_block = (tiles * chunks + sms - 1) / sms;
-    const long long cost = per_block * (lz + 2 * r);
+    const double cost = (double)(a.nz + chunks * 2 * r) * tiles / sms + (double)(lz + 2 * r);
     if (best < 0 || cost < best_cost) {
       best = lz;
       best_cost = cost;
@@ -581,10 +653,10 @@ cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms,
   const int R = a.pd.h;
   const long long m = sh.n_buckets + 1;
   const long long nblk = (m + kScanChunk - 1) / kScanChunk;
-  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R, a.st, a.pair);
   k_share_scan1<<<(unsigned)nblk, 1024, 0, s>>>(sh.cnt, sh.offs, sh.bsum, m);
   k_share_scan2<<<(unsigned)nblk, 1024, 0, s>>>(sh.offs, sh.bsum, m, sh.ss, sh.cap);
-  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R, a.st, a.pair);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 """sc_copy_sigmas: the sigmas of runs made without sigma pointers, copied in
-stream order, equal the synchronous runs' (the same float32 values)."""
+stream order, equal the synchronous runs' (the same float32 values); a run
+whose device-side status is an error leaves zeros."""
 import numpy as np
 import pytest
 import torch
@@ -44,6 +45,25 @@ def test_pipeline_without_synchronisation(ctx):
     ctx.copy_sigmas(part, None, 3)
     torch.cuda.synchronize()
     assert part.cpu().tolist() == [float(np.float32(x)) for x in ref[-1][1][:3]]
+
+
+def test_error_status_leaves_zeros(ctx):
+    """An all-NaN cube run without sigma pointers returns once enqueued; its
+    device-side status (no finite voxel) makes the copies zeros, and the next
+    good run's copies are its sigmas again."""
+    nk = len(KERNELS_12)
+    bad = torch.full((16, 24, 32), float("nan"), device="cuda")
+    ctx.run(bad, KERNELS_12, T, "mad", N_REPL, want_sigma=False)
+    dev = torch.full((nk,), -1.0, device="cuda")
+    host0 = torch.full((1,), -1.0).pin_memory()
+    ctx.copy_sigmas(dev, host0, nk)
+    torch.cuda.synchronize()
+    assert dev.cpu().tolist() == [0.0] * nk and host0.item() == 0.0
+    good = make_cube(SMALL).cuda()
+    _, sig, s0 = ctx.run(good, KERNELS_12, T, "mad", N_REPL)
+    ctx.copy_sigmas(dev, host0, nk)
+    torch.cuda.synchronize()
+    assert dev.cpu().tolist() == [float(np.float32(x)) for x in sig] and host0.item() == s0
 
 
 def test_arguments(ctx):

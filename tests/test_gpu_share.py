@@ -133,12 +133,19 @@ def test_ragged_shapes(ctx, shape):
 
 def test_dense_corrections_and_caller_mask(ctx):
     """A low threshold masks a large share of the cube, so buckets hold far
-    more entries than a plane stages in shared memory; a caller mask adds a
-    dense block from the start."""
+    more entries than a plane stages in shared memory (the cost bound is
+    lifted so that the shared pass takes them); a caller mask adds a dense
+    block from the start."""
     cube = make_cube(CubeSpec(nx=96, ny=80, nz=64, seed=24, n_gal=15, snr=(3.0, 30.0), fwhm_xy=(2.0, 8.0),
                               fwhm_z=(5.0, 30.0)))
     ks = [(6.0, 0), (6.0, 3), (6.0, 7), (6.0, 15)]
-    check_shared_equals_full(ctx, cube, ks, t=1.2)
+    ctx.set_share_limit(1 << 40)
+    try:
+        check_shared_equals_full(ctx, cube, ks, t=1.2)
+        check_shared_equals_full(ctx, cube, [(10.0, 0), (10.0, 31), (10.0, 3)], t=1.2)
+    finally:
+        ctx.set_share_limit(0)
+    check_shared_equals_full(ctx, cube, ks, t=1.2)  # the default cost bound routes this to the full kernel
     mask0 = np.zeros(cube.shape, dtype=bool)
     mask0[10:40, 20:60, 30:70] = True
     check_shared_equals_full(ctx, cube, ks, mask0=mask0)
