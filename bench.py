@@ -32,6 +32,8 @@ sys.path.insert(0, ROOT)
 METRIC = "S+C voxel·kernels/s on 1 GB300 (FP32 plain vs batched/BF16), % HBM roofline"
 UNIT = "voxel·kernels/s"
 SMOOTH_BYTES_PER_VOXEL = 4.0 + 4.0 + 1.0 / 8.0  # read C, write S, read the 1-bit mask
+STORE_BYTES_PER_VOXEL = SMOOTH_BYTES_PER_VOXEL + 8.0  # the same, also writing the int64 spatial sums P'
+SHARED_BYTES_PER_VOXEL = 8.0 + 4.0  # read P', write S (the correction lists add ~0.1 %)
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
              "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag",
              "wallaby-gauss", "medium-gauss", "wallaby-noisescale-gauss", "wallaby-autoflag-gauss")
@@ -71,7 +73,8 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_tile.cu", "sc_smooth_z.cu", "sc_tile_common.cuh",
+SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_tile.cu", "sc_smooth_z.cu", "sc_smooth_p.cu",
+                  "sc_tile_common.cuh",
                   "sc_device.cuh")  # the smoothing kernels' code (declarations elsewhere do not change their traffic)
 
 
@@ -99,59 +102,37 @@ def smooth_traffic_record():
 TRAFFIC_WORKLOAD_VOXELS = 512 ** 3  # the medium workload, whose every smoothing launch covers the whole cube
 
 
-def ncu_kernel_key(name):
-    """Key of an ncu kernel name in the traffic record (the names
-    smoothing_kernel_name gives), or None for other kernels."""
-    import re
-
-    m = re.search(r"k_smooth_ws<(\d+), (\d+), (\d+), [^,]+, [^,]+, (\d+)>", name)
-    if m:
-        return "k_smooth_ws<%s,%s,%s>" % m.group(1, 2, 3) + ("/16" if m.group(4) == "16" else "")
-    m = re.search(r"k_smooth_tile<(\d+), (\d+), (\d+),", name)
-    if m:
-        return "k_smooth_tile<%s,%s,%s>" % m.group(1, 2, 3)
-    m = re.search(r"k_smooth_p<(\d+), (\d+)>", name)
-    if m:
-        return "k_smooth_p<R=%s>" % m.group(2) + ("/16" if m.group(1) == "16" else "")
-    for k in ("k_smooth_z", "k_smooth_generic", "k_identity"):
-        if k + "<" in name or k + "(" in name:
-            return k
-    return None
-
-
-def record_traffic(csv_path, command):
-    """Write profiles/smooth_traffic.json from an ncu --csv log of
-    dram__bytes_read.sum + dram__bytes_write.sum per smoothing launch on the
-    medium workload: mean DRAM bytes per output voxel of each kernel, keyed by
-    the current smoothing-source hash."""
+def record_traffic(specs, command):
+    """Write profiles/smooth_traffic.json from one-kernel ncu captures of the
+    medium workload: specs are "key=path" pairs, each path an ncu --csv log of
+    dram__bytes_read.sum and dram__bytes_write.sum for a few launches of the
+    kernel named key (as pair_kernels names it). The record holds the mean
+    DRAM bytes per output voxel of each, keyed by the current smoothing-source
+    hash."""
     import csv
 
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    per_launch = {}
-    with open(csv_path) as f:
-        rows = [r for r in csv.reader(f) if len(r) >= 15]
-    head = rows[0]
-    ci = {k: head.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
-    for r in rows[1:]:
-        key = ncu_kernel_key(r[ci["Kernel Name"]])
-        if key is None or r[ci["Metric Name"]] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            continue
-        b = float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
-        d = per_launch.setdefault((key, r[ci["ID"]]), [0.0])
-        d[0] += b
-    sums = {}
-    for (key, _), (b,) in per_launch.items():
-        acc = sums.setdefault(key, [0.0, 0])
-        acc[0] += b / TRAFFIC_WORKLOAD_VOXELS
-        acc[1] += 1
+    kernels, launches = {}, {}
+    for spec in specs:
+        key, path = spec.split("=", 1)
+        per_launch = {}
+        with open(path) as f:
+            rows = [r for r in csv.reader(f) if len(r) >= 15]
+        head = rows[0]
+        ci = {k: head.index(k) for k in ("ID", "Metric Name", "Metric Unit", "Metric Value")}
+        for r in rows[1:]:
+            if r[ci["Metric Name"]] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                continue
+            b = float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
+            per_launch[r[ci["ID"]]] = per_launch.get(r[ci["ID"]], 0.0) + b
+        kernels[key] = round(sum(per_launch.values()) / len(per_launch) / TRAFFIC_WORKLOAD_VOXELS, 3)
+        launches[key] = len(per_launch)
     rec = {"source_sha256_16": smooth_source_hash(),
-           "what": "DRAM bytes (read + write) per output voxel of one launch, mean over the captured launches of each "
-                   "kernel, from ncu dram__bytes_read.sum + dram__bytes_write.sum on the medium 512^3 workload (537 MB "
-                   "cube, larger than L2; the autotuner's candidates and the timed step); traffic is proportional to "
-                   "voxels, so the bench scales it to the launch's voxels",
-           "command": command,
-           "kernels": {k: round(v[0] / v[1], 3) for k, v in sorted(sums.items())},
-           "launches": {k: v[1] for k, v in sorted(sums.items())}}
+           "what": "DRAM bytes (read + write) per output voxel of one launch, mean over the captured launches, from "
+                   "one-kernel ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, a few launches each) of "
+                   "the medium 512^3 workload (larger than L2); traffic is proportional to voxels, so the bench "
+                   "scales it to the launch's voxels",
+           "command": command, "kernels": kernels, "launches": launches}
     with open(os.path.join(ROOT, "profiles", "smooth_traffic.json"), "w") as f:
         json.dump(rec, f, indent=1)
         f.write("\n")
@@ -246,49 +227,121 @@ def make_workload(name: str, rank: int, device: str):
     return spec, cube
 
 
-def cpu_baseline(cube_dev, kernels, t, n_repl, mode="mad"):
-    """FP64 oracle (as it stands) on an interior 192 x 192 x 256 sub-cube."""
+SUB_SHAPE = (256, 192, 192)  # (z, y, x) of one oracle sub-cube
+
+
+def interior_subcubes(shape, count, border=16, sub=SUB_SHAPE):
+    """Corners (z, y, x) of `count` disjoint sub-cubes of shape `sub` inside
+    the cube, clear of a NaN border of `border` voxels in x and y, in z-major
+    order (fewer if the cube holds fewer)."""
+    nz, ny, nx = shape
+    sz, sy, sx = min(sub[0], nz), min(sub[1], max(1, ny - 2 * border)), min(sub[2], max(1, nx - 2 * border))
+    by0 = border if ny > 2 * border else 0
+    bx0 = border if nx > 2 * border else 0
+    out = []
+    for z in range(0, nz - sz + 1, sz):
+        for y in range(by0, ny - by0 - sy + 1, sy):
+            for x in range(bx0, nx - bx0 - sx + 1, sx):
+                out.append((z, y, x))
+                if len(out) == count:
+                    return out, (sz, sy, sx)
+    return out, (sz, sy, sx)
+
+
+def _oracle_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_job(job):
+    """One pool worker: S+C of one sub-cube with the oracle, timed after all
+    workers have their data (the barrier), one thread."""
+    sub, kernels, t, n_repl, mode = job
     from oracle.sc_oracle import sc_filter
 
-    nz, ny, nx = cube_dev.shape
-    sz, sy, sx = min(256, nz), min(192, ny), min(192, nx)
-    z0, y0, x0 = (nz - sz) // 2, (ny - sy) // 2, (nx - sx) // 2
-    sub = cube_dev[z0:z0 + sz, y0:y0 + sy, x0:x0 + sx].float().cpu().numpy()
+    _BARRIER.wait()
     t0 = time.perf_counter()
     sc_filter(sub, kernels, t, mode, n_repl)
-    dt = time.perf_counter() - t0
-    return {"value": sub.size * len(kernels) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"interior {sx}x{sy}x{sz} sub-cube of the same cube, {len(kernels)} pairs, numpy float64, "
-                      f"one thread, {dt:.1f} s"}
+    return time.perf_counter() - t0
+
+
+def oracle_pool(subs, kernels, t, n_repl, mode, rounds=1):
+    """The oracle on the host cores: one spawned process per sub-cube, each
+    single-threaded, all starting together; per round, the aggregate
+    voxel*kernels/s is the sub-cubes' voxels x pairs over the slowest worker's
+    time. Returns (rates per round, seconds per round)."""
+    import multiprocessing as mp
+
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+        barrier = ctx.Barrier(len(subs))
+        rates, secs = [], []
+        with ctx.Pool(len(subs), initializer=_oracle_init, initargs=(barrier,)) as pool:
+            for _ in range(rounds):
+                times = pool.map(_oracle_job, [(x, kernels, t, n_repl, mode) for x in subs], chunksize=1)
+                secs.append(max(times))
+                rates.append(sum(x.size for x in subs) * len(kernels) / max(times))
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return rates, secs
+
+
+def oracle_workers():
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def cpu_baseline(cube_dev, kernels, t, n_repl, mode="mad"):
+    """The FP64 oracle as it stands on all host cores (up to 64 processes):
+    one interior 192 x 192 x 256 sub-cube of the same cube per process; plus
+    the same sub-cube size on one thread for reference."""
+    n = oracle_workers()
+    corners, (sz, sy, sx) = interior_subcubes(tuple(cube_dev.shape), n)
+    subs = [cube_dev[z:z + sz, y:y + sy, x:x + sx].float().cpu().numpy() for z, y, x in corners]
+    rates, secs = oracle_pool(subs, kernels, t, n_repl, mode)
+    rate1, secs1 = oracle_pool(subs[:1], kernels, t, n_repl, mode)
+    return {"value": rates[0], "unit": UNIT, "cores": len(subs), "kind": "oracle",
+            "value_one_thread": rate1[0],
+            "sample": f"{len(subs)} disjoint interior {sx}x{sy}x{sz} sub-cubes of the same cube (one per host process, "
+                      f"os.cpu_count() = {os.cpu_count()}), {len(kernels)} pairs each, numpy float64, "
+                      f"{secs[0]:.1f} s; one sub-cube on one thread: {secs1[0]:.1f} s"}
 
 
 def run_reference(args, rank, world):
-    """The oracle on the host cores: each step is a bounded sample."""
+    """The oracle on the host cores: each step is one round of the CPU
+    baseline's sample (interior sub-cubes of the same WALLABY-shaped cube, one
+    process per core)."""
     if rank != 0:
         return 0
-    import numpy as np
+    import torch
 
-    from oracle.sc_oracle import sc_filter
-    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, WALLABY, CubeSpec, make_cube
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, SMALL, WALLABY, make_cube
 
-    # a 128 x 128 x 128 cube with the wallaby recipe (noise, ripple, galaxies, NaN border)
-    spec = CubeSpec(nx=128, ny=128, nz=128, seed=WALLABY.seed, n_gal=12, snr=WALLABY.snr, snr_log=True,
-                    fwhm_xy=WALLABY.fwhm_xy, fwhm_z=WALLABY.fwhm_z, ripple=0.1, nan_border=4, name="ref-sample")
-    c = make_cube(spec).numpy()
     mode = "gauss" if args.workload.endswith("-gauss") else "mad"
-    for _ in range(args.warmup):
-        sc_filter(c, KERNELS_12, SC_THRESHOLD, mode, SC_REPLACEMENT)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sc_filter(c, KERNELS_12, SC_THRESHOLD, mode, SC_REPLACEMENT)
-    dt = time.perf_counter() - t0
-    value = c.size * len(KERNELS_12) * args.steps / dt
-    sample = f"128x128x128 cube of the wallaby recipe per step, {len(KERNELS_12)} pairs, numpy float64, one thread"
+    dev = "cuda" if torch.cuda.is_available() else "cpu"  # the input generator only; S+C runs on the host
+    with torch.no_grad():
+        cube = make_cube(WALLABY if args.ref_cube == "wallaby" else SMALL, device=dev)
+    n = oracle_workers()
+    corners, (sz, sy, sx) = interior_subcubes(tuple(cube.shape), n)
+    subs = [cube[z:z + sz, y:y + sy, x:x + sx].float().cpu().numpy() for z, y, x in corners]
+    del cube
+    rates, secs = oracle_pool(subs, KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT, mode, rounds=args.warmup + args.steps)
+    rates, secs = rates[args.warmup:], secs[args.warmup:]
+    total = sum(secs)
+    value = sum(x.size for x in subs) * len(KERNELS_12) * len(secs) / total
+    sample = (f"{len(subs)} disjoint interior {sx}x{sy}x{sz} sub-cubes of the {args.ref_cube} cube per step (one "
+              f"host process each, os.cpu_count() = {os.cpu_count()}), {len(KERNELS_12)} pairs, numpy float64")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args.workload, KERNELS_12, mode),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(subs), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -304,11 +357,14 @@ def config_dict(workload, kernels, mode="mad"):
              "wallaby-fp16": "wallaby-1200x1200x1024 stored as FP16 + per-channel float32 scales",
              "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
     workload = workload.removesuffix("-gauss")
+    half = workload.endswith(("-bf16", "-fp16"))
+    precision = ("%s cube + per-channel float32 scales, decoded to float32 once per run, exact fixed-point smoothing"
+                 % workload.split("-")[-1].upper()) if half else "float32 cube, exact fixed-point smoothing"
+    big = workload in ("wallaby", "wallaby-bf16", "wallaby-fp16")
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
             "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": mode, "replacement": SC_REPLACEMENT,
-            "precision": "float32 cube, exact fixed-point smoothing", "l2": "inputs (cube 5.9 GB) larger than L2"
-            if workload == "wallaby" else ("inputs (10.9 GB of sub-cubes) larger than L2" if workload == "batch64"
-                                           else "no flush")}
+            "precision": precision, "l2": "inputs (cube 5.9 GB) larger than L2"
+            if big else ("inputs (10.9 GB of sub-cubes) larger than L2" if workload == "batch64" else "no flush")}
 
 
 def gauss_hist_roofline(st, peak, peak_kind):
@@ -322,64 +378,98 @@ def gauss_hist_roofline(st, peak, peak_kind):
             "frac": gbs / peak, "peak_kind": peak_kind, "bytes_per_value": 4, "traffic": None}
 
 
+def pair_kernels(sc, kernels, codes):
+    """(kernel name, algorithmic bytes per voxel) of every pair: a full
+    smoothing pass reads C and the mask bits and writes S; the first pair of a
+    run that the next pairs share also writes its int64 spatial sums; a shared
+    pass reads those and writes S."""
+    out = []
+    for k, pair in enumerate(kernels):
+        code = codes[k]
+        name = smoothing_kernel_name(sc, pair, code)
+        if code == sc.SC_KERNEL_SHARED:
+            out.append((name, SHARED_BYTES_PER_VOXEL))
+        elif (k + 1 < len(kernels) and codes[k + 1] == sc.SC_KERNEL_SHARED and kernels[k + 1][0] == pair[0]
+              and code in (sc.SC_KERNEL_WS32, sc.SC_KERNEL_WS16)):
+            out.append((name + "+P", STORE_BYTES_PER_VOXEL))
+        else:
+            out.append((name, SMOOTH_BYTES_PER_VOXEL))
+    return out
+
+
 def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
     """Roofline object of the smoothing kernel with the largest share of the
-    profiled smoothing time (per-pair CUDA events recorded by the library)."""
+    profiled smoothing time (per-pair CUDA events recorded by the library):
+    algorithmic bytes of its launches over their event time."""
     groups = {}
-    for k, pair in enumerate(kernels):
+    for k, (name, bpv) in enumerate(pair_kernels(sc, kernels, st["smooth_kernel_pair"])):
         n_l = st["smooth_launches_pair"][k]
         if n_l == 0:
             continue
-        g = groups.setdefault(smoothing_kernel_name(sc, pair, st["smooth_kernel_pair"][k]), [0.0, 0])
+        g = groups.setdefault(name, [0.0, 0, 0.0])
         g[0] += st["ms_smooth_pair"][k]
         g[1] += n_l
+        g[2] += bpv * voxels_per_launch * n_l
     dom = max(groups, key=lambda name: groups[name][0])
-    dom_ms, dom_launches = groups[dom]
+    dom_ms, dom_launches, dom_bytes = groups[dom]
     avg_ms = dom_ms / dom_launches
-    achieved = SMOOTH_BYTES_PER_VOXEL * voxels_per_launch / (avg_ms * 1e-3) / 1e9
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     tr = smooth_traffic_record()
     dram = tr["kernels"].get(dom) if tr else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": dram * voxels_per_launch if dram is not None else None,
             "kernel": dom, "launch_ms": avg_ms, "share_of_smoothing": dom_ms / max(1e-9, st["ms_smooth"]),
-            "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": SMOOTH_BYTES_PER_VOXEL,
+            "peak_kind": peak_kind, "algorithmic_bytes_per_voxel": dom_bytes / (voxels_per_launch * dom_launches),
             "smoothing_ms_by_kernel": {name: round(v[0] / steps, 3) for name, v in groups.items()}}
 
 
-def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world, mode="mad"):
-    """End to end through sc_run from pinned host memory: every step copies its
-    cube host -> device and its mask device -> host; with two device buffers
-    the next cube's copy and the previous mask's copy run on a copy stream
-    while the current step computes. The sigmas come back synchronously."""
+def pipelined_e2e(ctx, inputs, run_fn, nvox, nk, e2e_steps, pg, dev, world, api):
+    """End to end from pinned host memory: every step copies its inputs host
+    -> device and its mask device -> host; with two device buffer sets the next
+    step's inputs and the previous mask travel on a copy stream while the
+    current step computes (events order them). run_fn(device_inputs, mask)
+    enqueues one run without sigma pointers; each step's sigmas are collected
+    with sc_copy_sigmas into pinned host memory, in stream order (no
+    synchronisation per step), and checked after the timed region."""
     import torch
 
-    cube_h = torch.empty(cube.shape, dtype=torch.float32, pin_memory=True)
-    cube_h.copy_(cube)
-    mask_h = [torch.empty(cube.shape, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-    bufs = [torch.empty_like(cube) for _ in range(2)]
-    masks = [torch.empty(cube.shape, dtype=torch.uint8, device=dev) for _ in range(2)]
+    hosts = []
+    for x in inputs:
+        h = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        h.copy_(x)
+        hosts.append(h)
+    sig_h = [torch.empty(nk + 1, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+    shape = inputs[0].shape
+    mask_h = [torch.empty(shape, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+    bufs = [[torch.empty_like(x) for x in inputs] for _ in range(2)]
+    masks = [torch.empty(shape, dtype=torch.uint8, device=dev) for _ in range(2)]
     compute = torch.cuda.current_stream(dev)
     copy = torch.cuda.Stream(dev)
     loaded = [torch.cuda.Event() for _ in range(2)]
     computed = [torch.cuda.Event() for _ in range(2)]
     sent = [torch.cuda.Event() for _ in range(2)]
 
+    def load(b):
+        for d, h in zip(bufs[b], hosts):
+            d.copy_(h, non_blocking=True)
+
     def run(steps):
         with torch.cuda.stream(copy):
-            bufs[0].copy_(cube_h, non_blocking=True)
+            load(0)
             loaded[0].record(copy)
         for i in range(steps):
             b, nb = i % 2, (i + 1) % 2
             if i + 1 < steps:
                 with torch.cuda.stream(copy):
                     if i >= 1:
-                        copy.wait_event(computed[nb])  # step i - 1 is done with that buffer
-                    bufs[nb].copy_(cube_h, non_blocking=True)
+                        copy.wait_event(computed[nb])  # step i - 1 is done with that buffer set
+                    load(nb)
                     loaded[nb].record(copy)
             compute.wait_event(loaded[b])
             if i >= 2:
                 compute.wait_event(sent[b])  # its mask of step i - 2 has left the device
-            ctx.run(bufs[b], kernels, t, mode, n_repl, mask=masks[b])  # sigmas: synchronous
+            run_fn(bufs[b], masks[b])
+            ctx.copy_sigmas(sig_h[b][:nk], sig_h[b][nk:], nk)  # stream-ordered, into pinned memory
             computed[b].record(compute)
             with torch.cuda.stream(copy):
                 copy.wait_event(computed[b])
@@ -391,33 +481,27 @@ def pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world, mode="mad
     if pg:
         pg.barrier()
     t0 = time.perf_counter()
-    run(args.e2e_steps)
+    run(e2e_steps)
     dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
-    nvox = cube.numel()
-    return {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
-            "h2d_bytes_per_step": nvox * 4, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1),
-            "steps": args.e2e_steps,
-            "api": "sc_run on device copies of a pinned host cube; next cube's H2D and previous mask's D2H overlap "
-                   "the current step on a copy stream (two device buffers); sigmas read back synchronously"}
+    ok = all(float(x) > 0 for x in sig_h[(e2e_steps - 1) % 2])
+    return {"value": job_value(nvox, nk, e2e_steps, world, dt), "unit": UNIT,
+            "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in inputs),
+            "d2h_bytes_per_step": nvox + 4 * (nk + 1), "steps": e2e_steps, "sigmas_ok": ok,
+            "api": api + ", the copies made by torch; next step's H2D and previous mask's D2H overlap the current "
+                         "step on a copy stream (two device buffer sets); sigmas collected with sc_copy_sigmas into "
+                         "pinned memory, no per-step synchronisation"}
 
 
-def run_batch_bench(args, rank, world, local):
+def measure_batch(dev, local, steps, warmup, pg, world, rank, tune=True, with_e2e=False, e2e_steps=3):
     """The batched form: 64 uneven sub-cubes per rank in one graph-captured
-    sc_run_batch call per step, after autotuning every sub-cube shape."""
+    sc_run_batch call per step (optionally after autotuning every sub-cube
+    shape). Timed without profiling events; the roofline comes from one more,
+    profiled, batch (events per pair, no graph)."""
     import torch
 
     from paper_2106_15789_gb300 import Context, sc
     from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, batch_specs, make_cube
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
-    sc.lib()
     kernels, t, n_repl = KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT
     with torch.no_grad():
         cubes = [make_cube(spec, device=str(dev)) for spec in batch_specs(64, first_seed=64 * rank)]
@@ -426,14 +510,15 @@ def run_batch_bench(args, rank, world, local):
     ctx = Context(local, max(c.numel() for c in cubes))
     stream = torch.cuda.current_stream(dev)
     t0 = time.perf_counter()
-    for shape in sorted({tuple(c.shape) for c in cubes}):
-        ctx.autotune(shape, kernels)
+    if tune:
+        for shape in sorted({tuple(c.shape) for c in cubes}):
+            ctx.autotune(shape, kernels)
     tune_s = time.perf_counter() - t0
 
     def step():
         return ctx.run_batch(cubes, kernels, t, "mad", n_repl, masks=masks, flags=sc.SC_FLAG_GRAPH)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(2, warmup)):
         step()
     torch.cuda.synchronize()
     ctx.stats(reset=True)
@@ -444,7 +529,7 @@ def run_batch_bench(args, rank, world, local):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -453,9 +538,8 @@ def run_batch_bench(args, rank, world, local):
     sampler.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
     launches = int(ctx.stats(reset=True)["launches"])
-    value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
+    value = job_value(nvox, len(kernels), steps, world, ms * 1e-3)
 
-    # roofline: one more batch without the graph, with per-pair CUDA events
     ctx.set_profiling(True)
     ctx.run_batch(cubes, kernels, t, "mad", n_repl, masks=masks)
     torch.cuda.synchronize()
@@ -465,8 +549,27 @@ def run_batch_bench(args, rank, world, local):
     roofline = dominant_kernel(sc, kernels, st, nvox / len(cubes), 1, peak, peak_kind)
     roofline["measured_in"] = "one profiled batch after the timed region (events per pair, no graph)"
 
+    # the plain path on the same sub-cubes: one sc_run per cube, in sequence
+    def plain_all():
+        for c, m in zip(cubes, masks):
+            ctx.run(c, kernels, t, "mad", n_repl, mask=m)
+
+    plain_all()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(steps):
+        plain_all()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = max_over_ranks(p0.elapsed_time(p1), pg, dev)
+    plain_seq = {"value": job_value(nvox, len(kernels), steps, world, ms_plain * 1e-3),
+                 "ms_per_step": ms_plain / steps,
+                 "what": "the same 64 sub-cubes through sc_run one after the other (plain float32 path, sigmas "
+                         "read back per cube)"}
+
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         # pinned host sub-cubes; two device buffer sets so that the next
         # batch's H2D copies and the previous batch's mask D2H copies run on a
         # copy stream while the current batch computes
@@ -481,14 +584,14 @@ def run_batch_bench(args, rank, world, local):
         computed = [torch.cuda.Event() for _ in range(2)]
         sent = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_run(steps):
+        def e2e_run(n):
             with torch.cuda.stream(copy):
                 for w, h in zip(work[0], hosts):
                     w.copy_(h, non_blocking=True)
                 loaded[0].record(copy)
-            for i in range(steps):
+            for i in range(n):
                 b, nb = i % 2, (i + 1) % 2
-                if i + 1 < steps:
+                if i + 1 < n:
                     with torch.cuda.stream(copy):
                         if i >= 1:
                             copy.wait_event(computed[nb])
@@ -511,43 +614,31 @@ def run_batch_bench(args, rank, world, local):
         if pg:
             pg.barrier()
         t0 = time.perf_counter()
-        e2e_run(args.e2e_steps)
+        e2e_run(e2e_steps)
         dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
-        e2e = {"value": job_value(nvox, len(kernels), args.e2e_steps, world, dt), "unit": UNIT,
+        e2e = {"value": job_value(nvox, len(kernels), e2e_steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": 4 * nvox, "d2h_bytes_per_step": nvox + 8 * len(cubes) * (len(kernels) + 1),
-               "steps": args.e2e_steps,
-               "api": "sc_run_batch on device copies of pinned host sub-cubes; next batch's H2D and previous masks' "
-                      "D2H overlap the current batch on a copy stream (two buffer sets); sigmas read back synchronously"}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {**config_dict("batch64", kernels), "n_cubes": len(cubes), "voxels": nvox,
-                           "graph": True, "autotune_s": round(tune_s, 2)},
-                "roofline": roofline, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches,
-                "clocks": sampler.summary(),
-                "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
-        print(json.dumps(line), flush=True)
+               "steps": e2e_steps,
+               "api": "sc_run_batch on device copies of pinned host sub-cubes (torch copies); next batch's H2D and "
+                      "previous masks' D2H overlap the current batch on a copy stream (two buffer sets); sigmas read "
+                      "back synchronously"}
     ctx.close()
-    if pg:
-        pg.destroy_process_group()
-    return 0
+    del cubes, masks
+    torch.cuda.empty_cache()
+    peak, _ = measured_hbm_peak()
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": max(2, warmup),
+            "config": {**config_dict("batch64", kernels), "n_cubes": 64, "voxels": nvox, "graph": True,
+                       "autotune_s": round(tune_s, 2) if tune else None},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
+            "plain_sequential": plain_seq, "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
 
 
-def run_half_bench(args, rank, world, local):
-    """The precision form: the cube stored in 16 bits with per-channel float32
-    scales, run through sc_run_half; reports throughput and the sigma / mask
-    differences against plain float32 (and against the FP64 oracle for the
-    small cube)."""
-    import numpy as np
+def run_batch_bench(args, rank, world, local):
+    """The batched form as a bench line of its own."""
     import torch
 
-    from paper_2106_15789_gb300 import Context, sc
-    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, decode_half, encode_half
+    from paper_2106_15789_gb300 import sc
 
-    base, fmt = args.workload.split("-")
-    bf16 = fmt == "bf16"
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pg = None
@@ -557,71 +648,144 @@ def run_half_bench(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
     sc.lib()
+    r = measure_batch(dev, local, args.steps, args.warmup, pg, world, rank, tune=True, with_e2e=not args.no_e2e,
+                      e2e_steps=args.e2e_steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": r["config"],
+                "roofline": r["roofline"], "cpu_baseline": None, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+                "clocks": r["clocks"], "frac_of_19B_model": r["frac_of_19B_model"]}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def half_precision(cube, bits, scale, bf16, m_h, sig_h, s0_h, m_f, sig_f, s0_f, with_oracle):
+    """Differences of a 16-bit run against float32 on the GPU and, for cubes
+    small enough, against the FP64 oracle on the original float32 cube and on
+    the decoded 16-bit cube."""
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, decode_half
+
+    nvox = cube.numel()
+    nd = int((m_h != m_f).sum().item())
+    prec = {"format": "bf16" if bf16 else "fp16",
+            "sigma_rel_err_vs_float32": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h], sig_f + [s0_f])),
+            "mask_disagreement_vs_float32": nd, "mask_disagreement_frac_vs_float32": nd / nvox}
+    if with_oracle:
+        from oracle.sc_oracle import sc_filter
+
+        kernels, t, n_repl = KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT
+        m_o, s_o, s0_o = sc_filter(cube.cpu().numpy(), kernels, t, "mad", n_repl)
+        dec = decode_half(bits.cpu().numpy(), scale.cpu().numpy(), bf16)
+        m_d, s_d, s0_d = sc_filter(dec, kernels, t, "mad", n_repl)
+        mh = m_h.cpu().numpy()
+        no = int((mh != m_o).sum())
+        prec.update({"sigma_rel_err_vs_oracle_fp64": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h], s_o + [s0_o])),
+                     "mask_disagreement_vs_oracle_fp64": no, "mask_disagreement_frac_vs_oracle_fp64": no / nvox,
+                     "sigma_rel_err_vs_oracle_on_decoded": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h],
+                                                                                               s_d + [s0_d])),
+                     "mask_disagreement_vs_oracle_on_decoded": int((mh != m_d).sum())})
+    return prec
+
+
+def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None, with_oracle=False, e2e_steps=0):
+    """The precision form on one cube: stored in 16 bits with per-channel
+    float32 scales, run through sc_run_half; timed without profiling events,
+    then one profiled step for the roofline; differences against float32
+    (ref = its mask and sigmas, computed here when not given)."""
+    import torch
+
+    from paper_2106_15789_gb300 import sc
+    from synth.cubes import KERNELS_12, SC_REPLACEMENT, SC_THRESHOLD, encode_half
+
     kernels, t, n_repl = KERNELS_12, SC_THRESHOLD, SC_REPLACEMENT
-    spec, cube = make_workload(base, rank, str(dev))
     bits, scale = encode_half(cube, bf16)
     nvox = cube.numel()
     mask = torch.empty(cube.shape, dtype=torch.uint8, device=dev)
-    ctx = Context(local, nvox)
     stream = torch.cuda.current_stream(dev)
 
     def step():
         return ctx.run_half(bits, bf16, scale, kernels, t, "mad", n_repl, mask=mask)
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(2, warmup)):
         step()
     torch.cuda.synchronize()
     ctx.stats(reset=True)
-    ctx.set_profiling(True)
     sampler = ClockSampler(local)
     sampler.start()
     if pg:
         pg.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         m_h, sig_h, s0_h = step()
     e1.record(stream)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
     sampler.stop()
-    ctx.set_profiling(False)
     ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    launches = int(ctx.stats(reset=True)["launches"])
+    value = job_value(nvox, len(kernels), steps, world, ms * 1e-3)
+    ctx.set_profiling(True)
+    step()
+    torch.cuda.synchronize()
+    ctx.set_profiling(False)
     st = ctx.stats(reset=True)
-    value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
     peak, peak_kind = measured_hbm_peak()
-    roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
-
-    # precision: the same cube in float32 on the GPU, and (small cube) the oracle
+    roofline = dominant_kernel(sc, kernels, st, nvox, 1, peak, peak_kind)
+    roofline["measured_in"] = "one profiled step after the timed region"
     m_h = m_h.clone()
-    m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
-    prec = {"format": fmt, "sigma_rel_err_vs_float32": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h],
-                                                                                            sig_f + [s0_f])),
-            "mask_disagreement_vs_float32": int((m_h != m_f).sum().item()),
-            "mask_disagreement_frac_vs_float32": float((m_h != m_f).sum().item()) / nvox}
-    if base == "small":
-        from oracle.sc_oracle import sc_filter
+    e2e = None
+    if e2e_steps:
+        e2e = pipelined_e2e(
+            ctx, [bits, scale],
+            lambda ins, m: ctx.run_half(ins[0], bf16, ins[1], kernels, t, "mad", n_repl, mask=m, want_sigma=False),
+            nvox, len(kernels), e2e_steps, pg, dev, world,
+            "sc_run_half on device copies of the pinned 16-bit cube and its per-channel scales")
+    if ref is None:
+        m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
+        ref = (m_f.clone(), sig_f, s0_f)
+    prec = half_precision(cube, bits, scale, bf16, m_h, sig_h, s0_h, *ref, with_oracle)
+    del bits, scale, mask
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": max(2, warmup),
+            "dtype": "bf16" if bf16 else "fp16", "roofline": roofline, "gpu_launches": launches, "e2e": e2e,
+            "clocks": sampler.summary(), "precision": prec,
+            "breakdown_ms_per_step": {"smooth": st["ms_smooth"] + st["ms_share_prep"], "select": st["ms_select"],
+                                      "decode_and_mask": st["ms_clip"]},
+            "frac_of_17B_model": value / world * 17.0 / (peak * 1e9)}
 
-        m_o, s_o, s0_o = sc_filter(cube.cpu().numpy(), kernels, t, "mad", n_repl)
-        dec = decode_half(bits.cpu().numpy(), scale.cpu().numpy(), bf16)
-        m_d, s_d, s0_d = sc_filter(dec, kernels, t, "mad", n_repl)
-        mh = m_h.cpu().numpy()
-        prec.update({"sigma_rel_err_vs_oracle_fp64": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h], s_o + [s0_o])),
-                     "mask_disagreement_vs_oracle_fp64": int((mh != m_o).sum()),
-                     "sigma_rel_err_vs_oracle_on_decoded": max(abs(a - b) / b for a, b in zip(sig_h + [s0_h],
-                                                                                               s_d + [s0_d])),
-                     "mask_disagreement_vs_oracle_on_decoded": int((mh != m_d).sum())})
+
+def run_half_bench(args, rank, world, local):
+    """The precision form as a bench line of its own (small or WALLABY cube)."""
+    import torch
+
+    from paper_2106_15789_gb300 import Context, sc
+    from synth.cubes import KERNELS_12
+
+    base, fmt = args.workload.split("-")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sc.lib()
+    spec, cube = make_workload(base, rank, str(dev))
+    ctx = Context(local, cube.numel())
+    r = measure_half(ctx, cube, fmt == "bf16", args.steps, args.warmup, local, pg, world, dev,
+                     with_oracle=(base == "small"))
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": fmt, "data": "synthetic",
-                "config": {**config_dict(args.workload, kernels), "storage_bytes_per_voxel": 2},
-                "roofline": roofline, "cpu_baseline": None, "e2e": None, "gpu_launches": int(st["launches"]),
-                "clocks": sampler.summary(), "precision": prec,
-                "breakdown_ms_per_step": {"smooth": st["ms_smooth"] / args.steps,
-                                          "select": st["ms_select"] / args.steps,
-                                          "decode_and_mask": st["ms_clip"] / args.steps}}
+                "config": {**config_dict(args.workload, KERNELS_12), "storage_bytes_per_voxel": 2},
+                "roofline": r["roofline"], "cpu_baseline": None, "e2e": None, "gpu_launches": r["gpu_launches"],
+                "clocks": r["clocks"], "precision": r["precision"], "breakdown_ms_per_step": r["breakdown_ms_per_step"]}
         print(json.dumps(line), flush=True)
     ctx.close()
     if pg:
@@ -1027,9 +1191,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--record-traffic", metavar="NCU_CSV",
-                    help="write profiles/smooth_traffic.json from an ncu --csv DRAM capture of the medium workload "
-                         "and exit (no GPU)")
+    ap.add_argument("--ref-cube", choices=("wallaby", "small"), default="wallaby",
+                    help="cube whose interior sub-cubes the reference arm times (small: a quick check)")
+    ap.add_argument("--no-forms", action="store_true", help="default workload: skip the batched and 16-bit forms")
+    ap.add_argument("--record-traffic", metavar="KEY=NCU_CSV", nargs="+",
+                    help="write profiles/smooth_traffic.json from one-kernel ncu --csv DRAM captures of the medium "
+                         "workload and exit (no GPU)")
     ap.add_argument("--traffic-command", default="", help="the command that made NCU_CSV (stored in the record)")
     args = ap.parse_args()
     if args.record_traffic:
@@ -1084,40 +1251,77 @@ def main():
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
-    ctx.stats(reset=True)
-    ctx.set_profiling(True)
+
+    def timed(profiled):
+        """K steps between CUDA events on the launching stream (barrier and
+        synchronisation on both sides); returns ms and the library's stats."""
+        ctx.stats(reset=True)
+        ctx.set_profiling(profiled)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        ctx.set_profiling(False)
+        return max_over_ranks(e0.elapsed_time(e1), pg, dev), ctx.stats(reset=True), out
+
     sampler = ClockSampler(local)
     sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        _, sig, sig0 = step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if pg:
-        pg.barrier()
+    ms, st_plain, (_, sig, sig0) = timed(False)  # the headline: no profiling events
     sampler.stop()
-    ctx.set_profiling(False)
-    ms = max_over_ranks(e0.elapsed_time(e1), pg, dev)
-    st = ctx.stats(reset=True)
+    # the same steps again with the library's per-phase CUDA events, for the
+    # per-kernel times of the roofline and the breakdown
+    ms_prof, st, _ = timed(True)
     value = job_value(nvox, len(kernels), args.steps, world, ms * 1e-3)
 
     # roofline of the dominant kernel: the smoothing kernel with the largest
-    # share of device time in the timed region (live events, grouped by the
-    # kernel each pair runs)
+    # share of device time (live events, grouped by the kernel each pair runs)
     peak, peak_kind = measured_hbm_peak()
     roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
+    roofline["measured_in"] = "the profiled repeat of the timed steps (per-pair CUDA events on the launching stream)"
+    mask_f32 = mask.clone() if not args.no_forms and world == 1 and mode == "mad" else None
 
     e2e = None
     if not args.no_e2e:
-        e2e = pipelined_e2e(ctx, cube, kernels, t, n_repl, args, pg, dev, world, mode)
+        e2e = pipelined_e2e(ctx, [cube], lambda ins, m: ctx.run(ins[0], kernels, t, mode, n_repl, mask=m,
+                                                                  want_sigma=False),
+                            nvox, len(kernels), args.e2e_steps, pg, dev, world,
+                            "sc_run on device copies of a pinned host cube")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cube, kernels, t, n_repl, mode)
+
+    forms = None
+    if mask_f32 is not None:
+        # the metric's second half: the 16-bit forms of the same cube on the same
+        # context, the 16-bit forms of the small cube against the FP64 oracle,
+        # and the batched form, each timed like the headline (fewer steps)
+        from synth.cubes import SMALL, make_cube
+
+        fs = max(2, min(args.steps, 3))
+        forms = {}
+        for fmt in ("fp16", "bf16"):
+            forms["wallaby-" + fmt] = measure_half(ctx, cube, fmt == "bf16", fs, 2, local, pg, world, dev,
+                                                   ref=(mask_f32, sig, sig0), e2e_steps=0 if args.no_e2e else args.e2e_steps)
+        with torch.no_grad():
+            small = make_cube(SMALL, device=str(dev))
+        sctx = Context(local, small.numel())
+        for fmt in ("fp16", "bf16"):
+            r = measure_half(sctx, small, fmt == "bf16", 3, 2, local, pg, world, dev, with_oracle=True)
+            forms["small-" + fmt] = {"precision": r["precision"], "value": r["value"], "unit": UNIT}
+        sctx.close()
+        ctx.close()
+        ctx = None
+        del cube, mask_f32
+        torch.cuda.empty_cache()
+        forms["batch64"] = measure_batch(dev, local, fs, 2, pg, world, rank, tune=False)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -1125,8 +1329,10 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {**config_dict(args.workload, kernels, mode), "autotune_s": round(tune_s, 2)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(st["launches"]), "clocks": sampler.summary(),
+                "gpu_launches": int(st_plain["launches"]), "clocks": sampler.summary(),
+                "profiled_ms_per_step": ms_prof / args.steps,
                 "breakdown_ms_per_step": {"smooth": st["ms_smooth"] / args.steps,
+                                          "share_prep": st["ms_share_prep"] / args.steps,
                                           "select": st["ms_select"] / args.steps,
                                           "clip": st["ms_clip"] / args.steps,
                                           **({"gauss_hist": st["ms_gauss_hist"] / args.steps,
@@ -1134,9 +1340,11 @@ def main():
                                              else {})},
                 **({"roofline_gauss_hist": gauss_hist_roofline(st, peak, peak_kind)} if mode == "gauss" else {}),
                 "sigma0": sig0, "sigmas": sig, "mask_fraction": float(mask.float().mean().item()),
-                "frac_of_19B_model": value / world * 19.0 / (peak * 1e9)}
+                "frac_of_19B_model": value / world * 19.0 / (peak * 1e9),
+                **({"forms": forms} if forms else {})}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if pg:
         pg.destroy_process_group()
     return 0

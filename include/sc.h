@@ -128,6 +128,9 @@ typedef struct {
   double ms_gauss_hist;    /* SC_NOISE_GAUSS: device time of the 256-bin histogram passes (while profiling) */
   double ms_gauss_fit;     /* SC_NOISE_GAUSS: device time of the least-squares fits (while profiling) */
   uint64_t gauss_hist_values; /* values those histogram passes read */
+  double ms_share_prep;    /* shared spatial passes: device time of the correction lists and of the gated
+                              full-kernel launch, which holds the pair's smoothing when its list was over the
+                              cap (while profiling; not in ms_smooth) */
 } sc_stats;
 
 /* Create a context on CUDA device `device` with workspace for cubes of up to

@@ -147,7 +147,7 @@ cudaEvent_t take_event(sc_ctx* c) {
 }
 
 enum { EV_SMOOTH = 0, EV_SELECT = 1, EV_CLIP = 2, EV_NOISE_WINDOW = 3, EV_NOISE_APPLY = 4, EV_GAUSS_HIST = 5,
-       EV_GAUSS_FIT = 6 };
+       EV_GAUSS_FIT = 6, EV_SHARE_PREP = 7 };
 
 struct Phase {
   sc_ctx* c;
@@ -194,6 +194,8 @@ void flush_events(sc_ctx* c) {
     } else if (e.kind == EV_GAUSS_HIST) {
       c->stats.ms_gauss_hist += ms;
       c->stats.gauss_hist_values += e.voxels;
+    } else if (e.kind == EV_SHARE_PREP) {
+      c->stats.ms_share_prep += ms;
     } else if (e.kind == EV_GAUSS_FIT) {
       c->stats.ms_gauss_fit += ms;
     } else {
@@ -308,14 +310,18 @@ void apply_tuning(sc_ctx* c, const int64_t* dims, SmoothArgs* a) {
   a->tune_zfactor = it->second[1];
 }
 
-// Buffers of the shared spatial passes for a cube of these dimensions
-// (allocated or grown here; never inside a stream capture).
-int ensure_share(sc_ctx* c, const int64_t* dims) {
+// Sizes of the shared-pass buffers a cube needs: its spatial sums (an even
+// pitch: 16-byte aligned rows for TMA) and its buckets (those of the smaller
+// tile height, 16 rows, bound those of both heights).
+void share_needs(const int64_t* dims, size_t* need_p, size_t* need_bk) {
   const long long nx = dims[0], ny = dims[1], nz = dims[2];
-  const long long pitch = (nx + 1) & ~1LL;  // an even pitch: 16-byte aligned rows for TMA
-  const size_t need_p = (size_t)pitch * ny * nz;
-  // buckets of the smaller tile height (16 rows) bound those of both heights
-  const size_t need_bk = (size_t)((nx + 63) / 64) * ((ny + 15) / 16) * nz + 1;
+  *need_p = (size_t)((nx + 1) & ~1LL) * ny * nz;
+  *need_bk = (size_t)((nx + 63) / 64) * ((ny + 15) / 16) * nz + 1;
+}
+
+// Buffers of the shared spatial passes for these sizes (allocated or grown
+// here; never inside a stream capture).
+int ensure_share_sized(sc_ctx* c, size_t need_p, size_t need_bk) {
   const bool fits = c->sh_P_cap >= need_p && c->sh_bk_cap >= need_bk && c->sh_ent && c->sh_snap && c->sh_ss;
   if (fits) return SC_OK;
   if (c->capturing) return SC_ERR_BUDGET;
@@ -365,6 +371,12 @@ int ensure_share(sc_ctx* c, const int64_t* dims) {
     c->sh_bk_cap = need_bk;
   }
   return SC_OK;
+}
+
+int ensure_share(sc_ctx* c, const int64_t* dims) {
+  size_t need_p = 0, need_bk = 0;
+  share_needs(dims, &need_p, &need_bk);
+  return ensure_share_sized(c, need_p, need_bk);
 }
 
 bool same_spatial(const PairDesc& a, const PairDesc& b) {
@@ -456,7 +468,6 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     }
     if (share_mode != 2) p_owner = -1;
     if (share_mode == 2) {
-      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
       ShareArgs sh{};
       sh.P = c->sh_P;
       sh.pitch = (dims[0] + 1) & ~1LL;
@@ -474,24 +485,28 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       sh.tiles_x = (int)((dims[0] + 63) / 64);
       sh.tiles_y = (int)((dims[1] + sh.ty - 1) / sh.ty);
       sh.n_buckets = (long long)sh.tiles_x * sh.tiles_y * dims[2];
-      CK(cudaMemsetAsync(c->sh_ss, 0, sizeof(ShareState), s));
-      if (a.repl_possible) {
-        // voxels masked since the spatial sums were made, listed per bucket
-        if (!share_cnt_clear) {
-          CK(cudaMemsetAsync(c->sh_cnt, 0, sizeof(unsigned) * (size_t)(sh.n_buckets + 1), s));
-          share_cnt_clear = true;
+      {  // the correction lists, and the full kernel gated on their size
+        Phase ph(c, s, EV_SHARE_PREP);
+        CK(cudaMemsetAsync(c->sh_ss, 0, sizeof(ShareState), s));
+        if (a.repl_possible) {
+          // voxels masked since the spatial sums were made, listed per bucket
+          if (!share_cnt_clear) {
+            CK(cudaMemsetAsync(c->sh_cnt, 0, sizeof(unsigned) * c->sh_bk_cap, s));  // both tile heights
+            share_cnt_clear = true;
+          }
+          sh.offs = c->sh_offs;
+          CK(launch_share_prep(a, sh, c->sms, s));
+          c->stats.launches += 4;
         }
-        sh.offs = c->sh_offs;
-        CK(launch_share_prep(a, sh, c->sms, s));
-        c->stats.launches += 4;
+        // the full kernel, run only if the list overflowed
+        SmoothArgs full = a;
+        full.gate = &c->sh_ss->overflow;
+        full.tune_kind = TUNE_AUTO;
+        int l = 0, code = SC_KERNEL_NONE;
+        CK(launch_smooth(full, c->sms, s, &l, &code));
+        c->stats.launches += l;
       }
-      // the full kernel, run only if the list overflowed
-      SmoothArgs full = a;
-      full.gate = &c->sh_ss->overflow;
-      full.tune_kind = TUNE_AUTO;
-      int l = 0, code = SC_KERNEL_NONE;
-      CK(launch_smooth(full, c->sms, s, &l, &code));
-      c->stats.launches += l;
+      Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
       bool done = false;
       CK(launch_smooth_p(a, sh, c->sms, s, &done));
       if (!done) return SC_ERR_INTERNAL;
@@ -787,6 +802,18 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
   int rc_lanes = ensure_lanes(c);
   if (rc_lanes) return rc_lanes;
   const int n_lanes = (int)std::min<size_t>(c->lanes.size(), (size_t)n_cubes);
+  if (!(flags & (SC_FLAG_NO_SHARE | SC_FLAG_GENERIC))) {
+    // shared-pass buffers for the largest cube, made before any capture (a
+    // lane that cannot get them smooths every pair in full)
+    size_t mp = 0, mb = 0;
+    for (int i = 0; i < n_cubes; ++i) {
+      size_t p = 0, b = 0;
+      share_needs(dims + 3 * i, &p, &b);
+      mp = std::max(mp, p);
+      mb = std::max(mb, b);
+    }
+    for (int l = 0; l < n_lanes; ++l) ensure_share_sized(c->lanes[l], mp, mb);
+  }
   // Cube i runs on lane i % n_lanes; the lanes' streams fork from q and join
   // back into it, so cubes on different lanes overlap.
   auto enqueue = [&](cudaStream_t q) -> int {

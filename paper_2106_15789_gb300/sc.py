@@ -69,7 +69,7 @@ class sc_stats(C.Structure):
                 ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS),
                 ("smooth_kernel_pair", C.c_int32 * SC_MAX_KERNELS), ("ms_noise_window", C.c_double),
                 ("ms_noise_apply", C.c_double), ("ms_gauss_hist", C.c_double), ("ms_gauss_fit", C.c_double),
-                ("gauss_hist_values", C.c_uint64)]
+                ("gauss_hist_values", C.c_uint64), ("ms_share_prep", C.c_double)]
 
 
 class ScError(RuntimeError):

@@ -13,8 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 @pytest.mark.parametrize("workload", ["wallaby", "wallaby-gauss"])
 def test_reference_arm_line(workload):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--workload", workload], capture_output=True, text=True, cwd=ROOT,
-                       timeout=600)
+                        "--warmup", "0", "--workload", workload, "--ref-cube", "small"], capture_output=True,
+                       text=True, cwd=ROOT, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -26,3 +26,4 @@ def test_reference_arm_line(workload):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["noise"] == ("gauss" if workload.endswith("-gauss") else "mad")
+    assert d["cpu_baseline"]["cores"] >= 1 and "sub-cubes" in d["cpu_baseline"]["sample"]

@@ -1,6 +1,7 @@
-"""CPU checks of bench.py's host-side helpers: kernel-name grouping of ncu
-launch lists, the DRAM-traffic record, the roofline arithmetic of the dominant
-smoothing kernel and of the Gaussian-fit histogram pass."""
+"""CPU checks of bench.py's host-side helpers: the DRAM-traffic record, the
+per-pair kernel names and algorithmic bytes, the roofline arithmetic of the
+dominant smoothing kernel and of the Gaussian-fit histogram pass, and the
+sub-cubes of the CPU baseline."""
 import csv
 import json
 import os
@@ -10,16 +11,6 @@ import pytest
 import bench
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
-
-def test_kernel_key_grouping():
-    k = bench.ncu_kernel_key
-    assert k("void sc::k_smooth_ws<5, 5, 5, true, true, 32>(sc::SmoothArgs)") == "k_smooth_ws<5,5,5>"
-    assert k("void sc::k_smooth_ws<1, 3, 3, true, false, 16>(sc::SmoothArgs)") == "k_smooth_ws<1,3,3>/16"
-    assert k("void sc::k_smooth_tile<7, 9, 9, true>(sc::SmoothArgs)") == "k_smooth_tile<7,9,9>"
-    assert k("void sc::k_smooth_z<4, 1, 1, 512>(sc::SmoothArgs)") == "k_smooth_z"
-    assert k("sc::k_smooth_generic(sc::SmoothArgs)") == "k_smooth_generic"
-    assert k("void sc::k_pass2(const float *, long long)") is None
 
 
 def test_committed_traffic_record_matches_the_sources():
@@ -35,8 +26,9 @@ def test_committed_traffic_record_matches_the_sources():
 
 
 def test_record_traffic_means(tmp_path, monkeypatch):
-    """Two launches of one kernel (read + write in MB and GB), one of another,
-    and a kernel that is not a smoothing kernel: mean bytes per voxel."""
+    """One-kernel captures: two launches of one kernel (read + write in MB
+    and GB, a time metric that is ignored), one launch of another; mean
+    bytes per voxel of each key."""
     head = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
             "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
     nv = bench.TRAFFIC_WORKLOAD_VOXELS
@@ -45,28 +37,29 @@ def test_record_traffic_means(tmp_path, monkeypatch):
         return [str(i), "1", "python", "h", name, "1", "7", "(512,1,1)", "(152,1,1)", "0", "10.3", "Command line",
                 metric, unit, value]
 
-    ws = "void sc::k_smooth_ws<5, 5, 5, true, true, 32>(sc::SmoothArgs)"
+    p = "void sc::k_smooth_p<32, 6>(CUtensorMap_st, sc::SmoothArgs, sc::ShareArgs)"
     z = "void sc::k_smooth_z<4, 1, 1, 512>(sc::SmoothArgs)"
-    rows = [head,
-            row(0, ws, "dram__bytes_read.sum", "Mbyte", f"{4.0 * nv / 1e6:,.6f}"),
-            row(0, ws, "dram__bytes_write.sum", "Mbyte", f"{4.0 * nv / 1e6:,.6f}"),
-            row(1, ws, "dram__bytes_read.sum", "Gbyte", f"{4.2 * nv / 1e9:.9f}"),
-            row(1, ws, "dram__bytes_write.sum", "Gbyte", f"{4.0 * nv / 1e9:.9f}"),
-            row(1, ws, "gpu__time_duration.sum", "usecond", "1000"),
-            row(2, z, "dram__bytes_read.sum", "byte", str(int(4.1 * nv))),
-            row(2, z, "dram__bytes_write.sum", "byte", str(int(3.9 * nv))),
-            row(3, "void sc::k_pass2(const float *)", "dram__bytes_read.sum", "Mbyte", "537")]
-    src = tmp_path / "t.csv"
-    with open(src, "w", newline="") as f:
-        csv.writer(f).writerows(rows)
+    a = [head,
+         row(0, p, "dram__bytes_read.sum", "Mbyte", f"{8.0 * nv / 1e6:,.6f}"),
+         row(0, p, "dram__bytes_write.sum", "Mbyte", f"{4.0 * nv / 1e6:,.6f}"),
+         row(1, p, "dram__bytes_read.sum", "Gbyte", f"{8.2 * nv / 1e9:.9f}"),
+         row(1, p, "dram__bytes_write.sum", "Gbyte", f"{4.0 * nv / 1e9:.9f}"),
+         row(1, p, "gpu__time_duration.sum", "usecond", "1000")]
+    b = [head,
+         row(0, z, "dram__bytes_read.sum", "byte", str(int(4.1 * nv))),
+         row(0, z, "dram__bytes_write.sum", "byte", str(int(3.9 * nv)))]
+    for name, rows in (("p.csv", a), ("z.csv", b)):
+        with open(tmp_path / name, "w", newline="") as f:
+            csv.writer(f).writerows(rows)
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "smooth_source_hash", lambda: "0123456789abcdef")
-    assert bench.record_traffic(str(src), "cmd") == 0
+    specs = [f"k_smooth_p<5,5,5>={tmp_path / 'p.csv'}", f"k_smooth_z={tmp_path / 'z.csv'}"]
+    assert bench.record_traffic(specs, "cmd") == 0
     rec = json.load(open(tmp_path / "profiles" / "smooth_traffic.json"))
     assert rec["source_sha256_16"] == "0123456789abcdef" and rec["command"] == "cmd"
-    assert rec["launches"] == {"k_smooth_ws<5,5,5>": 2, "k_smooth_z": 1}
-    assert rec["kernels"]["k_smooth_ws<5,5,5>"] == pytest.approx(8.1, abs=1e-3)
+    assert rec["launches"] == {"k_smooth_p<5,5,5>": 2, "k_smooth_z": 1}
+    assert rec["kernels"]["k_smooth_p<5,5,5>"] == pytest.approx(12.1, abs=1e-3)
     assert rec["kernels"]["k_smooth_z"] == pytest.approx(8.0, abs=1e-3)
 
 
@@ -99,8 +92,45 @@ def test_dominant_kernel_roofline(monkeypatch):
     assert r["traffic"] is None
 
 
+def test_pair_kernels_with_shared_passes():
+    """The first pair of a shared run also writes its spatial sums (16.125 B),
+    the shared pairs read them and write S (12 B), other pairs 8.125 B; the
+    dominant group's bytes are the sum over its launches."""
+    kernels = [(0.0, 0), (0.0, 3), (3.0, 0), (3.0, 3), (3.0, 7), (6.0, 0), (6.0, 3)]
+    codes = [0, 2, 3, 7, 7, 3, 7] + [0] * 57
+    pk = bench.pair_kernels(_FakeSc, kernels, codes)
+    assert pk == [("none", 8.125), ("k_smooth_z", 8.125), ("k_smooth_ws<1,3,3>+P", 16.125),
+                  ("k_smooth_p<1,3,3>", 12.0), ("k_smooth_p<1,3,3>", 12.0), ("k_smooth_ws<5,5,5>+P", 16.125),
+                  ("k_smooth_p<5,5,5>", 12.0)]
+    st = {"smooth_launches_pair": [0, 1, 1, 1, 1, 1, 1] + [0] * 57, "smooth_kernel_pair": codes,
+          "ms_smooth_pair": [0.0, 4.0, 8.0, 3.0, 4.0, 10.0, 3.0] + [0.0] * 57, "ms_smooth": 32.0}
+    r = bench.dominant_kernel(_FakeSc, kernels, st, 1_000_000_000, 1, 6674.2, "measured")
+    assert r["kernel"] == "k_smooth_ws<5,5,5>+P" and r["algorithmic_bytes_per_voxel"] == 16.125
+    st["ms_smooth_pair"][3] = 9.0  # the shared FWHM-3 pairs now dominate: 13 ms for two launches
+    r = bench.dominant_kernel(_FakeSc, kernels, st, 1_000_000_000, 1, 6674.2, "measured")
+    assert r["kernel"] == "k_smooth_p<1,3,3>" and r["launch_ms"] == pytest.approx(6.5)
+    assert r["achieved"] == pytest.approx(2 * 12.0e9 / 13e-3 / 1e9)
+
+
 def test_gauss_hist_roofline():
     r = bench.gauss_hist_roofline({"ms_gauss_hist": 10.0, "gauss_hist_values": 1_500_000_000}, 6674.2, "measured")
     assert r["achieved"] == pytest.approx(4 * 1.5e9 / 10e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6674.2) and r["bound"] == "hbm"
     assert bench.gauss_hist_roofline({"ms_gauss_hist": 0.0, "gauss_hist_values": 0}, 6674.2, "measured") is None
+
+
+def test_interior_subcubes():
+    """Disjoint sub-cubes clear of the NaN border, z-major, as many as asked
+    (144 fit the WALLABY-shaped cube)."""
+    corners, shape = bench.interior_subcubes((1024, 1200, 1200), 200)
+    assert shape == (256, 192, 192) and len(corners) == 144
+    boxes = set()
+    for z, y, x in corners:
+        assert y >= 16 and x >= 16 and y + 192 <= 1184 and x + 192 <= 1184 and z + 256 <= 1024
+        for dz in (0, 255):
+            for dy in (0, 191):
+                for dx in (0, 191):
+                    assert (z + dz, y + dy, x + dx) not in boxes
+                    boxes.add((z + dz, y + dy, x + dx))
+    c16, _ = bench.interior_subcubes((1024, 1200, 1200), 16)
+    assert c16 == corners[:16]
