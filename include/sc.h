@@ -183,9 +183,9 @@ int sc_cascade_widths(float fwhm_px, int32_t *widths);
  * difference between their inputs, and the smoothing is linear and exact).
  * The results are bit for bit those of smoothing every pair in full
  * (SC_FLAG_NO_SHARE). The context allocates for this, on first use, 8 bytes
- * per voxel of the cube plus a correction list of max(2^20, max_voxels/16)
- * entries of 8 bytes and a copy of the working mask; a failed allocation
- * only switches the sharing off.
+ * per voxel of the cube (and a bit per voxel for the cube's NaN flags), a
+ * correction list of max(2^20, max_voxels/16) entries of 8 bytes and a copy
+ * of the working mask; a failed allocation only switches the sharing off.
  * Errors: SC_ERR_ARG (dims <= 0, more voxels than max_voxels -> SC_ERR_BUDGET,
  * even boxcar, negative or non-finite FWHM, t <= 0 or not finite, n_kernels
  * outside 1..SC_MAX_KERNELS, NULL pointers, unknown noise mode),
@@ -218,6 +218,16 @@ int sc_copy_sigmas(sc_ctx *ctx, float *sigma_dst, float *sigma0_dst, int n_kerne
  * internally, Sect. 5); used to check smoothed values. Errors: SC_ERR_ARG
  * (NULL, n < 0), SC_ERR_BUDGET (n > max_voxels), SC_ERR_CUDA. */
 int sc_copy_smoothed(sc_ctx *ctx, float *dst, int64_t n, void *cuda_stream);
+
+/* Test of the device-side failure path: with enable != 0, the next sc_run on
+ * this context makes one producer warp of its first warp-specialised
+ * smoothing launch skip its hand-off of one plane, and limits that kernel's
+ * waits to 1 ms, so that a consumer's bounded wait runs out. The run then
+ * returns SC_ERR_TIMEOUT (when it reads its status: sigma pointers given),
+ * its mask and sigmas are meaningless, and the context stays usable. The
+ * hook clears itself after that run. No GPU fault, trap or unbounded wait is
+ * involved. Library addition for tests. Errors: SC_ERR_ARG (NULL ctx). */
+int sc_test_skip_handoff(sc_ctx *ctx, int enable);
 
 /* Cap on the correction list of the shared spatial passes (see sc_run), in
  * entries (an entry is a voxel masked since the spatial sums were stored,

@@ -103,8 +103,10 @@ struct sc_ctx {
   cudaEvent_t clock_ev = nullptr;
   double clock_host = 0.0;
   // shared spatial passes (allocated on first use, grown for larger cubes)
-  long long* sh_P = nullptr;          // P' of the first pair of a spatial kernel
+  long long* sh_P = nullptr;          // spatial sums of the first pair of a spatial kernel
   size_t sh_P_cap = 0;                // elements
+  unsigned char* sh_nf = nullptr;     // their cube's nonfinite flags, a byte per column and 8 rows
+  size_t sh_nf_cap = 0;               // bytes
   uint32_t* sh_snap = nullptr;        // working mask when P' was made (max_voxels bits + padding)
   unsigned* sh_cnt = nullptr;         // per-bucket counts (kept zero between pairs)
   unsigned* sh_offs = nullptr;        // their exclusive scan
@@ -113,6 +115,7 @@ struct sc_ctx {
   unsigned long long* sh_ent = nullptr;  // correction entries
   unsigned long long sh_ent_cap = 0;
   unsigned long long sh_limit = 0;    // sc_set_share_limit (0: the buffer's capacity)
+  int test_skip_handoff = 0;          // sc_test_skip_handoff: armed for the next run
   ShareState* sh_ss = nullptr;
 };
 
@@ -313,16 +316,25 @@ void apply_tuning(sc_ctx* c, const int64_t* dims, SmoothArgs* a) {
 // Sizes of the shared-pass buffers a cube needs: its spatial sums (an even
 // pitch: 16-byte aligned rows for TMA) and its buckets (those of the smaller
 // tile height, 16 rows, bound those of both heights).
-void share_needs(const int64_t* dims, size_t* need_p, size_t* need_bk) {
+// Bytes per row of the nonfinite-flag map (16-byte aligned rows for TMA).
+long long nf_pitch(long long nx) { return (nx + 15) & ~15LL; }
+
+struct ShareNeeds {
+  size_t p, bk, nf;
+};
+
+ShareNeeds share_needs(const int64_t* dims) {
   const long long nx = dims[0], ny = dims[1], nz = dims[2];
-  *need_p = (size_t)((nx + 1) & ~1LL) * ny * nz;
-  *need_bk = (size_t)((nx + 63) / 64) * ((ny + 15) / 16) * nz + 1;
+  return ShareNeeds{(size_t)((nx + 1) & ~1LL) * ny * nz, (size_t)((nx + 63) / 64) * ((ny + 15) / 16) * nz + 1,
+                    (size_t)nf_pitch(nx) * ((ny + 7) / 8) * nz};
 }
 
 // Buffers of the shared spatial passes for these sizes (allocated or grown
 // here; never inside a stream capture).
-int ensure_share_sized(sc_ctx* c, size_t need_p, size_t need_bk) {
-  const bool fits = c->sh_P_cap >= need_p && c->sh_bk_cap >= need_bk && c->sh_ent && c->sh_snap && c->sh_ss;
+int ensure_share_sized(sc_ctx* c, const ShareNeeds& nd) {
+  const size_t need_p = nd.p, need_bk = nd.bk;
+  const bool fits = c->sh_P_cap >= need_p && c->sh_bk_cap >= need_bk && c->sh_nf_cap >= nd.nf && c->sh_ent &&
+                    c->sh_snap && c->sh_ss;
   if (fits) return SC_OK;
   if (c->capturing) return SC_ERR_BUDGET;
   if (!c->sh_snap) {
@@ -351,6 +363,17 @@ int ensure_share_sized(sc_ctx* c, size_t need_p, size_t need_bk) {
     }
     c->sh_P_cap = need_p;
   }
+  if (c->sh_nf_cap < nd.nf) {
+    cudaStreamSynchronize(c->last);
+    cudaFree(c->sh_nf);
+    c->sh_nf = nullptr;
+    c->sh_nf_cap = 0;
+    if (cudaMalloc(&c->sh_nf, nd.nf) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    c->sh_nf_cap = nd.nf;
+  }
   if (c->sh_bk_cap < need_bk) {
     cudaStreamSynchronize(c->last);
     cudaFree(c->sh_cnt);
@@ -373,11 +396,7 @@ int ensure_share_sized(sc_ctx* c, size_t need_p, size_t need_bk) {
   return SC_OK;
 }
 
-int ensure_share(sc_ctx* c, const int64_t* dims) {
-  size_t need_p = 0, need_bk = 0;
-  share_needs(dims, &need_p, &need_bk);
-  return ensure_share_sized(c, need_p, need_bk);
-}
+int ensure_share(sc_ctx* c, const int64_t* dims) { return ensure_share_sized(c, share_needs(dims)); }
 
 bool same_spatial(const PairDesc& a, const PairDesc& b) {
   return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2];
@@ -471,6 +490,8 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       ShareArgs sh{};
       sh.P = c->sh_P;
       sh.pitch = (dims[0] + 1) & ~1LL;
+      sh.nf = c->sh_nf;
+      sh.nfpitch = nf_pitch(dims[0]);
       sh.msnap = c->sh_snap;
       sh.cnt = c->sh_cnt;
       sh.bsum = c->sh_bsum;
@@ -514,10 +535,16 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
       c->stats.smooth_kernel_pair[k] = SC_KERNEL_SHARED;
     } else {
       Phase ph(c, s, EV_SMOOTH, (unsigned long long)n, k);
+      if (c->test_skip_handoff) {
+        a.test_skip_handoff = 1;  // taken by the first warp-specialised launch
+        a.tune_kind = TUNE_AUTO;
+      }
       if (share_mode == 1) {
         CK(cudaMemcpyAsync(c->sh_snap, c->mbits, sizeof(uint32_t) * nwords, cudaMemcpyDeviceToDevice, s));
         a.pout = c->sh_P;
         a.ppitch = (dims[0] + 1) & ~1LL;
+        a.nfout = c->sh_nf;
+        a.nfpitch = nf_pitch(dims[0]);
         a.tune_kind = TUNE_AUTO;
       }
       if (a.pd.h == 0 && a.pd.wz == 1) {
@@ -529,6 +556,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
         CK(launch_smooth(a, c->sms, s, &l, &code));
         c->stats.launches += l;
         c->stats.smooth_kernel_pair[k] = code;
+        if (code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16) c->test_skip_handoff = 0;
         if (share_mode == 1 && (code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16)) p_owner = k;
       }
     }
@@ -540,6 +568,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
     CK(launch_expand(c->mbits, n, mask_dev, (flags & SC_FLAG_ACCUMULATE) ? 1 : 0, s));
     c->stats.launches += 1;
   }
+  c->test_skip_handoff = 0;  // the hook serves one run
   return SC_OK;
 }
 
@@ -656,6 +685,7 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->lk_comp);
   cudaFree(c->af_buf);
   cudaFree(c->sh_P);
+  cudaFree(c->sh_nf);
   cudaFree(c->sh_snap);
   cudaFree(c->sh_cnt);
   cudaFree(c->sh_offs);
@@ -805,14 +835,14 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
   if (!(flags & (SC_FLAG_NO_SHARE | SC_FLAG_GENERIC))) {
     // shared-pass buffers for the largest cube, made before any capture (a
     // lane that cannot get them smooths every pair in full)
-    size_t mp = 0, mb = 0;
+    ShareNeeds m{0, 0, 0};
     for (int i = 0; i < n_cubes; ++i) {
-      size_t p = 0, b = 0;
-      share_needs(dims + 3 * i, &p, &b);
-      mp = std::max(mp, p);
-      mb = std::max(mb, b);
+      const ShareNeeds nd = share_needs(dims + 3 * i);
+      m.p = std::max(m.p, nd.p);
+      m.bk = std::max(m.bk, nd.bk);
+      m.nf = std::max(m.nf, nd.nf);
     }
-    for (int l = 0; l < n_lanes; ++l) ensure_share_sized(c->lanes[l], mp, mb);
+    for (int l = 0; l < n_lanes; ++l) ensure_share_sized(c->lanes[l], m);
   }
   // Cube i runs on lane i % n_lanes; the lanes' streams fork from q and join
   // back into it, so cubes on different lanes overlap.
@@ -1249,6 +1279,12 @@ int sc_copy_smoothed(sc_ctx* c, float* dst, int64_t n, void* cuda_stream) {
   if ((unsigned long long)n > c->max_voxels) return SC_ERR_BUDGET;
   DeviceGuard g(c->device);
   CK(cudaMemcpyAsync(dst, c->S, sizeof(float) * (size_t)n, cudaMemcpyDefault, (cudaStream_t)cuda_stream));
+  return SC_OK;
+}
+
+int sc_test_skip_handoff(sc_ctx* c, int enable) {
+  if (!c) return SC_ERR_ARG;
+  c->test_skip_handoff = enable ? 1 : 0;
   return SC_OK;
 }
 

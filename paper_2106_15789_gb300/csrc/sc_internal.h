@@ -176,11 +176,18 @@ struct SmoothArgs {
   int tune_kind;             // TUNE_* kernel choice (TUNE_AUTO: the dispatcher decides)
   int tune_zfactor;          // work items per SM targeted by the z chunking (0: 2)
   // Shared spatial passes (warp-specialised kernel only): when pout is set,
-  // the kernel also stores P' = 32 * (spatial sum of X_q) + nonfinite(C) of
-  // every voxel, row pitch ppitch elements.
+  // the kernel also stores the spatial sum P of X_q at every voxel (row pitch
+  // ppitch elements) and the nonfinite flags of C in nfout, a byte per column
+  // and 8 rows (bit y % 8 of byte [(z ceil(ny/8) + y/8) nfpitch + x]).
   long long* pout;
   long long ppitch;
+  unsigned char* nfout;
+  long long nfpitch;
   const unsigned* gate;      // non-null: the kernel runs only if *gate != 0
+  // Test hook of the warp-specialised kernel (0: off): producer warp 0 skips
+  // its hand-off of the block's second plane, and every wait is limited to
+  // 1 ms, so that a consumer's bounded wait runs out (SC_ST_TIMEOUT).
+  int test_skip_handoff;
 };
 
 // ---------------------------------------------------------------------------
@@ -195,13 +202,15 @@ struct ShareState {
 };
 
 struct ShareArgs {
-  long long* P;              // P' of the run's first pair, [nz][ny][pitch]
+  long long* P;              // spatial sums of the run's first pair, [nz][ny][pitch]
   long long pitch;
+  const unsigned char* nf;   // nonfinite flags, [nz][ceil(ny/8)][nfpitch] bytes (bit y % 8)
+  long long nfpitch;         // bytes per row of bytes (a multiple of 16 for TMA)
   const uint32_t* msnap;     // working mask when P' was made
   unsigned* cnt;             // [n_buckets + 1] per-bucket counts (all zero between pairs)
   unsigned* offs;            // [n_buckets + 1] exclusive scan of cnt (offs[n_buckets] = total); null: no corrections
   unsigned long long* bsum;  // block sums of the scan
-  unsigned long long* ent;   // entries: d * 2^16 + (hy << 8 | hx), d the voxel's fixed-point correction
+  unsigned long long* ent;   // entries: low 16 bits (hy << 8 | hx) in the halo'd tile, high 32 the cube value's bits
   unsigned long long cap;    // entry capacity (the buffer holds cap + 2)
   ShareState* ss;
   int ty;                    // tile height of the buckets and of k_smooth_p (32 or 16)

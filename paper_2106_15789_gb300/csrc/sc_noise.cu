@@ -907,7 +907,7 @@ cudaError_t launch_clip_full(const float* src, long long n, uint32_t* mbits, Dev
 // ---------------------------------------------------------------------------
 // After sigma_0: replacement value, bin window, fixed-point scales.
 // Fixed-point shift of every pair: X_q = rint(X * 2^f) with
-// max|X| * 2^f * Wf <= 2^57 (Wf >= W), so that no exact sum can overflow
+// max|X| * 2^f * Wf <= 2^62 (Wf >= W), so that no exact sum can overflow
 // int64. The replacement value repl_d (float64) is quantised once per pair.
 __device__ void fx_setup(DevState* st, double repl_d, const PairWeights& W, int n_pairs) {
   const float maxabs = __uint_as_float(st->maxabs_bits);
@@ -916,13 +916,12 @@ __device__ void fx_setup(DevState* st, double repl_d, const PairWeights& W, int 
   frexpf(mx, &ex);  // mx < 2^ex
   if (mx == 0.0f) ex = 0;
   // f depends on the spatial kernel (through wf) but not on a spectral width up
-  // to kShareMaxWz, so pairs with one spatial kernel quantise alike. The bound
-  // 2^57 leaves five bits below the sums for the nonfinite flag of the stored
-  // spatial sums P' = 32 P + flag (a spectral sum of P' stays below 2^62 + 31).
+  // to kShareMaxWz, so pairs with one spatial kernel quantise alike and can
+  // share their stored spatial sums.
   for (int k = 0; k < n_pairs; ++k) {
     const long long w = W.w[k];
     const int bits = 64 - __clzll((unsigned long long)(W.wf[k] - 1));  // bit length of wf - 1
-    int f = 57 - ex - bits;
+    int f = 62 - ex - bits;
     if (f > 120) f = 120;
     if (f < -120) f = -120;
     st->fx_shift[k] = f;

@@ -13,21 +13,22 @@
 //
 //   K_xy * X_j,q = P + K_xy * D_j,q  exactly,   P = K_xy * X_1,q.
 //
-// The first pair's warp-specialised kernel stores P' = 32 P + nonfinite(C)
-// (int64 per voxel). Every later pair then:
+// The first pair's warp-specialised kernel stores P (int64 per voxel) and
+// the nonfinite flags of C (a bit per voxel). Every later pair then:
 //
 //   prep        lists the voxels of M_j \ M_1 once per bucket (a 64 x ty tile
 //               of this kernel and a plane) whose halo'd region holds them,
-//               with their fixed-point corrections d = X_j,q - X_1,q: a count
-//               pass, an exclusive scan and a fill pass over the two masks;
-//   k_smooth_p  streams the P' tiles by TMA and the bucket's list by a bulk
-//               copy; every voxel gathers d K(a) K(b) from the listed voxels
-//               within reach; then the spectral boxcar runs over the
-//               corrected planes (ring in Tensor Memory) and S and its
-//               histogram are written.
+//               with their cube values: a count pass, an exclusive scan and a
+//               fill pass over the two masks;
+//   k_smooth_p  streams the P tiles and their flag words by TMA and the
+//               bucket's list by a bulk copy; every voxel gathers
+//               d K(a) K(b), d = X_j,q - X_1,q, from the listed voxels within
+//               reach; then the spectral boxcar runs over the corrected
+//               planes (ring in Tensor Memory) and S and its histogram are
+//               written.
 //
 // The result is bit for bit the full kernel's on X_j: the two differ only in
-// the order of exact integer additions. Reading 8 bytes of P' replaces the
+// the order of exact integer additions. Reading 8 bytes of P replaces the
 // cube read, quantisation and both spatial cascades of the pair. When a
 // pair's list does not fit its buffer, k_smooth_p does nothing and a gated
 // launch of the full kernel computes the pair instead.
@@ -46,7 +47,7 @@ using namespace tc;
 
 constexpr int TX = 64;            // tile width
 constexpr int VPT = 4;            // rows of one column per compute thread
-constexpr int kStages = 8;        // P' tiles in flight (a power of two)
+constexpr int kStages = 8;        // P tiles in flight (a power of two)
 constexpr int kEnt = 768;         // list entries staged per plane (the rest are read from global memory)
 constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
 
@@ -73,20 +74,15 @@ __device__ __forceinline__ void for_buckets(long long v, long long nx, long long
 }
 
 // Delta words M_j & ~M_1, four at a time (both masks carry padding words).
-// An entry is the voxel's exact fixed-point correction
-// d = sgn(C) (qrepl - rint(|C| 2^f)) (sgn(0) = +1) times 2^16 plus its place
-// (hy << 8 | hx) in the bucket's halo'd tile; |d| < 2^46 for every cascade
-// served (f leaves bitlen((w1 w2 w3)^2 31 - 1) >= 12 bits of headroom).
+// An entry holds the voxel's cube value (high 32 bits) and its place
+// (hy << 8 | hx) in the bucket's halo'd tile (low 16 bits).
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__ mbits, const float* __restrict__ C,
-                                                    long long n, long long nx, long long ny, ShareArgs sh, int R,
-                                                    const DevState* st, int pair) {
+                                                    long long n, long long nx, long long ny, ShareArgs sh, int R) {
   const long long nq = ((n + 31) / 32 + 3) / 4;
   const uint4* m4 = reinterpret_cast<const uint4*>(mbits);
   const uint4* s4 = reinterpret_cast<const uint4*>(sh.msnap);
   const bool write = FILL && sh.ss->overflow == 0u;
-  const float fscale = FILL ? st->fx_scale[pair] : 0.0f;
-  const long long qrepl = FILL ? st->fx_qrepl[pair] : 0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
        q += (long long)gridDim.x * blockDim.x) {
     const uint4 a = __ldg(m4 + q), b = __ldg(s4 + q);
@@ -101,14 +97,11 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
         const long long v = (4 * q + k) * 32 + bit;
         if (v >= n) break;
         if (FILL) {
-          const float c = __ldg(C + v);
-          long long d = qrepl - quantize(fabsf(c), fscale);
-          if (c < 0.0f) d = -d;
-          const unsigned long long dhi = (unsigned long long)(d * 65536);
+          const unsigned long long cb = (unsigned long long)__float_as_uint(__ldg(C + v)) << 32;
           for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned pos) {
             const unsigned slot = atomicSub(sh.cnt + bk, 1u) - 1u;
             const unsigned long long idx = (unsigned long long)__ldg(sh.offs + bk) + slot;
-            if (write && idx < sh.cap) sh.ent[idx] = dhi | pos;
+            if (write && idx < sh.cap) sh.ent[idx] = cb | pos;
           });
         } else {
           for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned) { atomicAdd(sh.cnt + bk, 1u); });
@@ -244,13 +237,14 @@ struct PGeo {
   static constexpr int kColsPerWarp = kTmemCols / (kCW / 4);
   static constexpr int kMaxWz = (kColsPerWarp / kSlotCols - 1) | 1;
   static constexpr size_t kPBytes = sizeof(long long) * TY * TX;
+  static constexpr size_t kNfBytes = TX * (TY / 8);  // a flag byte per column and 8 rows
   static_assert(kCT == TX * (TY / VPT), "one compute thread per column segment");
   static_assert(kCW % 4 == 0, "compute warps cover the TMEM lane quarters evenly");
   static_assert(TY + 2 * R <= 256 && TX + 2 * R <= 256, "positions fit 8 bits per axis");
 };
 
 struct PSmem {
-  size_t p, e, kk, meta, hist, mbar, total;
+  size_t p, nf, e, kk, meta, hist, mbar, total;
 };
 constexpr int kBars = 2 * kStages;  // full[kStages] (TMA landed), empty[kStages] (consumed)
 
@@ -259,8 +253,10 @@ __host__ __device__ constexpr PSmem p_layout() {
   using G = PGeo<TY, R>;
   PSmem s{};
   size_t o = 0;
-  s.p = o;  // [kStages][TY][64] P' tiles
+  s.p = o;  // [kStages][TY][64] P tiles
   o = al128(o + kStages * G::kPBytes);
+  s.nf = o;  // [kStages][TY / 8][64] flag bytes
+  o = al128(o + kStages * G::kNfBytes);
   s.e = o;  // [kStages][kEnt] list entries
   o = al128(o + sizeof(unsigned long long) * kStages * kEnt);
   s.kk = o;  // [NT] 1-D taps
@@ -280,14 +276,15 @@ __host__ __device__ constexpr PSmem p_layout() {
 // Work items (a 64 x TY tile and a chunk of lz planes, with r halo planes on
 // each side) are handed out by an atomic counter, so blocks whose tiles hold
 // many corrections do not hold the kernel up. Per plane: the issuing warp
-// takes a free stage and loads the P' tile (TMA) and the bucket's list (bulk
+// takes a free stage and loads the P tile and its flag words (TMA) and the bucket's list (bulk
 // copy); each compute warp gathers the corrections of its 32 x VPT voxels
 // from the list (32 entries tested at once by a ballot; a lane adds only to
 // its own voxels, so no atomics), runs the spectral ring and writes S. Stages carry the item and plane index,
 // and a last stage with item -1 ends the block.
 template <int TY, int R>
 __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
-    k_smooth_p(const __grid_constant__ CUtensorMap pmap, SmoothArgs a, ShareArgs sh) {
+    k_smooth_p(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap nfmap, SmoothArgs a,
+               ShareArgs sh) {
   using namespace share;
   using G = PGeo<TY, R>;
   constexpr int NT = G::NT, kCW = G::kCW, kThreads = G::kThreads;
@@ -296,6 +293,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
   unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   constexpr PSmem L = p_layout<TY, R>();
   long long* const Ps = reinterpret_cast<long long*>(smem + L.p);
+  const unsigned char* const NFs = smem + L.nf;
   unsigned long long* const Es = reinterpret_cast<unsigned long long*>(smem + L.e);
   int* const taps1 = reinterpret_cast<int*>(smem + L.kk);
   constexpr TapArr K = taps_for<R>();
@@ -384,8 +382,9 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
           unsigned ncp = cnt ? min(cnt + shift, (unsigned)kEnt) : 0u;
           ncp = (ncp + 1u) & ~1u;  // whole 16-byte units (the list has two spare entries)
           meta[s] = Meta{(int)cur, j0 + jj, cnt, b0, shift, 0u};
-          mbar_expect_tx(full + 8 * s, (unsigned)(G::kPBytes + 8u * ncp));
+          mbar_expect_tx(full + 8 * s, (unsigned)(G::kPBytes + G::kNfBytes + 8u * ncp));
           tma_load_3d(smem_u32(Ps + (size_t)s * TY * TX), &pmap, x0, y0, z0 - r + j0 + jj, full + 8 * s);
+          tma_load_3d(smem_u32(NFs + (size_t)s * G::kNfBytes), &nfmap, x0, y0 / 8, z0 - r + j0 + jj, full + 8 * s);
           if (ncp) bulk_load(smem_u32(Es + (size_t)s * kEnt), sh.ent + (b0 - shift), 8u * ncp, full + 8 * s);
         }
         __syncwarp();
@@ -421,6 +420,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
         tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(G::kColsPerWarp * (warp >> 2));
     const BinCfg cfg = a.win ? a.st->win : kFullRange;
     const float inv = a.st->fx_inv[a.pair];
+    const float fscale = a.st->fx_scale[a.pair];
     const long long qrepl = a.st->fx_qrepl[a.pair];
     const int wx0 = xc & ~31, wy0 = grp * VPT;  // the warp's 32 x VPT voxels
     const bool want_hist = a.hist != nullptr;
@@ -475,8 +475,16 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
           unsigned long long e = 0xffffull;  // beyond the list: a place no warp can reach
           if (i < md.cnt) e = (i + md.shift < (unsigned)kEnt) ? es[i + md.shift] : __ldg(sh.ent + md.off0 + i);
           const int ly = (int)(((unsigned)e >> 8) & 0xffu) - R, lx = (int)((unsigned)e & 0xffu) - R;
-          unsigned reach =
-              __ballot_sync(0xffffffffu, lx + R >= wx0 && lx - R < wx0 + 32 && ly + R >= wy0 && ly - R < wy0 + VPT);
+          const bool near = lx + R >= wx0 && lx - R < wx0 + 32 && ly + R >= wy0 && ly - R < wy0 + VPT;
+          unsigned reach = __ballot_sync(0xffffffffu, near);
+          // each lane quantises its own entry: d = X_j,q - X_1,q at that voxel,
+          // sgn(C) (qrepl - rint(|C| 2^f)) with sgn(0) = +1
+          long long dl = 0;
+          if (near) {
+            const float c = __uint_as_float((unsigned)(e >> 32));
+            dl = qrepl - quantize(fabsf(c), fscale);
+            if (c < 0.0f) dl = -dl;
+          }
           while (reach) {
             // two entries per round, so that their latencies overlap (a
             // missing second one is the unreachable place)
@@ -485,15 +493,17 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
             const int s1 = reach ? __ffs(reach) - 1 : 0;
             const bool two = reach != 0u;
             reach &= reach - 1u;
-            const unsigned long long ej0 = __shfl_sync(0xffffffffu, e, s0);
-            unsigned long long ej1 = __shfl_sync(0xffffffffu, e, s1);
-            if (!two) ej1 = 0xffffull;
-            const int jy0 = (int)(((unsigned)ej0 >> 8) & 0xffu) - R, jx0 = (int)((unsigned)ej0 & 0xffu) - R;
-            const int jy1 = (int)(((unsigned)ej1 >> 8) & 0xffu) - R, jx1 = (int)((unsigned)ej1 & 0xffu) - R;
+            const unsigned ej0 = __shfl_sync(0xffffffffu, (unsigned)e, s0);
+            unsigned ej1 = __shfl_sync(0xffffffffu, (unsigned)e, s1);
+            const long long d0 = __shfl_sync(0xffffffffu, dl, s0);
+            const long long d1 = __shfl_sync(0xffffffffu, dl, s1);
+            if (!two) ej1 = 0xffffu;
+            const int jy0 = (int)((ej0 >> 8) & 0xffu) - R, jx0 = (int)(ej0 & 0xffu) - R;
+            const int jy1 = (int)((ej1 >> 8) & 0xffu) - R, jx1 = (int)(ej1 & 0xffu) - R;
             const int b0 = xc - jx0 + R, b1 = xc - jx1 + R;
             const bool in0 = (unsigned)b0 < (unsigned)NT, in1 = (unsigned)b1 < (unsigned)NT;
-            const long long dk0 = in0 ? ((long long)ej0 >> 16) * (32 * taps1[b0]) : 0ll;
-            const long long dk1 = in1 ? ((long long)ej1 >> 16) * (32 * taps1[b1]) : 0ll;
+            const long long dk0 = in0 ? d0 * taps1[b0] : 0ll;
+            const long long dk1 = in1 ? d1 * taps1[b1] : 0ll;
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
               const int a0 = wy0 + k - jy0 + R, a1 = wy0 + k - jy1 + R;
@@ -503,9 +513,9 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
           }
         }
       }
-      unsigned nb = 0u;
-#pragma unroll
-      for (int i = 0; i < VPT; ++i) nb |= (unsigned)(p[i] & 1ll) << i;
+      // rows grp VPT .. + VPT - 1: half of the flag byte of their 8 rows
+      const unsigned nb = ((unsigned)NFs[(size_t)s * G::kNfBytes + (grp * VPT / 8) * TX + xc] >> ((grp * VPT) & 7)) &
+                          ((1u << VPT) - 1u);
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + 8 * s);
       if (wz > 1) {
@@ -530,8 +540,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
 #pragma unroll
         for (int i = 0; i < VPT; ++i) {
           const bool isn = (nbo >> i) & 1u;
-          // sum of P' = 32 sum(P) + (number of nonfinite flags < 32)
-          const float sv = dequantize(zsum[i] >> 5, inv);
+          const float sv = dequantize(zsum[i], inv);
           const float sval = isn ? __int_as_float(0x7fc00000) : sv;
           if ((rows_in >> i) & 1u) {
             out[i * nx] = sval;
@@ -560,18 +569,36 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
 // ---------------------------------------------------------------------------
 namespace {
 
+// int64 tensor map of a [nz][ny][pitch] array with an nx-wide row, (bx, ty, 1) boxes
 bool encode_p_map(CUtensorMap* map, const long long* base, long long nx, long long ny, long long nz, long long pitch,
-                  int ty) {
+                  int bx, int ty) {
   memset(map, 0, sizeof(*map));
   if (pitch % 2 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tc::tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[2] = {(cuuint64_t)pitch * 8, (cuuint64_t)pitch * ny * 8};
-  const cuuint32_t box[3] = {(cuuint32_t)share::TX, (cuuint32_t)ty, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)ty, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, const_cast<long long*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS;
+}
+
+// uint8 tensor map of the [nz][nyb][pitch] flag bytes, (bx, by, 1) boxes
+bool encode_nf_map(CUtensorMap* map, const unsigned char* base, long long nx, long long nyb, long long nz,
+                   long long pitch, int bx, int by) {
+  memset(map, 0, sizeof(*map));
+  if (pitch % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tc::tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)nyb, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch, (cuuint64_t)pitch * nyb};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<unsigned char*>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return cr == CUDA_SUCCESS;
 }
@@ -594,8 +621,10 @@ cudaError_t launch_p(const SmoothArgs& a0, const ShareArgs& sh, int sms, cudaStr
   for (int i = 0; i < 2 * R + 1; ++i)
     if (a0.pd.taps[i] != K.v[i]) return cudaErrorInvalidValue;  // not the cascade this instance serves
   SmoothArgs a = a0;
-  CUtensorMap map;
-  if (!encode_p_map(&map, sh.P, a.nx, a.ny, a.nz, sh.pitch, TY)) return cudaErrorInvalidValue;
+  CUtensorMap map, nfmap;
+  if (!encode_p_map(&map, sh.P, a.nx, a.ny, a.nz, sh.pitch, TX, TY) ||
+      !encode_nf_map(&nfmap, sh.nf, a.nx, (a.ny + 7) / 8, a.nz, sh.nfpitch, TX, TY / 8))
+    return cudaErrorInvalidValue;
   // z chunks (items are handed out dynamically): the planes a block streams
   // on average, halo planes included, plus one item's planes for the tail
   const long long tiles = (long long)sh.tiles_x * sh.tiles_y;
@@ -616,7 +645,7 @@ cudaError_t launch_p(const SmoothArgs& a0, const ShareArgs& sh, int sms, cudaStr
   a.zchunks = (a.nz + a.lz - 1) / a.lz;
   const long long items = tiles * a.zchunks;
   const int grid = (int)std::min<long long>(items, (long long)sms);
-  k_smooth_p<TY, R><<<grid, PGeo<TY, R>::kThreads, tc::one_block_per_sm_smem(L.total), s>>>(map, a, sh);
+  k_smooth_p<TY, R><<<grid, PGeo<TY, R>::kThreads, tc::one_block_per_sm_smem(L.total), s>>>(map, nfmap, a, sh);
   return cudaGetLastError();
 }
 
@@ -653,10 +682,10 @@ cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms,
   const int R = a.pd.h;
   const long long m = sh.n_buckets + 1;
   const long long nblk = (m + kScanChunk - 1) / kScanChunk;
-  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R, a.st, a.pair);
+  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
   k_share_scan1<<<(unsigned)nblk, 1024, 0, s>>>(sh.cnt, sh.offs, sh.bsum, m);
   k_share_scan2<<<(unsigned)nblk, 1024, 0, s>>>(sh.offs, sh.bsum, m, sh.ss, sh.cap);
-  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R, a.st, a.pair);
+  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
   return cudaGetLastError();
 }
 

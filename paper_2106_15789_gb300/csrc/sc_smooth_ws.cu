@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
   tmem_fence_after();
   const unsigned tbase = tmem_holder;
   bool timed_out = false;
+  const unsigned long long wait_ns = a.test_skip_handoff ? 1000000ull : kWaitNs;
 
   auto item_geo = [&](long long it, int* x0, int* y0, int* z0, int* ns) {
     const long long t = it % n_tiles;
@@ -347,8 +348,8 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         const int zp = z0 - r + j;
         const int s = (int)(g % kStages), b = (int)(g & 1);
         const MaskLd m_after = (do_repl && j + 2 < n_steps) ? mask_load(x0, y0, zp + 2) : MaskLd{0u, 0u, 0u};
-        mbar_wait_bounded(raw_full + 8 * s, (unsigned)((g / kStages) & 1), &timed_out);
-        mbar_wait_bounded(bt_empty + 8 * b, (unsigned)(((g >> 1) & 1) ^ 1), &timed_out);
+        mbar_wait_bounded(raw_full + 8 * s, (unsigned)((g / kStages) & 1), &timed_out, wait_ns);
+        mbar_wait_bounded(bt_empty + 8 * b, (unsigned)(((g >> 1) & 1) ^ 1), &timed_out, wait_ns);
         const float* rb = raw0 + s * kRawStride;
         const unsigned* mwb = mw + b * 4 * G::BY;
         long long* const X = Xt + (G::XBUF == 2 ? (size_t)b * G::BY * G::XP : 0);
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
                                  Bt + (size_t)b * G::BY * G::BP + row * G::BP + seg * G::SEGX);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(bt_full + 8 * b);
+        if (lane == 0 && !(a.test_skip_handoff && warp == 0 && g == 1)) mbar_arrive(bt_full + 8 * b);
         if (G::XBUF == 1) named_bar_sync(kBarProducers, kPT);  // the only quantised tile is free again
       }
     }
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         unsigned old[kSlotCols];
         const unsigned ta = tmine + (unsigned)(kSlotCols * (j % (wz > 1 ? wz : 1)));
         if (wz > 1) tmem_ld16(ta, old);
-        mbar_wait_bounded(bt_full + 8 * b, (unsigned)((g >> 1) & 1), &timed_out);
+        mbar_wait_bounded(bt_full + 8 * b, (unsigned)((g >> 1) & 1), &timed_out, wait_ns);
         long long P[SEGY];
         {
           const long long* src = Bt + (size_t)b * G::BY * G::BP + (grp * SEGY) * G::BP + xc;
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         {
           // the tile's load completed before the producers used it; observing
           // its barrier makes the TMA writes visible to this thread as well
-          mbar_wait_bounded(raw_full + 8 * (int)(g % kStages), (unsigned)((g / kStages) & 1), &timed_out);
+          mbar_wait_bounded(raw_full + 8 * (int)(g % kStages), (unsigned)((g / kStages) & 1), &timed_out, wait_ns);
           const float* rb = raw0 + (size_t)(g % kStages) * kRawStride + (R + grp * SEGY) * G::BX + RA + xc;
 #pragma unroll
           for (int i = 0; i < SEGY; ++i)
@@ -441,12 +442,14 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         nan_hi = (nan_hi << SEGY) | (nan_lo >> (64 - SEGY));
         nan_lo = (nan_lo << SEGY) | nbyte;
         if (a.pout && j >= r && j < n_steps - r) {
-          // the plane's spatial sums for the later pairs of this spatial
-          // kernel: P' = 32 P + nonfinite flag (planes of this chunk only)
+          // the plane's spatial sums and nonfinite flags for the later pairs
+          // of this spatial kernel (planes of this chunk only); the thread's
+          // 8 rows start at a multiple of 8, so their flags are one byte
           long long* po = a.pout + ((long long)zp * ny + gy0) * a.ppitch + gx;
 #pragma unroll
           for (int i = 0; i < SEGY; ++i)
-            if ((rows_in >> i) & 1u) po[i * a.ppitch] = P[i] * 32 + (long long)((nbyte >> i) & 1u);
+            if ((rows_in >> i) & 1u) po[i * a.ppitch] = P[i];
+          if (rows_in & 1u) a.nfout[((long long)zp * ((ny + 7) / 8) + gy0 / 8) * a.nfpitch + gx] = (unsigned char)nbyte;
         }
         if (wz > 1) {
           unsigned nw[kSlotCols];

@@ -138,15 +138,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the barrier phase with the given parity for at most kWaitNs of
-// wall time. A thread whose wait ran out sets *timed_out and from then on
-// waits no more, so a broken hand-off ends the kernel quickly with an error.
-__device__ __forceinline__ void mbar_wait_bounded(unsigned addr, unsigned parity, bool* timed_out) {
+// Wait for the barrier phase with the given parity for at most limit_ns of
+// wall time (kWaitNs by default). A thread whose wait ran out sets
+// *timed_out and from then on waits no more, so a broken hand-off ends the
+// kernel quickly with an error.
+__device__ __forceinline__ void mbar_wait_bounded(unsigned addr, unsigned parity, bool* timed_out,
+                                                  unsigned long long limit_ns = kWaitNs) {
   if (*timed_out) return;
   if (mbar_try(addr, parity)) return;
   const unsigned long long t0 = global_ns();
   while (!mbar_try(addr, parity)) {
-    if (global_ns() - t0 > kWaitNs) {
+    if (global_ns() - t0 > limit_ns) {
       *timed_out = true;
       return;
     }

@@ -113,6 +113,7 @@ _SIGS = {
     "sc_noise": (C.c_int, [_P, _P, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_copy_sigmas": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "sc_set_share_limit": (C.c_int, [_P, C.c_uint64]),
+    "sc_test_skip_handoff": (C.c_int, [_P, C.c_int]),
     "sc_copy_smoothed": (C.c_int, [_P, _P, C.c_int64, _P]),
     "sc_noise_static": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_double), _P]),
     "sc_noise_scale": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int,
@@ -590,6 +591,9 @@ class Context:
 
     def copy_smoothed(self, shape, stream=None):
         return sc_copy_smoothed(self.handle, shape, self.device, stream)
+
+    def test_skip_handoff(self, enable=True):
+        _check(lib().sc_test_skip_handoff(self.handle, 1 if enable else 0), "sc_test_skip_handoff")
 
     def set_share_limit(self, max_entries):
         sc_set_share_limit(self.handle, max_entries)

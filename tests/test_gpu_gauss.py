@@ -129,12 +129,32 @@ def check_run(ctx, cube, kernels, t=T, n=N_REPL, flags=0, mask0=None):
     mask = None if mask0 is None else torch.from_numpy(mask0.astype(np.uint8)).cuda()
     m, sig, s0 = ctx.run(cube.cuda(), kernels, t, "gauss", n, mask=mask, flags=flags)
     m_ref, s_ref, s0_ref, ss = O.sc_filter(c_np, kernels, t, "gauss", n, mask=mask0, return_smoothed=True)
-    # sigma_0 from the raw cube; sigma_k from S_k, which depends on the earlier
-    # pairs' masks and so can differ where a voxel sat on a threshold
+    # sigma_0 from the raw cube. sigma_k from S_k as the library stores it
+    # (float32; the binning is decided in float32 on both sides), at 1e-6 for
+    # every pair up to the first pair at which a voxel whose final mask
+    # differs sat inside the threshold band: until then both sides replaced
+    # the same voxels. Later pairs' S_k can differ at the voxels a band
+    # decision changed; they are held to 4e-6 and counted.
     assert close_to_any(s0, gauss_refs(c_np[np.isfinite(c_np)].astype(np.float64))), (s0, s0_ref)
-    for k, (a, b) in enumerate(zip(sig, s_ref)):
-        assert abs(a - b) <= 4 * SIG_RTOL * b, (k, kernels[k], a, b)
-    ndiff, bad = band_disagreements(m.cpu().numpy(), m_ref, ss, s_ref, t)
+    mg = m.cpu().numpy()
+    diff = np.argwhere(mg != m_ref)
+    first = len(kernels)
+    for p in map(tuple, diff):
+        for k, (s_k, sk) in enumerate(zip(ss, s_ref)):
+            if sk > 0 and abs(abs(s_k[p]) / sk - t) < BAND:
+                first = min(first, k)
+                break
+    relaxed = 0
+    for k, a in enumerate(sig):
+        refs = gauss_refs(ss[k].astype(np.float32).astype(np.float64))
+        if k <= first:
+            assert close_to_any(a, refs), (k, kernels[k], a, refs)
+        else:
+            relaxed += 1
+            assert close_to_any(a, refs, 4 * SIG_RTOL), (k, kernels[k], a, refs)
+    if relaxed:
+        print(f"{relaxed} pair(s) after a band decision at pair {first} checked at 4e-6")
+    ndiff, bad = band_disagreements(mg, m_ref, ss, s_ref, t)
     assert not bad, f"{len(bad)} mask disagreements outside the threshold band, e.g. {bad[:5]}"
     return m, sig, s0
 

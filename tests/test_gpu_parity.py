@@ -78,7 +78,26 @@ def noise_cases():
     cases["cauchy"] = rng.standard_cauchy(300_000)
     cases["skewed"] = rng.exponential(1.0, 100_000)
     cases["constant"] = np.full(1000, 2.5)
+    # subnormal float32 values (|x| < 2^-126), some exactly 0
+    sub = rng.standard_normal(100_001) * 1e-40
+    sub[::97] = 0.0
+    cases["subnormal"] = sub
+    # -0 and +0 as the two middle order statistics of an even count
+    pm = np.concatenate([np.full(5000, -0.0), np.full(5000, 0.0), -1.0 - rng.random(4000), 1.0 + rng.random(4000)])
+    cases["pm_zero_middle"] = rng.permutation(pm)
+    # keys that share their top 24 bits or more: 1 + k 2^-23 with k < 256 (one
+    # exponent, the top 15 mantissa bits equal), many duplicates
+    cases["shared_top_bits"] = 1.0 + rng.integers(0, 256, 200_001) * 2.0 ** -23
+    cases["shared_top_bits_neg"] = -(1.0 + rng.integers(0, 64, 50_000) * 2.0 ** -23)
     return cases
+
+
+def sigma_close(got: float, ref: float) -> bool:
+    """Within SIG_RTOL of the oracle, or within one float32 ulp of it where
+    the library's float32 sigma is subnormal (its resolution there is 2^-149)."""
+    if ref == 0.0:
+        return got == 0.0
+    return abs(got - ref) <= max(SIG_RTOL * ref, 2.0 ** -149)
 
 
 @pytest.mark.parametrize("name", list(noise_cases().keys()))
@@ -91,10 +110,7 @@ def test_noise_matches_oracle(ctx, name):
     for mode in ("mad", "std"):
         ref = O.noise(fin, mode)
         got = ctx.noise(d, mode)
-        if ref == 0.0:
-            assert got == 0.0
-        else:
-            assert abs(got - ref) <= SIG_RTOL * ref, (mode, got, ref)
+        assert sigma_close(got, ref), (mode, got, ref)
     # full passes instead of candidate lists: identical float result
     assert ctx.noise(d, "mad", flags=sc.SC_FLAG_NO_FAST_SELECT) == ctx.noise(d, "mad")
 
@@ -313,3 +329,46 @@ def test_specialised_kernels_equal_generic(ctx, shape):
             a = ctx.smooth(cube, kernel, mask=m, replacement_value=v)
             b = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_FLAG_GENERIC)
             assert torch.equal(torch.nan_to_num(a, nan=7e7), torch.nan_to_num(b, nan=7e7)), (shape, kernel, m is None)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("peak", [1e5, 1e7])
+def test_bright_point_source(ctx, peak):
+    """A point source of `peak` noise levels in unit noise. The fixed-point
+    scale follows max|C|, so up to 1e5 sigma the smoothed values stay within
+    1e-5 sigma_k of the oracle, or within 4 float32 ulps where |S| is so large
+    that the float32 S itself cannot resolve 1e-5 sigma_k (next to the
+    source), and the sigmas within 1e-6. Beyond 2^20 sigma_0 the library says
+    that exactness may be lost (SC_WARN_RANGE); only sigma_0 and the warning
+    are checked there."""
+    from paper_2106_15789_gb300 import sc
+
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal((64, 72, 80)).astype(np.float32)
+    c[30, 36, 41] = peak
+    kernels = [(0.0, 0), (6.0, 0), (6.0, 7), (10.0, 15)]
+    ctx.stats(reset=True)
+    m, sig, s0 = ctx.run(torch.from_numpy(c).cuda(), kernels, T, "mad", N_REPL)
+    warned = bool(ctx.stats()["warnings"] & sc.SC_WARN_RANGE)
+    assert warned == (peak > 2.0 ** 20 * s0), (peak, s0, warned)
+    m_ref, s_ref, s0_ref, ss = O.sc_filter(c, kernels, T, "mad", N_REPL, return_smoothed=True)
+    assert abs(s0 - s0_ref) <= SIG_RTOL * s0_ref
+    if peak > 2.0 ** 20:
+        return
+    for a, b in zip(sig, s_ref):
+        assert abs(a - b) <= SIG_RTOL * b, (a, b)
+    ndiff, bad = band_disagreements(m.cpu().numpy(), m_ref, ss, s_ref, T)
+    assert not bad
+    got = ctx.copy_smoothed(c.shape).cpu().numpy().astype(np.float64)  # the last pair's S
+    ref = ss[-1]
+    err = np.abs(got - ref)
+    tol = np.maximum(S_TOL * s_ref[-1], 4 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64))
+    assert np.all(err <= tol), (err.max(), s_ref[-1])
+    # without replacement the source itself is smoothed by every pair
+    ctx.run(torch.from_numpy(c).cuda(), kernels, T, "mad", 0.0)
+    got = ctx.copy_smoothed(c.shape).cpu().numpy().astype(np.float64)
+    _, s_ref0, _, ss0 = O.sc_filter(c, kernels, T, "mad", 0.0, return_smoothed=True)
+    ref = ss0[-1]
+    assert np.abs(ref).max() > 10.0
+    tol = np.maximum(S_TOL * s_ref0[-1], 4 * np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64))
+    assert np.all(np.abs(got - ref) <= tol)
