@@ -1194,6 +1194,8 @@ def main():
     ap.add_argument("--ref-cube", choices=("wallaby", "small"), default="wallaby",
                     help="cube whose interior sub-cubes the reference arm times (small: a quick check)")
     ap.add_argument("--no-forms", action="store_true", help="default workload: skip the batched and 16-bit forms")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (predictable launch order for profiling captures)")
     ap.add_argument("--record-traffic", metavar="KEY=NCU_CSV", nargs="+",
                     help="write profiles/smooth_traffic.json from one-kernel ncu --csv DRAM captures of the medium "
                          "workload and exit (no GPU)")
@@ -1240,7 +1242,8 @@ def main():
     ctx = Context(local, nvox)
     stream = torch.cuda.current_stream(dev)
     t_tune = time.perf_counter()
-    ctx.autotune(cube.shape, kernels)  # once per cube shape, before timing (as a user would)
+    if not args.no_autotune:
+        ctx.autotune(cube.shape, kernels)  # once per cube shape, before timing (as a user would)
     tune_s = time.perf_counter() - t_tune
 
     def step():
