@@ -28,6 +28,11 @@ The paper gives no formulas for S+C, so the readings below fill its gaps
 1. Gaussian of FWHM f: a cascade of 3 centred boxcars (Kovesi 2010, "Fast
    almost-Gaussian filtering") with widths from :func:`cascade_widths`, applied
    along x and then y. f <= 0 means no spatial smoothing.
+1b. The sampled variant (spatial="sampled"): the Gaussian itself, sampled at
+   the integer offsets within +-4 sigma (sigma = f / sqrt(8 ln 2)), each sample
+   expressed in units of 1/1024 of the central one and rounded to an integer
+   (:func:`gauss_taps`), the kernel being these taps over their sum, applied
+   along x and then y with zero padding.
 2. Spectral boxcar of odd width w: mean of w channels centred on z. w <= 1
    means no spectral smoothing. Even w is rejected.
 3. Edges: zero padding outside the cube, kernels not renormalised.
@@ -118,33 +123,84 @@ def box_mean(x: np.ndarray, w: int, axis: int) -> np.ndarray:
     return out / w
 
 
-def smooth(x: np.ndarray, fwhm: float, wz: int) -> np.ndarray:
+def smooth(x: np.ndarray, fwhm: float, wz: int, spatial: str = "cascade") -> np.ndarray:
     """Separable 3-D smoothing of an (nz, ny, nx) float64 array with no NaNs:
-    boxcar cascade along x, the same cascade along y, then the spectral
-    boxcar along z.
+    the spatial kernel along x, the same along y, then the spectral boxcar
+    along z.
 
-    The cube is zero-padded once, by the cascade's half-width h = sum((w-1)/2),
-    and the cascade runs over the padded array, so the result is the
-    convolution of the zero-padded cube with the composed kernel (the
-    intermediate boxcar outputs just outside the cube are kept, not cut).
+    spatial="cascade" (reading 1): the cube is zero-padded once, by the
+    cascade's half-width h = sum((w-1)/2), and the cascade runs over the
+    padded array, so the result is the convolution of the zero-padded cube
+    with the composed kernel (the intermediate boxcar outputs just outside the
+    cube are kept, not cut). spatial="sampled" (reading 1b): one zero-padded
+    pass of the sampled Gaussian along x, then one along y.
     """
     s = np.asarray(x, dtype=np.float64)
-    widths = cascade_widths(fwhm)
-    h = sum((w - 1) // 2 for w in widths)
-    if widths:
-        s = np.pad(s, ((0, 0), (h, h), (h, h)))
-        for w in widths:
-            s = box_mean(s, w, axis=2)
-        for w in widths:
-            s = box_mean(s, w, axis=1)
-        s = s[:, h:s.shape[1] - h, h:s.shape[2] - h]
+    if spatial == "cascade":
+        widths = cascade_widths(fwhm)
+        h = sum((w - 1) // 2 for w in widths)
+        if widths:
+            s = np.pad(s, ((0, 0), (h, h), (h, h)))
+            for w in widths:
+                s = box_mean(s, w, axis=2)
+            for w in widths:
+                s = box_mean(s, w, axis=1)
+            s = s[:, h:s.shape[1] - h, h:s.shape[2] - h]
+    elif spatial == "sampled":
+        if fwhm > 0:
+            k = kernel_1d(fwhm, "sampled")
+            s = fir_along(s, k, axis=2)
+            s = fir_along(s, k, axis=1)
+    else:
+        raise ValueError(f"unknown spatial kernel {spatial!r}")
     if wz > 1:
         s = box_mean(s, wz, axis=0)
     return s
 
 
-def kernel_1d(fwhm: float) -> np.ndarray:
-    """The composed 1-D spatial kernel (convolution of the cascade's boxes)."""
+GAUSS_TAP_UNIT = 1024  # the central tap of the sampled Gaussian (reading 1b)
+GAUSS_TRUNCATE = 4.0   # its support, in sigmas either side
+
+
+def gauss_taps(fwhm: float) -> np.ndarray:
+    """Integer taps of the sampled spatial Gaussian of this FWHM (reading 1b).
+
+    sigma = FWHM / sqrt(8 ln 2); offsets i = -h..h with h = floor(4 sigma);
+    tap i = the Gaussian's value exp(-i^2 / (2 sigma^2)) times 1024 (the
+    central value's units), rounded to the nearest integer. FWHM <= 0 gives
+    the single tap 1024 (no smoothing).
+    """
+    if not fwhm > 0:
+        return np.array([GAUSS_TAP_UNIT], dtype=np.int64)
+    sigma = fwhm / math.sqrt(8.0 * math.log(2.0))
+    h = int(math.floor(GAUSS_TRUNCATE * sigma))
+    i = np.arange(-h, h + 1, dtype=np.float64)
+    return np.rint(GAUSS_TAP_UNIT * np.exp(-i * i / (2.0 * sigma * sigma))).astype(np.int64)
+
+
+def fir_along(x: np.ndarray, k: np.ndarray, axis: int) -> np.ndarray:
+    """Centred FIR of odd length 2h+1 along one axis, zero outside the array:
+    out[i] = sum_{d=-h..h} k[d + h] * x[i + d]."""
+    h = (k.size - 1) // 2
+    n = x.shape[axis]
+    out = np.zeros_like(x)
+    for d in range(-h, h + 1):
+        if abs(d) >= n:
+            continue
+        src = [slice(None)] * x.ndim
+        dst = [slice(None)] * x.ndim
+        src[axis] = slice(max(d, 0), n + min(d, 0))
+        dst[axis] = slice(max(-d, 0), n - max(d, 0))
+        out[tuple(dst)] += k[d + h] * x[tuple(src)]
+    return out
+
+
+def kernel_1d(fwhm: float, spatial: str = "cascade") -> np.ndarray:
+    """The composed 1-D spatial kernel: the convolution of the cascade's boxes,
+    or the sampled Gaussian's taps over their sum."""
+    if spatial == "sampled":
+        t = gauss_taps(fwhm).astype(np.float64)
+        return t / t.sum()
     k = np.ones(1)
     for w in cascade_widths(fwhm):
         k = np.convolve(k, np.full(w, 1.0 / w))
@@ -258,18 +314,21 @@ def replaced_input(c: np.ndarray, mask: np.ndarray, finite: np.ndarray, value: f
     return x
 
 
-def smoothed(c: np.ndarray, mask: np.ndarray, fwhm: float, wz: int, value: float) -> np.ndarray:
+def smoothed(c: np.ndarray, mask: np.ndarray, fwhm: float, wz: int, value: float,
+             spatial: str = "cascade") -> np.ndarray:
     """S for one kernel pair: replace, smooth, re-blank NaN input voxels."""
     c = np.asarray(c, dtype=np.float64)
     finite = np.isfinite(c)
-    s = smooth(replaced_input(c, mask, finite, value), fwhm, wz)
+    s = smooth(replaced_input(c, mask, finite, value), fwhm, wz, spatial)
     s[~finite] = np.nan
     return s
 
 
 def sc_filter(cube: np.ndarray, kernels, threshold: float, noise_mode: str = "mad",
-              replacement: float = 2.0, mask: np.ndarray | None = None, return_smoothed: bool = False):
-    """Smooth-and-clip over a list of (spatial FWHM px, spectral width ch) pairs.
+              replacement: float = 2.0, mask: np.ndarray | None = None, return_smoothed: bool = False,
+              spatial: str = "cascade"):
+    """Smooth-and-clip over a list of (spatial FWHM px, spectral width ch) pairs,
+    with the spatial kernel of reading 1 (cascade) or 1b (sampled).
 
     Returns (mask uint8, [sigma_k], sigma_0) and, if asked, the list of smoothed
     cubes S_k.
@@ -286,7 +345,7 @@ def sc_filter(cube: np.ndarray, kernels, threshold: float, noise_mode: str = "ma
     value = replacement * sigma0 if replacement > 0 else 0.0
     sigmas, all_s = [], []
     for fs, wz in kernels:
-        s = smoothed(c, m, fs, wz, value)
+        s = smoothed(c, m, fs, wz, value, spatial)
         ok = np.isfinite(s)
         sk = noise(s[ok], noise_mode)
         if sk > 0:
@@ -298,7 +357,7 @@ def sc_filter(cube: np.ndarray, kernels, threshold: float, noise_mode: str = "ma
     return out + (all_s,) if return_smoothed else out
 
 
-def smoothed_at(x: np.ndarray, fwhm: float, wz: int, points: np.ndarray) -> np.ndarray:
+def smoothed_at(x: np.ndarray, fwhm: float, wz: int, points: np.ndarray, spatial: str = "cascade") -> np.ndarray:
     """S at a few voxels by direct summation over the composed 3-D kernel.
 
     x is the already replaced input (NaN -> 0); points is an (m, 3) array of
@@ -306,7 +365,7 @@ def smoothed_at(x: np.ndarray, fwhm: float, wz: int, points: np.ndarray) -> np.n
     zero outside the cube. Used for sampled checks of cubes too large for
     :func:`smooth`.
     """
-    kxy = kernel_1d(fwhm)
+    kxy = kernel_1d(fwhm, spatial)
     kz = np.full(wz, 1.0 / wz) if wz > 1 else np.ones(1)
     h, r = (kxy.size - 1) // 2, (kz.size - 1) // 2
     nz, ny, nx = x.shape

@@ -351,7 +351,9 @@ def _mut_median_lower(orig):
 
 
 def _mut_smooth_no_y(orig):
-    def f(x, fwhm, wz):
+    def f(x, fwhm, wz, spatial="cascade"):
+        if spatial != "cascade":
+            return orig(x, fwhm, wz, spatial)
         s = np.asarray(x, dtype=np.float64)
         for w in O.cascade_widths(fwhm):
             s = O.box_mean(s, w, axis=2)
@@ -362,14 +364,15 @@ def _mut_smooth_no_y(orig):
 
 
 def _mut_smooth_z_narrow(orig):
-    def f(x, fwhm, wz):
-        return orig(x, fwhm, wz - 2 if wz > 3 else wz)
+    def f(x, fwhm, wz, spatial="cascade"):
+        return orig(x, fwhm, wz - 2 if wz > 3 else wz, spatial)
     return f
 
 
 def _mut_sc_sigmak_replacement(orig):
     # replacement value taken from the previous pair's sigma instead of sigma_0
-    def f(cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, return_smoothed=False):
+    def f(cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, return_smoothed=False,
+          spatial="cascade"):
         c = np.asarray(cube, dtype=np.float64)
         fin = np.isfinite(c)
         s0 = O.noise(c[fin], noise_mode)
@@ -377,7 +380,7 @@ def _mut_sc_sigmak_replacement(orig):
         last = s0
         sig, ss = [], []
         for fs, wz in kernels:
-            s = O.smoothed(c, m, fs, wz, replacement * last if replacement > 0 else 0.0)
+            s = O.smoothed(c, m, fs, wz, replacement * last if replacement > 0 else 0.0, spatial)
             ok = np.isfinite(s)
             sk = O.noise(s[ok], noise_mode)
             m |= ok & (np.abs(s) > threshold * sk)
@@ -390,16 +393,18 @@ def _mut_sc_sigmak_replacement(orig):
 
 
 def _mut_no_reblank(orig):
-    def f(c, mask, fwhm, wz, value):
+    def f(c, mask, fwhm, wz, value, spatial="cascade"):
         c = np.asarray(c, dtype=np.float64)
         fin = np.isfinite(c)
-        return O.smooth(O.replaced_input(c, mask, fin, value), fwhm, wz)
+        return O.smooth(O.replaced_input(c, mask, fin, value), fwhm, wz, spatial)
     return f
 
 
 def _mut_smooth_truncate_each_pass(orig):
     # zero padding applied again after every boxcar (intermediates cut at the edge)
-    def f(x, fwhm, wz):
+    def f(x, fwhm, wz, spatial="cascade"):
+        if spatial != "cascade":
+            return orig(x, fwhm, wz, spatial)
         s = np.asarray(x, dtype=np.float64)
         for w in O.cascade_widths(fwhm):
             s = O.box_mean(s, w, axis=2)
@@ -411,14 +416,15 @@ def _mut_smooth_truncate_each_pass(orig):
 
 def _mut_clip_positive_only(orig):
     # only positive excursions enter the mask (the paper keeps both signs)
-    def f(cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, return_smoothed=False):
+    def f(cube, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None, return_smoothed=False,
+          spatial="cascade"):
         c = np.asarray(cube, dtype=np.float64)
         fin = np.isfinite(c)
         s0 = O.noise(c[fin], noise_mode)
         m = np.zeros(c.shape, dtype=bool)
         sig, ss = [], []
         for fs, wz in kernels:
-            s = O.smoothed(c, m, fs, wz, replacement * s0 if replacement > 0 else 0.0)
+            s = O.smoothed(c, m, fs, wz, replacement * s0 if replacement > 0 else 0.0, spatial)
             ok = np.isfinite(s)
             sk = O.noise(s[ok], noise_mode)
             if sk > 0:
@@ -440,15 +446,15 @@ def _mut_std_biased(orig):
 
 
 def _mut_kernel1d_flip(orig):
-    def f(fwhm):
-        k = orig(fwhm)
+    def f(fwhm, spatial="cascade"):
+        k = orig(fwhm, spatial)
         return np.roll(k, 1)
     return f
 
 
 def _mut_smoothed_at_transposed(orig):
-    def f(x, fwhm, wz, points):
-        return orig(np.swapaxes(x, 0, 2).copy() if x.shape[0] == x.shape[2] else x[::-1], fwhm, wz, points)
+    def f(x, fwhm, wz, points, spatial="cascade"):
+        return orig(np.swapaxes(x, 0, 2).copy() if x.shape[0] == x.shape[2] else x[::-1], fwhm, wz, points, spatial)
     return f
 
 
