@@ -36,7 +36,8 @@ STORE_BYTES_PER_VOXEL = SMOOTH_BYTES_PER_VOXEL + 8.0  # the same, also writing t
 SHARED_BYTES_PER_VOXEL = 8.0 + 4.0  # read P', write S (the correction lists add ~0.1 %)
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
              "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag",
-             "wallaby-gauss", "medium-gauss", "wallaby-noisescale-gauss", "wallaby-autoflag-gauss")
+             "wallaby-gauss", "medium-gauss", "wallaby-noisescale-gauss", "wallaby-autoflag-gauss",
+             "wallaby-sampled", "medium-sampled", "small-sampled")
 FLAG_METRIC = "auto-flagger voxels/s on 1 GB300 (channel and pixel MAD noise, k = 4)"
 LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
@@ -256,16 +257,16 @@ def _oracle_init(barrier):
 def _oracle_job(job):
     """One pool worker: S+C of one sub-cube with the oracle, timed after all
     workers have their data (the barrier), one thread."""
-    sub, kernels, t, n_repl, mode = job
+    sub, kernels, t, n_repl, mode, spatial = job
     from oracle.sc_oracle import sc_filter
 
     _BARRIER.wait()
     t0 = time.perf_counter()
-    sc_filter(sub, kernels, t, mode, n_repl)
+    sc_filter(sub, kernels, t, mode, n_repl, spatial=spatial)
     return time.perf_counter() - t0
 
 
-def oracle_pool(subs, kernels, t, n_repl, mode, rounds=1):
+def oracle_pool(subs, kernels, t, n_repl, mode, rounds=1, spatial="cascade"):
     """The oracle on the host cores: one spawned process per sub-cube, each
     single-threaded, all starting together; per round, the aggregate
     voxel*kernels/s is the sub-cubes' voxels x pairs over the slowest worker's
@@ -281,7 +282,7 @@ def oracle_pool(subs, kernels, t, n_repl, mode, rounds=1):
         rates, secs = [], []
         with ctx.Pool(len(subs), initializer=_oracle_init, initargs=(barrier,)) as pool:
             for _ in range(rounds):
-                times = pool.map(_oracle_job, [(x, kernels, t, n_repl, mode) for x in subs], chunksize=1)
+                times = pool.map(_oracle_job, [(x, kernels, t, n_repl, mode, spatial) for x in subs], chunksize=1)
                 secs.append(max(times))
                 rates.append(sum(x.size for x in subs) * len(kernels) / max(times))
     finally:
@@ -297,15 +298,15 @@ def oracle_workers():
     return max(1, min(os.cpu_count() or 1, 64))
 
 
-def cpu_baseline(cube_dev, kernels, t, n_repl, mode="mad"):
+def cpu_baseline(cube_dev, kernels, t, n_repl, mode="mad", spatial="cascade"):
     """The FP64 oracle as it stands on all host cores (up to 64 processes):
     one interior 192 x 192 x 256 sub-cube of the same cube per process; plus
     the same sub-cube size on one thread for reference."""
     n = oracle_workers()
     corners, (sz, sy, sx) = interior_subcubes(tuple(cube_dev.shape), n)
     subs = [cube_dev[z:z + sz, y:y + sy, x:x + sx].float().cpu().numpy() for z, y, x in corners]
-    rates, secs = oracle_pool(subs, kernels, t, n_repl, mode)
-    rate1, secs1 = oracle_pool(subs[:1], kernels, t, n_repl, mode)
+    rates, secs = oracle_pool(subs, kernels, t, n_repl, mode, spatial=spatial)
+    rate1, secs1 = oracle_pool(subs[:1], kernels, t, n_repl, mode, spatial=spatial)
     return {"value": rates[0], "unit": UNIT, "cores": len(subs), "kind": "oracle",
             "value_one_thread": rate1[0],
             "sample": f"{len(subs)} disjoint interior {sx}x{sy}x{sz} sub-cubes of the same cube (one per host process, "
@@ -357,11 +358,14 @@ def config_dict(workload, kernels, mode="mad"):
              "wallaby-fp16": "wallaby-1200x1200x1024 stored as FP16 + per-channel float32 scales",
              "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
     workload = workload.removesuffix("-gauss")
+    sampled = workload.endswith("-sampled")
+    workload = workload.removesuffix("-sampled")
     half = workload.endswith(("-bf16", "-fp16"))
     precision = ("%s cube + per-channel float32 scales, decoded to float32 once per run, exact fixed-point smoothing"
                  % workload.split("-")[-1].upper()) if half else "float32 cube, exact fixed-point smoothing"
     big = workload in ("wallaby", "wallaby-bf16", "wallaby-fp16")
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
+            "spatial_kernel": "sampled Gaussian (integer taps within 4 sigma)" if sampled else "3-box cascade",
             "n_pairs": len(kernels), "threshold": SC_THRESHOLD, "noise": mode, "replacement": SC_REPLACEMENT,
             "precision": precision, "l2": "inputs (cube 5.9 GB) larger than L2"
             if big else ("inputs (10.9 GB of sub-cubes) larger than L2" if workload == "batch64" else "no flush")}
@@ -1236,7 +1240,10 @@ def main():
     kernels = KERNELS_12
     t, n_repl = SC_THRESHOLD, SC_REPLACEMENT
     mode = "gauss" if args.workload.endswith("-gauss") else "mad"
-    spec, cube = make_workload(args.workload.removesuffix("-gauss"), rank, str(dev))
+    sampled = args.workload.endswith("-sampled")
+    run_flags = sc.SC_FLAG_SAMPLED_GAUSS if sampled else 0
+    spatial = "sampled" if sampled else "cascade"
+    spec, cube = make_workload(args.workload.removesuffix("-gauss").removesuffix("-sampled"), rank, str(dev))
     nvox = cube.numel()
     mask = torch.empty(cube.shape, dtype=torch.uint8, device=dev)
     ctx = Context(local, nvox)
@@ -1247,7 +1254,7 @@ def main():
     tune_s = time.perf_counter() - t_tune
 
     def step():
-        return ctx.run(cube, kernels, t, mode, n_repl, mask=mask)
+        return ctx.run(cube, kernels, t, mode, n_repl, mask=mask, flags=run_flags)
 
     for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
         step()
@@ -1288,18 +1295,18 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
     roofline["measured_in"] = "the profiled repeat of the timed steps (per-pair CUDA events on the launching stream)"
-    mask_f32 = mask.clone() if not args.no_forms and world == 1 and mode == "mad" else None
+    mask_f32 = mask.clone() if not args.no_forms and world == 1 and mode == "mad" and not sampled else None
 
     e2e = None
     if not args.no_e2e:
         e2e = pipelined_e2e(ctx, [cube], lambda ins, m: ctx.run(ins[0], kernels, t, mode, n_repl, mask=m,
-                                                                  want_sigma=False),
+                                                                  want_sigma=False, flags=run_flags),
                             nvox, len(kernels), args.e2e_steps, pg, dev, world,
                             "sc_run on device copies of a pinned host cube")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(cube, kernels, t, n_repl, mode)
+        cpu = cpu_baseline(cube, kernels, t, n_repl, mode, spatial)
 
     forms = None
     if mask_f32 is not None:

@@ -67,6 +67,7 @@ extern "C" {
 #define SC_FLAG_NO_FAST_SELECT 0x4u /* skip the one-pass candidate selection; select by full passes (slow, for tests) */
 #define SC_FLAG_GRAPH 0x8u          /* sc_run_batch: capture the batch once into a CUDA graph and replay it */
 #define SC_FLAG_NO_SHARE 0x10u      /* smooth every pair in full (no shared spatial passes; same results, slower) */
+#define SC_FLAG_SAMPLED_GAUSS 0x20u /* spatial kernels are sampled Gaussians (sc_gauss_taps), not 3-box cascades */
 
 /* ---- warning bits (sc_stats.warnings, set per run) -------------------- */
 #define SC_WARN_ZERO_SIGMA 0x1u     /* some pair had sigma == 0 and added nothing to the mask */
@@ -156,6 +157,20 @@ const char *sc_last_cuda_error(void);
  * identity). widths must hold 3 ints. Errors: SC_ERR_ARG (NULL, FWHM not
  * finite or so large that a width exceeds 4095). */
 int sc_cascade_widths(float fwhm_px, int32_t *widths);
+
+/* Host helper: the integer taps of the sampled spatial Gaussian of this FWHM,
+ * the spatial kernel of runs with SC_FLAG_SAMPLED_GAUSS. The paper names a
+ * Gaussian of given FWHM (Sect. 5; Hydra-field figure caption, Sect. 7); this
+ * is its sampled form: sigma = FWHM / sqrt(8 ln 2), offsets i = -h..h with
+ * h = floor(4 sigma), tap i = exp(-i^2 / (2 sigma^2)) in units of 1/1024 of the
+ * central sample rounded to the nearest integer; the kernel is the taps over
+ * their sum, applied along x and then y with zero padding (the cube edges are
+ * not renormalised). FWHM <= 0 gives the single tap 1024. Writes 2h+1 taps to
+ * taps[] and returns 2h+1. The smoothing kernels drop zero taps at both ends
+ * (which add nothing) and serve half-widths up to 40 after that, i.e. FWHM up
+ * to about 23.5 px; beyond that a run returns SC_ERR_UNSUPPORTED.
+ * Errors: SC_ERR_ARG (NULL, FWHM not finite, or more than max_taps taps). */
+int sc_gauss_taps(float fwhm_px, int32_t *taps, int max_taps);
 
 /* Full S+C (Sect. 4.2) on a device cube.
  *   cube_dev     float32 [nz][ny][nx], read only.

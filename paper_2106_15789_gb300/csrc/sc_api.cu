@@ -285,7 +285,7 @@ int measure(sc_ctx* c, const float* src, long long n, int win, float t, int clip
 }
 
 int validate_common(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kernel* kernels, int nk, float t,
-                    int noise_mode, long long* n, std::vector<PairDesc>* pds) {
+                    int noise_mode, long long* n, std::vector<PairDesc>* pds, uint32_t flags) {
   if (!c || !cube || !kernels) return SC_ERR_ARG;
   int rc = check_dims(c, dims, n);
   if (rc) return rc;
@@ -294,7 +294,7 @@ int validate_common(sc_ctx* c, const float* cube, const int64_t* dims, const sc_
   if (noise_mode != SC_NOISE_MAD && noise_mode != SC_NOISE_STD && noise_mode != SC_NOISE_GAUSS) return SC_ERR_ARG;
   pds->resize(nk);
   for (int k = 0; k < nk; ++k) {
-    rc = make_pair(kernels[k], &(*pds)[k]);
+    rc = make_pair(kernels[k], &(*pds)[k], (flags & SC_FLAG_SAMPLED_GAUSS) != 0);
     if (rc) return rc;
   }
   return SC_OK;
@@ -306,7 +306,7 @@ std::array<long long, 7> tune_key(const int64_t* dims, const PairDesc& pd) {
 
 // Kernel choice of sc_autotune for this cube shape and pair, if any.
 void apply_tuning(sc_ctx* c, const int64_t* dims, SmoothArgs* a) {
-  if (c->tune.empty()) return;
+  if (c->tune.empty() || a->pd.sampled) return;  // the tuner times cascade pairs only
   auto it = c->tune.find(tune_key(dims, a->pd));
   if (it == c->tune.end()) return;
   a->tune_kind = it->second[0];
@@ -399,6 +399,9 @@ int ensure_share_sized(sc_ctx* c, const ShareNeeds& nd) {
 int ensure_share(sc_ctx* c, const int64_t* dims) { return ensure_share_sized(c, share_needs(dims)); }
 
 bool same_spatial(const PairDesc& a, const PairDesc& b) {
+  if (a.sampled != b.sampled || a.h != b.h) return false;
+  for (int i = 0; i < 2 * a.h + 1; ++i)
+    if (a.taps[i] != b.taps[i]) return false;
   return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2];
 }
 
@@ -419,7 +422,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
                int noise_mode, float replacement, uint8_t* mask_dev, uint32_t flags, cudaStream_t s) {
   long long n = 0;
   std::vector<PairDesc> pds;
-  int rc = validate_common(c, cube, dims, kernels, nk, t, noise_mode, &n, &pds);
+  int rc = validate_common(c, cube, dims, kernels, nk, t, noise_mode, &n, &pds, flags);
   if (rc) return rc;
   if (!mask_dev) return SC_ERR_ARG;
   if (!std::isfinite(replacement)) return SC_ERR_ARG;
@@ -612,6 +615,15 @@ int sc_cascade_widths(float fwhm_px, int32_t* widths) {
   if (cascade_widths(fwhm_px, w) != 0) return SC_ERR_ARG;
   for (int i = 0; i < 3; ++i) widths[i] = w[i];
   return SC_OK;
+}
+
+int sc_gauss_taps(float fwhm_px, int32_t* taps, int max_taps) {
+  if (!taps || max_taps < 1 || !std::isfinite(fwhm_px)) return SC_ERR_ARG;
+  std::vector<int> t((size_t)max_taps);
+  const int n = gauss_taps(fwhm_px, t.data(), max_taps);
+  if (n < 1) return SC_ERR_ARG;
+  for (int i = 0; i < n; ++i) taps[i] = t[i];
+  return n;
 }
 
 int sc_create(sc_ctx** out, int device, size_t max_voxels) {
@@ -807,7 +819,8 @@ int sc_run_batch(sc_ctx* c, int n_cubes, const float* const* cubes, const int64_
     if (!cubes[i] || !masks[i]) return SC_ERR_ARG;
     long long n = 0;
     std::vector<PairDesc> pds;
-    const int rc = validate_common(c, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, &n, &pds);
+    const int rc =
+        validate_common(c, cubes[i], dims + 3 * i, kernels, n_kernels, threshold, noise_mode, &n, &pds, flags);
     if (rc) return rc;
   }
   const size_t need = sizeof(BatchRes) * (size_t)n_cubes;
@@ -975,7 +988,7 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
   long long n = 0;
   std::vector<PairDesc> pds;
   int rc = validate_common(c, storage == SC_STORE_F32 ? (const float*)cube_dev : c->S, dims, kernels, n_kernels,
-                           threshold, noise_mode, &n, &pds);
+                           threshold, noise_mode, &n, &pds, flags);
   if (rc) return rc;
   if (!std::isfinite(replacement)) return SC_ERR_ARG;
   const unsigned long long bytes = (unsigned long long)n * ((storage == SC_STORE_F32 ? 4u : 2u) + 1u);
@@ -1231,7 +1244,7 @@ int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel k
   int rc = check_dims(c, dims, &n);
   if (rc) return rc;
   PairDesc pd;
-  rc = make_pair(kernel, &pd);
+  rc = make_pair(kernel, &pd, (flags & SC_FLAG_SAMPLED_GAUSS) != 0);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   c->last = s;

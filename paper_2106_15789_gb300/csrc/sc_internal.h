@@ -142,14 +142,16 @@ constexpr int kMaxBoxcar = 127; // largest spectral boxcar
 // Spectral widths up to this share one fixed-point scale per spatial kernel
 // (so that the pairs of one spatial kernel can share its spatial passes).
 constexpr int kShareMaxWz = 31;
+constexpr int kGaussTapUnit = 1024;  // central tap of the sampled Gaussian: taps are in its 1/1024 units
 
 struct PairDesc {
-  int w[3];       // spatial cascade widths (1 = identity)
+  int w[3];       // spatial cascade widths (1 = identity; 0 = not a cascade: sampled Gaussian)
   int h;          // spatial half-width
   int wz;         // spectral width (1 = identity)
-  long long W;    // integer weight total (w0 w1 w2)^2 * wz
-  long long Wf;   // weight bound fixing the scale: (w0 w1 w2)^2 * max(wz, kShareMaxWz)
-  int taps[2 * kMaxHalf + 1];  // composed integer kernel, 2h+1 taps, sum = w0 w1 w2
+  int sampled;    // 1: the spatial kernel is the sampled Gaussian (taps below), not a cascade
+  long long W;    // integer weight total T^2 * wz, T = sum of the 1-D taps (w0 w1 w2 for a cascade)
+  long long Wf;   // weight bound fixing the scale: T^2 * max(wz, kShareMaxWz)
+  int taps[2 * kMaxHalf + 1];  // composed integer kernel, 2h+1 taps, sum T
 };
 
 struct PairWeights {
@@ -321,7 +323,10 @@ cudaError_t launch_link_filter(const long long dims[3], int* lab, int* chunk_off
 
 // Host helpers.
 int cascade_widths(double fwhm, int w[3]);
-int make_pair(const sc_kernel& k, PairDesc* pd);
+// Integer taps of the sampled Gaussian of this FWHM (2h+1 of them, h =
+// floor(4 sigma)); returns 2h+1, or -1 if more than max_taps would be needed.
+int gauss_taps(double fwhm, int* taps, int max_taps);
+int make_pair(const sc_kernel& k, PairDesc* pd, bool sampled = false);
 void choose_tiles(SmoothArgs* a);
 size_t smooth_smem_bytes(const SmoothArgs& a);
 

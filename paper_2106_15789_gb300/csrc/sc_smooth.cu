@@ -378,30 +378,73 @@ int cascade_widths(double fwhm, int w[3]) {
   return 0;
 }
 
-int make_pair(const sc_kernel& k, PairDesc* pd) {
+int gauss_taps(double fwhm, int* taps, int max_taps) {
+  // sigma = FWHM / sqrt(8 ln 2); taps at offsets |i| <= floor(4 sigma), each
+  // exp(-i^2 / (2 sigma^2)) in units of 1/1024 of the central sample, rounded
+  // to the nearest integer (ties to even).
+  if (!(fwhm > 0.0)) {
+    if (max_taps < 1) return -1;
+    taps[0] = kGaussTapUnit;
+    return 1;
+  }
+  const double sigma = fwhm / sqrt(8.0 * log(2.0));
+  const double hr = floor(4.0 * sigma);
+  if (!(hr < 4096.0) || 2 * (int)hr + 1 > max_taps) return -1;
+  const int h = (int)hr;
+  for (int i = -h; i <= h; ++i)
+    taps[i + h] = (int)llrint(kGaussTapUnit * exp(-(double)i * i / (2.0 * sigma * sigma)));
+  return 2 * h + 1;
+}
+
+int make_pair(const sc_kernel& k, PairDesc* pd, bool sampled) {
   if (!(k.fwhm_spatial_px >= 0.0f) || !isfinite(k.fwhm_spatial_px)) return SC_ERR_ARG;
   if (k.boxcar_chan < 0 || (k.boxcar_chan > 1 && k.boxcar_chan % 2 == 0)) return SC_ERR_ARG;
   if (k.boxcar_chan > kMaxBoxcar) return SC_ERR_UNSUPPORTED;
-  if (cascade_widths(k.fwhm_spatial_px, pd->w) != 0) return SC_ERR_ARG;
-  pd->h = (pd->w[0] - 1) / 2 + (pd->w[1] - 1) / 2 + (pd->w[2] - 1) / 2;
-  if (pd->h > kMaxHalf) return SC_ERR_UNSUPPORTED;
   pd->wz = k.boxcar_chan > 1 ? k.boxcar_chan : 1;
-  // composed integer kernel: convolution of three all-ones boxes
+  pd->sampled = 0;
   long long t[2 * kMaxHalf + 1] = {0};
   int len = 1;
-  t[0] = 1;
-  for (int b = 0; b < 3; ++b) {
-    const int w = pd->w[b];
-    long long nt[2 * kMaxHalf + 1] = {0};
-    for (int i = 0; i < len; ++i)
-      for (int d = 0; d < w; ++d) nt[i + d] += t[i];
-    len += w - 1;
-    for (int i = 0; i < len; ++i) t[i] = nt[i];
+  if (sampled) {
+    // the sampled Gaussian: its taps, less the zero taps at both ends (which
+    // add nothing), so that the support is as short as the kernel allows
+    if (cascade_widths(k.fwhm_spatial_px, pd->w) != 0) return SC_ERR_ARG;  // the same FWHM range
+    int g[2 * 4096 + 1];
+    const int n = gauss_taps(k.fwhm_spatial_px, g, 2 * 4096 + 1);
+    if (n < 1) return SC_ERR_ARG;
+    int lo = 0;
+    while (2 * lo + 1 < n && g[lo] == 0) ++lo;
+    len = n - 2 * lo;
+    if ((len - 1) / 2 > kMaxHalf) return SC_ERR_UNSUPPORTED;
+    for (int i = 0; i < len; ++i) t[i] = g[lo + i];
+    if (len > 1) {
+      pd->sampled = 1;
+      pd->w[0] = pd->w[1] = pd->w[2] = 0;  // no cascade kernel serves this pair
+    } else {
+      pd->w[0] = pd->w[1] = pd->w[2] = 1;  // a single tap: no spatial smoothing
+      t[0] = 1;
+    }
+  } else {
+    if (cascade_widths(k.fwhm_spatial_px, pd->w) != 0) return SC_ERR_ARG;
+    // composed integer kernel: convolution of three all-ones boxes
+    t[0] = 1;
+    for (int b = 0; b < 3; ++b) {
+      const int w = pd->w[b];
+      if ((len - 1) / 2 + (w - 1) / 2 > kMaxHalf) return SC_ERR_UNSUPPORTED;
+      long long nt[2 * kMaxHalf + 1] = {0};
+      for (int i = 0; i < len; ++i)
+        for (int d = 0; d < w; ++d) nt[i + d] += t[i];
+      len += w - 1;
+      for (int i = 0; i < len; ++i) t[i] = nt[i];
+    }
   }
-  for (int i = 0; i < 2 * kMaxHalf + 1; ++i) pd->taps[i] = (i < len) ? (int)t[i] : 0;
-  const long long wxy = (long long)pd->w[0] * pd->w[1] * pd->w[2];
-  pd->W = wxy * wxy * pd->wz;
-  pd->Wf = wxy * wxy * (pd->wz > kShareMaxWz ? pd->wz : kShareMaxWz);
+  pd->h = (len - 1) / 2;
+  long long tsum = 0;
+  for (int i = 0; i < 2 * kMaxHalf + 1; ++i) {
+    pd->taps[i] = (i < len) ? (int)t[i] : 0;
+    tsum += (i < len) ? t[i] : 0;
+  }
+  pd->W = tsum * tsum * pd->wz;
+  pd->Wf = tsum * tsum * (pd->wz > kShareMaxWz ? pd->wz : kShareMaxWz);
   return SC_OK;
 }
 

@@ -673,7 +673,7 @@ int share_tile_rows(int wz) {
 }
 
 bool share_supported(const PairDesc& pd) {
-  return pd.h > 0 && share_R(pd) == pd.h && pd.wz <= kShareMaxWz && share_tile_rows(pd.wz) > 0;
+  return !pd.sampled && pd.h > 0 && share_R(pd) == pd.h && pd.wz <= kShareMaxWz && share_tile_rows(pd.wz) > 0;
 }
 
 cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s) {

@@ -35,6 +35,7 @@ SC_FLAG_GENERIC = 0x2
 SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
 SC_FLAG_NO_SHARE = 0x10
+SC_FLAG_SAMPLED_GAUSS = 0x20
 SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
 # sc_smooth kernel variants (flags |= variant << 16)
 SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512 = \
@@ -94,6 +95,7 @@ _SIGS = {
     "sc_strerror": (C.c_char_p, [C.c_int]),
     "sc_last_cuda_error": (C.c_char_p, []),
     "sc_cascade_widths": (C.c_int, [C.c_float, C.POINTER(C.c_int32)]),
+    "sc_gauss_taps": (C.c_int, [C.c_float, C.POINTER(C.c_int32), C.c_int]),
     "sc_run": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int, C.c_float,
                          _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_run_host": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int,
@@ -180,6 +182,13 @@ def sc_cascade_widths(fwhm_px: float) -> tuple:
     w = (C.c_int32 * 3)()
     _check(lib().sc_cascade_widths(float(fwhm_px), w), "sc_cascade_widths")
     return tuple(int(x) for x in w)
+
+
+def sc_gauss_taps(fwhm_px: float, max_taps: int = 8193) -> tuple:
+    t = (C.c_int32 * max_taps)()
+    n = lib().sc_gauss_taps(float(fwhm_px), t, int(max_taps))
+    _check(min(n, 0), "sc_gauss_taps")
+    return tuple(int(x) for x in t[:n])
 
 
 def sc_create(device: int, max_voxels: int) -> C.c_void_p:

@@ -63,6 +63,23 @@ def test_cascade_widths_match_oracle(lib):
     assert lib.sc_cascade_widths(ctypes.c_float(1e9), w) == sc.SC_ERR_ARG
 
 
+def test_sampled_gauss_taps_match_oracle(lib):
+    """The library's sampled-Gaussian taps (its own host code) equal the
+    oracle's for 2,400 FWHMs; too small a buffer or a bad FWHM is refused."""
+    from oracle.sc_oracle import gauss_taps
+    from paper_2106_15789_gb300 import sc
+
+    for f in np.linspace(0.05, 60.0, 2400):
+        f32 = float(np.float32(f))
+        assert sc.sc_gauss_taps(f32) == tuple(int(v) for v in gauss_taps(f32)), f32
+    assert sc.sc_gauss_taps(0.0) == (1024,)
+    t = (ctypes.c_int32 * 5)()
+    assert lib.sc_gauss_taps(ctypes.c_float(6.0), t, 5) == sc.SC_ERR_ARG  # needs 21 taps
+    assert lib.sc_gauss_taps(ctypes.c_float(2.0), t, 5) == sc.SC_ERR_ARG  # needs 7
+    assert lib.sc_gauss_taps(ctypes.c_float(float("nan")), t, 5) == sc.SC_ERR_ARG
+    assert lib.sc_gauss_taps(ctypes.c_float(1.0), t, 5) == 3
+
+
 def test_null_and_bad_args(lib):
     from paper_2106_15789_gb300 import sc
 
