@@ -74,8 +74,8 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_tile.cu", "sc_smooth_z.cu", "sc_smooth_p.cu",
-                  "sc_tile_common.cuh",
+SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_ws.cuh", "sc_smooth_fir.cu", "sc_smooth_tile.cu",
+                  "sc_smooth_z.cu", "sc_smooth_p.cu", "sc_tile_common.cuh",
                   "sc_device.cuh")  # the smoothing kernels' code (declarations elsewhere do not change their traffic)
 
 
@@ -149,7 +149,8 @@ def smoothing_kernel_name(sc, pair, code):
     names = {sc.SC_KERNEL_NONE: "none", sc.SC_KERNEL_IDENTITY: "k_identity", sc.SC_KERNEL_Z: "k_smooth_z",
              sc.SC_KERNEL_WS32: "k_smooth_ws<%d,%d,%d>" % w, sc.SC_KERNEL_WS16: "k_smooth_ws<%d,%d,%d>/16" % w,
              sc.SC_KERNEL_TILE: "k_smooth_tile<%d,%d,%d>" % w, sc.SC_KERNEL_GENERIC: "k_smooth_generic",
-             sc.SC_KERNEL_SHARED: "k_smooth_p<%d,%d,%d>" % w}
+             sc.SC_KERNEL_SHARED: "k_smooth_p<%d,%d,%d>" % w,
+             getattr(sc, "SC_KERNEL_FIR", -1): "k_smooth_ws<sampled %g px>" % fwhm}
     return names.get(code, "unknown")
 
 

@@ -109,6 +109,7 @@ typedef struct {
 #define SC_KERNEL_TILE 5     /* one tile per block, spatial cascade + boxcar */
 #define SC_KERNEL_GENERIC 6  /* any kernel pair */
 #define SC_KERNEL_SHARED 7   /* spectral pass over the spatial sums of an earlier pair with the same spatial kernel */
+#define SC_KERNEL_FIR 8      /* warp-specialised kernel with the sampled Gaussian's x and y FIRs + boxcar */
 
 /* Counters and timings of the context (cumulative unless reset). */
 typedef struct {

@@ -248,9 +248,11 @@ void choose_tiles(SmoothArgs* a) {
 
 cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 cudaError_t launch_smooth_ws(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
+cudaError_t launch_smooth_fir(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* done);
 void init_tile_attrs();
 void init_ws_attrs();
+void init_fir_attrs();
 void init_z_attrs();
 
 __global__ void k_fill_noise(float* __restrict__ x, long long n, unsigned int seed) {
@@ -313,6 +315,9 @@ cudaError_t launch_smooth(const SmoothArgs& a0, int sms, cudaStream_t s, int* la
   et = launch_smooth_ws(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
   if (done) return ran(ws_tile_rows(a0) == 16 ? SC_KERNEL_WS16 : SC_KERNEL_WS32);
+  et = launch_smooth_fir(a0, sms, s, &done);
+  if (et != cudaSuccess) return et;
+  if (done) return ran(SC_KERNEL_FIR);
   et = launch_smooth_tile(a0, sms, s, &done);
   if (et != cudaSuccess) return et;
   if (done) return ran(SC_KERNEL_TILE);
@@ -347,6 +352,7 @@ void init_kernel_attrs() {
   cudaFuncSetAttribute(k_smooth_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   init_tile_attrs();
   init_ws_attrs();
+  init_fir_attrs();
   init_z_attrs();
   init_share_attrs();
   init_noise_attrs();

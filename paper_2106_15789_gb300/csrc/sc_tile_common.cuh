@@ -59,6 +59,61 @@ __device__ __forceinline__ void cascade_stream(Load load, Out out) {
   }
 }
 
+// Streams NOUT + 2R inputs load(i) through a centred FIR of 2R + 1 integer
+// taps (non-negative, below 2^20): out(k, v) receives the exact sum
+// v = sum_d taps[d] * load(k + d), d = 0..2R. Each int64 input is split into
+// its unsigned low and signed high 32-bit halves, whose wide products with the
+// tap accumulate in two 64-bit sums (neither can overflow for fewer than 2^12
+// taps); the two recombine modulo 2^64, exact whenever the true sum fits in
+// int64. With compile-time indices the taps are read straight from the
+// kernel's parameters.
+template <int R, int NOUT, class Load, class Out>
+__device__ __forceinline__ void fir_stream(const int* __restrict__ taps, Load load, Out out) {
+  if constexpr (NOUT > 8) {
+    // in runs of 8 outputs: fewer live sums (registers) for a few more loads
+    fir_stream<R, 8>(taps, load, out);
+    fir_stream<R, NOUT - 8>(
+        taps, [&](int i) { return load(i + 8); }, [&](int k, long long v) { out(k + 8, v); });
+  } else {
+    unsigned long long lo_acc[NOUT];
+    long long hi_acc[NOUT];
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) {
+      lo_acc[k] = 0ull;
+      hi_acc[k] = 0ll;
+    }
+#pragma unroll
+    for (int i = 0; i < NOUT + 2 * R; ++i) {
+      const long long x = load(i);
+      const unsigned lo = (unsigned)((unsigned long long)x & 0xffffffffull);
+      const int hi = (int)(x >> 32);
+#pragma unroll
+      for (int k = 0; k < NOUT; ++k) {
+        const int d = i - k;
+        if (d >= 0 && d <= 2 * R) {
+          const int t = taps[d];
+          lo_acc[k] += (unsigned long long)lo * (unsigned)t;
+          hi_acc[k] += (long long)hi * (long long)t;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) out(k, (long long)(lo_acc[k] + ((unsigned long long)hi_acc[k] << 32)));
+  }
+}
+
+// The spatial kernel along one axis: the 3-box cascade <W1, W2, W3>, or, for
+// W1 == 0, the FIR of half-width W2 with the 2 W2 + 1 taps `taps` (unused by
+// the cascade).
+template <int W1, int W2, int W3, int NOUT, class Load, class Out>
+__device__ __forceinline__ void spatial_stream(const int* __restrict__ taps, Load load, Out out) {
+  if constexpr (W1 == 0) {
+    fir_stream<W2, NOUT>(taps, load, out);
+  } else {
+    cascade_stream<W1, W2, W3, NOUT>(load, out);
+  }
+}
+
 // ---- Tensor Memory as ring storage ----------------------------------------
 // A block allocates all 512 columns of its SM's TMEM (one block per SM). Warp
 // w may access lanes 32*(w%4) .. +31 only.

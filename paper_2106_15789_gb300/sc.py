@@ -56,7 +56,7 @@ SC_MAX_KERNELS = 64
 
 # smoothing kernel a pair ran on (stats()["smooth_kernel_pair"])
 SC_KERNEL_NONE, SC_KERNEL_IDENTITY, SC_KERNEL_Z, SC_KERNEL_WS32, SC_KERNEL_WS16, SC_KERNEL_TILE, SC_KERNEL_GENERIC, \
-    SC_KERNEL_SHARED = range(8)
+    SC_KERNEL_SHARED, SC_KERNEL_FIR = range(9)
 
 
 class sc_kernel(C.Structure):

@@ -65,7 +65,7 @@ def test_record_traffic_means(tmp_path, monkeypatch):
 
 class _FakeSc:
     SC_KERNEL_NONE, SC_KERNEL_IDENTITY, SC_KERNEL_Z, SC_KERNEL_WS32, SC_KERNEL_WS16 = 0, 1, 2, 3, 4
-    SC_KERNEL_TILE, SC_KERNEL_GENERIC, SC_KERNEL_SHARED = 5, 6, 7
+    SC_KERNEL_TILE, SC_KERNEL_GENERIC, SC_KERNEL_SHARED, SC_KERNEL_FIR = 5, 6, 7, 8
 
     @staticmethod
     def sc_cascade_widths(fwhm):

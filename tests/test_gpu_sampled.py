@@ -102,7 +102,7 @@ def check_run(ctx, cube, kernels, t=T, n=N_REPL, mode="mad"):
     for (fs, wz), kind in zip(kernels, kinds):
         assert kind != sc.SC_KERNEL_SHARED
         if fs > 1.0:
-            assert kind == sc.SC_KERNEL_GENERIC, (fs, wz, kind)
+            assert kind == (sc.SC_KERNEL_FIR if fs <= 10.0 and wz <= 31 else sc.SC_KERNEL_GENERIC), (fs, wz, kind)
     return sig
 
 
