@@ -16,6 +16,7 @@ namespace sc {
 namespace {
 
 // Re-centre the pair's 2h + 1 taps on a support of 2R + 1 (zeros outside).
+// The sampled Gaussian's taps are symmetric, as the FIR passes require.
 SmoothArgs padded_taps(const SmoothArgs& a0, int R) {
   SmoothArgs a = a0;
   const int h = a0.pd.h;
@@ -53,6 +54,8 @@ cudaError_t launch_smooth_fir(const SmoothArgs& a, int sms, cudaStream_t s, bool
   *done = false;
   if (a.generic || !a.pd.sampled || a.pd.h < 1 || a.pd.wz > ws::Tile<16>::kMaxWz) return cudaSuccess;
   const int h = a.pd.h;
+  for (int i = 0; i < h; ++i)
+    if (a.pd.taps[i] != a.pd.taps[2 * h - i]) return cudaSuccess;  // not symmetric: not served
   if (h <= 4) return launch_fir<4>(a, sms, s, done);
   if (h <= 8) return launch_fir<8>(a, sms, s, done);
   if (h <= 9) return launch_fir<9>(a, sms, s, done);

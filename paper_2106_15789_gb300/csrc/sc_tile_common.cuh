@@ -59,46 +59,42 @@ __device__ __forceinline__ void cascade_stream(Load load, Out out) {
   }
 }
 
-// Streams NOUT + 2R inputs load(i) through a centred FIR of 2R + 1 integer
-// taps (non-negative, below 2^20): out(k, v) receives the exact sum
-// v = sum_d taps[d] * load(k + d), d = 0..2R. Each int64 input is split into
-// its unsigned low and signed high 32-bit halves, whose wide products with the
-// tap accumulate in two 64-bit sums (neither can overflow for fewer than 2^12
-// taps); the two recombine modulo 2^64, exact whenever the true sum fits in
-// int64. With compile-time indices the taps are read straight from the
-// kernel's parameters.
+// Streams NOUT + 2R inputs load(i) through a centred FIR of 2R + 1 symmetric
+// integer taps (taps[d] == taps[2R - d], non-negative, below 2^20): out(k, v)
+// receives the exact sum v = sum_d taps[d] * load(k + d), d = 0..2R, taken as
+// taps[R] * x[k + R] + sum_{d < R} taps[d] * (x[k + d] + x[k + 2R - d]), so
+// that the two inputs sharing a tap are added before one multiplication. Each
+// int64 operand is split into its unsigned low and signed high 32-bit halves,
+// whose wide products with the tap accumulate in two 64-bit sums (neither can
+// overflow for fewer than 2^12 taps); the two recombine modulo 2^64, exact
+// whenever the true sum fits in int64 (so does every pair sum, each at most
+// twice an input). Outputs are made C at a time from a register window of
+// C + 2R inputs. With compile-time indices the taps are read straight from
+// the kernel's parameters.
 template <int R, int NOUT, class Load, class Out>
 __device__ __forceinline__ void fir_stream(const int* __restrict__ taps, Load load, Out out) {
-  if constexpr (NOUT > 8) {
-    // in runs of 8 outputs: fewer live sums (registers) for a few more loads
-    fir_stream<R, 8>(taps, load, out);
-    fir_stream<R, NOUT - 8>(
-        taps, [&](int i) { return load(i + 8); }, [&](int k, long long v) { out(k + 8, v); });
-  } else {
-    unsigned long long lo_acc[NOUT];
-    long long hi_acc[NOUT];
+  constexpr int C = NOUT < 4 ? NOUT : 4;
 #pragma unroll
-    for (int k = 0; k < NOUT; ++k) {
-      lo_acc[k] = 0ull;
-      hi_acc[k] = 0ll;
-    }
+  for (int c0 = 0; c0 < NOUT; c0 += C) {
+    long long w[C + 2 * R];
 #pragma unroll
-    for (int i = 0; i < NOUT + 2 * R; ++i) {
-      const long long x = load(i);
-      const unsigned lo = (unsigned)((unsigned long long)x & 0xffffffffull);
-      const int hi = (int)(x >> 32);
+    for (int i = 0; i < C + 2 * R; ++i) w[i] = (c0 + i < NOUT + 2 * R) ? load(c0 + i) : 0ll;
 #pragma unroll
-      for (int k = 0; k < NOUT; ++k) {
-        const int d = i - k;
-        if (d >= 0 && d <= 2 * R) {
-          const int t = taps[d];
-          lo_acc[k] += (unsigned long long)lo * (unsigned)t;
-          hi_acc[k] += (long long)hi * (long long)t;
+    for (int k = 0; k < C; ++k) {
+      if (c0 + k < NOUT) {
+        const long long xc = w[k + R];
+        unsigned long long lo_acc = (unsigned long long)(unsigned)((unsigned long long)xc & 0xffffffffull) *
+                                    (unsigned)taps[R];
+        long long hi_acc = (long long)(int)(xc >> 32) * (long long)taps[R];
+#pragma unroll
+        for (int d = 0; d < R; ++d) {
+          const long long p = w[k + d] + w[k + 2 * R - d];
+          lo_acc += (unsigned long long)(unsigned)((unsigned long long)p & 0xffffffffull) * (unsigned)taps[d];
+          hi_acc += (long long)(int)(p >> 32) * (long long)taps[d];
         }
+        out(c0 + k, (long long)(lo_acc + ((unsigned long long)hi_acc << 32)));
       }
     }
-#pragma unroll
-    for (int k = 0; k < NOUT; ++k) out(k, (long long)(lo_acc[k] + ((unsigned long long)hi_acc[k] << 32)));
   }
 }
 
