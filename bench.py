@@ -141,11 +141,16 @@ def record_traffic(specs, command):
     return 0
 
 
-def smoothing_kernel_name(sc, pair, code):
+def smoothing_kernel_name(sc, pair, code, sampled=False):
     """Name of the smoothing kernel a pair ran on, from the SC_KERNEL_* code
-    the library reports for it and the pair's cascade widths."""
+    the library reports for it and the pair's cascade widths (or, for the
+    sampled Gaussian, its FWHM)."""
     fwhm, _ = pair
     w = tuple(sc.sc_cascade_widths(fwhm)) if fwhm > 0 else (1, 1, 1)
+    if sampled and fwhm > 0:
+        names = {sc.SC_KERNEL_Z: "k_smooth_z", getattr(sc, "SC_KERNEL_FIR", -1): "k_smooth_ws<sampled %g px>" % fwhm,
+                 sc.SC_KERNEL_SHARED: "k_smooth_p<sampled %g px>" % fwhm, sc.SC_KERNEL_GENERIC: "k_smooth_generic"}
+        return names.get(code, "unknown")
     names = {sc.SC_KERNEL_NONE: "none", sc.SC_KERNEL_IDENTITY: "k_identity", sc.SC_KERNEL_Z: "k_smooth_z",
              sc.SC_KERNEL_WS32: "k_smooth_ws<%d,%d,%d>" % w, sc.SC_KERNEL_WS16: "k_smooth_ws<%d,%d,%d>/16" % w,
              sc.SC_KERNEL_TILE: "k_smooth_tile<%d,%d,%d>" % w, sc.SC_KERNEL_GENERIC: "k_smooth_generic",
@@ -383,7 +388,7 @@ def gauss_hist_roofline(st, peak, peak_kind):
             "frac": gbs / peak, "peak_kind": peak_kind, "bytes_per_value": 4, "traffic": None}
 
 
-def pair_kernels(sc, kernels, codes):
+def pair_kernels(sc, kernels, codes, sampled=False):
     """(kernel name, algorithmic bytes per voxel) of every pair: a full
     smoothing pass reads C and the mask bits and writes S; the first pair of a
     run that the next pairs share also writes its int64 spatial sums; a shared
@@ -391,23 +396,23 @@ def pair_kernels(sc, kernels, codes):
     out = []
     for k, pair in enumerate(kernels):
         code = codes[k]
-        name = smoothing_kernel_name(sc, pair, code)
+        name = smoothing_kernel_name(sc, pair, code, sampled)
         if code == sc.SC_KERNEL_SHARED:
             out.append((name, SHARED_BYTES_PER_VOXEL))
         elif (k + 1 < len(kernels) and codes[k + 1] == sc.SC_KERNEL_SHARED and kernels[k + 1][0] == pair[0]
-              and code in (sc.SC_KERNEL_WS32, sc.SC_KERNEL_WS16)):
+              and code in (sc.SC_KERNEL_WS32, sc.SC_KERNEL_WS16, getattr(sc, "SC_KERNEL_FIR", -1))):
             out.append((name + "+P", STORE_BYTES_PER_VOXEL))
         else:
             out.append((name, SMOOTH_BYTES_PER_VOXEL))
     return out
 
 
-def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind):
+def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind, sampled=False):
     """Roofline object of the smoothing kernel with the largest share of the
     profiled smoothing time (per-pair CUDA events recorded by the library):
     algorithmic bytes of its launches over their event time."""
     groups = {}
-    for k, (name, bpv) in enumerate(pair_kernels(sc, kernels, st["smooth_kernel_pair"])):
+    for k, (name, bpv) in enumerate(pair_kernels(sc, kernels, st["smooth_kernel_pair"], sampled)):
         n_l = st["smooth_launches_pair"][k]
         if n_l == 0:
             continue
@@ -1294,7 +1299,7 @@ def main():
     # roofline of the dominant kernel: the smoothing kernel with the largest
     # share of device time (live events, grouped by the kernel each pair runs)
     peak, peak_kind = measured_hbm_peak()
-    roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind)
+    roofline = dominant_kernel(sc, kernels, st, nvox, args.steps, peak, peak_kind, sampled)
     roofline["measured_in"] = "the profiled repeat of the timed steps (per-pair CUDA events on the launching stream)"
     mask_f32 = mask.clone() if not args.no_forms and world == 1 and mode == "mad" and not sampled else None
 

@@ -559,8 +559,11 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
         CK(launch_smooth(a, c->sms, s, &l, &code));
         c->stats.launches += l;
         c->stats.smooth_kernel_pair[k] = code;
-        if (code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16) c->test_skip_handoff = 0;
-        if (share_mode == 1 && (code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16)) p_owner = k;
+        // the warp-specialised kernel (cascade or FIR) takes the test hook and
+        // is the one that stores the spatial sums
+        const bool ws_kernel = code == SC_KERNEL_WS32 || code == SC_KERNEL_WS16 || code == SC_KERNEL_FIR;
+        if (ws_kernel) c->test_skip_handoff = 0;
+        if (share_mode == 1 && ws_kernel) p_owner = k;
       }
     }
     rc = measure(c, c->S, n, 1, t, 1, noise_mode, k, force, s);

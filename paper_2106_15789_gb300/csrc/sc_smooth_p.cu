@@ -296,7 +296,6 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
   const unsigned char* const NFs = smem + L.nf;
   unsigned long long* const Es = reinterpret_cast<unsigned long long*>(smem + L.e);
   int* const taps1 = reinterpret_cast<int*>(smem + L.kk);
-  constexpr TapArr K = taps_for<R>();
   Meta* const meta = reinterpret_cast<Meta*>(smem + L.meta);
   unsigned* const hist = reinterpret_cast<unsigned*>(smem + L.hist);
   const unsigned mbar = smem_u32(smem + L.mbar);
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
     for (int i = tid; i < kNumBins; i += kThreads) hist[i] = 0u;
 #pragma unroll
   for (int i = 0; i < NT; ++i)
-    if (tid == i) taps1[i] = K.v[i];  // compile-time indices keep K out of local memory
+    if (tid == i) taps1[i] = a.pd.taps[i];  // compile-time indices: read from the kernel parameters
   __shared__ unsigned tmem_holder;
   if (warp == 0) tmem_alloc(&tmem_holder);
   if (tid == 0) {
@@ -603,8 +602,15 @@ bool encode_nf_map(CUtensorMap* map, const unsigned char* base, long long nx, lo
   return cr == CUDA_SUCCESS;
 }
 
-// Spatial half-width R of the cascades the warp-specialised kernel serves.
+// Half-width R of the shared-pass instance that serves a spatial kernel: the
+// cascades' own half-widths; for a sampled Gaussian of half-width h the
+// smallest instantiated R >= h (its taps centred and zero-padded to 2R + 1).
 int share_R(const PairDesc& pd) {
+  if (pd.sampled) {
+    for (int r : {4, 8, 9, 12, 16})
+      if (pd.h <= r) return pd.h >= 1 ? r : -1;
+    return -1;
+  }
   const int* w = pd.w;
   if (w[0] == 1 && w[1] == 3 && w[2] == 3) return 2;
   if (w[0] == 3 && w[1] == 5 && w[2] == 5) return 5;
@@ -617,10 +623,20 @@ template <int TY, int R>
 cudaError_t launch_p(const SmoothArgs& a0, const ShareArgs& sh, int sms, cudaStream_t s) {
   using namespace share;
   constexpr PSmem L = p_layout<TY, R>();
-  constexpr TapArr K = taps_for<R>();
-  for (int i = 0; i < 2 * R + 1; ++i)
-    if (a0.pd.taps[i] != K.v[i]) return cudaErrorInvalidValue;  // not the cascade this instance serves
   SmoothArgs a = a0;
+  if (a0.pd.sampled) {
+    // the sampled Gaussian's 2h + 1 taps centred in 2R + 1
+    const int h = a0.pd.h;
+    if (h > R) return cudaErrorInvalidValue;
+    for (int i = 0; i < 2 * kMaxHalf + 1; ++i) a.pd.taps[i] = 0;
+    for (int i = 0; i < 2 * h + 1; ++i) a.pd.taps[R - h + i] = a0.pd.taps[i];
+  } else if (R <= 11) {
+    constexpr TapArr K = taps_for<(R <= 11 ? R : 11)>();
+    for (int i = 0; i < 2 * R + 1; ++i)
+      if (a0.pd.taps[i] != K.v[i]) return cudaErrorInvalidValue;  // not the cascade this instance serves
+  } else {
+    return cudaErrorInvalidValue;
+  }
   CUtensorMap map, nfmap;
   if (!encode_p_map(&map, sh.P, a.nx, a.ny, a.nz, sh.pitch, TX, TY) ||
       !encode_nf_map(&nfmap, sh.nf, a.nx, (a.ny + 7) / 8, a.nz, sh.nfpitch, TX, TY / 8))
@@ -653,9 +669,15 @@ template <int TY>
 cudaError_t launch_p_ty(const SmoothArgs& a, const ShareArgs& sh, int R, int sms, cudaStream_t s) {
   switch (R) {
     case 2: return launch_p<TY, 2>(a, sh, sms, s);
+    case 4: return launch_p<TY, 4>(a, sh, sms, s);
     case 5: return launch_p<TY, 5>(a, sh, sms, s);
     case 6: return launch_p<TY, 6>(a, sh, sms, s);
-    default: return launch_p<TY, 11>(a, sh, sms, s);
+    case 8: return launch_p<TY, 8>(a, sh, sms, s);
+    case 9: return launch_p<TY, 9>(a, sh, sms, s);
+    case 11: return launch_p<TY, 11>(a, sh, sms, s);
+    case 12: return launch_p<TY, 12>(a, sh, sms, s);
+    case 16: return launch_p<TY, 16>(a, sh, sms, s);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -673,13 +695,14 @@ int share_tile_rows(int wz) {
 }
 
 bool share_supported(const PairDesc& pd) {
-  return !pd.sampled && pd.h > 0 && share_R(pd) == pd.h && pd.wz <= kShareMaxWz && share_tile_rows(pd.wz) > 0;
+  const int R = share_R(pd);
+  return pd.h > 0 && (pd.sampled ? R >= pd.h : R == pd.h) && pd.wz <= kShareMaxWz && share_tile_rows(pd.wz) > 0;
 }
 
 cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms, cudaStream_t s) {
   using namespace share;
   const long long n = (long long)a.nx * a.ny * a.nz;
-  const int R = a.pd.h;
+  const int R = share_R(a.pd);  // the reach the shared pass decodes its entries with
   const long long m = sh.n_buckets + 1;
   const long long nblk = (m + kScanChunk - 1) / kScanChunk;
   k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
@@ -694,7 +717,8 @@ cudaError_t launch_smooth_p(const SmoothArgs& a, const ShareArgs& sh, int sms, c
   if (!share_supported(a.pd)) return cudaSuccess;
   const int ty = share_tile_rows(a.pd.wz);
   if (ty != sh.ty) return cudaSuccess;
-  const cudaError_t e = ty == 32 ? launch_p_ty<32>(a, sh, a.pd.h, sms, s) : launch_p_ty<16>(a, sh, a.pd.h, sms, s);
+  const int R = share_R(a.pd);
+  const cudaError_t e = ty == 32 ? launch_p_ty<32>(a, sh, R, sms, s) : launch_p_ty<16>(a, sh, R, sms, s);
   if (e == cudaSuccess) *done = true;
   return e;
 }
@@ -708,6 +732,17 @@ void init_share_attrs() {
   set_p_attr<16, 5>();
   set_p_attr<16, 6>();
   set_p_attr<16, 11>();
+  // sampled Gaussians (half-widths up to 4, 8, 9, 12, 16)
+  set_p_attr<32, 4>();
+  set_p_attr<32, 8>();
+  set_p_attr<32, 9>();
+  set_p_attr<32, 12>();
+  set_p_attr<32, 16>();
+  set_p_attr<16, 4>();
+  set_p_attr<16, 8>();
+  set_p_attr<16, 9>();
+  set_p_attr<16, 12>();
+  set_p_attr<16, 16>();
 }
 
 }  // namespace sc

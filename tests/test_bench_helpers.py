@@ -134,3 +134,14 @@ def test_interior_subcubes():
                     boxes.add((z + dz, y + dy, x + dx))
     c16, _ = bench.interior_subcubes((1024, 1200, 1200), 16)
     assert c16 == corners[:16]
+
+
+def test_pair_kernels_sampled_gaussian():
+    """Sampled-Gaussian runs: the FIR kernel stores the spatial sums of its
+    run (+P) and the shared passes are named by the FWHM."""
+    kernels = [(0.0, 0), (0.0, 3), (3.0, 0), (3.0, 3), (6.0, 0), (6.0, 7)]
+    codes = [0, 2, 8, 7, 8, 7] + [0] * 58
+    pk = bench.pair_kernels(_FakeSc, kernels, codes, sampled=True)
+    assert pk == [("none", 8.125), ("k_smooth_z", 8.125), ("k_smooth_ws<sampled 3 px>+P", 16.125),
+                  ("k_smooth_p<sampled 3 px>", 12.0), ("k_smooth_ws<sampled 6 px>+P", 16.125),
+                  ("k_smooth_p<sampled 6 px>", 12.0)]

@@ -5,8 +5,9 @@ within +-4 sigma with integer taps, over their sum).
 Smoothing: element by element within the parity tolerance (1e-5 sigma) and
 within a few float ulps plus the fixed-point quantum, with and without a
 replacement mask, on the small cube and on ragged shapes. S+C: sigmas within
-1e-6 relative, mask bit-exact outside the threshold band. Runs never take the
-shared spatial passes for these pairs, and a kernel too wide for the smoothing
+1e-6 relative, mask bit-exact outside the threshold band; the first pair of a
+spatial kernel runs the warp-specialised FIR kernel, the later ones share its
+spatial sums (half-widths up to 16). A kernel too wide for the smoothing
 kernels is refused.
 """
 import numpy as np
@@ -99,10 +100,12 @@ def check_run(ctx, cube, kernels, t=T, n=N_REPL, mode="mad"):
     diff = np.argwhere(m.cpu().numpy() != m_ref)
     for p in map(tuple, diff):
         assert any(sk > 0 and abs(abs(s[p]) / sk - t) < BAND for s, sk in zip(ss, s_ref)), p
-    for (fs, wz), kind in zip(kernels, kinds):
-        assert kind != sc.SC_KERNEL_SHARED
-        if fs > 1.0:
-            assert kind == (sc.SC_KERNEL_FIR if fs <= 10.0 and wz <= 31 else sc.SC_KERNEL_GENERIC), (fs, wz, kind)
+    for k, ((fs, wz), kind) in enumerate(zip(kernels, kinds)):
+        if fs > 1.0 and fs <= 10.0 and wz <= 31:
+            shared = k > 0 and kernels[k - 1][0] == fs
+            assert kind == (sc.SC_KERNEL_SHARED if shared else sc.SC_KERNEL_FIR), (fs, wz, kind)
+        elif fs > 1.0:
+            assert kind == sc.SC_KERNEL_GENERIC, (fs, wz, kind)
     return sig
 
 

@@ -49,14 +49,14 @@ def same_bits(a: torch.Tensor, b: torch.Tensor) -> bool:
     return torch.equal(a.view(torch.int32), b.view(torch.int32))
 
 
-def check_shared_equals_full(ctx, cube, kernels, t=T, n=N_REPL, mask0=None, expect_shared=True):
+def check_shared_equals_full(ctx, cube, kernels, t=T, n=N_REPL, mask0=None, expect_shared=True, flags=0):
     from paper_2106_15789_gb300 import sc
 
     dev = cube.cuda()
     ctx.stats(reset=True)
-    m1, sig1, s01, S1 = run_s(ctx, dev, kernels, 0, t, n, mask0)
+    m1, sig1, s01, S1 = run_s(ctx, dev, kernels, flags, t, n, mask0)
     kinds = ctx.stats()["smooth_kernel_pair"][: len(kernels)]
-    m2, sig2, s02, S2 = run_s(ctx, dev, kernels, sc.SC_FLAG_NO_SHARE, t, n, mask0)
+    m2, sig2, s02, S2 = run_s(ctx, dev, kernels, flags | sc.SC_FLAG_NO_SHARE, t, n, mask0)
     assert s01 == s02
     assert sig1 == sig2, (sig1, sig2)
     assert np.array_equal(m1, m2), int((m1 != m2).sum())
@@ -167,3 +167,27 @@ def test_list_overflow_falls_back_to_full_kernel(ctx):
     _, sig0, _, S0, _ = check_shared_equals_full(ctx, cube, KERNELS_12, t=2.5)
     assert sig == sig0
     assert same_bits(S, S0)
+
+
+@pytest.mark.parametrize("fwhm", [2.5, 3.0, 5.0, 6.0, 7.3, 10.0])
+def test_sampled_gaussian_pairs_shared(ctx, fwhm):
+    """Sampled-Gaussian pairs (half-widths 3 to 16, taps zero-padded to the
+    instance's reach) share their spatial sums bit for bit, with 32- and
+    16-row tiles, a caller mask, and against the oracle's reading of them."""
+    from paper_2106_15789_gb300 import sc
+
+    cube = make_cube(CubeSpec(nx=90, ny=70, nz=80, seed=25, n_gal=10, snr=(3.0, 20.0), fwhm_xy=(2.0, 8.0),
+                              fwhm_z=(5.0, 30.0), nan_corner=(15, 10, 20)))
+    ks = [(0.0, 0), (fwhm, 0), (fwhm, 3), (fwhm, 7), (fwhm, 31), (fwhm, 15)]
+    m, sig, s0, S, kinds = check_shared_equals_full(ctx, cube, ks, flags=sc.SC_FLAG_SAMPLED_GAUSS)
+    assert kinds[1] == sc.SC_KERNEL_FIR and all(k == sc.SC_KERNEL_SHARED for k in kinds[2:]), kinds
+    mask0 = np.zeros(cube.shape, dtype=bool)
+    mask0[5:30, 10:40, 20:60] = True
+    check_shared_equals_full(ctx, cube, ks[1:4], mask0=mask0, flags=sc.SC_FLAG_SAMPLED_GAUSS)
+    m_ref, s_ref, s0_ref, ss = O.sc_filter(cube.numpy(), ks, T, "mad", N_REPL, return_smoothed=True,
+                                           spatial="sampled")
+    assert abs(s0 - s0_ref) <= 1e-6 * s0_ref
+    for k, (a, b) in enumerate(zip(sig, s_ref)):
+        assert abs(a - b) <= 1e-6 * b, (k, a, b)
+    for p in map(tuple, np.argwhere(m != m_ref)):
+        assert any(abs(abs(s[p]) / sk - T) < BAND for s, sk in zip(ss, s_ref)), p
