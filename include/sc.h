@@ -98,6 +98,7 @@ typedef struct {
 #define SC_VARIANT_Z4 5        /* spectral-only, 4 voxels per thread */
 #define SC_VARIANT_WS16 6      /* warp-specialised, 64 x 16 tiles */
 #define SC_VARIANT_Z4_512 7    /* spectral-only, 4 voxels per thread, 512-thread blocks */
+#define SC_VARIANT_Z8_512 8    /* spectral-only, 8 voxels per thread, 512-thread blocks (boxcars up to 7) */
 #define SC_SMOOTH_VARIANT(v) (((uint32_t)(v) & 0xffu) << 16)
 
 /* Smoothing kernel a kernel pair ran on (sc_stats.smooth_kernel_pair). */

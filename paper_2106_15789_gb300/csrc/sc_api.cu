@@ -1141,6 +1141,7 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
         cands.push_back({TUNE_Z8, zf});
         cands.push_back({TUNE_Z4, zf});
         if (pd.wz <= 15) cands.push_back({TUNE_Z4W, zf});
+        if (pd.wz <= 7) cands.push_back({TUNE_Z8W, zf});
       }
     }
     // fixed-point scales of this pair on the synthetic cube, replacement value 1
@@ -1240,7 +1241,7 @@ int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc
 int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel kernel, const uint8_t* mask_dev,
               float replacement_value, float* out_dev, uint32_t flags, void* cuda_stream) {
   if (!c || !cube_dev || !out_dev || (const void*)cube_dev == (const void*)out_dev) return SC_ERR_ARG;
-  if (((flags >> 16) & 0xffu) > (unsigned)SC_VARIANT_Z4_512) return SC_ERR_ARG;
+  if (((flags >> 16) & 0xffu) > (unsigned)SC_VARIANT_Z8_512) return SC_ERR_ARG;
   if (!std::isfinite(replacement_value)) return SC_ERR_ARG;
   DeviceGuard g(c->device);
   long long n = 0;

@@ -239,11 +239,12 @@ enum TuneKind : int {
   TUNE_Z8 = 4,       // spectral-only kernel, 8 voxels per thread
   TUNE_Z4 = 5,       // spectral-only kernel, 4 voxels per thread
   TUNE_WS16 = 6,     // warp-specialised kernel with 64 x 16 tiles
-  TUNE_Z4W = 7       // spectral-only kernel, 4 voxels per thread, 512 threads per block
+  TUNE_Z4W = 7,      // spectral-only kernel, 4 voxels per thread, 512 threads per block
+  TUNE_Z8W = 8       // spectral-only kernel, 8 voxels per thread, 512 threads per block (boxcars up to 7)
 };
 static_assert(TUNE_WS == SC_VARIANT_WS && TUNE_TILE == SC_VARIANT_TILE && TUNE_GENERIC == SC_VARIANT_GENERIC &&
                   TUNE_Z8 == SC_VARIANT_Z8 && TUNE_Z4 == SC_VARIANT_Z4 && TUNE_WS16 == SC_VARIANT_WS16 &&
-                  TUNE_Z4W == SC_VARIANT_Z4_512,
+                  TUNE_Z4W == SC_VARIANT_Z4_512 && TUNE_Z8W == SC_VARIANT_Z8_512,
               "the public variant codes are the tuning kinds");
 inline long long tune_items_per_sm(const SmoothArgs& a) { return a.tune_zfactor > 0 ? a.tune_zfactor : 2; }
 

@@ -312,6 +312,7 @@ cudaError_t launch_z_vpt(const SmoothArgs& a, int sms, cudaStream_t s) {
 }  // namespace
 
 void init_z_attrs() {
+  set_z_attrs<8, 512>();
   set_z_attrs<4, 512>();
   set_z_attrs<8>();
   set_z_attrs<4>();
@@ -326,6 +327,8 @@ cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* 
   if (a.tune_kind == TUNE_Z4 && a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   // 512 threads of 4 voxels: twice the warps per scheduler, a 16-slot ring
   if (a.tune_kind == TUNE_Z4W && a.pd.wz <= 15) return launch_z_vpt<4, 512>(a, sms, s);
+  // 512 threads of 8 voxels: as many warps, 8 ring slots
+  if (a.tune_kind == TUNE_Z8W && a.pd.wz <= 7) return launch_z_vpt<8, 512>(a, sms, s);
   if (a.pd.wz <= 15) return launch_z_vpt<8>(a, sms, s);
   if (a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   return launch_z_vpt<1>(a, sms, s);

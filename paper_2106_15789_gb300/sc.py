@@ -38,8 +38,8 @@ SC_FLAG_NO_SHARE = 0x10
 SC_FLAG_SAMPLED_GAUSS = 0x20
 SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
 # sc_smooth kernel variants (flags |= variant << 16)
-SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512 = \
-    range(1, 8)
+SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512, \
+    SC_VARIANT_Z8_512 = range(1, 9)
 
 
 def SC_SMOOTH_VARIANT(v: int) -> int:

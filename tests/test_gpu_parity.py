@@ -301,9 +301,9 @@ def test_every_variant_gives_the_same_floats(ctx, shape):
     cube = torch.from_numpy(c).cuda()
     mask = torch.from_numpy((rng.random(shape) < 0.05).astype(np.uint8)).cuda()
     spatial = [sc.SC_VARIANT_WS, sc.SC_VARIANT_WS16, sc.SC_VARIANT_TILE]
-    spectral = [sc.SC_VARIANT_Z8, sc.SC_VARIANT_Z4, sc.SC_VARIANT_Z4_512]
-    for kernel, variants in (((0.0, 3), spectral), ((0.0, 15), spectral), ((3.0, 7), spatial), ((6.0, 15), spatial),
-                             ((5.0, 1), spatial)):
+    spectral = [sc.SC_VARIANT_Z8, sc.SC_VARIANT_Z4, sc.SC_VARIANT_Z4_512, sc.SC_VARIANT_Z8_512]
+    for kernel, variants in (((0.0, 3), spectral), ((0.0, 7), spectral), ((0.0, 15), spectral), ((3.0, 7), spatial),
+                             ((6.0, 15), spatial), ((5.0, 1), spatial)):
         for m, v in ((None, 0.0), (mask, 2.5)):
             ref = ctx.smooth(cube, kernel, mask=m, replacement_value=v, flags=sc.SC_FLAG_GENERIC).clone()
             for var in variants:
