@@ -37,7 +37,7 @@ SHARED_BYTES_PER_VOXEL = 8.0 + 4.0  # read P', write S (the correction lists add
 WORKLOADS = ("wallaby", "medium", "small", "batch64", "small-bf16", "small-fp16", "wallaby-bf16", "wallaby-fp16",
              "stream512", "wallaby-noisescale", "medium-noisescale", "wallaby-link", "wallaby-autoflag",
              "wallaby-gauss", "medium-gauss", "wallaby-noisescale-gauss", "wallaby-autoflag-gauss",
-             "wallaby-sampled", "medium-sampled", "small-sampled")
+             "wallaby-sampled", "medium-sampled", "small-sampled", "medium-fp16", "medium-bf16")
 FLAG_METRIC = "auto-flagger voxels/s on 1 GB300 (channel and pixel MAD noise, k = 4)"
 LINK_METRIC = "linker voxels/s on 1 GB300 (friends-of-friends, radius 2, minimum sizes 8 px / 5 ch)"
 NOISE_SCALE_METRIC = "local noise normalisation voxels/s on 1 GB300 (31-voxel windows, 16-voxel cells)"
@@ -74,7 +74,7 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_ws.cuh", "sc_smooth_fir.cu", "sc_smooth_tile.cu",
+SMOOTH_SOURCES = ("sc_smooth.cu", "sc_smooth_ws.cu", "sc_smooth_ws.cuh", "sc_smooth_fir.cu", "sc_smooth_ws16.cu", "sc_smooth_tile.cu",
                   "sc_smooth_z.cu", "sc_smooth_p.cu", "sc_tile_common.cuh",
                   "sc_device.cuh")  # the smoothing kernels' code (declarations elsewhere do not change their traffic)
 
@@ -362,13 +362,15 @@ def config_dict(workload, kernels, mode="mad"):
              "small-fp16": "small-64x64x128 stored as FP16 + per-channel float32 scales",
              "wallaby-bf16": "wallaby-1200x1200x1024 stored as BF16 + per-channel float32 scales",
              "wallaby-fp16": "wallaby-1200x1200x1024 stored as FP16 + per-channel float32 scales",
+             "medium-bf16": "medium-512x512x512 stored as BF16 + per-channel float32 scales",
+             "medium-fp16": "medium-512x512x512 stored as FP16 + per-channel float32 scales",
              "batch64": "batch-64-subcubes-x,y~logU[128,512]-z~logU[256,1024]"}
     workload = workload.removesuffix("-gauss")
     sampled = workload.endswith("-sampled")
     workload = workload.removesuffix("-sampled")
     half = workload.endswith(("-bf16", "-fp16"))
-    precision = ("%s cube + per-channel float32 scales, decoded to float32 once per run, exact fixed-point smoothing"
-                 % workload.split("-")[-1].upper()) if half else "float32 cube, exact fixed-point smoothing"
+    precision = ("%s cube + per-channel float32 scales, read as 16-bit values by the kernels, exact fixed-point "
+                 "smoothing" % workload.split("-")[-1].upper()) if half else "float32 cube, exact fixed-point smoothing"
     big = workload in ("wallaby", "wallaby-bf16", "wallaby-fp16")
     return {"workload": names[workload], "kernels": "spatial {0,3,6} px x spectral {0,3,7,15} ch",
             "spatial_kernel": "sampled Gaussian (integer taps within 4 sigma)" if sampled else "3-box cascade",
@@ -388,11 +390,13 @@ def gauss_hist_roofline(st, peak, peak_kind):
             "frac": gbs / peak, "peak_kind": peak_kind, "bytes_per_value": 4, "traffic": None}
 
 
-def pair_kernels(sc, kernels, codes, sampled=False):
+def pair_kernels(sc, kernels, codes, sampled=False, cube_bytes=4.0):
     """(kernel name, algorithmic bytes per voxel) of every pair: a full
     smoothing pass reads C and the mask bits and writes S; the first pair of a
     run that the next pairs share also writes its int64 spatial sums; a shared
-    pass reads those and writes S."""
+    pass reads those and writes S. cube_bytes: bytes per cube value read (2
+    for a 16-bit cube the kernels read as such)."""
+    d = 4.0 - cube_bytes
     out = []
     for k, pair in enumerate(kernels):
         code = codes[k]
@@ -401,18 +405,18 @@ def pair_kernels(sc, kernels, codes, sampled=False):
             out.append((name, SHARED_BYTES_PER_VOXEL))
         elif (k + 1 < len(kernels) and codes[k + 1] == sc.SC_KERNEL_SHARED and kernels[k + 1][0] == pair[0]
               and code in (sc.SC_KERNEL_WS32, sc.SC_KERNEL_WS16, getattr(sc, "SC_KERNEL_FIR", -1))):
-            out.append((name + "+P", STORE_BYTES_PER_VOXEL))
+            out.append((name + "+P", STORE_BYTES_PER_VOXEL - d))
         else:
-            out.append((name, SMOOTH_BYTES_PER_VOXEL))
+            out.append((name, SMOOTH_BYTES_PER_VOXEL - d))
     return out
 
 
-def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind, sampled=False):
+def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind, sampled=False, cube_bytes=4.0):
     """Roofline object of the smoothing kernel with the largest share of the
     profiled smoothing time (per-pair CUDA events recorded by the library):
     algorithmic bytes of its launches over their event time."""
     groups = {}
-    for k, (name, bpv) in enumerate(pair_kernels(sc, kernels, st["smooth_kernel_pair"], sampled)):
+    for k, (name, bpv) in enumerate(pair_kernels(sc, kernels, st["smooth_kernel_pair"], sampled, cube_bytes)):
         n_l = st["smooth_launches_pair"][k]
         if n_l == 0:
             continue
@@ -745,7 +749,8 @@ def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None
     ctx.set_profiling(False)
     st = ctx.stats(reset=True)
     peak, peak_kind = measured_hbm_peak()
-    roofline = dominant_kernel(sc, kernels, st, nvox, 1, peak, peak_kind)
+    in_kernel = int(st["half_path"]) == 1
+    roofline = dominant_kernel(sc, kernels, st, nvox, 1, peak, peak_kind, cube_bytes=2.0 if in_kernel else 4.0)
     roofline["measured_in"] = "one profiled step after the timed region"
     m_h = m_h.clone()
     e2e = None
@@ -759,6 +764,21 @@ def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None
         m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
         ref = (m_f.clone(), sig_f, s0_f)
     prec = half_precision(cube, bits, scale, bf16, m_h, sig_h, s0_h, *ref, with_oracle)
+    prec["cube_read_by_kernels"] = in_kernel
+    if not bf16 and not with_oracle:
+        # mitigation study: FP16 plus a float32 sideband of the values above
+        # 2.5 sigma_0 (the float32 path on the decoded cube with those values
+        # restored), against float32
+        from synth.cubes import decode_half
+
+        dec = torch.from_numpy(decode_half(bits.cpu().numpy(), scale.cpu().numpy(), False)).to(dev)
+        side = cube.abs() > 2.5 * ref[2]
+        patched = torch.where(side, cube, dec)
+        del dec
+        m_s, _, _ = ctx.run(patched, kernels, t, "mad", n_repl)
+        prec["sideband_2p5_sigma0"] = {"sideband_frac": float(side.float().mean().item()),
+                                       "mask_disagreement_frac_vs_float32": int((m_s != ref[0]).sum().item()) / nvox}
+        del patched, side
     del bits, scale, mask
     return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": max(2, warmup),
             "dtype": "bf16" if bf16 else "fp16", "roofline": roofline, "gpu_launches": launches, "e2e": e2e,
@@ -787,6 +807,8 @@ def run_half_bench(args, rank, world, local):
     sc.lib()
     spec, cube = make_workload(base, rank, str(dev))
     ctx = Context(local, cube.numel())
+    if not args.no_autotune:
+        ctx.autotune(cube.shape, KERNELS_12)  # as the plain form does, once per cube shape before timing
     r = measure_half(ctx, cube, fmt == "bf16", args.steps, args.warmup, local, pg, world, dev,
                      with_oracle=(base == "small"))
     if rank == 0:

@@ -68,6 +68,7 @@ extern "C" {
 #define SC_FLAG_GRAPH 0x8u          /* sc_run_batch: capture the batch once into a CUDA graph and replay it */
 #define SC_FLAG_NO_SHARE 0x10u      /* smooth every pair in full (no shared spatial passes; same results, slower) */
 #define SC_FLAG_SAMPLED_GAUSS 0x20u /* spatial kernels are sampled Gaussians (sc_gauss_taps), not 3-box cascades */
+#define SC_FLAG_HALF_DIRECT 0x40u   /* sc_run_half / 16-bit jobs: every kernel reads the 16-bit cube (no float32 copy) */
 
 /* ---- warning bits (sc_stats.warnings, set per run) -------------------- */
 #define SC_WARN_ZERO_SIGMA 0x1u     /* some pair had sigma == 0 and added nothing to the mask */
@@ -117,7 +118,9 @@ typedef struct {
   uint64_t launches;      /* CUDA kernels this library launched */
   uint64_t runs;          /* completed sc_run / sc_run_host calls */
   uint32_t warnings;      /* SC_WARN_* bits of the last run */
-  uint32_t reserved;
+  uint32_t half_path;     /* last run's cube: 0 float32; 16-bit (sc_run_half, 16-bit jobs): 1 read as such by
+                             every kernel (SC_FLAG_HALF_DIRECT), 2 decoded into a float32 copy by a pass of its
+                             own, 3 decoded into that copy by the first raw-cube histogram pass */
   double ms_smooth;       /* device time of smoothing kernels (only while profiling is on) */
   double ms_select;       /* device time of histogram/plan/candidate/select kernels */
   double ms_clip;         /* device time of mask kernels and of the 16-bit decode (sc_run_half) */

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["sc_api.cu", "sc_smooth.cu", "sc_smooth_tile.cu", "sc_smooth_ws.cu", "sc_smooth_fir.cu", "sc_smooth_z.cu", "sc_smooth_p.cu", "sc_noise.cu", "sc_noise_scale.cu", "sc_linker.cu", "sc_flagger.cu", "sc_static.cu",
+SOURCES = ["sc_api.cu", "sc_smooth.cu", "sc_smooth_tile.cu", "sc_smooth_ws.cu", "sc_smooth_fir.cu", "sc_smooth_ws16.cu", "sc_smooth_z.cu", "sc_smooth_p.cu", "sc_noise.cu", "sc_noise_scale.cu", "sc_linker.cu", "sc_flagger.cu", "sc_static.cu",
            "sc_gauss.cu"]
 
 

@@ -405,10 +405,11 @@ bool same_spatial(const PairDesc& a, const PairDesc& b) {
   return a.w[0] == b.w[0] && a.w[1] == b.w[1] && a.w[2] == b.w[2];
 }
 
-SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims) {
+SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims, const Half16* h16 = nullptr) {
   SmoothArgs a;
   memset(&a, 0, sizeof(a));
   a.C = cube;
+  if (h16) a.h16 = *h16;
   a.mbits = c->mbits;
   a.S = c->S;
   a.nx = (int)dims[0];
@@ -418,11 +419,46 @@ SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims) {
   return a;
 }
 
+// A 16-bit cube is read as such by the kernels when its rows are 16-byte
+// multiples (TMA tiles of 16-bit values, 16-byte vector loads of 8 values
+// within a plane) and its base is 16-byte aligned, unless the run asks for the
+// generic or sampled-Gaussian kernels (which have no 16-bit forms); otherwise
+// it is decoded once into a float32 copy.
+bool half_in_kernel(const void* cube_dev, const int64_t* dims, uint32_t flags) {
+  return dims[0] % 8 == 0 && (reinterpret_cast<uintptr_t>(cube_dev) & 15u) == 0 &&
+         !(flags & (SC_FLAG_GENERIC | SC_FLAG_SAMPLED_GAUSS));
+}
+
+// Device staging cube and mask of max_voxels elements (allocated on first use).
+int ensure_stage(sc_ctx* c) {
+  if (c->stage_cube) return SC_OK;
+  if (cudaMalloc(&c->stage_cube, sizeof(float) * c->max_voxels) != cudaSuccess ||
+      cudaMalloc(&c->stage_mask, c->max_voxels) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->stage_cube);
+    cudaFree(c->stage_mask);
+    c->stage_cube = nullptr;
+    c->stage_mask = nullptr;
+    return SC_ERR_NOMEM;
+  }
+  return SC_OK;
+}
+
+// One S+C run on the device. The cube is the float32 one at `cube`, or, with
+// h16 (cube null), a 16-bit one. The raw-cube histograms read the 16-bit
+// values; by default the first of them also decodes the cube into the
+// context's float32 working copy, which every later pass reads (the float32
+// kernels, no decoding pass of its own). With SC_FLAG_HALF_DIRECT no copy is
+// made: the last histogram pass decodes into S (the float32 cube the sigma_0
+// selection and the first pair read) and the smoothing kernels and correction
+// lists decode their own 16-bit values.
 int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kernel* kernels, int nk, float t,
-               int noise_mode, float replacement, uint8_t* mask_dev, uint32_t flags, cudaStream_t s) {
+               int noise_mode, float replacement, uint8_t* mask_dev, uint32_t flags, cudaStream_t s,
+               const Half16* h16 = nullptr) {
   long long n = 0;
   std::vector<PairDesc> pds;
-  int rc = validate_common(c, cube, dims, kernels, nk, t, noise_mode, &n, &pds, flags);
+  int rc = validate_common(c, h16 ? reinterpret_cast<const float*>(h16->bits) : cube, dims, kernels, nk, t,
+                           noise_mode, &n, &pds, flags);
   if (rc) return rc;
   if (!mask_dev) return SC_ERR_ARG;
   if (!std::isfinite(replacement)) return SC_ERR_ARG;
@@ -435,8 +471,16 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   }
   CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), s));
   const long long nwords = (n + 31) / 32;
+  const long long plane = dims[0] * dims[1];
+  const bool direct = h16 && (flags & SC_FLAG_HALF_DIRECT);
+  if (h16 && !direct) {
+    rc = ensure_stage(c);  // the float32 working copy
+    if (rc) return rc;
+  }
+  c->stats.half_path = h16 ? (direct ? 1u : 3u) : 0u;
   if (flags & SC_FLAG_ACCUMULATE) {
-    CK(launch_pack(mask_dev, cube, n, c->mbits, s));
+    if (h16) CK(launch_pack16(mask_dev, *h16, plane, n, c->mbits, s));  // (before the copy exists)
+    else CK(launch_pack(mask_dev, cube, n, c->mbits, s));
     c->stats.launches += 1;
   } else {
     CK(cudaMemsetAsync(c->mbits, 0, sizeof(uint32_t) * nwords, s));
@@ -445,21 +489,34 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
 
   // sigma_0 of the raw cube (and the first pair when it is (0, 0))
   CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
+  // the float32 raw cube the sigma_0 selection reads: the cube, the working
+  // copy of a 16-bit cube, or (direct) S
+  const float* src0 = h16 ? (direct ? c->S : c->stage_cube) : cube;
   {
     Phase ph(c, s, EV_SELECT);
-    CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));  // full range, and max |C|
+    // full range, and max |C| (a 16-bit cube: decoded into the copy by this
+    // pass, or into S by the last histogram pass when direct)
+    if (h16)
+      CK(launch_hist16(*h16, plane, n, c->st, c->hist, 0, 1, direct ? (std_mode ? c->S : nullptr) : c->stage_cube,
+                       c->sms, s));
+    else CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));
     c->stats.launches += 1;
     if (!std_mode) {
       // a second, windowed histogram around the median |C|: a fine plan
       CK(launch_window_from_hist(c->st, c->hist, s));
       CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
-      CK(launch_hist(cube, n, c->st, c->hist, 1, 0, c->sms, s));
+      if (h16) CK(launch_hist16(*h16, plane, n, c->st, c->hist, 1, 0, direct ? c->S : nullptr, c->sms, s));
+      else CK(launch_hist(cube, n, c->st, c->hist, 1, 0, c->sms, s));
       c->stats.launches += 2;
     }
   }
-  rc = measure(c, cube, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, noise_mode, first_identity ? 0 : -1, force,
+  rc = measure(c, src0, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, noise_mode, first_identity ? 0 : -1, force,
                s);
   if (rc) return rc;
+  if (h16 && !direct) {  // the pairs read the float32 working copy
+    cube = c->stage_cube;
+    h16 = nullptr;
+  }
   CK(launch_sigma0_done(c->st, replacement, W, nk, s));
   c->stats.launches += 1;
 
@@ -471,7 +528,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   int p_owner = -1;  // pair whose spatial sums sh_P holds
   for (int k = first_identity ? 1 : 0; k < nk; ++k) {
     CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
-    SmoothArgs a = base_args(c, cube, dims);
+    SmoothArgs a = base_args(c, cube, dims, h16);
     a.pd = pds[k];
     a.pair = k;
     apply_tuning(c, dims, &a);
@@ -744,21 +801,6 @@ int sc_run(sc_ctx* c, const float* cube_dev, const int64_t* dims, const sc_kerne
 }
 
 namespace {
-
-// Device staging cube and mask of max_voxels elements (allocated on first use).
-int ensure_stage(sc_ctx* c) {
-  if (c->stage_cube) return SC_OK;
-  if (cudaMalloc(&c->stage_cube, sizeof(float) * c->max_voxels) != cudaSuccess ||
-      cudaMalloc(&c->stage_mask, c->max_voxels) != cudaSuccess) {
-    cudaGetLastError();
-    cudaFree(c->stage_cube);
-    cudaFree(c->stage_mask);
-    c->stage_cube = nullptr;
-    c->stage_mask = nullptr;
-    return SC_ERR_NOMEM;
-  }
-  return SC_OK;
-}
 
 // The batch lanes (created on first use, same workspace size as the context).
 int ensure_lanes(sc_ctx* c) {
@@ -1035,7 +1077,9 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
   }
   const double t_submit = host_seconds();
   const float* src = (const float*)cube_dev;
-  if (storage != SC_STORE_F32) {
+  const bool h_in = storage != SC_STORE_F32 && half_in_kernel(cube_dev, dims, flags);
+  const Half16 h{(const unsigned short*)cube_dev, chan_scale_dev, storage};
+  if (storage != SC_STORE_F32 && !h_in) {
     rc = ensure_stage(lc);
     if (rc == SC_OK && launch_decode_half((const uint16_t*)cube_dev, chan_scale_dev, (long long)dims[0] * dims[1], n,
                                          storage == SC_STORE_BF16 ? 1 : 0, lc->stage_cube, lc->sms, ls) != cudaSuccess)
@@ -1043,7 +1087,8 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
     src = lc->stage_cube;
   }
   if (rc == SC_OK)
-    rc = run_device(lc, src, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, ls);
+    rc = run_device(lc, h_in ? nullptr : src, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev,
+                    flags, ls, h_in ? &h : nullptr);
   if (rc == SC_OK) {
     BatchRes* r = reinterpret_cast<BatchRes*>(slot);
     if (cudaMemcpyAsync(r, lc->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ls) != cudaSuccess ||
@@ -1052,7 +1097,7 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
         cudaEventRecord(done, ls) != cudaSuccess)
       rc = cuda_fail(cudaGetLastError(), "sc_submit", __LINE__);
   }
-  c->stats.launches += lc->stats.launches + (storage != SC_STORE_F32 ? 1 : 0);
+  c->stats.launches += lc->stats.launches + (storage != SC_STORE_F32 && !h_in ? 1 : 0);
   lc->stats.launches = 0;
   memcpy(c->stats.smooth_kernel_pair, lc->stats.smooth_kernel_pair, sizeof(c->stats.smooth_kernel_pair));
   if (rc) {
@@ -1198,17 +1243,24 @@ int sc_run_half(sc_ctx* c, const uint16_t* cube_dev, int is_bf16, const float* c
   long long n = 0;
   int rc = check_dims(c, dims, &n);
   if (rc) return rc;
-  rc = ensure_stage(c);
-  if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   c->last = s;
-  {
-    Phase ph(c, s, EV_CLIP);
-    CK(launch_decode_half(cube_dev, chan_scale_dev, (long long)dims[0] * dims[1], n, is_bf16 ? 1 : 0,
-                          c->stage_cube, c->sms, s));
-    c->stats.launches += 1;
+  if (half_in_kernel(cube_dev, dims, flags)) {
+    const Half16 h{cube_dev, chan_scale_dev, is_bf16 ? SC_STORE_BF16 : SC_STORE_FP16};
+    rc = run_device(c, nullptr, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, s, &h);
+  } else {
+    rc = ensure_stage(c);
+    if (rc) return rc;
+    {
+      Phase ph(c, s, EV_CLIP);
+      CK(launch_decode_half(cube_dev, chan_scale_dev, (long long)dims[0] * dims[1], n, is_bf16 ? 1 : 0,
+                            c->stage_cube, c->sms, s));
+      c->stats.launches += 1;
+    }
+    rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags,
+                    s);
+    c->stats.half_path = 2u;
   }
-  rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, s);
   if (rc) return rc;
   rc = finish(c, n_kernels, sigma_host, sigma0_host, s, false);
   if (rc == SC_OK) c->stats.runs += 1;

@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "sc_internal.h"
 
 namespace sc {
@@ -132,6 +134,14 @@ __device__ __forceinline__ float dequantize(long long q, float inv) {
   const float hi = __int2float_rn((int)(q >> 32));
   const float lo = __uint2float_rn((unsigned int)((unsigned long long)q & 0xffffffffull));
   return __fmul_rn(__fmaf_rn(hi, 4294967296.0f, lo), inv);
+}
+
+// Value of a 16-bit cube element: the BF16 or FP16 number times its channel's
+// float32 scale, one float32 rounding (the same product the decoding pass
+// forms, so both paths see identical values).
+__device__ __forceinline__ float half16_value(unsigned short b, int fmt, float scale) {
+  const float v = fmt == SC_STORE_BF16 ? __uint_as_float((unsigned)b << 16) : __half2float(__ushort_as_half(b));
+  return __fmul_rn(v, scale);
 }
 
 __device__ __forceinline__ bool mask_bit(const uint32_t* mbits, long long v) {

@@ -159,8 +159,17 @@ struct PairWeights {
   long long wf[SC_MAX_KERNELS];  // the bound that fixes each pair's fixed-point scale
 };
 
+// A cube stored in 16 bits (SC_STORE_BF16 / SC_STORE_FP16) with one float32
+// scale per channel, read as such by the kernels: value = fl32(v * scale[z]).
+struct Half16 {
+  const unsigned short* bits;  // [nz][ny][nx]
+  const float* scale;          // [nz]
+  int fmt;                     // 0: no 16-bit cube; SC_STORE_BF16 or SC_STORE_FP16
+};
+
 struct SmoothArgs {
-  const float* C;
+  const float* C;         // float32 cube (null when h16.fmt != 0)
+  Half16 h16;             // the cube in its 16-bit form (fmt 0: C is the cube)
   const uint32_t* mbits;  // working mask, 1 bit per voxel, flat order (may be null: empty)
   float* S;
   int nx, ny, nz;
@@ -252,6 +261,9 @@ inline long long tune_items_per_sm(const SmoothArgs& a) { return a.tune_zfactor 
 // Launchers (all enqueue on `s`, return cudaError_t of the launch).
 cudaError_t launch_hist(const float* x, long long n, DevState* st, unsigned long long* hist, int win,
                         int want_maxabs, int sms, cudaStream_t s);
+// Histogram (and max) of a 16-bit cube, decoding it into out (if non-null).
+cudaError_t launch_hist16(const Half16& h, long long plane, long long n, DevState* st, unsigned long long* hist,
+                          int win, int want_maxabs, float* out, int sms, cudaStream_t s);
 cudaError_t launch_plan(DevState* st, const unsigned long long* hist, int win, const float* src, long long n_total,
                         Lists L, float threshold, int clip, int std_mode, unsigned int force_flags, cudaStream_t s);
 cudaError_t launch_pass2(const float* src, long long n, uint32_t* mbits, DevState* st, Lists L, int sms,
@@ -279,6 +291,8 @@ cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeight
 cudaError_t launch_sigma_out(const DevState* st, int n, float* out, cudaStream_t s);
 cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W, int n_pairs, cudaStream_t s);
 cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s);
+cudaError_t launch_pack16(const uint8_t* m8, const Half16& h, long long plane, long long n, uint32_t* mbits,
+                          cudaStream_t s);
 cudaError_t launch_expand(const uint32_t* mbits, long long n, uint8_t* m8, int keep, cudaStream_t s);
 cudaError_t launch_maxabs(const float* x, long long n, DevState* st, int sms, cudaStream_t s);
 // out[i] = float(x[i]) * scale[i / plane], x BF16 (bf16 != 0) or FP16 bits

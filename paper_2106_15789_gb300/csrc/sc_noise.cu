@@ -97,6 +97,75 @@ cudaError_t launch_hist(const float* x, long long n, DevState* st, unsigned long
   return cudaGetLastError();
 }
 
+// The same histogram (and max |value|) of a 16-bit cube, whose planes hold a
+// multiple of 8 values: a thread takes 8 values (16 bytes) at a time and
+// decodes them with their plane's scale (the plane followed along the
+// grid-stride loop). With out != null the decoded float32 values are written
+// there as well (the cube for the passes that read it as float32).
+__global__ void __launch_bounds__(512) k_hist16(Half16 h, long long plane, long long n, DevState* st,
+                                                unsigned long long* __restrict__ hist, int win, int want_maxabs,
+                                                float* __restrict__ out) {
+  extern __shared__ unsigned int sh[];
+  for (int i = threadIdx.x; i < kNumBins; i += blockDim.x) sh[i] = 0u;
+  __syncthreads();
+  const BinCfg cfg = win ? st->win : kFullRange;
+  unsigned int mx = 0u;
+  const long long ng = n / 8, pg = plane / 8;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long dz = stride / pg, doff = stride - dz * pg;
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long z = g / pg, off = g - z * pg;
+  const uint4* b4 = reinterpret_cast<const uint4*>(h.bits);
+  for (; g < ng; g += stride) {
+    const uint4 q = __ldg(b4 + g);
+    const float cs = __ldg(h.scale + z);
+    const unsigned w[4] = {q.x, q.y, q.z, q.w};
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = half16_value((unsigned short)(w[k] & 0xffffu), h.fmt, cs);
+      v[2 * k + 1] = half16_value((unsigned short)(w[k] >> 16), h.fmt, cs);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (isfinite(v[i])) {
+        atomicAdd(&sh[bin_of(v[i], cfg)], 1u);
+        mx = max(mx, __float_as_uint(fabsf(v[i])));
+      }
+    }
+    if (out) {
+      float4* o4 = reinterpret_cast<float4*>(out) + 2 * g;
+      o4[0] = make_float4(v[0], v[1], v[2], v[3]);
+      o4[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    z += dz;
+    off += doff;
+    if (off >= pg) {
+      off -= pg;
+      ++z;
+    }
+  }
+  if (want_maxabs) {
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&st->maxabs_bits, mx);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kNumBins; i += blockDim.x)
+    if (sh[i]) atomicAdd(hist + i, (unsigned long long)sh[i]);
+}
+
+cudaError_t launch_hist16(const Half16& h, long long plane, long long n, DevState* st, unsigned long long* hist,
+                          int win, int want_maxabs, float* out, int sms, cudaStream_t s) {
+  if (plane % 8 != 0 || (reinterpret_cast<uintptr_t>(h.bits) & 15u) != 0 ||
+      (out && (reinterpret_cast<uintptr_t>(out) & 15u) != 0))
+    return cudaErrorInvalidValue;  // the caller takes the 16-bit path only for such cubes
+  const size_t smem = kNumBins * sizeof(unsigned int);
+  long long want = (n / 8 + 511) / 512;
+  int grid = (int)(want < 1 ? 1 : (want > 4LL * sms ? 4LL * sms : want));
+  k_hist16<<<grid, 512, smem, s>>>(h, plane, n, st, hist, win, want_maxabs, out);
+  return cudaGetLastError();
+}
+
 // Max |x| over finite values only (for sc_smooth's fixed-point scale).
 __global__ void k_maxabs(const float* __restrict__ x, long long n, DevState* st) {
   unsigned int mx = 0u;
@@ -1016,6 +1085,34 @@ __global__ void k_pack(const uint8_t* __restrict__ m8, const float* __restrict__
     mbits[w] = bits;
   }
 }
+// The same for a 16-bit cube (finiteness of the decoded value).
+__global__ void k_pack16(const uint8_t* __restrict__ m8, Half16 h, long long plane, long long n,
+                         uint32_t* __restrict__ mbits) {
+  const long long nw = (n + 31) / 32;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (long long)gridDim.x * blockDim.x) {
+    unsigned int bits = 0u;
+    const long long v0 = w * 32;
+    const long long z0 = v0 / plane, next = (z0 + 1) * plane;
+    for (int i = 0; i < 32; ++i) {
+      const long long v = v0 + i;
+      if (v < n && m8[v]) {
+        const float cs = __ldg(h.scale + (v >= next ? z0 + 1 : z0));
+        if (isfinite(half16_value(__ldg(h.bits + v), h.fmt, cs))) bits |= 1u << i;
+      }
+    }
+    mbits[w] = bits;
+  }
+}
+
+cudaError_t launch_pack16(const uint8_t* m8, const Half16& h, long long plane, long long n, uint32_t* mbits,
+                          cudaStream_t s) {
+  long long nw = (n + 31) / 32;
+  long long want = (nw + 255) / 256;
+  int grid = (int)(want < 1 ? 1 : (want > 4096 ? 4096 : want));
+  k_pack16<<<grid, 256, 0, s>>>(m8, h, plane, n, mbits);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack(const uint8_t* m8, const float* cube, long long n, uint32_t* mbits, cudaStream_t s) {
   long long nw = (n + 31) / 32;
   long long want = (nw + 255) / 256;

@@ -116,13 +116,14 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth_generic(SmoothArgs a)
       long long P[kMaxOuts];
       if (valid) {
         const long long pbase = (long long)zp * ny * nx;
+        const float cs = a.h16.fmt ? __ldg(a.h16.scale + zp) : 1.0f;
         for (int e = tid; e < L.rows * L.px; e += blockDim.x) {
           const int row = e / L.px, col = e - row * L.px;
           const long long gx = (long long)x0 - h + col, gy = (long long)y0 - h + row;
           long long q = 0ll;
           if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
             const long long v = pbase + gy * nx + gx;
-            const float c = __ldg(a.C + v);
+            const float c = a.h16.fmt ? half16_value(__ldg(a.h16.bits + v), a.h16.fmt, cs) : __ldg(a.C + v);
             if (isfinite(c)) {
               if (do_repl && mask_bit(a.mbits, v)) {
                 q = (c >= 0.0f) ? qrepl : -qrepl;
@@ -168,7 +169,8 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth_generic(SmoothArgs a)
           const long long gx = x0 + ox, gy = y0 + oy;
           if (gx < nx && gy < ny) {
             const long long v = ((long long)zo * ny + gy) * nx + gx;
-            const float c = __ldg(a.C + v);
+            const float c = a.h16.fmt ? half16_value(__ldg(a.h16.bits + v), a.h16.fmt, __ldg(a.h16.scale + zo))
+                                      : __ldg(a.C + v);
             float s;
             if (isfinite(c)) {
               s = dequantize(zsum[i], inv);
@@ -199,8 +201,19 @@ __global__ void __launch_bounds__(512) k_identity(SmoothArgs a, long long n) {
   const BinCfg cfg = a.win ? a.st->win : kFullRange;
   const float repl = a.use_fixed_repl ? a.repl_value : a.st->repl;
   const bool do_repl = repl > 0.0f && a.mbits != nullptr;
-  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    float c = __ldg(a.C + v);
+  // a 16-bit cube: the plane of v (for its scale), advanced with v
+  const long long plane = (long long)a.nx * a.ny, stride = (long long)gridDim.x * blockDim.x;
+  const long long dz = stride / plane, doff = stride - dz * plane;
+  long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long z = v / plane, off = v - z * plane;
+  for (; v < n; v += stride) {
+    const float c = a.h16.fmt ? half16_value(__ldg(a.h16.bits + v), a.h16.fmt, __ldg(a.h16.scale + z)) : __ldg(a.C + v);
+    z += dz;
+    off += doff;
+    if (off >= plane) {
+      off -= plane;
+      ++z;
+    }
     float s;
     if (isfinite(c)) {
       s = (do_repl && mask_bit(a.mbits, v)) ? ((c >= 0.0f) ? repl : -repl) : c;
@@ -253,6 +266,7 @@ cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* 
 void init_tile_attrs();
 void init_ws_attrs();
 void init_fir_attrs();
+void init_ws16_attrs();
 void init_z_attrs();
 
 __global__ void k_fill_noise(float* __restrict__ x, long long n, unsigned int seed) {
@@ -353,6 +367,7 @@ void init_kernel_attrs() {
   init_tile_attrs();
   init_ws_attrs();
   init_fir_attrs();
+  init_ws16_attrs();
   init_z_attrs();
   init_share_attrs();
   init_noise_attrs();

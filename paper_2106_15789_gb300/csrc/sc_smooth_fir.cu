@@ -52,7 +52,7 @@ void init_fir_attrs() {
 // spectral widths up to 31; *done = false for other pairs.
 cudaError_t launch_smooth_fir(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
-  if (a.generic || !a.pd.sampled || a.pd.h < 1 || a.pd.wz > ws::Tile<16>::kMaxWz) return cudaSuccess;
+  if (a.generic || a.h16.fmt || !a.pd.sampled || a.pd.h < 1 || a.pd.wz > ws::Tile<16>::kMaxWz) return cudaSuccess;
   const int h = a.pd.h;
   for (int i = 0; i < h; ++i)
     if (a.pd.taps[i] != a.pd.taps[2 * h - i]) return cudaSuccess;  // not symmetric: not served

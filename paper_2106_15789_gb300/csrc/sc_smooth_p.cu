@@ -78,7 +78,8 @@ __device__ __forceinline__ void for_buckets(long long v, long long nx, long long
 // (hy << 8 | hx) in the bucket's halo'd tile (low 16 bits).
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__ mbits, const float* __restrict__ C,
-                                                    long long n, long long nx, long long ny, ShareArgs sh, int R) {
+                                                    Half16 h16, long long n, long long nx, long long ny, ShareArgs sh,
+                                                    int R) {
   const long long nq = ((n + 31) / 32 + 3) / 4;
   const uint4* m4 = reinterpret_cast<const uint4*>(mbits);
   const uint4* s4 = reinterpret_cast<const uint4*>(sh.msnap);
@@ -97,7 +98,9 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
         const long long v = (4 * q + k) * 32 + bit;
         if (v >= n) break;
         if (FILL) {
-          const unsigned long long cb = (unsigned long long)__float_as_uint(__ldg(C + v)) << 32;
+          const float cv = h16.fmt ? half16_value(__ldg(h16.bits + v), h16.fmt, __ldg(h16.scale + v / (nx * ny)))
+                                   : __ldg(C + v);
+          const unsigned long long cb = (unsigned long long)__float_as_uint(cv) << 32;
           for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned pos) {
             const unsigned slot = atomicSub(sh.cnt + bk, 1u) - 1u;
             const unsigned long long idx = (unsigned long long)__ldg(sh.offs + bk) + slot;
@@ -705,10 +708,10 @@ cudaError_t launch_share_prep(const SmoothArgs& a, const ShareArgs& sh, int sms,
   const int R = share_R(a.pd);  // the reach the shared pass decodes its entries with
   const long long m = sh.n_buckets + 1;
   const long long nblk = (m + kScanChunk - 1) / kScanChunk;
-  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  k_share_list<false><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, a.h16, n, a.nx, a.ny, sh, R);
   k_share_scan1<<<(unsigned)nblk, 1024, 0, s>>>(sh.cnt, sh.offs, sh.bsum, m);
   k_share_scan2<<<(unsigned)nblk, 1024, 0, s>>>(sh.offs, sh.bsum, m, sh.ss, sh.cap);
-  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, n, a.nx, a.ny, sh, R);
+  k_share_list<true><<<8 * sms, 256, 0, s>>>(a.mbits, a.C, a.h16, n, a.nx, a.ny, sh, R);
   return cudaGetLastError();
 }
 

@@ -396,7 +396,7 @@ void init_tile_attrs() {
 // spectral widths up to 15; *done = false when the pair is not served.
 cudaError_t launch_smooth_tile(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
-  if (a.generic || a.pd.wz > tile::kMaxWz) return cudaSuccess;
+  if (a.generic || a.h16.fmt || a.pd.wz > tile::kMaxWz) return cudaSuccess;  // float32 cubes only
   const int* w = a.pd.w;
   if (w[0] == 1 && w[1] == 1 && w[2] == 1) return launch_tile<1, 1, 1>(a, sms, s, done);
   if (w[0] == 1 && w[1] == 3 && w[2] == 3) return launch_tile<1, 3, 3>(a, sms, s, done);

@@ -67,10 +67,12 @@ struct Tile {
 };
 
 // W1 == 0: the FIR of half-width W2 (sampled Gaussian) instead of a cascade.
-template <int W1, int W2, int W3, int TY>
+// EB: bytes per raw cube value (4: float32; 2: a 16-bit cube decoded in the
+// producers with its per-channel scale).
+template <int W1, int W2, int W3, int TY, int EB = 4>
 struct Geo {
   static constexpr int R = W1 == 0 ? W2 : (W1 - 1) / 2 + (W2 - 1) / 2 + (W3 - 1) / 2;
-  static constexpr int RA = (R + 3) & ~3;  // x halo of the raw tile (16-byte aligned TMA x coordinate)
+  static constexpr int RA = (R + 16 / EB - 1) & ~(16 / EB - 1);  // x halo (16-byte aligned TMA x coordinate)
   static constexpr int BX = TX + 2 * RA;   // raw tile width
   static constexpr int BY = TY + 2 * R;    // raw and quantised tile height
   static constexpr int PX = TX + 2 * R;    // quantised tile width
@@ -89,14 +91,14 @@ struct Smem {
   size_t raw[kStages], mw, x, b, hist, mbar, total;
 };
 
-template <int W1, int W2, int W3, int TY>
+template <int W1, int W2, int W3, int TY, int EB = 4>
 __host__ __device__ constexpr Smem smem_layout(bool hist) {
-  using G = Geo<W1, W2, W3, TY>;
+  using G = Geo<W1, W2, W3, TY, EB>;
   Smem s{};
   size_t o = 0;
   for (int b = 0; b < kStages; ++b) {
     s.raw[b] = o;
-    o = al128(o + sizeof(float) * (size_t)G::BY * G::BX);
+    o = al128(o + (size_t)EB * G::BY * G::BX);
   }
   s.mw = o;  // [2][BY][4] tile-aligned mask words
   o = al128(o + sizeof(unsigned) * 2 * (size_t)G::BY * 4);
@@ -114,12 +116,12 @@ __host__ __device__ constexpr Smem smem_layout(bool hist) {
 
 // Quantise the halo'd raw tile into X, in chunks of kConvChunk elements whose
 // loads are all issued before their stores (the pointers do not alias).
-constexpr int kConvChunk = 4;
-template <int W1, int W2, int W3, int TY, bool REPL>
-__device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const unsigned* __restrict__ mwb,
+template <int W1, int W2, int W3, int TY, bool REPL, int EB>
+__device__ __forceinline__ void convert_tile(const void* __restrict__ rbv, const unsigned* __restrict__ mwb,
                                              long long* __restrict__ X, int pt, float fscale, long long qrepl,
-                                             bool do_repl) {
-  using G = Geo<W1, W2, W3, TY>;
+                                             bool do_repl, int fmt16, float cscale) {
+  constexpr int kConvChunk = 4;
+  using G = Geo<W1, W2, W3, TY, EB>;
   constexpr int R = G::R, RA = G::RA;
 #pragma unroll
   for (int k0 = 0; k0 < G::NCONV; k0 += kConvChunk) {
@@ -130,7 +132,12 @@ __device__ __forceinline__ void convert_tile(const float* __restrict__ rb, const
       const int k = k0 + i, e = pt + k * kPT;
       const bool ok = k < G::NCONV && (k + 1 < G::NCONV || e < G::BY * G::PX);
       const int row = e / G::PX, col = e - row * G::PX;
-      v[i] = ok ? rb[row * G::BX + col + (RA - R)] : 0.0f;
+      const int ri = row * G::BX + col + (RA - R);
+      if constexpr (EB == 4) {
+        v[i] = ok ? static_cast<const float*>(rbv)[ri] : 0.0f;
+      } else {
+        v[i] = ok ? half16_value(static_cast<const unsigned short*>(rbv)[ri], fmt16, cscale) : 0.0f;
+      }
       word[i] = (REPL && do_repl && ok) ? mwb[row * 4 + (col >> 5)] : 0u;
     }
 #pragma unroll
@@ -157,20 +164,21 @@ __device__ __forceinline__ void xpass_item(const int* __restrict__ taps, const l
 
 }  // namespace ws
 
-template <int W1, int W2, int W3, bool REPL, bool TMA, int TY>
+template <int W1, int W2, int W3, bool REPL, bool TMA, int TY, int EB = 4>
 __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
     k_smooth_ws(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ SmoothArgs a) {
   using namespace ws;
-  using G = Geo<W1, W2, W3, TY>;
+  using G = Geo<W1, W2, W3, TY, EB>;
+  static_assert(EB == 4 || TMA, "16-bit cubes are loaded by TMA only");
   using T = Tile<TY>;
   constexpr int kCW = T::kCW, kCT = T::kCT, kThreads = T::kThreads;
   constexpr int R = G::R, RA = G::RA;
   if (a.gate && *a.gate == 0u) return;  // a fallback launch that is not needed (block-uniform)
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
-  const Smem L = smem_layout<W1, W2, W3, TY>(a.hist != nullptr);
-  float* const raw0 = reinterpret_cast<float*>(smem + L.raw[0]);
-  constexpr size_t kRawStride = al128(sizeof(float) * (size_t)G::BY * G::BX) / sizeof(float);
+  const Smem L = smem_layout<W1, W2, W3, TY, EB>(a.hist != nullptr);
+  float* const raw0 = reinterpret_cast<float*>(smem + L.raw[0]);  // (EB == 2: 16-bit values)
+  constexpr size_t kRawStride = al128((size_t)EB * G::BY * G::BX) / sizeof(float);
   unsigned* const mw = reinterpret_cast<unsigned*>(smem + L.mw);
   long long* const Xt = reinterpret_cast<long long*>(smem + L.x);
   long long* const Bt = reinterpret_cast<long long*>(smem + L.b);
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
   auto issue_tma = [&]() {
     if (la_item >= n_items) return;
     const int s = (int)(issued % kStages);
-    mbar_expect_tx(raw_full + 8 * s, (unsigned)(sizeof(float) * G::BX * G::BY));
+    mbar_expect_tx(raw_full + 8 * s, (unsigned)(EB * G::BX * G::BY));
     tma_load_3d(smem_u32(raw0 + s * kRawStride), &tmap, la_x0 - RA, la_y0 - R, la_z0 - r + la_j, raw_full + 8 * s);
     advance();
   };
@@ -239,19 +247,21 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
   // elements ct, ct + kCT, ...; zero fill outside the cube), completing on the
   // buffer's barrier once each thread's copies have landed
   auto issue_async = [&](int ct) {
-    if (la_item >= n_items) return;
-    const int s = (int)(issued % kStages);
-    float* dst = raw0 + s * kRawStride;
-    const long long zp = (long long)la_z0 - r + la_j;
-    const bool zok = zp >= 0 && zp < nz;
-    for (int e = ct; e < G::BY * G::BX; e += kCT) {
-      const int row = e / G::BX, col = e - row * G::BX;
-      const long long gx = (long long)la_x0 - RA + col, gy = (long long)la_y0 - R + row;
-      const bool ok = zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-      cp_async4(smem_u32(dst + e), ok ? a.C + zp * plane + gy * nx + gx : a.C, ok);
+    if constexpr (EB == 4) {
+      if (la_item >= n_items) return;
+      const int s = (int)(issued % kStages);
+      float* dst = raw0 + s * kRawStride;
+      const long long zp = (long long)la_z0 - r + la_j;
+      const bool zok = zp >= 0 && zp < nz;
+      for (int e = ct; e < G::BY * G::BX; e += kCT) {
+        const int row = e / G::BX, col = e - row * G::BX;
+        const long long gx = (long long)la_x0 - RA + col, gy = (long long)la_y0 - R + row;
+        const bool ok = zok && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        cp_async4(smem_u32(dst + e), ok ? a.C + zp * plane + gy * nx + gx : a.C, ok);
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(raw_full + 8 * s) : "memory");
+      advance();
     }
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(raw_full + 8 * s) : "memory");
-    advance();
   };
 
   if (warp < kPW) {
@@ -303,10 +313,16 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         m_next = mask_load(x0, y0, z0 - r + 1);
         if (pt < 4 * G::BY) mw[(g & 1) * 4 * G::BY + pt] = mask_finish(x0, m0);
       }
+      // a 16-bit cube's values are decoded with their plane's scale, loaded a
+      // plane ahead so that its latency hides behind the hand-off waits
+      auto plane_scale = [&](int zq) { return (EB == 2 && zq >= 0 && zq < nz) ? __ldg(a.h16.scale + zq) : 1.0f; };
+      float cs_next = plane_scale(z0 - r);
       named_bar_sync(kBarProducers, kPT);
       for (int j = 0; j < n_steps; ++j, ++g) {
         const int zp = z0 - r + j;
         const int s = (int)(g % kStages), b = (int)(g & 1);
+        const float cs = cs_next;
+        cs_next = plane_scale(zp + 1);
         const MaskLd m_after = (do_repl && j + 2 < n_steps) ? mask_load(x0, y0, zp + 2) : MaskLd{0u, 0u, 0u};
         mbar_wait_bounded(raw_full + 8 * s, (unsigned)((g / kStages) & 1), &timed_out, wait_ns);
         mbar_wait_bounded(bt_empty + 8 * b, (unsigned)(((g >> 1) & 1) ^ 1), &timed_out, wait_ns);
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
         const unsigned* mwb = mw + b * 4 * G::BY;
         long long* const X = Xt + (G::XBUF == 2 ? (size_t)b * G::BY * G::XP : 0);
         // quantise the halo'd tile once
-        convert_tile<W1, W2, W3, TY, REPL>(rb, mwb, X, pt, fscale, qrepl, do_repl);
+        convert_tile<W1, W2, W3, TY, REPL, EB>(rb, mwb, X, pt, fscale, qrepl, do_repl, a.h16.fmt, cs);
         if (do_repl && j + 1 < n_steps && pt < 4 * G::BY) mw[((g + 1) & 1) * 4 * G::BY + pt] = mask_finish(x0, m_next);
         m_next = m_after;
         // quantised tile and next mask words done; with two tiles, also every
@@ -369,9 +385,13 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
       unsigned rows_in = 0u;  // rows of this thread inside the cube
 #pragma unroll
       for (int i = 0; i < SEGY; ++i) rows_in |= (gx < nx && gy0 + i < ny ? 1u : 0u) << i;
+      auto plane_scale = [&](int zq) { return (EB == 2 && zq >= 0 && zq < nz) ? __ldg(a.h16.scale + zq) : 1.0f; };
+      float cs_next = plane_scale(z0 - r);  // 16-bit cube: the plane's scale, a plane ahead
       for (int j = 0; j < n_steps; ++j, ++g) {
         const int zp = z0 - r + j;
         const int b = (int)(g & 1);
+        const float cs_plane = cs_next;
+        cs_next = plane_scale(zp + 1);
         // ring slot of this plane: load early, use after the y pass
         unsigned old[kSlotCols];
         const unsigned ta = tmine + (unsigned)(kSlotCols * (j % (wz > 1 ? wz : 1)));
@@ -388,10 +408,21 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
           // the tile's load completed before the producers used it; observing
           // its barrier makes the TMA writes visible to this thread as well
           mbar_wait_bounded(raw_full + 8 * (int)(g % kStages), (unsigned)((g / kStages) & 1), &timed_out, wait_ns);
-          const float* rb = raw0 + (size_t)(g % kStages) * kRawStride + (R + grp * SEGY) * G::BX + RA + xc;
+          const float* rbase = raw0 + (size_t)(g % kStages) * kRawStride;
+          const int ro = (R + grp * SEGY) * G::BX + RA + xc;
+          if constexpr (EB == 4) {
 #pragma unroll
-          for (int i = 0; i < SEGY; ++i)
-            nbyte |= ((__float_as_uint(rb[i * G::BX]) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
+            for (int i = 0; i < SEGY; ++i)
+              nbyte |= ((__float_as_uint(rbase[ro + i * G::BX]) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
+          } else {
+            // the decoded value decides (a finite 16-bit value times its scale may overflow)
+            const unsigned short* rb16 = reinterpret_cast<const unsigned short*>(rbase) + ro;
+#pragma unroll
+            for (int i = 0; i < SEGY; ++i) {
+              const float v = half16_value(rb16[i * G::BX], a.h16.fmt, cs_plane);
+              nbyte |= ((__float_as_uint(v) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
+            }
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(bt_empty + 8 * b);
@@ -459,16 +490,25 @@ __global__ void __launch_bounds__(ws::Tile<TY>::kThreads, 1)
 
 namespace ws {
 
-template <int W1, int W2, int W3, int TY>
+// One launch of the warp-specialised kernel for the pair (EB = 2: the cube is
+// the 16-bit one in a.h16, loaded by TMA; no launch, *done = false, where the
+// tiles do not fit or a 16-bit cube is not TMA-addressable).
+template <int W1, int W2, int W3, int TY, int EB = 4>
 cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done) {
   using namespace ws;
-  using G = Geo<W1, W2, W3, TY>;
+  using G = Geo<W1, W2, W3, TY, EB>;
   constexpr int kThreads = Tile<TY>::kThreads;
   SmoothArgs a = a0;
-  const Smem L = smem_layout<W1, W2, W3, TY>(a.hist != nullptr);
+  const Smem L = smem_layout<W1, W2, W3, TY, EB>(a.hist != nullptr);
   if (L.total + 1024 > 227 * 1024) return cudaSuccess;  // not served: the caller falls back
   CUtensorMap map;
-  const bool tma = encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY);  // else the cp.async variant
+  bool tma;
+  if constexpr (EB == 4) {
+    tma = encode_cube_map(&map, a.C, a.nx, a.ny, a.nz, G::BX, G::BY);  // else the cp.async variant
+  } else {
+    tma = encode_cube16_map(&map, a.h16.bits, a.nx, a.ny, a.nz, G::BX, G::BY);
+    if (!tma) return cudaSuccess;
+  }
   a.tx = TX;
   a.ty = TY;
   a.tiles_x = (a.nx + TX - 1) / TX;
@@ -485,9 +525,9 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
   const bool repl = a.mbits != nullptr && a.repl_possible;
   const size_t smem_req = one_block_per_sm_smem(L.total);
   if (tma) {
-    if (repl) k_smooth_ws<W1, W2, W3, true, true, TY><<<grid, kThreads, smem_req, s>>>(map, a);
-    else k_smooth_ws<W1, W2, W3, false, true, TY><<<grid, kThreads, smem_req, s>>>(map, a);
-  } else {
+    if (repl) k_smooth_ws<W1, W2, W3, true, true, TY, EB><<<grid, kThreads, smem_req, s>>>(map, a);
+    else k_smooth_ws<W1, W2, W3, false, true, TY, EB><<<grid, kThreads, smem_req, s>>>(map, a);
+  } else if constexpr (EB == 4) {
     if (repl) k_smooth_ws<W1, W2, W3, true, false, TY><<<grid, kThreads, smem_req, s>>>(map, a);
     else k_smooth_ws<W1, W2, W3, false, false, TY><<<grid, kThreads, smem_req, s>>>(map, a);
   }
@@ -498,26 +538,28 @@ cudaError_t launch_ws(const SmoothArgs& a0, int sms, cudaStream_t s, bool* done)
 // Tile height for a spectral width: 32 rows while the ring of w planes fits
 // two consumer warps per TMEM lane quarter, else (or when the autotuner chose
 // it) 16 rows.
-template <int W1, int W2, int W3>
+template <int W1, int W2, int W3, int EB = 4>
 cudaError_t launch_ws_for_wz(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   const int rows = ws_tile_rows(a);
-  if (rows == 32) return launch_ws<W1, W2, W3, 32>(a, sms, s, done);
-  if (rows == 16) return launch_ws<W1, W2, W3, 16>(a, sms, s, done);
+  if (rows == 32) return launch_ws<W1, W2, W3, 32, EB>(a, sms, s, done);
+  if (rows == 16) return launch_ws<W1, W2, W3, 16, EB>(a, sms, s, done);
   return cudaSuccess;
 }
 
-template <int W1, int W2, int W3, int TY>
+template <int W1, int W2, int W3, int TY, int EB = 4>
 void set_ws_attr_ty() {
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, true, TY>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, true, TY>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, false, TY>);
-  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, false, TY>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, true, TY, EB>);
+  tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, true, TY, EB>);
+  if constexpr (EB == 4) {
+    tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, false, false, TY>);
+    tc::set_dyn_smem_limit(k_smooth_ws<W1, W2, W3, true, false, TY>);
+  }
 }
 
-template <int W1, int W2, int W3>
+template <int W1, int W2, int W3, int EB = 4>
 void set_ws_attr() {
-  set_ws_attr_ty<W1, W2, W3, 32>();
-  set_ws_attr_ty<W1, W2, W3, 16>();
+  set_ws_attr_ty<W1, W2, W3, 32, EB>();
+  set_ws_attr_ty<W1, W2, W3, 16, EB>();
 }
 
 }  // namespace ws

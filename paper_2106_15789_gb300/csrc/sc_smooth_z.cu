@@ -74,6 +74,9 @@ constexpr int kDepth = 8;  // planes in flight per thread (cp.async ring in shar
 __device__ __forceinline__ void cp16(unsigned dst, const void* src, bool ok) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
 }
+__device__ __forceinline__ void cp8(unsigned dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
 __device__ __forceinline__ void cp4(unsigned dst, const void* src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
 }
@@ -85,15 +88,18 @@ __device__ __forceinline__ void cp_wait() {
 
 }  // namespace zonly
 
-template <int VPT, bool VEC, bool REPL, int THREADS>
+// EB: bytes per cube value (4: float32; 2: a 16-bit cube, copied as such and
+// decoded with its channel's scale when a thread takes its values).
+template <int VPT, bool VEC, bool REPL, int THREADS, int EB = 4>
 __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
   using namespace zonly;
+  static_assert(EB == 4 || (VEC && VPT >= 4), "16-bit cubes take the vector copies");
   extern __shared__ __align__(16) unsigned char zsmem[];
-  float* const zring = reinterpret_cast<float*>(zsmem);  // [kDepth][THREADS * VPT]
+  unsigned char* const zring = zsmem;  // [kDepth][THREADS * VPT] values of EB bytes
   unsigned long long* const zmask =
-      reinterpret_cast<unsigned long long*>(zsmem + sizeof(float) * kDepth * THREADS * VPT);  // [kDepth][THREADS]
+      reinterpret_cast<unsigned long long*>(zsmem + (size_t)EB * kDepth * THREADS * VPT);  // [kDepth][THREADS]
   unsigned int* const zhist =
-      reinterpret_cast<unsigned int*>(zsmem + sizeof(float) * kDepth * THREADS * VPT + 8 * kDepth * THREADS);
+      reinterpret_cast<unsigned int*>(zsmem + (size_t)EB * kDepth * THREADS * VPT + 8 * kDepth * THREADS);
   __shared__ unsigned tmem_holder;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (a.hist)
@@ -147,23 +153,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
     // Per-thread ring of kDepth planes in shared memory, filled by cp.async:
     // the thread's VPT values and the mask word(s) holding its bits. Each
     // thread reads back only what it copied itself, so no barrier is needed.
-    float* my_vals = zring + (size_t)tid * VPT;                       // stage stride THREADS*VPT floats
+    unsigned char* my_vals = zring + (size_t)EB * tid * VPT;          // stage stride THREADS*VPT values
     unsigned long long* my_mask = zmask + tid;                        // stage stride THREADS
     auto issue = [&](int zp, int stage) {
       const bool zok = zp >= 0 && zp < nz;
       const long long base = (long long)zp * P + p0;
-      float* dv = my_vals + (size_t)stage * THREADS * VPT;
-      if (VEC) {
+      unsigned char* dv = my_vals + (size_t)EB * stage * THREADS * VPT;
+      if constexpr (EB == 2) {
+        // 16-bit values: VPT of them in one 16-byte (VPT 8) or 8-byte (VPT 4)
+        // copy; nv is a multiple of VPT here (the plane and p0 are)
+        const bool ok = zok && nv > 0;
+        const unsigned short* src = ok ? a.h16.bits + base : a.h16.bits;
+        if (VPT == 8) cp16(smem_u32(dv), src, ok);
+        else cp8(smem_u32(dv), src, ok);
+      } else if (VEC) {
         // nv is a multiple of 4 here (the plane and p0 are), so whole quads
 #pragma unroll
         for (int q = 0; q < VPT / 4; ++q) {
           const bool ok = zok && 4 * q < nv;
-          cp16(smem_u32(dv + 4 * q), ok ? (const void*)(a.C + base + 4 * q) : (const void*)a.C, ok);
+          cp16(smem_u32(dv + 16 * q), ok ? (const void*)(a.C + base + 4 * q) : (const void*)a.C, ok);
         }
       } else {
 #pragma unroll
         for (int i = 0; i < VPT; ++i)
-          cp4(smem_u32(dv + i), zok && i < nv ? (const void*)(a.C + base + i) : (const void*)a.C, zok && i < nv);
+          cp4(smem_u32(dv + 4 * i), zok && i < nv ? (const void*)(a.C + base + i) : (const void*)a.C, zok && i < nv);
       }
       if (do_repl) {
         unsigned* dm = reinterpret_cast<unsigned*>(my_mask + (size_t)stage * THREADS);
@@ -176,15 +189,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
       cp_commit();
     };
     for (int k = 0; k < kDepth - 1; ++k) issue(z0 - r + k, k);  // plane index beyond n_steps: harmless zero fill
+    // a 16-bit cube: its planes' scales, loaded a plane ahead
+    auto plane_scale = [&](int zq) { return (EB == 2 && zq >= 0 && zq < nz) ? __ldg(a.h16.scale + zq) : 1.0f; };
+    float cs_next = plane_scale(z0 - r);
     for (int j = 0; j < n_steps; ++j) {
       const int zp = z0 - r + j;
+      const float cs_plane = cs_next;
+      cs_next = plane_scale(zp + 1);
       issue(zp + kDepth - 1, (j + kDepth - 1) % kDepth);
       cp_wait<kDepth - 1>();
       const int st = j % kDepth;
       float cur[VPT];
-      const float* sv = my_vals + (size_t)st * THREADS * VPT;
+      const unsigned char* sv = my_vals + (size_t)EB * st * THREADS * VPT;
+      if constexpr (EB == 2) {
+        const unsigned short* sv16 = reinterpret_cast<const unsigned short*>(sv);
 #pragma unroll
-      for (int i = 0; i < VPT; ++i) cur[i] = sv[i];
+        for (int i = 0; i < VPT; ++i) cur[i] = half16_value(sv16[i], a.h16.fmt, cs_plane);
+      } else {
+        const float* svf = reinterpret_cast<const float*>(sv);
+#pragma unroll
+        for (int i = 0; i < VPT; ++i) cur[i] = svf[i];
+      }
       unsigned mcur = 0u;
       if (do_repl && zp >= 0 && zp < nz && nv > 0) {
         const unsigned* mm = reinterpret_cast<const unsigned*>(my_mask + (size_t)st * THREADS);
@@ -259,14 +284,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
 namespace {
 
 
-template <int VPT, bool VEC, bool REPL, int THREADS>
+template <int VPT, bool VEC, bool REPL, int THREADS, int EB = 4>
 void set_z_attr() {
   cudaFuncAttributes fa{};
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (cudaFuncGetAttributes(&fa, k_smooth_z<VPT, VEC, REPL, THREADS>) != cudaSuccess) return;
-  cudaFuncSetAttribute(k_smooth_z<VPT, VEC, REPL, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncGetAttributes(&fa, k_smooth_z<VPT, VEC, REPL, THREADS, EB>) != cudaSuccess) return;
+  cudaFuncSetAttribute(k_smooth_z<VPT, VEC, REPL, THREADS, EB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        optin - (int)fa.sharedSizeBytes);
 }
 
@@ -276,9 +301,13 @@ void set_z_attrs() {
   set_z_attr<VPT, false, true, THREADS>();
   set_z_attr<VPT, true, false, THREADS>();
   set_z_attr<VPT, true, true, THREADS>();
+  if constexpr (VPT >= 4) {
+    set_z_attr<VPT, true, false, THREADS, 2>();
+    set_z_attr<VPT, true, true, THREADS, 2>();
+  }
 }
 
-template <int VPT, bool VEC, bool REPL, int THREADS>
+template <int VPT, bool VEC, bool REPL, int THREADS, int EB = 4>
 cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   SmoothArgs a = a0;
   const long long P = (long long)a.nx * a.ny;
@@ -293,15 +322,21 @@ cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   const int grid = (int)(items < sms ? items : sms);
   // one block per SM (it holds all of the SM's TMEM): request more than half
   // of the shared memory
-  const size_t need = sizeof(float) * zonly::kDepth * THREADS * VPT + 8 * zonly::kDepth * THREADS +
+  const size_t need = (size_t)EB * zonly::kDepth * THREADS * VPT + 8 * zonly::kDepth * THREADS +
                       (a.hist ? sizeof(unsigned) * kNumBins : 0);
   const size_t smem = tc::one_block_per_sm_smem(need);
-  k_smooth_z<VPT, VEC, REPL, THREADS><<<grid, THREADS, smem, s>>>(a);
+  k_smooth_z<VPT, VEC, REPL, THREADS, EB><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int VPT, int THREADS = zonly::kThreads>
 cudaError_t launch_z_vpt(const SmoothArgs& a, int sms, cudaStream_t s) {
+  if constexpr (VPT >= 4) {
+    if (a.h16.fmt) {  // the caller checked z16_ok
+      const bool repl = a.mbits != nullptr && a.repl_possible;
+      return repl ? launch_z<VPT, true, true, THREADS, 2>(a, sms, s) : launch_z<VPT, true, false, THREADS, 2>(a, sms, s);
+    }
+  }
   const bool vec = VPT >= 4 && ((long long)a.nx * a.ny) % 4 == 0 && (reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 &&
                    (reinterpret_cast<uintptr_t>(a.S) & 15u) == 0;
   const bool repl = a.mbits != nullptr && a.repl_possible;
@@ -320,9 +355,18 @@ void init_z_attrs() {
 }
 
 // Spectral-only pairs (no spatial smoothing, boxcar up to 127 channels).
+// A 16-bit cube takes 16- and 8-byte copies of 8 and 4 values: its planes
+// must be multiples of 8 values, its base and S 16-byte aligned, and the
+// boxcar at most 31 (the forms with 4 or 8 values per thread).
+bool z16_ok(const SmoothArgs& a) {
+  return ((long long)a.nx * a.ny) % 8 == 0 && (reinterpret_cast<uintptr_t>(a.h16.bits) & 15u) == 0 &&
+         (reinterpret_cast<uintptr_t>(a.S) & 15u) == 0 && a.pd.wz <= 31;
+}
+
 cudaError_t launch_smooth_z(const SmoothArgs& a, int sms, cudaStream_t s, bool* done) {
   *done = false;
   if (a.generic || a.pd.h != 0 || a.pd.wz <= 1) return cudaSuccess;
+  if (a.h16.fmt && !z16_ok(a)) return cudaSuccess;
   *done = true;
   if (a.tune_kind == TUNE_Z4 && a.pd.wz <= 31) return launch_z_vpt<4>(a, sms, s);
   // 512 threads of 4 voxels: twice the warps per scheduler, a 16-slot ring

@@ -231,6 +231,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 // outside. False when the cube is not TMA-addressable (row pitch or base not
 // 16-byte aligned) or the driver refuses.
 bool encode_cube_map(CUtensorMap* map, const float* base, long long nx, long long ny, long long nz, int bx, int by);
+// The same for a 16-bit cube (rows must be 16-byte multiples: nx % 8 == 0).
+bool encode_cube16_map(CUtensorMap* map, const unsigned short* base, long long nx, long long ny, long long nz, int bx,
+                       int by);
 
 // Let `kernel` use all opt-in shared memory left beside its static shared memory.
 template <typename K>

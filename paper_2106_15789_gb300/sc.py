@@ -36,6 +36,7 @@ SC_FLAG_NO_FAST_SELECT = 0x4
 SC_FLAG_GRAPH = 0x8
 SC_FLAG_NO_SHARE = 0x10
 SC_FLAG_SAMPLED_GAUSS = 0x20
+SC_FLAG_HALF_DIRECT = 0x40
 SC_AUTOFLAG_CHANNELS, SC_AUTOFLAG_PIXELS = 0x1, 0x2
 # sc_smooth kernel variants (flags |= variant << 16)
 SC_VARIANT_WS, SC_VARIANT_TILE, SC_VARIANT_GENERIC, SC_VARIANT_Z8, SC_VARIANT_Z4, SC_VARIANT_WS16, SC_VARIANT_Z4_512, \
@@ -64,7 +65,7 @@ class sc_kernel(C.Structure):
 
 
 class sc_stats(C.Structure):
-    _fields_ = [("launches", C.c_uint64), ("runs", C.c_uint64), ("warnings", C.c_uint32), ("reserved", C.c_uint32),
+    _fields_ = [("launches", C.c_uint64), ("runs", C.c_uint64), ("warnings", C.c_uint32), ("half_path", C.c_uint32),
                 ("ms_smooth", C.c_double), ("ms_select", C.c_double), ("ms_clip", C.c_double),
                 ("smooth_launches", C.c_uint64), ("smooth_voxels", C.c_uint64),
                 ("ms_smooth_pair", C.c_double * SC_MAX_KERNELS), ("smooth_launches_pair", C.c_uint64 * SC_MAX_KERNELS),
@@ -513,8 +514,6 @@ def sc_get_stats(ctx, reset: bool = False) -> dict:
     _check(lib().sc_get_stats(ctx, C.byref(st), 1 if reset else 0), "sc_get_stats")
     out = {}
     for name, _ in sc_stats._fields_:
-        if name == "reserved":
-            continue
         v = getattr(st, name)
         out[name] = list(v) if name.endswith("_pair") else v
     return out
