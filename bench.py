@@ -113,10 +113,10 @@ def record_traffic(specs, command):
     import csv
 
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    kernels, launches = {}, {}
+    per_key = {}  # key -> {(path, launch id): bytes}; a key may be given several captures
     for spec in specs:
         key, path = spec.split("=", 1)
-        per_launch = {}
+        per_launch = per_key.setdefault(key, {})
         with open(path) as f:
             rows = [r for r in csv.reader(f) if len(r) >= 15]
         head = rows[0]
@@ -125,9 +125,10 @@ def record_traffic(specs, command):
             if r[ci["Metric Name"]] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
                 continue
             b = float(r[ci["Metric Value"]].replace(",", "")) * scale[r[ci["Metric Unit"]]]
-            per_launch[r[ci["ID"]]] = per_launch.get(r[ci["ID"]], 0.0) + b
-        kernels[key] = round(sum(per_launch.values()) / len(per_launch) / TRAFFIC_WORKLOAD_VOXELS, 3)
-        launches[key] = len(per_launch)
+            lid = (path, r[ci["ID"]])
+            per_launch[lid] = per_launch.get(lid, 0.0) + b
+    kernels = {k: round(sum(v.values()) / len(v) / TRAFFIC_WORKLOAD_VOXELS, 3) for k, v in per_key.items()}
+    launches = {k: len(v) for k, v in per_key.items()}
     rec = {"source_sha256_16": smooth_source_hash(),
            "what": "DRAM bytes (read + write) per output voxel of one launch, mean over the captured launches, from "
                    "one-kernel ncu captures (dram__bytes_read.sum + dram__bytes_write.sum, a few launches each) of "

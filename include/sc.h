@@ -304,9 +304,23 @@ int sc_autotune(sc_ctx *ctx, const int64_t *dims, const sc_kernel *kernels, int 
  *   chan_scale_dev  float32 [nz] device array; the cube value of voxel
  *                   (x, y, z) is the float32 product decode(x) * scale[z]
  *                   (rounded once; NaN and Inf decode as such).
- * The cube is decoded once per call into the context's float32 staging cube
- * (allocated on first use, max_voxels floats), and S+C then runs exactly as
- * sc_run on those values (same arguments, outputs and errors). */
+ * S+C then runs exactly as sc_run on those values (same arguments, outputs
+ * and errors, bit-identical results). How the 16-bit cube is read
+ * (sc_stats.half_path):
+ *   3 (default, nx a multiple of 8 and cube_dev 16-byte aligned): the
+ *     raw-cube histogram passes of sigma_0 read the 16-bit values, and the
+ *     first of them also writes the decoded cube into the context's float32
+ *     staging cube (allocated on first use, max_voxels floats), which every
+ *     later pass reads; no decoding pass of its own.
+ *   1 (SC_FLAG_HALF_DIRECT, same shapes): no float32 copy at all: every
+ *     kernel reads the 16-bit values (TMA tiles of 16-bit values in the
+ *     warp-specialised kernel, 16- and 8-byte copies in the spectral one,
+ *     the correction lists and mask pack likewise); the sampled-Gaussian and
+ *     generic kernels have no 16-bit forms, so runs with SC_FLAG_SAMPLED_GAUSS
+ *     or SC_FLAG_GENERIC take path 3. Saves the staging cube's memory; on
+ *     GB300 the 16-bit decoding in the warp-specialised kernel's producers
+ *     makes it slower than the default.
+ *   2 (other shapes): a decoding pass writes the staging cube first. */
 int sc_run_half(sc_ctx *ctx, const uint16_t *cube_dev, int is_bf16, const float *chan_scale_dev,
                 const int64_t *dims, const sc_kernel *kernels, int n_kernels, float threshold, int noise_mode,
                 float replacement, uint8_t *mask_dev, double *sigma_host, double *sigma0_host, uint32_t flags,

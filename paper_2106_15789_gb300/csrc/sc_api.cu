@@ -419,14 +419,18 @@ SmoothArgs base_args(sc_ctx* c, const float* cube, const int64_t* dims, const Ha
   return a;
 }
 
-// A 16-bit cube is read as such by the kernels when its rows are 16-byte
-// multiples (TMA tiles of 16-bit values, 16-byte vector loads of 8 values
-// within a plane) and its base is 16-byte aligned, unless the run asks for the
-// generic or sampled-Gaussian kernels (which have no 16-bit forms); otherwise
-// it is decoded once into a float32 copy.
-bool half_in_kernel(const void* cube_dev, const int64_t* dims, uint32_t flags) {
-  return dims[0] % 8 == 0 && (reinterpret_cast<uintptr_t>(cube_dev) & 15u) == 0 &&
-         !(flags & (SC_FLAG_GENERIC | SC_FLAG_SAMPLED_GAUSS));
+// A 16-bit cube is read by the kernels (the raw-cube histograms, and with
+// SC_FLAG_HALF_DIRECT every kernel) when its rows are 16-byte multiples (TMA
+// tiles of 16-bit values, 16-byte loads of 8 values within a plane) and its
+// base is 16-byte aligned; otherwise it is decoded by a pass of its own.
+bool half_in_kernel(const void* cube_dev, const int64_t* dims) {
+  return dims[0] % 8 == 0 && (reinterpret_cast<uintptr_t>(cube_dev) & 15u) == 0;
+}
+
+// The generic and sampled-Gaussian kernels have no 16-bit forms: such runs
+// read the float32 copy.
+uint32_t half_flags(uint32_t flags) {
+  return (flags & (SC_FLAG_GENERIC | SC_FLAG_SAMPLED_GAUSS)) ? flags & ~(uint32_t)SC_FLAG_HALF_DIRECT : flags;
 }
 
 // Device staging cube and mask of max_voxels elements (allocated on first use).
@@ -1077,7 +1081,7 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
   }
   const double t_submit = host_seconds();
   const float* src = (const float*)cube_dev;
-  const bool h_in = storage != SC_STORE_F32 && half_in_kernel(cube_dev, dims, flags);
+  const bool h_in = storage != SC_STORE_F32 && half_in_kernel(cube_dev, dims);
   const Half16 h{(const unsigned short*)cube_dev, chan_scale_dev, storage};
   if (storage != SC_STORE_F32 && !h_in) {
     rc = ensure_stage(lc);
@@ -1088,7 +1092,7 @@ int sc_submit(sc_ctx* c, const void* cube_dev, int storage, const float* chan_sc
   }
   if (rc == SC_OK)
     rc = run_device(lc, h_in ? nullptr : src, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev,
-                    flags, ls, h_in ? &h : nullptr);
+                    h_in ? half_flags(flags) : flags & ~(uint32_t)SC_FLAG_HALF_DIRECT, ls, h_in ? &h : nullptr);
   if (rc == SC_OK) {
     BatchRes* r = reinterpret_cast<BatchRes*>(slot);
     if (cudaMemcpyAsync(r, lc->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, ls) != cudaSuccess ||
@@ -1245,9 +1249,10 @@ int sc_run_half(sc_ctx* c, const uint16_t* cube_dev, int is_bf16, const float* c
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   c->last = s;
-  if (half_in_kernel(cube_dev, dims, flags)) {
+  if (half_in_kernel(cube_dev, dims)) {
     const Half16 h{cube_dev, chan_scale_dev, is_bf16 ? SC_STORE_BF16 : SC_STORE_FP16};
-    rc = run_device(c, nullptr, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags, s, &h);
+    rc = run_device(c, nullptr, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev,
+                    half_flags(flags), s, &h);
   } else {
     rc = ensure_stage(c);
     if (rc) return rc;
@@ -1257,8 +1262,8 @@ int sc_run_half(sc_ctx* c, const uint16_t* cube_dev, int is_bf16, const float* c
                             c->stage_cube, c->sms, s));
       c->stats.launches += 1;
     }
-    rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev, flags,
-                    s);
+    rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, mask_dev,
+                    flags & ~(uint32_t)SC_FLAG_HALF_DIRECT, s);
     c->stats.half_path = 2u;
   }
   if (rc) return rc;

@@ -92,10 +92,10 @@ def _decoded(bits, scale, bf16):
 @pytest.mark.parametrize("mode", ["mad", "std", "gauss"])
 def test_kernels_read_16_bit_values(ctx, bf16, mode):
     """Rows of 16-byte multiples: the copy made by the histogram pass
-    (half_path 3) and every kernel reading 16-bit values (half_path 1, the
-    16-bit forms of the warp-specialised and spectral kernels) give the same
-    floats as the decoding pass (half_path 2, forced by the generic kernels)
-    and as sc_run on the decoded cube; with a caller mask too."""
+    (half_path 3, also with the generic kernels, which have no 16-bit form)
+    and every kernel reading 16-bit values (half_path 1, the 16-bit forms of
+    the warp-specialised and spectral kernels) give the same floats as sc_run
+    on the decoded cube; with a caller mask too."""
     from paper_2106_15789_gb300 import sc
 
     cube = make_cube(SMALL)
@@ -109,8 +109,9 @@ def test_kernels_read_16_bit_values(ctx, bf16, mode):
     st = ctx.stats(reset=True)
     assert st["half_path"] == 1
     assert sc.SC_KERNEL_WS32 in st["smooth_kernel_pair"] and sc.SC_KERNEL_Z in st["smooth_kernel_pair"]
-    staged = ctx.run_half(bits, bf16, scale, KERNELS_12, T, mode, N_REPL, flags=sc.SC_FLAG_GENERIC)
-    assert ctx.stats()["half_path"] == 2
+    staged = ctx.run_half(bits, bf16, scale, KERNELS_12, T, mode, N_REPL,
+                          flags=sc.SC_FLAG_GENERIC | sc.SC_FLAG_HALF_DIRECT)
+    assert ctx.stats()["half_path"] == 3
     for r in (ref, direct, staged):
         assert torch.equal(got[0], r[0]) and got[1] == r[1] and got[2] == r[2]
     # a caller mask (the 16-bit pack of the working mask)
