@@ -765,7 +765,11 @@ def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None
         m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
         ref = (m_f.clone(), sig_f, s0_f)
     prec = half_precision(cube, bits, scale, bf16, m_h, sig_h, s0_h, *ref, with_oracle)
-    prec["cube_read_by_kernels"] = in_kernel
+    prec["half_path"] = int(st["half_path"])
+    prec["cube_read"] = {1: "16-bit values by every kernel (SC_FLAG_HALF_DIRECT)",
+                         2: "decoded into a float32 copy by a pass of its own",
+                         3: "16-bit values by the raw-cube histogram passes, the first of which writes the float32 "
+                            "working copy every later pass reads"}.get(int(st["half_path"]), "float32")
     if not bf16 and not with_oracle:
         # mitigation study: FP16 plus a float32 sideband of the values above
         # 2.5 sigma_0 (the float32 path on the decoded cube with those values
