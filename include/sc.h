@@ -271,8 +271,8 @@ int sc_set_share_limit(sc_ctx *ctx, uint64_t max_entries);
  *                unless SC_FLAG_ACCUMULATE).
  *   sigma_host   NULL or double[n_cubes * n_kernels], row i = cube i.
  *   sigma0_host  NULL or double[n_cubes].
- * The cubes run with no host synchronisation between them on four
- * concurrent lanes (the context's workspace and three more of the same size,
+ * The cubes run with no host synchronisation between them on eight
+ * concurrent lanes (the context's workspace and seven more of the same size,
  * created on first use, each with its own stream forked from and joined back
  * into cuda_stream), so one cube's selection overlaps another's smoothing.
  * With SC_FLAG_GRAPH the whole
@@ -338,10 +338,11 @@ int sc_run_half(sc_ctx *ctx, const uint16_t *cube_dev, int is_bf16, const float 
 int sc_set_budget(sc_ctx *ctx, uint64_t bytes);
 
 /* Enqueue S+C of one cube and return at once with *job_id (> 0). The job runs
- * on one of the context's three job lanes (workspaces of max_voxels voxels
+ * on one of the context's seven job lanes (workspaces of max_voxels voxels
  * with their own streams, shared with sc_run_batch: do not run a batch while
  * jobs are in flight), round robin, after the lane's earlier jobs; 16-bit
- * storage is decoded into the lane's staging cube first. The caller keeps
+ * storage is read as sc_run_half reads it (decoded into the lane's staging
+ * cube by its first histogram pass, or by a pass of its own). The caller keeps
  * cube_dev, chan_scale_dev (16-bit storage only) and mask_dev alive and
  * untouched until sc_poll returns the job. The job starts after the work
  * enqueued on cuda_stream before the call (whatever produced the cube); once

@@ -120,7 +120,7 @@ struct sc_ctx {
 };
 
 namespace {
-constexpr int kBatchLanes = 4;  // concurrent cubes of a batch (the context itself and 3 lanes)
+constexpr int kBatchLanes = 8;  // concurrent cubes of a batch (the context itself and 7 lanes)
 }
 
 namespace {
