@@ -499,9 +499,23 @@ def pipelined_e2e(ctx, inputs, run_fn, nvox, nk, e2e_steps, pg, dev, world, api)
     run(e2e_steps)
     dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
     ok = all(float(x) > 0 for x in sig_h[(e2e_steps - 1) % 2])
+    # the copies alone (after the timed region): the pipeline's fill (the first
+    # step's inputs) and drain (the last mask) do not overlap any compute
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with torch.cuda.stream(copy):
+        e0.record(copy)
+        load(0)
+        e1.record(copy)
+        mask_h[0].copy_(masks[0], non_blocking=True)
+        e2.record(copy)
+    torch.cuda.synchronize(dev)
+    h2d_b = sum(x.numel() * x.element_size() for x in inputs)
+    h2d_ms, d2h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
     return {"value": job_value(nvox, nk, e2e_steps, world, dt), "unit": UNIT,
-            "h2d_bytes_per_step": sum(x.numel() * x.element_size() for x in inputs),
+            "h2d_bytes_per_step": h2d_b,
             "d2h_bytes_per_step": nvox + 4 * (nk + 1), "steps": e2e_steps, "sigmas_ok": ok,
+            "h2d_gbs": h2d_b / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": nvox / (d2h_ms * 1e-3) / 1e9,
+            "fill_and_drain_ms": h2d_ms + d2h_ms,
             "api": api + ", the copies made by torch; next step's H2D and previous mask's D2H overlap the current "
                          "step on a copy stream (two device buffer sets); sigmas collected with sc_copy_sigmas into "
                          "pinned memory, no per-step synchronisation"}
@@ -1225,7 +1239,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=WORKLOADS, default="wallaby")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cube", choices=("wallaby", "small"), default="wallaby",
