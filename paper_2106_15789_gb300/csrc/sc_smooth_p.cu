@@ -54,15 +54,12 @@ constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
 __device__ __forceinline__ int floor_div64(int a) { return a >= 0 ? a / TX : -((-a + TX - 1) / TX); }
 __device__ __forceinline__ int floor_divt(int a, int t) { return a >= 0 ? a / t : -((-a + t - 1) / t); }
 
-// Calls f(bucket, pos) for every bucket whose halo'd region holds voxel v:
-// tiles t with t*T - R <= c < t*T + T + R along each axis; pos = (hy << 8) | hx
-// is the voxel's place in that region.
+// Calls f(bucket, pos) for every bucket whose halo'd region holds the voxel
+// at (x, y) of plane z: tiles t with t*T - R <= c < t*T + T + R along each
+// axis; pos = (hy << 8) | hx is the voxel's place in that region. Returns the
+// number of buckets.
 template <class F>
-__device__ __forceinline__ void for_buckets(long long v, long long nx, long long ny, const ShareArgs& sh, int R, F f) {
-  const long long plane = nx * ny;
-  const long long z = v / plane;
-  const long long rem = v - z * plane;
-  const int y = (int)(rem / nx), x = (int)(rem - (long long)y * nx);
+__device__ __forceinline__ int for_buckets(long long z, int y, int x, const ShareArgs& sh, int R, F f) {
   const int tx_lo = max(0, floor_div64(x - R)), tx_hi = min(sh.tiles_x - 1, (x + R) / TX);
   const int ty_lo = max(0, floor_divt(y - R, sh.ty)), ty_hi = min(sh.tiles_y - 1, (y + R) / sh.ty);
   for (int ty = ty_lo; ty <= ty_hi; ++ty)
@@ -71,6 +68,7 @@ __device__ __forceinline__ void for_buckets(long long v, long long nx, long long
       const unsigned pos = ((unsigned)(y - (ty * sh.ty - R)) << 8) | (unsigned)(x - (tx * TX - R));
       f(b, pos);
     }
+  return (tx_hi - tx_lo + 1) * (ty_hi - ty_lo + 1);
 }
 
 // Delta words M_j & ~M_1, four at a time (both masks carry padding words).
@@ -81,6 +79,7 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
                                                     Half16 h16, long long n, long long nx, long long ny, ShareArgs sh,
                                                     int R) {
   const long long nq = ((n + 31) / 32 + 3) / 4;
+  const long long plane = nx * ny;
   const uint4* m4 = reinterpret_cast<const uint4*>(mbits);
   const uint4* s4 = reinterpret_cast<const uint4*>(sh.msnap);
   const bool write = FILL && sh.ss->overflow == 0u;
@@ -89,6 +88,16 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
     const uint4 a = __ldg(m4 + q), b = __ldg(s4 + q);
     const unsigned d[4] = {a.x & ~b.x, a.y & ~b.y, a.z & ~b.z, a.w & ~b.w};
     if ((d[0] | d[1] | d[2] | d[3]) == 0u) continue;
+    // coordinates of the group's first voxel (divisions once per 128 voxels),
+    // then followed voxel by voxel
+    long long vcur = 128 * q;
+    long long z = vcur / plane;
+    const long long rem = vcur - z * plane;
+    int y = (int)(rem / nx), x = (int)(rem - (long long)y * nx);
+    // counts: consecutive voxels whose halo reaches one and the same bucket
+    // (the common case) add to it with one atomic
+    long long run_b = -1;
+    unsigned run_n = 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       unsigned w = d[k];
@@ -97,20 +106,43 @@ __global__ void __launch_bounds__(256) k_share_list(const uint32_t* __restrict__
         w &= w - 1u;
         const long long v = (4 * q + k) * 32 + bit;
         if (v >= n) break;
+        x += (int)(v - vcur);
+        vcur = v;
+        while (x >= nx) {
+          x -= (int)nx;
+          if (++y == ny) {
+            y = 0;
+            ++z;
+          }
+        }
         if (FILL) {
-          const float cv = h16.fmt ? half16_value(__ldg(h16.bits + v), h16.fmt, __ldg(h16.scale + v / (nx * ny)))
-                                   : __ldg(C + v);
+          const float cv = h16.fmt ? half16_value(__ldg(h16.bits + v), h16.fmt, __ldg(h16.scale + z)) : __ldg(C + v);
           const unsigned long long cb = (unsigned long long)__float_as_uint(cv) << 32;
-          for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned pos) {
+          for_buckets(z, y, x, sh, R, [&](long long bk, unsigned pos) {
             const unsigned slot = atomicSub(sh.cnt + bk, 1u) - 1u;
             const unsigned long long idx = (unsigned long long)__ldg(sh.offs + bk) + slot;
             if (write && idx < sh.cap) sh.ent[idx] = cb | pos;
           });
         } else {
-          for_buckets(v, nx, ny, sh, R, [&](long long bk, unsigned) { atomicAdd(sh.cnt + bk, 1u); });
+          long long only = -1;
+          const int nb = for_buckets(z, y, x, sh, R, [&](long long bk, unsigned) { only = bk; });
+          if (nb == 1 && only == run_b) {
+            ++run_n;
+          } else {
+            if (run_n) atomicAdd(sh.cnt + run_b, run_n);
+            run_b = -1;
+            run_n = 0u;
+            if (nb == 1) {
+              run_b = only;
+              run_n = 1u;
+            } else {
+              for_buckets(z, y, x, sh, R, [&](long long bk, unsigned) { atomicAdd(sh.cnt + bk, 1u); });
+            }
+          }
         }
       }
     }
+    if (!FILL && run_n) atomicAdd(sh.cnt + run_b, run_n);
   }
 }
 
