@@ -196,8 +196,12 @@ int sc_gauss_taps(float fwhm_px, int32_t *taps, int max_taps);
  * all work is enqueued: launch errors are still returned, but that device-side
  * status is not read (the next run clears it), so a caller that needs it
  * passes sigma0_host.
+ * Spatial kernel: the 3-box cascade of sc_cascade_widths, or with
+ * SC_FLAG_SAMPLED_GAUSS the sampled Gaussian of sc_gauss_taps (half-widths up
+ * to 40 after its zero end taps are dropped; wider ones SC_ERR_UNSUPPORTED).
  * Shared spatial passes: when consecutive pairs have the same spatial kernel
- * (FWHM 3, 5, 6 or 10 px, boxcars up to 31 channels), the first of them also
+ * (cascades of FWHM 3, 5, 6 or 10 px, sampled Gaussians of half-width up to
+ * 16, boxcars up to 31 channels), the first of them also
  * stores its spatial sums (int64 per voxel) and each later one adds only the
  * corrections for voxels masked since then (Sect. 6.2 replacement is the only
  * difference between their inputs, and the smoothing is linear and exact).
@@ -376,11 +380,13 @@ int sc_run_host(sc_ctx *ctx, const float *cube_host, const int64_t *dims, const 
 /* One pair's smoothed cube S (Sect. 4.2 smoothing, Sect. 6.2 replacement):
  *   X = C with NaN -> 0 and, where mask_dev != 0 and C is finite,
  *       sign(C)*replacement_value (sign(0) = +1; replacement_value <= 0: off);
- *   S = spectral boxcar * spatial cascade (x, y) of the zero-padded X;
+ *   S = spectral boxcar * spatial cascade (x, y) of the zero-padded X (the
+ *       sampled Gaussian of sc_gauss_taps instead with SC_FLAG_SAMPLED_GAUSS);
  *   S = NaN where C is NaN.
  * mask_dev may be NULL (empty mask). out_dev: float32 [nz][ny][nx], may not
  * alias cube_dev. The smoothing is exact fixed-point integer arithmetic
- * rounded once to float32. Errors as sc_run. Asynchronous. */
+ * rounded once to float32. flags: SC_FLAG_GENERIC, SC_FLAG_SAMPLED_GAUSS and
+ * SC_SMOOTH_VARIANT(v). Errors as sc_run. Asynchronous. */
 int sc_smooth(sc_ctx *ctx, const float *cube_dev, const int64_t *dims, sc_kernel kernel, const uint8_t *mask_dev,
               float replacement_value, float *out_dev, uint32_t flags, void *cuda_stream);
 
