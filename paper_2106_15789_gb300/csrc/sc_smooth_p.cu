@@ -50,6 +50,10 @@ constexpr int VPT = 4;            // rows of one column per compute thread
 constexpr int kStages = 8;        // P tiles in flight (a power of two)
 constexpr int kEnt = 768;         // list entries staged per plane (the rest are read from global memory)
 constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
+// Zero taps either side of the 1-D taps in shared memory: a correction's tap
+// index along x (32 columns of a warp against an entry within R) or y
+// (4 rows) then never needs a range check.
+constexpr int kTapPad = 32;
 
 __device__ __forceinline__ int floor_div64(int a) { return a >= 0 ? a / TX : -((-a + TX - 1) / TX); }
 __device__ __forceinline__ int floor_divt(int a, int t) { return a >= 0 ? a / t : -((-a + t - 1) / t); }
@@ -294,8 +298,8 @@ __host__ __device__ constexpr PSmem p_layout() {
   o = al128(o + kStages * G::kNfBytes);
   s.e = o;  // [kStages][kEnt] list entries
   o = al128(o + sizeof(unsigned long long) * kStages * kEnt);
-  s.kk = o;  // [NT] 1-D taps
-  o = al128(o + sizeof(int) * G::NT);
+  s.kk = o;  // [kTapPad + NT + kTapPad] 1-D taps, zero outside
+  o = al128(o + sizeof(int) * (G::NT + 2 * kTapPad));
   s.meta = o;
   o = al128(o + sizeof(Meta) * kStages);
   s.hist = o;
@@ -343,9 +347,11 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
 
   if (a.hist)
     for (int i = tid; i < kNumBins; i += kThreads) hist[i] = 0u;
+  for (int i = tid; i < NT + 2 * kTapPad; i += kThreads) taps1[i] = 0;
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < NT; ++i)
-    if (tid == i) taps1[i] = a.pd.taps[i];  // compile-time indices: read from the kernel parameters
+    if (tid == i) taps1[kTapPad + i] = a.pd.taps[i];  // compile-time indices: read from the kernel parameters
   __shared__ unsigned tmem_holder;
   if (warp == 0) tmem_alloc(&tmem_holder);
   if (tid == 0) {
@@ -528,21 +534,20 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
             const bool two = reach != 0u;
             reach &= reach - 1u;
             const unsigned ej0 = __shfl_sync(0xffffffffu, (unsigned)e, s0);
-            unsigned ej1 = __shfl_sync(0xffffffffu, (unsigned)e, s1);
+            const unsigned ej1 = __shfl_sync(0xffffffffu, (unsigned)e, two ? s1 : s0);
             const long long d0 = __shfl_sync(0xffffffffu, dl, s0);
-            const long long d1 = __shfl_sync(0xffffffffu, dl, s1);
-            if (!two) ej1 = 0xffffu;
+            const long long d1 = two ? __shfl_sync(0xffffffffu, dl, s1) : 0ll;  // a missing second entry adds 0
+            // entries within reach: tap indices b in [-31, 31 + 2R] along x and
+            // a in [-3, 3 + 2R] along y, inside the zero-padded taps
             const int jy0 = (int)((ej0 >> 8) & 0xffu) - R, jx0 = (int)(ej0 & 0xffu) - R;
             const int jy1 = (int)((ej1 >> 8) & 0xffu) - R, jx1 = (int)(ej1 & 0xffu) - R;
-            const int b0 = xc - jx0 + R, b1 = xc - jx1 + R;
-            const bool in0 = (unsigned)b0 < (unsigned)NT, in1 = (unsigned)b1 < (unsigned)NT;
-            const long long dk0 = in0 ? d0 * taps1[b0] : 0ll;
-            const long long dk1 = in1 ? d1 * taps1[b1] : 0ll;
+            const int* tp = taps1 + kTapPad + R;
+            const long long dk0 = d0 * tp[xc - jx0];
+            const long long dk1 = d1 * tp[xc - jx1];
 #pragma unroll
             for (int k = 0; k < VPT; ++k) {
-              const int a0 = wy0 + k - jy0 + R, a1 = wy0 + k - jy1 + R;
-              if ((unsigned)a0 < (unsigned)NT) p[k] += dk0 * taps1[a0];
-              if ((unsigned)a1 < (unsigned)NT) p[k] += dk1 * taps1[a1];
+              p[k] += dk0 * tp[wy0 + k - jy0];
+              p[k] += dk1 * tp[wy0 + k - jy1];
             }
           }
         }
