@@ -1,6 +1,9 @@
 // Warp-specialised smoothing kernel for the spatial cascades of FWHM 3, 5, 6
-// and 10 px (SoFiA 2 Sect. 4.2 / 5) with spectral boxcars up to 15 channels,
-// and the replacement of Sect. 6.2.
+// and 10 px (SoFiA 2 Sect. 4.2 / 5) with spectral boxcars up to 15 channels
+// (31 with 64 x 16 tiles), and the replacement of Sect. 6.2. Instances with
+// W1 = 0 run the sampled Gaussian's integer FIR of half-width W2 instead of a
+// cascade (sc_smooth_fir.cu); instances with EB = 2 read a 16-bit cube with
+// per-channel scales (sc_smooth_ws16.cu).
 //
 // Same exact int64 fixed-point arithmetic as every other smoothing kernel of
 // this library (quantise once, exact box sums, one final rounding), hence the
@@ -28,7 +31,8 @@
 // Hand-off barriers: bt_full[b] (one arrival per producer warp once its x
 // pass items are written) and bt_empty[b] (one arrival per consumer warp; it
 // also frees the raw tile of that plane, which the TMA refills two planes
-// later). Every wait is bounded in wall time; a wait that runs out
+// later). Every wait is bounded in wall time; a wait that runs out sets
+// SC_ST_TIMEOUT and the kernel finishes without further waiting.
 #pragma once
 
 #include <cstdint>
