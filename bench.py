@@ -438,87 +438,53 @@ def dominant_kernel(sc, kernels, st, voxels_per_launch, steps, peak, peak_kind, 
             "smoothing_ms_by_kernel": {name: round(v[0] / steps, 3) for name, v in groups.items()}}
 
 
-def pipelined_e2e(ctx, inputs, run_fn, nvox, nk, e2e_steps, pg, dev, world, api):
-    """End to end from pinned host memory: every step copies its inputs host
-    -> device and its mask device -> host; with two device buffer sets the next
-    step's inputs and the previous mask travel on a copy stream while the
-    current step computes (events order them). run_fn(device_inputs, mask)
-    enqueues one run without sigma pointers; each step's sigmas are collected
-    with sc_copy_sigmas into pinned host memory, in stream order (no
-    synchronisation per step), and checked after the timed region."""
+def host_e2e(ctx, host_cube, kernels, t, mode, n_repl, nvox, e2e_steps, pg, dev, world, storage=0,
+             host_scale=None, flags=0):
+    """End to end through the C ABI's host-buffer entry sc_run_host_many: the
+    step's cube (pinned host memory) goes host -> device and its mask device ->
+    host inside the call, the next cube's copy and the previous mask's copy
+    overlapped with the current run by the library; e2e_steps cubes per call
+    (the same host cube, two host masks in turn), timed on the host around the
+    call, which synchronises. The copy bandwidths are measured afterwards with
+    the same pinned buffers."""
     import torch
 
-    hosts = []
-    for x in inputs:
-        h = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-        h.copy_(x)
-        hosts.append(h)
-    sig_h = [torch.empty(nk + 1, dtype=torch.float32, pin_memory=True) for _ in range(2)]
-    shape = inputs[0].shape
-    mask_h = [torch.empty(shape, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
-    bufs = [[torch.empty_like(x) for x in inputs] for _ in range(2)]
-    masks = [torch.empty(shape, dtype=torch.uint8, device=dev) for _ in range(2)]
-    compute = torch.cuda.current_stream(dev)
-    copy = torch.cuda.Stream(dev)
-    loaded = [torch.cuda.Event() for _ in range(2)]
-    computed = [torch.cuda.Event() for _ in range(2)]
-    sent = [torch.cuda.Event() for _ in range(2)]
+    shape = tuple(host_cube.shape)
+    masks = [torch.empty(shape, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
 
-    def load(b):
-        for d, h in zip(bufs[b], hosts):
-            d.copy_(h, non_blocking=True)
-
-    def run(steps):
-        with torch.cuda.stream(copy):
-            load(0)
-            loaded[0].record(copy)
-        for i in range(steps):
-            b, nb = i % 2, (i + 1) % 2
-            if i + 1 < steps:
-                with torch.cuda.stream(copy):
-                    if i >= 1:
-                        copy.wait_event(computed[nb])  # step i - 1 is done with that buffer set
-                    load(nb)
-                    loaded[nb].record(copy)
-            compute.wait_event(loaded[b])
-            if i >= 2:
-                compute.wait_event(sent[b])  # its mask of step i - 2 has left the device
-            run_fn(bufs[b], masks[b])
-            ctx.copy_sigmas(sig_h[b][:nk], sig_h[b][nk:], nk)  # stream-ordered, into pinned memory
-            computed[b].record(compute)
-            with torch.cuda.stream(copy):
-                copy.wait_event(computed[b])
-                mask_h[b].copy_(masks[b], non_blocking=True)
-                sent[b].record(copy)
-        torch.cuda.synchronize(dev)
+    def run(k):
+        return ctx.run_host_many([host_cube] * k, kernels, t, mode, n_repl, masks_host=[masks[i % 2] for i in range(k)],
+                                 storage=storage, chan_scales_host=[host_scale] * k if host_scale is not None else None,
+                                 flags=flags)
 
     run(2)
+    torch.cuda.synchronize(dev)
     if pg:
         pg.barrier()
     t0 = time.perf_counter()
-    run(e2e_steps)
+    _, sigs, s0s = run(e2e_steps)
     dt = max_over_ranks(time.perf_counter() - t0, pg, dev)
-    ok = all(float(x) > 0 for x in sig_h[(e2e_steps - 1) % 2])
-    # the copies alone (after the timed region): the pipeline's fill (the first
-    # step's inputs) and drain (the last mask) do not overlap any compute
+    ok = all(s > 0 for s in s0s) and all(x > 0 for row in sigs for x in row)
+    # the copies alone: the pipeline's fill (the first cube) and drain (the
+    # last mask) overlap no compute
+    d_in = torch.empty(shape, dtype=host_cube.dtype, device=dev)
+    d_m = torch.empty(shape, dtype=torch.uint8, device=dev)
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    with torch.cuda.stream(copy):
-        e0.record(copy)
-        load(0)
-        e1.record(copy)
-        mask_h[0].copy_(masks[0], non_blocking=True)
-        e2.record(copy)
+    e0.record()
+    d_in.copy_(host_cube, non_blocking=True)
+    e1.record()
+    masks[0].copy_(d_m, non_blocking=True)
+    e2.record()
     torch.cuda.synchronize(dev)
-    h2d_b = sum(x.numel() * x.element_size() for x in inputs)
+    h2d_b = host_cube.numel() * host_cube.element_size() + (host_scale.numel() * 4 if host_scale is not None else 0)
     h2d_ms, d2h_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    return {"value": job_value(nvox, nk, e2e_steps, world, dt), "unit": UNIT,
-            "h2d_bytes_per_step": h2d_b,
-            "d2h_bytes_per_step": nvox + 4 * (nk + 1), "steps": e2e_steps, "sigmas_ok": ok,
-            "h2d_gbs": h2d_b / (h2d_ms * 1e-3) / 1e9, "d2h_gbs": nvox / (d2h_ms * 1e-3) / 1e9,
-            "fill_and_drain_ms": h2d_ms + d2h_ms,
-            "api": api + ", the copies made by torch; next step's H2D and previous mask's D2H overlap the current "
-                         "step on a copy stream (two device buffer sets); sigmas collected with sc_copy_sigmas into "
-                         "pinned memory, no per-step synchronisation"}
+    return {"value": job_value(nvox, len(kernels), e2e_steps, world, dt), "unit": UNIT,
+            "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": nvox + 8 * (len(kernels) + 1), "steps": e2e_steps,
+            "sigmas_ok": ok, "h2d_gbs": host_cube.numel() * host_cube.element_size() / (h2d_ms * 1e-3) / 1e9,
+            "d2h_gbs": nvox / (d2h_ms * 1e-3) / 1e9, "fill_and_drain_ms": h2d_ms + d2h_ms,
+            "api": "sc_run_host_many (C ABI, pinned host buffers): every cube host -> device and its mask "
+                   "device -> host inside the call, the next cube's copy and the previous mask's overlapped with "
+                   "the current run by the library; sigmas returned by the call"}
 
 
 def measure_batch(dev, local, steps, warmup, pg, world, rank, tune=True, with_e2e=False, e2e_steps=3):
@@ -770,11 +736,8 @@ def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None
     m_h = m_h.clone()
     e2e = None
     if e2e_steps:
-        e2e = pipelined_e2e(
-            ctx, [bits, scale],
-            lambda ins, m: ctx.run_half(ins[0], bf16, ins[1], kernels, t, "mad", n_repl, mask=m, want_sigma=False),
-            nvox, len(kernels), e2e_steps, pg, dev, world,
-            "sc_run_half on device copies of the pinned 16-bit cube and its per-channel scales")
+        e2e = host_e2e(ctx, bits.cpu().pin_memory(), kernels, t, "mad", n_repl, nvox, e2e_steps, pg, dev, world,
+                       storage=sc.SC_STORE_BF16 if bf16 else sc.SC_STORE_FP16, host_scale=scale.cpu().pin_memory())
     if ref is None:
         m_f, sig_f, s0_f = ctx.run(cube, kernels, t, "mad", n_repl)
         ref = (m_f.clone(), sig_f, s0_f)
@@ -1346,10 +1309,8 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = pipelined_e2e(ctx, [cube], lambda ins, m: ctx.run(ins[0], kernels, t, mode, n_repl, mask=m,
-                                                                  want_sigma=False, flags=run_flags),
-                            nvox, len(kernels), args.e2e_steps, pg, dev, world,
-                            "sc_run on device copies of a pinned host cube")
+        e2e = host_e2e(ctx, cube.cpu().pin_memory(), kernels, t, mode, n_repl, nvox, args.e2e_steps, pg, dev, world,
+                       flags=run_flags)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -377,6 +377,27 @@ int sc_run_host(sc_ctx *ctx, const float *cube_host, const int64_t *dims, const 
                 int n_kernels, float threshold, int noise_mode, float replacement, uint8_t *mask_host,
                 double *sigma_host, double *sigma0_host, uint32_t flags, void *cuda_stream);
 
+/* S+C on n_cubes cubes of one shape in host memory, with the copies
+ * overlapped: while cube i runs on cuda_stream, cube i + 1 is copied to the
+ * device and cube i - 1's mask back, on a copy stream of the context (two
+ * device input / mask sets of max_voxels, allocated on first use).
+ *   cubes_host[i]        float32 [nz][ny][nx] (storage SC_STORE_F32) or the
+ *                        BF16 / FP16 bits (SC_STORE_BF16 / SC_STORE_FP16);
+ *   chan_scales_host[i]  float32 [nz] per-channel scales of 16-bit cubes
+ *                        (ignored, may be NULL, for float32);
+ *   masks_host[i]        uint8 [nz][ny][nx], the output mask (read first with
+ *                        SC_FLAG_ACCUMULATE);
+ *   sigma_host           NULL or double[n_cubes * n_kernels], row i = cube i;
+ *   sigma0_host          NULL or double[n_cubes].
+ * Every cube's result is sc_run's (float32) or sc_run_half's (16-bit) on the
+ * same values. Pinned host memory gives full copy bandwidth. Returns after all
+ * cubes have finished (the stream is synchronised), with the first failing
+ * cube's status (its sigmas 0). Errors: as sc_run / sc_run_half, SC_ERR_NOMEM. */
+int sc_run_host_many(sc_ctx *ctx, int n_cubes, const void *const *cubes_host, int storage,
+                     const float *const *chan_scales_host, const int64_t *dims, const sc_kernel *kernels,
+                     int n_kernels, float threshold, int noise_mode, float replacement, uint8_t *const *masks_host,
+                     double *sigma_host, double *sigma0_host, uint32_t flags, void *cuda_stream);
+
 /* One pair's smoothed cube S (Sect. 4.2 smoothing, Sect. 6.2 replacement):
  *   X = C with NaN -> 0 and, where mask_dev != 0 and C is finite,
  *       sign(C)*replacement_value (sign(0) = +1; replacement_value <= 0: off);

@@ -53,6 +53,16 @@ struct sc_ctx {
   unsigned char* af_buf = nullptr;  // sc_autoflag: noises, flags and statistics (lazy, grown)
   size_t af_cap = 0;
   uint8_t* stage_mask = nullptr;
+  // sc_run_host_many (lazy): two device input / mask sets, the per-channel
+  // scales of 16-bit cubes, the copy stream and its events, per-cube results
+  void* hm_in[2] = {nullptr, nullptr};       // max_voxels float32 (16-bit cubes use half)
+  uint8_t* hm_mask[2] = {nullptr, nullptr};
+  float* hm_scale[2] = {nullptr, nullptr};
+  size_t hm_scale_cap = 0;
+  cudaStream_t hm_copy = nullptr;
+  cudaEvent_t hm_ev[6] = {};                 // loaded[2], computed[2], sent[2]
+  unsigned char* hm_res = nullptr;           // pinned: one BatchRes per cube
+  size_t hm_res_cap = 0;
   int profiling = 0;
   sc_stats stats{};
   struct Ev {
@@ -769,6 +779,15 @@ void sc_destroy(sc_ctx* c) {
   cudaFree(c->sh_ent);
   cudaFree(c->sh_ss);
   if (c->st_host) cudaFreeHost(c->st_host);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(c->hm_in[i]);
+    cudaFree(c->hm_mask[i]);
+    cudaFree(c->hm_scale[i]);
+  }
+  if (c->hm_copy) cudaStreamDestroy(c->hm_copy);
+  for (cudaEvent_t e : c->hm_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->hm_res) cudaFreeHost(c->hm_res);
   cudaFree(c->batch_res);
   if (c->batch_res_host) cudaFreeHost(c->batch_res_host);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -1293,6 +1312,132 @@ int sc_run_host(sc_ctx* c, const float* cube_host, const int64_t* dims, const sc
   rc = finish(c, n_kernels, sigma_host, sigma0_host, s, true);
   if (rc == SC_OK) c->stats.runs += 1;
   return rc;
+}
+
+int sc_run_host_many(sc_ctx* c, int n_cubes, const void* const* cubes_host, int storage,
+                     const float* const* chan_scales_host, const int64_t* dims, const sc_kernel* kernels,
+                     int n_kernels, float threshold, int noise_mode, float replacement, uint8_t* const* masks_host,
+                     double* sigma_host, double* sigma0_host, uint32_t flags, void* cuda_stream) {
+  if (!c || n_cubes < 1 || !cubes_host || !masks_host || !dims) return SC_ERR_ARG;
+  if (storage != SC_STORE_F32 && storage != SC_STORE_BF16 && storage != SC_STORE_FP16) return SC_ERR_ARG;
+  if (storage != SC_STORE_F32 && !chan_scales_host) return SC_ERR_ARG;
+  if (n_kernels < 1 || n_kernels > SC_MAX_KERNELS || !std::isfinite(replacement)) return SC_ERR_ARG;
+  for (int i = 0; i < n_cubes; ++i)
+    if (!cubes_host[i] || !masks_host[i] || (storage != SC_STORE_F32 && !chan_scales_host[i])) return SC_ERR_ARG;
+  DeviceGuard g(c->device);
+  long long n = 0;
+  int rc = check_dims(c, dims, &n);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  c->last = s;
+  const size_t in_bytes = (storage == SC_STORE_F32 ? 4u : 2u) * (size_t)n;
+  const size_t nz = (size_t)dims[2];
+  // buffers, copy stream and events (first use)
+  for (int b = 0; b < 2; ++b) {
+    if (!c->hm_in[b] && cudaMalloc(&c->hm_in[b], sizeof(float) * c->max_voxels) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    if (!c->hm_mask[b] && cudaMalloc(&c->hm_mask[b], c->max_voxels) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+  }
+  if (storage != SC_STORE_F32 && nz > c->hm_scale_cap) {
+    for (int b = 0; b < 2; ++b) {
+      cudaFree(c->hm_scale[b]);
+      c->hm_scale[b] = nullptr;
+    }
+    c->hm_scale_cap = 0;
+    for (int b = 0; b < 2; ++b)
+      if (cudaMalloc(&c->hm_scale[b], sizeof(float) * nz) != cudaSuccess) {
+        cudaGetLastError();
+        return SC_ERR_NOMEM;
+      }
+    c->hm_scale_cap = nz;
+  }
+  if (!c->hm_copy) CK(cudaStreamCreateWithFlags(&c->hm_copy, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : c->hm_ev)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  const size_t need = sizeof(BatchRes) * (size_t)n_cubes;
+  if (need > c->hm_res_cap) {
+    if (c->hm_res) cudaFreeHost(c->hm_res);
+    c->hm_res = nullptr;
+    c->hm_res_cap = 0;
+    if (cudaHostAlloc(&c->hm_res, need, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return SC_ERR_NOMEM;
+    }
+    c->hm_res_cap = need;
+  }
+  cudaEvent_t* loaded = c->hm_ev;
+  cudaEvent_t* computed = c->hm_ev + 2;
+  cudaEvent_t* sent = c->hm_ev + 4;
+  cudaStream_t cp = c->hm_copy;
+  BatchRes* res = reinterpret_cast<BatchRes*>(c->hm_res);
+  auto load = [&](int i, int b) -> int {
+    CK(cudaMemcpyAsync(c->hm_in[b], cubes_host[i], in_bytes, cudaMemcpyHostToDevice, cp));
+    if (storage != SC_STORE_F32)
+      CK(cudaMemcpyAsync(c->hm_scale[b], chan_scales_host[i], sizeof(float) * nz, cudaMemcpyHostToDevice, cp));
+    if (flags & SC_FLAG_ACCUMULATE) CK(cudaMemcpyAsync(c->hm_mask[b], masks_host[i], n, cudaMemcpyHostToDevice, cp));
+    CK(cudaEventRecord(loaded[b], cp));
+    return SC_OK;
+  };
+  // The copy stream starts after the work enqueued on s; cube i + 1 is copied
+  // in, and cube i - 1's mask out, while cube i computes on s.
+  CK(cudaEventRecord(computed[1], s));
+  CK(cudaStreamWaitEvent(cp, computed[1], 0));
+  rc = load(0, 0);
+  if (rc) return rc;
+  for (int i = 0; i < n_cubes; ++i) {
+    const int b = i & 1, nb = b ^ 1;
+    if (i + 1 < n_cubes) {
+      if (i >= 1) CK(cudaStreamWaitEvent(cp, computed[nb], 0));  // cube i - 1 is done with that set
+      if (i >= 1) CK(cudaStreamWaitEvent(cp, sent[nb], 0));
+      rc = load(i + 1, nb);
+      if (rc) return rc;
+    }
+    CK(cudaStreamWaitEvent(s, loaded[b], 0));
+    if (i >= 2) CK(cudaStreamWaitEvent(s, sent[b], 0));  // its mask of cube i - 2 has left the device
+    if (storage == SC_STORE_F32) {
+      rc = run_device(c, static_cast<const float*>(c->hm_in[b]), dims, kernels, n_kernels, threshold, noise_mode,
+                      replacement, c->hm_mask[b], flags & ~(uint32_t)SC_FLAG_HALF_DIRECT, s);
+    } else if (half_in_kernel(c->hm_in[b], dims)) {
+      const Half16 h{static_cast<const unsigned short*>(c->hm_in[b]), c->hm_scale[b], storage};
+      rc = run_device(c, nullptr, dims, kernels, n_kernels, threshold, noise_mode, replacement, c->hm_mask[b],
+                      half_flags(flags), s, &h);
+    } else {
+      rc = ensure_stage(c);
+      if (rc) return rc;
+      CK(launch_decode_half(static_cast<const uint16_t*>(c->hm_in[b]), c->hm_scale[b], dims[0] * dims[1], n,
+                            storage == SC_STORE_BF16 ? 1 : 0, c->stage_cube, c->sms, s));
+      c->stats.launches += 1;
+      rc = run_device(c, c->stage_cube, dims, kernels, n_kernels, threshold, noise_mode, replacement, c->hm_mask[b],
+                      flags & ~(uint32_t)SC_FLAG_HALF_DIRECT, s);
+    }
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(&res[i], c->st, 3 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(res[i].sigma, c->st->sigma, sizeof(float) * n_kernels, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(computed[b], s));
+    CK(cudaStreamWaitEvent(cp, computed[b], 0));
+    CK(cudaMemcpyAsync(masks_host[i], c->hm_mask[b], n, cudaMemcpyDeviceToHost, cp));
+    CK(cudaEventRecord(sent[b], cp));
+  }
+  CK(cudaStreamWaitEvent(s, sent[(n_cubes - 1) & 1], 0));
+  CK(cudaStreamSynchronize(s));
+  int first = SC_OK;
+  c->stats.warnings = 0;
+  for (int i = 0; i < n_cubes; ++i) {
+    const int code = status_code(res[i].status);
+    if (code != SC_OK && first == SC_OK) first = code;
+    c->stats.warnings |= res[i].warn;
+    if (sigma0_host) sigma0_host[i] = code == SC_OK ? (double)res[i].sigma0 : 0.0;
+    if (sigma_host)
+      for (int k = 0; k < n_kernels; ++k)
+        sigma_host[(size_t)i * n_kernels + k] = code == SC_OK ? (double)res[i].sigma[k] : 0.0;
+  }
+  if (first == SC_OK) c->stats.runs += (unsigned long long)n_cubes;
+  return first;
 }
 
 int sc_smooth(sc_ctx* c, const float* cube_dev, const int64_t* dims, sc_kernel kernel, const uint8_t* mask_dev,

@@ -99,6 +99,9 @@ _SIGS = {
     "sc_gauss_taps": (C.c_int, [C.c_float, C.POINTER(C.c_int32), C.c_int]),
     "sc_run": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int, C.c_float,
                          _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
+    "sc_run_host_many": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.c_int, C.POINTER(_P), C.POINTER(C.c_int64),
+                                   C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int, C.c_float, C.POINTER(_P),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_run_host": (C.c_int, [_P, _P, C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int, C.c_float, C.c_int,
                               C.c_float, _P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_uint32, _P]),
     "sc_run_batch": (C.c_int, [_P, C.c_int, C.POINTER(_P), C.POINTER(C.c_int64), C.POINTER(sc_kernel), C.c_int,
@@ -356,6 +359,45 @@ def sc_run_host(ctx, cube_host: torch.Tensor, kernels, threshold: float, noise_m
     return mask_host, [float(x) for x in sig], float(sig0[0])
 
 
+def sc_run_host_many(ctx, cubes_host, kernels, threshold: float, noise_mode="mad", replacement: float = 2.0,
+                     masks_host=None, storage: int = SC_STORE_F32, chan_scales_host=None, flags: int = 0,
+                     stream=None, device: int = 0):
+    """S+C on a sequence of same-shape host (CPU) cubes with the copies
+    overlapped (cube i + 1 in and mask i - 1 out while cube i runs). cubes_host:
+    contiguous CPU tensors (float32, or int16/uint16 bit patterns for 16-bit
+    storage, then with chan_scales_host: float32 [nz] CPU tensors). Returns
+    (masks, sigmas [n][n_kernels], sigma0s [n]); pinned tensors copy fastest."""
+    n = len(cubes_host)
+    if n < 1:
+        raise ValueError("at least one cube")
+    shape = tuple(cubes_host[0].shape)
+    for i, cb in enumerate(cubes_host):
+        want = 4 if storage == SC_STORE_F32 else 2
+        if cb.device.type != "cpu" or not cb.is_contiguous() or tuple(cb.shape) != shape or cb.element_size() != want:
+            raise ValueError(f"cube {i}: a contiguous CPU tensor of the first cube's shape and {want}-byte values")
+    if masks_host is None:
+        masks_host = [torch.empty(shape, dtype=torch.uint8) for _ in range(n)]
+    if storage != SC_STORE_F32:
+        if chan_scales_host is None or len(chan_scales_host) != n:
+            raise ValueError("16-bit storage needs a scale tensor per cube")
+        sc_arr = (_P * n)(*[C.c_void_p(t.data_ptr()) for t in chan_scales_host])
+    else:
+        sc_arr = None
+    kk, nk = _kernels(kernels)
+    mode = NOISE_MODES.get(noise_mode, noise_mode)
+    sig = (C.c_double * (n * nk))()
+    sig0 = (C.c_double * n)()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    cubes = (_P * n)(*[C.c_void_p(t.data_ptr()) for t in cubes_host])
+    masks = (_P * n)(*[C.c_void_p(t.data_ptr()) for t in masks_host])
+    code = lib().sc_run_host_many(ctx, n, cubes, int(storage), sc_arr, _dims(shape), kk, nk, float(threshold),
+                                  int(mode), float(replacement), masks, sig, sig0, int(flags),
+                                  C.c_void_p(stream.cuda_stream))
+    _check(code, "sc_run_host_many")
+    return masks_host, [[float(sig[i * nk + k]) for k in range(nk)] for i in range(n)], [float(x) for x in sig0]
+
+
 def sc_smooth(ctx, cube: torch.Tensor, kernel, mask: torch.Tensor | None = None, replacement_value: float = 0.0,
               out: torch.Tensor | None = None, flags: int = 0, stream=None) -> torch.Tensor:
     """Smoothed cube S of one (spatial FWHM, spectral width) pair."""
@@ -552,6 +594,11 @@ class Context:
                   want_sigma=True):
         return sc_run_batch(self.handle, cubes, kernels, threshold, noise_mode, replacement, masks, flags, stream,
                             want_sigma)
+
+    def run_host_many(self, cubes_host, kernels, threshold, noise_mode="mad", replacement=2.0, masks_host=None,
+                      storage=SC_STORE_F32, chan_scales_host=None, flags=0, stream=None):
+        return sc_run_host_many(self.handle, cubes_host, kernels, threshold, noise_mode, replacement, masks_host,
+                                storage, chan_scales_host, flags, stream, self.device)
 
     def run_half(self, cube16, bf16, chan_scale, kernels, threshold, noise_mode="mad", replacement=2.0, mask=None,
                  flags=0, stream=None, want_sigma=True):
