@@ -586,7 +586,7 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
         if (a.repl_possible) {
           // voxels masked since the spatial sums were made, listed per bucket
           if (!share_cnt_clear) {
-            CK(cudaMemsetAsync(c->sh_cnt, 0, sizeof(unsigned) * c->sh_bk_cap, s));  // both tile heights
+            CK(cudaMemsetAsync(c->sh_cnt, 0, sizeof(unsigned) * c->sh_bk_cap, s));  // every tile height
             share_cnt_clear = true;
           }
           sh.offs = c->sh_offs;

@@ -46,13 +46,11 @@ namespace share {
 using namespace tc;
 
 constexpr int TX = 64;            // tile width
-constexpr int VPT = 4;            // rows of one column per compute thread
-constexpr int kStages = 8;        // P tiles in flight (a power of two)
 constexpr int kEnt = 768;         // list entries staged per plane (the rest are read from global memory)
 constexpr int kScanChunk = 4096;  // counts per scan block (1024 threads x 4)
 // Zero taps either side of the 1-D taps in shared memory: a correction's tap
 // index along x (32 columns of a warp against an entry within R) or y
-// (4 rows) then never needs a range check.
+// (4 or 8 rows) then never needs a range check.
 constexpr int kTapPad = 32;
 
 __device__ __forceinline__ int floor_div64(int a) { return a >= 0 ? a / TX : -((-a + TX - 1) / TX); }
@@ -264,10 +262,16 @@ __host__ __device__ constexpr TapArr taps_for() {
 // Roles of a block: kCW compute warps (a thread owns VPT rows of one column
 // of the 64 x TY tile, so a warp owns 32 columns x VPT rows; the warps of one
 // TMEM lane quarter split its 512 columns, which bounds the spectral ring to
-// kMaxWz planes: 15 for TY 32, 31 for TY 16) and one issuing warp.
+// kMaxWz planes: 7 for TY 64, 15 for TY 32, 31 for TY 16) and one issuing
+// warp. TY 64 tiles give a thread 8 rows (the per-plane work of a thread is
+// spread over twice the voxels, and twice the voxels are in flight) and keep
+// 4 P tiles of 32 KB in flight; the others 8 tiles of 16 or 8 KB.
 template <int TY, int R>
 struct PGeo {
-  static constexpr int kCW = TY / 2;           // compute warps
+  static constexpr int VPT = TY >= 64 ? 8 : 4;
+  static constexpr int kStages = TY >= 64 ? 4 : 8;  // P tiles in flight (a power of two)
+  static constexpr int kBars = 2 * kStages;          // full[kStages] (TMA landed), empty[kStages] (consumed)
+  static constexpr int kCW = TX * TY / (32 * VPT);   // compute warps
   static constexpr int kCT = 32 * kCW;
   static constexpr int kIssuer = kCW;          // warp index of the issuing warp
   static constexpr int kThreads = kCT + 32;
@@ -279,17 +283,19 @@ struct PGeo {
   static constexpr size_t kNfBytes = TX * (TY / 8);  // a flag byte per column and 8 rows
   static_assert(kCT == TX * (TY / VPT), "one compute thread per column segment");
   static_assert(kCW % 4 == 0, "compute warps cover the TMEM lane quarters evenly");
+  static_assert(VPT <= 8 && 8 % VPT == 0, "a thread's rows lie in one flag byte");
+  static_assert(VPT - 1 <= kTapPad, "row tap indices stay inside the padded taps");
   static_assert(TY + 2 * R <= 256 && TX + 2 * R <= 256, "positions fit 8 bits per axis");
 };
 
 struct PSmem {
   size_t p, nf, e, kk, meta, hist, mbar, total;
 };
-constexpr int kBars = 2 * kStages;  // full[kStages] (TMA landed), empty[kStages] (consumed)
 
 template <int TY, int R>
 __host__ __device__ constexpr PSmem p_layout() {
   using G = PGeo<TY, R>;
+  constexpr int kStages = G::kStages;
   PSmem s{};
   size_t o = 0;
   s.p = o;  // [kStages][TY][64] P tiles
@@ -305,7 +311,7 @@ __host__ __device__ constexpr PSmem p_layout() {
   s.hist = o;
   o = al128(o + sizeof(unsigned) * kNumBins);
   s.mbar = o;
-  o = al128(o + kBars * sizeof(unsigned long long));
+  o = al128(o + G::kBars * sizeof(unsigned long long));
   s.total = o + 128;
   return s;
 }
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
                ShareArgs sh) {
   using namespace share;
   using G = PGeo<TY, R>;
-  constexpr int NT = G::NT, kCW = G::kCW, kThreads = G::kThreads;
+  constexpr int NT = G::NT, kCW = G::kCW, kThreads = G::kThreads, VPT = G::VPT, kStages = G::kStages;
   if (sh.ss->overflow) return;  // the gated full kernel computes this pair (block-uniform)
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -498,9 +504,13 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
         for (int i = 0; i < VPT; ++i) rows_in |= (gx < nx && gy0 + i < ny ? 1u : 0u) << i;
         out = a.S + (long long)z0 * plane + gy0 * nx + gx;  // output plane z0 + (j - 2r) once j >= 2r
       }
-      unsigned old[2 * VPT];
+      // 4 rows a thread: the ring's oldest plane is loaded before the
+      // corrections, so that its latency overlaps them
+      unsigned old[8];
       const unsigned ta = tmine + (unsigned)(G::kSlotCols * slot);
-      if (wz > 1) TmRing<VPT>::ld(ta, old);
+      if constexpr (VPT == 4) {
+        if (wz > 1) TmRing<4>::ld(ta, old);
+      }
       long long p[VPT];
       const long long* pt = Ps + (size_t)s * TY * TX + (grp * VPT) * TX + xc;
 #pragma unroll
@@ -552,22 +562,28 @@ __global__ void __launch_bounds__(share::PGeo<TY, R>::kThreads, 1)
           }
         }
       }
-      // rows grp VPT .. + VPT - 1: half of the flag byte of their 8 rows
+      // rows grp VPT .. + VPT - 1: the flag byte of their 8 rows, or half of it
       const unsigned nb = ((unsigned)NFs[(size_t)s * G::kNfBytes + (grp * VPT / 8) * TX + xc] >> ((grp * VPT) & 7)) &
                           ((1u << VPT) - 1u);
       __syncwarp();
       if (lane == 0) mbar_arrive(empty + 8 * s);
       if (wz > 1) {
-        unsigned nw[2 * VPT];
-        tmem_wait_ld();
+        // 8 rows a thread: the oldest plane is taken and replaced 4 rows at a
+        // time (fewer registers live across the corrections)
 #pragma unroll
-        for (int i = 0; i < VPT; ++i) {
-          const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
-          zsum[i] += p[i] - o;
-          nw[2 * i] = (unsigned)((unsigned long long)p[i] & 0xffffffffull);
-          nw[2 * i + 1] = (unsigned)((unsigned long long)p[i] >> 32);
+        for (int h = 0; h < VPT / 4; ++h) {
+          unsigned nw[8];
+          if constexpr (VPT == 8) tmem_ld8(ta + 8u * h, old);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const long long o = (long long)(((unsigned long long)old[2 * i + 1] << 32) | old[2 * i]);
+            zsum[4 * h + i] += p[4 * h + i] - o;
+            nw[2 * i] = (unsigned)((unsigned long long)p[4 * h + i] & 0xffffffffull);
+            nw[2 * i + 1] = (unsigned)((unsigned long long)p[4 * h + i] >> 32);
+          }
+          tmem_st8(ta + 8u * h, nw);
         }
-        TmRing<VPT>::st(ta, nw);
         if (++slot == wz) slot = 0;
       } else {
 #pragma unroll
@@ -729,6 +745,7 @@ void set_p_attr() {
 }  // namespace
 
 int share_tile_rows(int wz) {
+  if (wz <= share::PGeo<64, 2>::kMaxWz) return 64;
   if (wz <= share::PGeo<32, 2>::kMaxWz) return 32;
   if (wz <= share::PGeo<16, 2>::kMaxWz) return 16;
   return 0;
@@ -758,12 +775,18 @@ cudaError_t launch_smooth_p(const SmoothArgs& a, const ShareArgs& sh, int sms, c
   const int ty = share_tile_rows(a.pd.wz);
   if (ty != sh.ty) return cudaSuccess;
   const int R = share_R(a.pd);
-  const cudaError_t e = ty == 32 ? launch_p_ty<32>(a, sh, R, sms, s) : launch_p_ty<16>(a, sh, R, sms, s);
+  const cudaError_t e = ty == 64   ? launch_p_ty<64>(a, sh, R, sms, s)
+                        : ty == 32 ? launch_p_ty<32>(a, sh, R, sms, s)
+                                   : launch_p_ty<16>(a, sh, R, sms, s);
   if (e == cudaSuccess) *done = true;
   return e;
 }
 
 void init_share_attrs() {
+  set_p_attr<64, 2>();
+  set_p_attr<64, 5>();
+  set_p_attr<64, 6>();
+  set_p_attr<64, 11>();
   set_p_attr<32, 2>();
   set_p_attr<32, 5>();
   set_p_attr<32, 6>();
@@ -773,6 +796,11 @@ void init_share_attrs() {
   set_p_attr<16, 6>();
   set_p_attr<16, 11>();
   // sampled Gaussians (half-widths up to 4, 8, 9, 12, 16)
+  set_p_attr<64, 4>();
+  set_p_attr<64, 8>();
+  set_p_attr<64, 9>();
+  set_p_attr<64, 12>();
+  set_p_attr<64, 16>();
   set_p_attr<32, 4>();
   set_p_attr<32, 8>();
   set_p_attr<32, 9>();
