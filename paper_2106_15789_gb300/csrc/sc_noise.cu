@@ -635,6 +635,37 @@ __device__ __forceinline__ bool sel_key(const SelJob& J, double m, float s, unsi
   return true;
 }
 
+// A candidate list of |s - m| keys (not the whole array) holds, after the
+// first round, the keys themselves in place of the values: that round forms
+// each key once in float64 (slow on this GPU) and the later rounds read it.
+// kNoKey marks a non-finite value (no finite key is that large; read as a
+// float it is a NaN, so it is no value either).
+constexpr unsigned int kNoKey = 0xffffffffu;
+__device__ __forceinline__ bool sel_keys_stored(const SelJob& J) {
+  return J.mode == SEL_ABSDEV && J.count_ptr != nullptr;
+}
+__device__ __forceinline__ bool sel_key_of(const SelJob& J, bool stored, double m, float v, unsigned int* key) {
+  if (stored) {
+    *key = __float_as_uint(v);
+    return *key != kNoKey;
+  }
+  return sel_key(J, m, v, key);
+}
+
+// The lists are read kSelUnroll values a thread at a time, loads first, so
+// that enough of them are in flight (a list of millions of candidates is
+// otherwise bound by the latency of one load per thread).
+constexpr int kSelUnroll = 16;
+__device__ __forceinline__ void sel_load(const float* __restrict__ list, unsigned long long i0,
+                                         unsigned long long stride, unsigned long long count,
+                                         float (&v)[kSelUnroll]) {
+#pragma unroll
+  for (int u = 0; u < kSelUnroll; ++u) {
+    const unsigned long long i = i0 + u * stride;
+    v[u] = i < count ? __ldg(list + i) : __uint_as_float(kNoKey);  // past the end: no key either way
+  }
+}
+
 // Elements in the list: the candidate count, clamped to the buffer capacity
 // (count_fixed), or the whole array.
 __device__ __forceinline__ unsigned long long sel_count(const SelJob& J) {
@@ -726,14 +757,34 @@ __global__ void __launch_bounds__(256) k_sel_round(DevState* st, int which, int 
   const int shift_prev = (r == 0) ? 32 : sel_shift(r - 1);
   const int shift = sel_shift(r);
   const unsigned int dmask = (1u << sel_bits(r)) - 1u;
-  const float* list = J->list;
   const SelJob Jl = *J;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned int key;
-    if (!sel_key(Jl, m, __ldg(list + i), &key)) continue;
-    if (shift_prev < 32 && (key >> shift_prev) != prefix) continue;
-    atomicAdd(&sh[(key >> shift) & dmask], 1u);
+  const bool stored = r > 0 && sel_keys_stored(Jl);
+  // the first round of a list of |s - m| values writes their keys over them
+  float* const keys_out = (r == 0 && sel_keys_stored(Jl)) ? const_cast<float*>(Jl.list) : nullptr;
+  // whole warps iterate together: a warp whose 32 values share one digit (a
+  // list's candidates cluster in few digits, in the first round mostly in
+  // one) adds to its bin once
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); w0 < count;
+       w0 += kSelUnroll * stride) {
+    float v[kSelUnroll];
+    sel_load(Jl.list, w0 + lane, stride, count, v);
+#pragma unroll
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const unsigned long long i = w0 + u * stride + lane;
+      unsigned int key = 0u;
+      bool ok = i < count && sel_key_of(Jl, stored, m, v[u], &key);
+      if (keys_out && i < count) keys_out[i] = __uint_as_float(ok ? key : kNoKey);
+      ok = ok && !(shift_prev < 32 && (key >> shift_prev) != prefix);
+      const unsigned digit = ok ? (key >> shift) & dmask : 0xffffffffu;
+      const unsigned d0 = __shfl_sync(0xffffffffu, digit, 0);
+      if (__all_sync(0xffffffffu, digit == d0)) {
+        if (lane == 0 && ok) atomicAdd(&sh[d0], 32u);
+      } else if (ok) {
+        atomicAdd(&sh[digit], 1u);
+      }
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kSelBins; i += blockDim.x)
@@ -755,13 +806,20 @@ __global__ void __launch_bounds__(256) k_sel_succ(DevState* st, int which) {
   if (blockIdx.x == 0 && threadIdx.x == 0) J->key_lo = key_lo;
   const double m = st->m;
   const SelJob Jl = *J;
+  const bool stored = sel_keys_stored(Jl);
   unsigned long long c = 0;
   unsigned int mn = 0xffffffffu;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned int key;
-    if (!sel_key(Jl, m, __ldg(Jl.list + i), &key)) continue;
-    if (key <= key_lo) ++c; else mn = min(mn, key);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < count;
+       i0 += kSelUnroll * stride) {
+    float v[kSelUnroll];
+    sel_load(Jl.list, i0, stride, count, v);
+#pragma unroll
+    for (int u = 0; u < kSelUnroll; ++u) {
+      unsigned int key;
+      if (!sel_key_of(Jl, stored, m, v[u], &key)) continue;  // includes the places past the end
+      if (key <= key_lo) ++c; else mn = min(mn, key);
+    }
   }
   c = warp_sum_u64(c);
   for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
