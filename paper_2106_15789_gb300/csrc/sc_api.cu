@@ -1200,7 +1200,7 @@ int sc_autotune(sc_ctx* c, const int64_t* dims, const sc_kernel* kernels, int n_
     const auto key = tune_key(dims, pd);
     if (done.count(key)) continue;
     std::vector<Cand> cands;
-    for (int zf : {1, 2, 4}) {
+    for (int zf : {0, 2, 4}) {  // 0: the chunking of the balance model
       if (pd.h > 0) {
         cands.push_back({TUNE_WS, zf});
         cands.push_back({TUNE_WS16, zf});

@@ -185,7 +185,7 @@ struct SmoothArgs {
   int tiles_x, tiles_y, zchunks;
   int generic;               // force the generic FIR path
   int tune_kind;             // TUNE_* kernel choice (TUNE_AUTO: the dispatcher decides)
-  int tune_zfactor;          // work items per SM targeted by the z chunking (0: 2)
+  int tune_zfactor;          // work items per SM targeted by the z chunking (0: the balance model)
   // Shared spatial passes (warp-specialised kernel only): when pout is set,
   // the kernel also stores the spatial sum P of X_q at every voxel (row pitch
   // ppitch elements) and the nonfinite flags of C in nfout, a byte per column
@@ -255,7 +255,30 @@ static_assert(TUNE_WS == SC_VARIANT_WS && TUNE_TILE == SC_VARIANT_TILE && TUNE_G
                   TUNE_Z8 == SC_VARIANT_Z8 && TUNE_Z4 == SC_VARIANT_Z4 && TUNE_WS16 == SC_VARIANT_WS16 &&
                   TUNE_Z4W == SC_VARIANT_Z4_512 && TUNE_Z8W == SC_VARIANT_Z8_512,
               "the public variant codes are the tuning kinds");
-inline long long tune_items_per_sm(const SmoothArgs& a) { return a.tune_zfactor > 0 ? a.tune_zfactor : 2; }
+// Z chunks of the (tiles x chunks) work items that the blocks of a smoothing
+// kernel take round-robin (at most max_ch chunks). An autotuner factor asks
+// for about that many items per SM; without one, the chunking whose busiest
+// block streams the fewest planes: ceil(items / blocks) items of lz planes
+// plus the 2r halo planes of the spectral boxcar each.
+inline long long z_chunks(const SmoothArgs& a, long long tiles, int sms, long long max_ch) {
+  max_ch = max_ch < 1 ? 1 : max_ch;
+  if (a.tune_zfactor > 0) {
+    const long long zch = (a.tune_zfactor * sms + tiles - 1) / tiles;
+    return zch < 1 ? 1 : (zch > max_ch ? max_ch : zch);
+  }
+  const long long nz = a.nz, r = a.pd.wz > 1 ? (a.pd.wz - 1) / 2 : 0;
+  long long best = 1, best_cost = -1;
+  for (long long zch = 1; zch <= max_ch && zch <= 64; ++zch) {
+    const long long lz = (nz + zch - 1) / zch, chunks = (nz + lz - 1) / lz;
+    const long long items = tiles * chunks, blocks = items < sms ? items : sms;
+    const long long cost = (items + blocks - 1) / blocks * (lz + 2 * r);
+    if (best_cost < 0 || cost < best_cost) {
+      best = zch;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (all enqueue on `s`, return cudaError_t of the launch).

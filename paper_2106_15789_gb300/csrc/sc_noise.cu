@@ -1075,25 +1075,57 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
 // bin of the median of |x| gives the scale, and the window spans 2^-20 .. 2^12
 // of it (as for the smoothed cubes), so the plan of the sigma_0 measurement
 // resolves 128 bins per octave instead of 16.
-__global__ void k_window_from_hist(DevState* st, const unsigned long long* __restrict__ hist) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+constexpr int kWinThreads = 1024;
+__global__ void __launch_bounds__(kWinThreads) k_window_from_hist(DevState* st,
+                                                                   const unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ int s_mb;
   const BinCfg full = kFullRange;
-  unsigned long long n = 0;
-  for (int i = 0; i < kNumBins; ++i) n += hist[i];
-  unsigned long long acc = 0;
-  float scale = 0.0f;
-  for (int mb = 0; mb < kBinsPerSign && n > 0; ++mb) {
-    acc += hist[kBinsPerSign + mb] + hist[kBinsPerSign - 1 - mb];  // both signs, magnitude bin mb
-    if (2 * acc > n) {
-      scale = (float)mag_hi(mb, full);
-      break;
-    }
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // thread t holds magnitude bins [t * per, t * per + per), both signs
+  constexpr int per = (kBinsPerSign + kWinThreads - 1) / kWinThreads;
+  unsigned long long c[per], loc = 0;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const int mb = t * per + j;
+    c[j] = mb < kBinsPerSign ? hist[kBinsPerSign + mb] + hist[kBinsPerSign - 1 - mb] : 0ull;
+    loc += c[j];
   }
-  st->win = window_cfg(isfinite(scale) ? scale : 3.0e38f);
+  unsigned long long inc = loc;  // inclusive scan over the warp, then over the warps
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  if (t == 0) s_mb = -1;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = s_w[lane];
+    unsigned long long xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += y;
+    }
+    s_w[lane] = xi;  // inclusive over warps; s_w[31] is the total
+  }
+  __syncthreads();
+  const unsigned long long n = s_w[31];
+  // the first magnitude bin whose cumulative count exceeds half of all values
+  unsigned long long run = (warp ? s_w[warp - 1] : 0ull) + inc - loc;
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    if (2 * run <= n && 2 * (run + c[j]) > n) s_mb = t * per + j;
+    run += c[j];
+  }
+  __syncthreads();
+  if (t == 0) {
+    const float scale = (n > 0 && s_mb >= 0) ? (float)mag_hi(s_mb, full) : 0.0f;
+    st->win = window_cfg(isfinite(scale) ? scale : 3.0e38f);
+  }
 }
 
 cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s) {
-  k_window_from_hist<<<1, 1, 0, s>>>(st, hist);
+  k_window_from_hist<<<1, kWinThreads, 0, s>>>(st, hist);
   return cudaGetLastError();
 }
 

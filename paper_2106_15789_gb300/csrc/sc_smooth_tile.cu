@@ -349,10 +349,7 @@ cudaError_t launch_tile(const SmoothArgs& a0, int sms, cudaStream_t s, bool* don
   a.tiles_x = (a.nx + TX - 1) / TX;
   a.tiles_y = (a.ny + TY - 1) / TY;
   const long long tiles = (long long)a.tiles_x * a.tiles_y;
-  const long long target = tune_items_per_sm(a) * sms;
-  long long zch = (target + tiles - 1) / tiles;
-  const long long max_ch = (a.nz + 31) / 32;
-  zch = zch < 1 ? 1 : (zch > max_ch ? max_ch : zch);
+  const long long zch = z_chunks(a, tiles, sms, (a.nz + 31) / 32);
   a.lz = (int)((a.nz + zch - 1) / zch);
   a.zchunks = (a.nz + a.lz - 1) / a.lz;
   const long long items = tiles * a.zchunks;

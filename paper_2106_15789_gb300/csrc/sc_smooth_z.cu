@@ -313,9 +313,7 @@ cudaError_t launch_z(const SmoothArgs& a0, int sms, cudaStream_t s) {
   const long long P = (long long)a.nx * a.ny;
   const long long per_block = (long long)THREADS * VPT;
   const long long groups = (P + per_block - 1) / per_block;
-  long long zch = (tune_items_per_sm(a) * sms + groups - 1) / groups;
-  const long long max_ch = (a.nz + 15) / 16;
-  zch = zch < 1 ? 1 : (zch > max_ch ? max_ch : zch);
+  const long long zch = z_chunks(a, groups, sms, (a.nz + 15) / 16);
   a.lz = (int)((a.nz + zch - 1) / zch);
   a.zchunks = (a.nz + a.lz - 1) / a.lz;
   const long long items = groups * a.zchunks;
