@@ -22,9 +22,12 @@ def test_committed_traffic_record_matches_the_sources():
         return
     assert bench.smooth_traffic_record() is not None
     for name, b in rec["kernels"].items():
-        # near the algorithmic bytes: 8.125 full kernels, 12 shared passes, 16.125 full kernels storing P'
+        # near the algorithmic bytes: 8.125 full kernels, 12 shared passes, 16.125 full kernels storing P;
+        # a shared pass also re-reads the 2r halo planes of P at each of its z chunks (on the 512^3 capture
+        # cube 32-plane chunks for boxcars of 3 and 7: up to 6 / 32 more P reads), so it may sit above 12
         want = 16.125 if name.endswith("+P") else (12.0 if name.startswith("k_smooth_p") else 8.125)
-        assert abs(b - want) < 0.5, (name, b)
+        above = 1.0 if name.startswith("k_smooth_p") else 0.5
+        assert want - 0.5 < b < want + above, (name, b)
 
 
 def test_record_traffic_means(tmp_path, monkeypatch):
