@@ -508,21 +508,18 @@ int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kerne
   const float* src0 = h16 ? (direct ? c->S : c->stage_cube) : cube;
   {
     Phase ph(c, s, EV_SELECT);
-    // full range, and max |C| (a 16-bit cube: decoded into the copy by this
-    // pass, or into S by the last histogram pass when direct)
-    if (h16)
-      CK(launch_hist16(*h16, plane, n, c->st, c->hist, 0, 1, direct ? (std_mode ? c->S : nullptr) : c->stage_cube,
-                       c->sms, s));
-    else CK(launch_hist(cube, n, c->st, c->hist, 0, 1, c->sms, s));
-    c->stats.launches += 1;
+    // one histogram pass with max |C| (a 16-bit cube: decoded by it into the
+    // working copy, or into S when direct): windowed around the median |C| of
+    // an even sample (a fine plan), or over the full range for STD mode
     if (!std_mode) {
-      // a second, windowed histogram around the median |C|: a fine plan
-      CK(launch_window_from_hist(c->st, c->hist, s));
-      CK(cudaMemsetAsync(c->hist, 0, sizeof(unsigned long long) * kNumBins, s));
-      if (h16) CK(launch_hist16(*h16, plane, n, c->st, c->hist, 1, 0, direct ? c->S : nullptr, c->sms, s));
-      else CK(launch_hist(cube, n, c->st, c->hist, 1, 0, c->sms, s));
-      c->stats.launches += 2;
+      CK(launch_window_from_sample(cube, h16, plane, n, c->st, s));
+      c->stats.launches += 1;
     }
+    const int win0 = std_mode ? 0 : 1;
+    if (h16)
+      CK(launch_hist16(*h16, plane, n, c->st, c->hist, win0, 1, direct ? c->S : c->stage_cube, c->sms, s));
+    else CK(launch_hist(cube, n, c->st, c->hist, win0, 1, c->sms, s));
+    c->stats.launches += 1;
   }
   rc = measure(c, src0, n, std_mode ? 0 : 1, t, first_identity ? 1 : 0, noise_mode, first_identity ? 0 : -1, force,
                s);

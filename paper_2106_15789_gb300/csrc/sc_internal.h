@@ -307,7 +307,10 @@ cudaError_t launch_gauss_hist(const float* src, long long n, const DevState* st,
                               cudaStream_t s);
 cudaError_t launch_gauss_fit(DevState* st, const unsigned long long* ghist, int pair, int clip, cudaStream_t s);
 // DevState::win from the full-range histogram of a raw cube (median of |x|)
-cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s);
+// Window of the raw cube's fine histogram from an even sample of its values
+// (the 16-bit cube when h16 is non-null, else x).
+cudaError_t launch_window_from_sample(const float* x, const Half16* h16, long long plane, long long n, DevState* st,
+                                      cudaStream_t s);
 cudaError_t launch_sigma0_done(DevState* st, float replacement, const PairWeights& W, int n_pairs,
                                cudaStream_t s);
 // out[0..n-1] = sigma_k, out[n] = sigma_0, or zeros after a device-side error

@@ -1071,24 +1071,49 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
   return cudaGetLastError();
 }
 
-// Window of the fine histogram of the raw cube from its full-range one: the
-// bin of the median of |x| gives the scale, and the window spans 2^-20 .. 2^12
-// of it (as for the smoothed cubes), so the plan of the sigma_0 measurement
-// resolves 128 bins per octave instead of 16.
+// Window of the fine histogram of the raw cube: the bin of the median of |x|
+// gives the scale, and the window spans 2^-20 .. 2^12 of it (as for the
+// smoothed cubes), so the plan of the sigma_0 measurement resolves 128 bins
+// per octave instead of 16. The median |x| comes from kWinSample values
+// spread evenly over the cube (all of them in a smaller cube): a window 32
+// octaves wide needs its scale only roughly, and the exact selection that
+// follows does not depend on it (a poorly placed window costs candidates,
+// never exactness).
 constexpr int kWinThreads = 1024;
-__global__ void __launch_bounds__(kWinThreads) k_window_from_hist(DevState* st,
-                                                                   const unsigned long long* __restrict__ hist) {
+constexpr long long kWinSample = 65536;
+constexpr int kWinPerThread = (int)(kWinSample / kWinThreads);
+__global__ void __launch_bounds__(kWinThreads) k_window_from_sample(const float* __restrict__ x, Half16 h,
+                                                                    long long plane, long long n, DevState* st) {
+  extern __shared__ unsigned int wh[];  // full-range histogram of the sample
   __shared__ unsigned long long s_w[32];
   __shared__ int s_mb;
   const BinCfg full = kFullRange;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int i = t; i < kNumBins; i += kWinThreads) wh[i] = 0u;
+  __syncthreads();
+  const long long m = n < kWinSample ? n : kWinSample;
+  constexpr int kBatch = 16;  // loads in flight per thread
+  for (int j0 = 0; j0 < kWinPerThread; j0 += kBatch) {
+    float v[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      const long long k = (long long)(j0 + j) * kWinThreads + t;
+      const long long i = (long long)(((unsigned long long)k * (unsigned long long)n) / (unsigned long long)m);
+      v[j] = __int_as_float(0x7fc00000);
+      if (k < m) v[j] = h.fmt ? half16_value(__ldg(h.bits + i), h.fmt, __ldg(h.scale + i / plane)) : __ldg(x + i);
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j)
+      if (isfinite(v[j])) atomicAdd(&wh[bin_of(v[j], full)], 1u);
+  }
+  __syncthreads();
   // thread t holds magnitude bins [t * per, t * per + per), both signs
   constexpr int per = (kBinsPerSign + kWinThreads - 1) / kWinThreads;
   unsigned long long c[per], loc = 0;
 #pragma unroll
   for (int j = 0; j < per; ++j) {
     const int mb = t * per + j;
-    c[j] = mb < kBinsPerSign ? hist[kBinsPerSign + mb] + hist[kBinsPerSign - 1 - mb] : 0ull;
+    c[j] = mb < kBinsPerSign ? (unsigned long long)wh[kBinsPerSign + mb] + wh[kBinsPerSign - 1 - mb] : 0ull;
     loc += c[j];
   }
   unsigned long long inc = loc;  // inclusive scan over the warp, then over the warps
@@ -1100,8 +1125,8 @@ __global__ void __launch_bounds__(kWinThreads) k_window_from_hist(DevState* st,
   if (t == 0) s_mb = -1;
   __syncthreads();
   if (warp == 0) {
-    const unsigned long long x = s_w[lane];
-    unsigned long long xi = x;
+    const unsigned long long xw = s_w[lane];
+    unsigned long long xi = xw;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, xi, o);
       if (lane >= o) xi += y;
@@ -1109,23 +1134,26 @@ __global__ void __launch_bounds__(kWinThreads) k_window_from_hist(DevState* st,
     s_w[lane] = xi;  // inclusive over warps; s_w[31] is the total
   }
   __syncthreads();
-  const unsigned long long n = s_w[31];
-  // the first magnitude bin whose cumulative count exceeds half of all values
+  const unsigned long long total = s_w[31];
+  // the first magnitude bin whose cumulative count exceeds half of the sample
   unsigned long long run = (warp ? s_w[warp - 1] : 0ull) + inc - loc;
 #pragma unroll
   for (int j = 0; j < per; ++j) {
-    if (2 * run <= n && 2 * (run + c[j]) > n) s_mb = t * per + j;
+    if (2 * run <= total && 2 * (run + c[j]) > total) s_mb = t * per + j;
     run += c[j];
   }
   __syncthreads();
   if (t == 0) {
-    const float scale = (n > 0 && s_mb >= 0) ? (float)mag_hi(s_mb, full) : 0.0f;
+    const float scale = (total > 0 && s_mb >= 0) ? (float)mag_hi(s_mb, full) : 0.0f;
     st->win = window_cfg(isfinite(scale) ? scale : 3.0e38f);
   }
 }
 
-cudaError_t launch_window_from_hist(DevState* st, const unsigned long long* hist, cudaStream_t s) {
-  k_window_from_hist<<<1, kWinThreads, 0, s>>>(st, hist);
+cudaError_t launch_window_from_sample(const float* x, const Half16* h16, long long plane, long long n, DevState* st,
+                                      cudaStream_t s) {
+  Half16 h{};
+  if (h16) h = *h16;
+  k_window_from_sample<<<1, kWinThreads, kNumBins * sizeof(unsigned int), s>>>(x, h, plane, n, st);
   return cudaGetLastError();
 }
 
