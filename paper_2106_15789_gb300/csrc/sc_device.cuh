@@ -43,7 +43,8 @@ __host__ __device__ __forceinline__ int bin_of_bits(unsigned int u, BinCfg c) {
   int b = key - (c.e_base << c.MB) + 1;
   b = b < 0 ? 0 : b;
   b = b > (c.E << c.MB) + 1 ? (c.E << c.MB) + 1 : b;
-  return (u >> 31) ? (kBinsPerSign - 1 - b) : (kBinsPerSign + b);
+  // negative values mirror: kBinsPerSign - 1 - b = kBinsPerSign + (b ^ -1)
+  return kBinsPerSign + (b ^ -(int)(u >> 31));
 }
 __device__ __forceinline__ int bin_of(float s, BinCfg c) { return bin_of_bits(__float_as_uint(s), c); }
 

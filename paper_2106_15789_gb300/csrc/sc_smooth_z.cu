@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
     const int z0 = zc * a.lz;
     const int z1 = (int)min((long long)z0 + a.lz, nz);
     const int n_steps = (z1 - z0) + 2 * r;
+    // the thread's voxels that enter the histogram (all of them but past the plane's end)
+    const unsigned hist_rows = a.hist ? (nv >= VPT ? (1u << VPT) - 1u : (1u << nv) - 1u) : 0u;
     long long zsum[VPT];
 #pragma unroll
     for (int i = 0; i < VPT; ++i) zsum[i] = 0;
@@ -226,9 +228,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
 #pragma unroll
       for (int i = 0; i < VPT; ++i) {
         const float c = cur[i];
-        // c + (c - c) is NaN for NaN and Inf, whose quantised value is 0
-        Pq[i] = quantize(c + (c - c), fscale);
-        nanbits |= ((__float_as_uint(c) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) << i;
+        // c - c is NaN exactly for NaN and Inf, whose quantised value is then 0
+        const float d = c - c;
+        Pq[i] = quantize(c + d, fscale);
+        nanbits |= (d != d ? 1u : 0u) << i;
       }
       if (do_repl && mcur != 0u) {  // masked voxels are finite (the working mask holds no others)
 #pragma unroll
@@ -248,13 +251,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_smooth_z(SmoothArgs a) {
       if (j >= 2 * r && nv > 0) {
         const int zo = zp - r;
         const unsigned nb = (unsigned)(nan_hist >> (VPT * r)) & ((1u << VPT) - 1u);
+        const unsigned binned = hist_rows & ~nb;  // finite voxels of the thread's own, when histogrammed
         float s[VPT];
 #pragma unroll
         for (int i = 0; i < VPT; ++i) {
           const bool isn = (nb >> i) & 1u;
           const float sv = dequantize(zsum[i], inv);
           s[i] = isn ? __int_as_float(0x7fc00000) : sv;
-          if (a.hist && !isn && i < nv) atomicAdd(&zhist[bin_of(s[i], cfg)], 1u);
+          if ((binned >> i) & 1u) atomicAdd(&zhist[bin_of(s[i], cfg)], 1u);
         }
         float* out = a.S + (long long)zo * P + p0;
         if (VEC) {
