@@ -564,13 +564,15 @@ __global__ void __launch_bounds__(kP2Threads, 2) k_pass2(const float* __restrict
         // most groups of 32 values hold no listed, sure or ambiguous value:
         // one vote settles them
         if (!__any_sync(0xffffffffu, k[c] != 0u)) continue;
-        sure_w[c] = __ballot_sync(0xffffffffu, (k[c] & CLS_SURE) != 0u);
-        const unsigned int kc = k[c] & ~CLS_SURE;
-        if (__any_sync(0xffffffffu, kc != 0u) && !__any_sync(0xffffffffu, (kc & ~CLS_MAD) != 0u)) {
+        // the classes present in the group, one reduction for the warp
+        const unsigned int present = __reduce_or_sync(0xffffffffu, k[c]);
+        if (present & CLS_SURE) sure_w[c] = __ballot_sync(0xffffffffu, (k[c] & CLS_SURE) != 0u);
+        const unsigned int kc = k[c] & ~CLS_SURE, listed = present & ~CLS_SURE;
+        if (listed == CLS_MAD) {
           // the common case: MAD candidates only (values around +-MAD)
           const bool pa = kc != 0u;
           stage_push(__ballot_sync(0xffffffffu, pa), pa, lanes_below, a[u][c], smad, nmad);
-        } else if (__any_sync(0xffffffffu, kc != 0u)) {
+        } else if (listed != 0u) {
           const float s = a[u][c];
           const float as = fabsf(s);
           const bool pm = (k[c] & CLS_MED) != 0u, pa = (k[c] & CLS_MAD) != 0u;
