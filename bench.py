@@ -745,8 +745,8 @@ def measure_half(ctx, cube, bf16, steps, warmup, local, pg, world, dev, ref=None
     prec["half_path"] = int(st["half_path"])
     prec["cube_read"] = {1: "16-bit values by every kernel (SC_FLAG_HALF_DIRECT)",
                          2: "decoded into a float32 copy by a pass of its own",
-                         3: "16-bit values by the raw-cube histogram passes, the first of which writes the float32 "
-                            "working copy every later pass reads"}.get(int(st["half_path"]), "float32")
+                         3: "16-bit values by the raw-cube histogram pass, which writes the float32 working copy "
+                            "every later pass reads"}.get(int(st["half_path"]), "float32")
     if not bf16 and not with_oracle:
         # mitigation study: FP16 plus a float32 sideband of the values above
         # 2.5 sigma_0 (the float32 path on the decoded cube with those values

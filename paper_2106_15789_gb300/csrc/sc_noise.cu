@@ -1076,8 +1076,8 @@ cudaError_t launch_fx_setup(DevState* st, float repl_value, const PairWeights& W
 // Window of the fine histogram of the raw cube: the bin of the median of |x|
 // gives the scale, and the window spans 2^-20 .. 2^12 of it (as for the
 // smoothed cubes), so the plan of the sigma_0 measurement resolves 128 bins
-// per octave instead of 16. The median |x| comes from kWinSample values
-// spread evenly over the cube (all of them in a smaller cube): a window 32
+// per octave instead of 16. The median |x| comes from kWinSample values at
+// a fixed step through the cube (all of them in a smaller cube): a window 32
 // octaves wide needs its scale only roughly, and the exact selection that
 // follows does not depend on it (a poorly placed window costs candidates,
 // never exactness).
@@ -1093,14 +1093,15 @@ __global__ void __launch_bounds__(kWinThreads) k_window_from_sample(const float*
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int i = t; i < kNumBins; i += kWinThreads) wh[i] = 0u;
   __syncthreads();
-  const long long m = n < kWinSample ? n : kWinSample;
+  // m values step apart (every value of a cube of at most kWinSample)
+  const long long m = n < kWinSample ? n : kWinSample, step = n / (m > 0 ? m : 1);
   constexpr int kBatch = 16;  // loads in flight per thread
   for (int j0 = 0; j0 < kWinPerThread; j0 += kBatch) {
     float v[kBatch];
 #pragma unroll
     for (int j = 0; j < kBatch; ++j) {
       const long long k = (long long)(j0 + j) * kWinThreads + t;
-      const long long i = (long long)(((unsigned long long)k * (unsigned long long)n) / (unsigned long long)m);
+      const long long i = k * step;
       v[j] = __int_as_float(0x7fc00000);
       if (k < m) v[j] = h.fmt ? half16_value(__ldg(h.bits + i), h.fmt, __ldg(h.scale + i / plane)) : __ldg(x + i);
     }
