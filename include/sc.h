@@ -120,7 +120,7 @@ typedef struct {
   uint32_t warnings;      /* SC_WARN_* bits of the last run */
   uint32_t half_path;     /* last run's cube: 0 float32; 16-bit (sc_run_half, 16-bit jobs): 1 read as such by
                              every kernel (SC_FLAG_HALF_DIRECT), 2 decoded into a float32 copy by a pass of its
-                             own, 3 decoded into that copy by the first raw-cube histogram pass */
+                             own, 3 decoded into that copy by the raw-cube histogram pass */
   double ms_smooth;       /* device time of smoothing kernels (only while profiling is on) */
   double ms_select;       /* device time of histogram/plan/candidate/select kernels */
   double ms_clip;         /* device time of mask kernels and of the 16-bit decode (sc_run_half) */
@@ -312,10 +312,10 @@ int sc_autotune(sc_ctx *ctx, const int64_t *dims, const sc_kernel *kernels, int 
  * and errors, bit-identical results). How the 16-bit cube is read
  * (sc_stats.half_path):
  *   3 (default, nx a multiple of 8 and cube_dev 16-byte aligned): the
- *     raw-cube histogram passes of sigma_0 read the 16-bit values, and the
- *     first of them also writes the decoded cube into the context's float32
- *     staging cube (allocated on first use, max_voxels floats), which every
- *     later pass reads; no decoding pass of its own.
+ *     raw-cube histogram pass of sigma_0 reads the 16-bit values and also
+ *     writes the decoded cube into the context's float32 staging cube
+ *     (allocated on first use, max_voxels floats), which every later pass
+ *     reads; no decoding pass of its own.
  *   1 (SC_FLAG_HALF_DIRECT, same shapes): no float32 copy at all: every
  *     kernel reads the 16-bit values (TMA tiles of 16-bit values in the
  *     warp-specialised kernel, 16- and 8-byte copies in the spectral one,

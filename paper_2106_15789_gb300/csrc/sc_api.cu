@@ -459,13 +459,13 @@ int ensure_stage(sc_ctx* c) {
 }
 
 // One S+C run on the device. The cube is the float32 one at `cube`, or, with
-// h16 (cube null), a 16-bit one. The raw-cube histograms read the 16-bit
-// values; by default the first of them also decodes the cube into the
-// context's float32 working copy, which every later pass reads (the float32
-// kernels, no decoding pass of its own). With SC_FLAG_HALF_DIRECT no copy is
-// made: the last histogram pass decodes into S (the float32 cube the sigma_0
-// selection and the first pair read) and the smoothing kernels and correction
-// lists decode their own 16-bit values.
+// h16 (cube null), a 16-bit one. The raw-cube histogram pass reads the
+// 16-bit values; by default it also decodes the cube into the context's
+// float32 working copy, which every later pass reads (the float32 kernels, no
+// decoding pass of its own). With SC_FLAG_HALF_DIRECT no copy is made: the
+// histogram pass decodes into S (the float32 cube the sigma_0 selection and
+// the first pair read) and the smoothing kernels and correction lists decode
+// their own 16-bit values.
 int run_device(sc_ctx* c, const float* cube, const int64_t* dims, const sc_kernel* kernels, int nk, float t,
                int noise_mode, float replacement, uint8_t* mask_dev, uint32_t flags, cudaStream_t s,
                const Half16* h16 = nullptr) {

@@ -4,7 +4,7 @@ The library's result on a BF16 / FP16 cube with per-channel scales must be
 the result of S+C on the decoded float32 cube (decode(x) * scale[z], one
 float32 rounding): bit-identical to sc_run on that cube and within the usual
 tolerances of the oracle on it, whichever way the cube is read: decoded into
-the float32 working copy by the first raw-cube histogram pass (the default for
+the float32 working copy by the raw-cube histogram pass (the default for
 rows of 16-byte multiples), by a decoding pass of its own (other shapes, the
 generic kernels), or read as 16-bit values by every kernel
 (SC_FLAG_HALF_DIRECT). Against the original float32 cube the 16-bit
